@@ -1,0 +1,342 @@
+"""Benchmark of the corrector-step PCG path on GB300.
+
+Workload (default): anisotropic porous block in a channel on a jittered
+1024 x 1024-vertex triangular lattice (2,093,058 cells), CP2 matrix,
+Dirichlet eta = 0 on the right edge, b = A_e N(0,1).  One step = one pass of
+the hot path: assemble (geometry, transmissibilities, ELL pack, Jacobi
+set-up) and one FP64 Jacobi-PCG solve to relative residual 1e-10.
+
+value = PCG cell-iterations per second of the whole step (cells x iterations
+/ step time), summed over ranks.  Extra keys report the mixed-precision
+time-to-1e-10, the iteration roofline and the oracle CPU baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--n 1024]
+    python bench.py --impl reference   # the CPU oracle on the host cores
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "PCG cell-iters/s (FP64 Jacobi-PCG to 1e-10, assemble+solve)"
+UNIT = "cell-iters/s"
+# Algorithmic bytes per cell per iteration of the FP64 Jacobi loop on the
+# scaled matrix: k_spmv_dot reads p, 3 values, 3 columns and writes q
+# (8 + 24 + 12 + 8); k_update reads y, p, r, q and writes y, r (32 + 16);
+# k_pupdate reads r, p and writes p (16 + 8); every 8th k_update also reads s
+# (8/8 = 1 per iteration).  Neighbour gathers are counted once.
+BYTES_PER_CELL_ITER_FP64 = 52 + 48 + 24 + 1
+BYTES_PER_CELL_ITER_MIXED = 32 + 24 + 12 + 0.5
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--n", type=int, default=1024, help="lattice vertices per side")
+    ap.add_argument("--rtol", type=float, default=1e-10)
+    ap.add_argument("--impl", default="cps", choices=["cps", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-iters", type=int, default=0,
+                    help="oracle PCG iterations in the CPU sample (0: auto)")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def cpu_baseline(problem, b, iters: int) -> dict:
+    """The oracle as it stands (single thread) on a bounded sample: assembly
+    plus a fixed number of Jacobi-PCG iterations on the same workload."""
+    import oracle
+    t0 = time.perf_counter()
+    A = oracle.assemble_problem(problem)
+    t1 = time.perf_counter()
+    x, st = oracle.pcg(A, b, rtol=0.0, maxit=iters, precond=oracle.PC_JACOBI,
+                       raise_on_error=False)
+    t2 = time.perf_counter()
+    nt = problem.mesh.nt
+    return {"value": nt * st.iters / (t2 - t0), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle assembly ({t1 - t0:.2f} s) + {st.iters} Jacobi-PCG iterations "
+                      f"({t2 - t1:.2f} s) on the same {nt}-cell system, single thread",
+            "pcg_only_cell_iters_per_s": nt * st.iters / (t2 - t1)}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle timed on the host cores."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    p = synth.channel_block_problem(args.n, seed=0)
+    b = synth.rhs(p.mesh, seed=1)
+    iters = args.cpu_iters or max(20, int(1e9 / p.mesh.nt))
+    vals = []
+    for k in range(args.warmup + args.steps):
+        r = cpu_baseline(p, b, iters)
+        if k >= args.warmup:
+            vals.append(r)
+    v = float(np.mean([r["value"] for r in vals]))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"channel-block-aniso lattice n={args.n}",
+                       "cells": p.mesh.nt},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": vals[0]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import paper_2309_03543_gb300 as cps
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    # Each rank solves its own independent instance (weak scaling, no
+    # collective in the data path).
+    seed = 1000 * rank
+    p = synth.channel_block_problem(args.n, seed=seed)
+    m = p.mesh
+    b_np = synth.rhs(m, seed=seed + 1)
+    nt = m.nt
+    ctx = cps.Context(local)
+    stream = torch.cuda.current_stream(dev)
+
+    host = {"xy": torch.as_tensor(m.xy).pin_memory(), "tri": torch.as_tensor(m.tri).pin_memory(),
+            "dir": torch.as_tensor(m.dirichlet).pin_memory(),
+            "eps": torch.as_tensor(p.eps).pin_memory(),
+            "kinv": torch.as_tensor(p.kinv).pin_memory(), "b": torch.as_tensor(b_np).pin_memory()}
+    d = {k: v.to(dev) for k, v in host.items()}
+    x = torch.zeros(nt, dtype=torch.float64, device=dev)
+    x_host = torch.empty(nt, dtype=torch.float64).pin_memory()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    h2d_bytes = sum(v.numel() * v.element_size() for v in host.values())
+    d2h_bytes = nt * 8
+
+    def step(src, precision=cps.FP64):
+        s = ctx.assemble(src["xy"], src["tri"], src["dir"], src["eps"], src["kinv"],
+                         cps.PER_VERTEX, cps.KIND_CP2, p.nu, p.dt)
+        x.zero_()
+        _, st = s.solve(src["b"], x=x, rtol=args.rtol, precision=precision)
+        launches = s.info()["setup_launches"] + st.launches
+        s.free()
+        return st, launches
+
+    # warm-up
+    for _ in range(args.warmup):
+        step(d)
+    barrier()
+
+    # ---- timed region: device-resident inputs
+    sampler = ClockSampler(local)
+    sampler.start()
+    times, iters, launches = [], [], 0
+    for _ in range(args.steps):
+        flush.zero_()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, nl = step(d)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        iters.append(st.iters)
+        launches += nl
+        assert st.rel_res <= args.rtol, st
+    barrier()
+    clocks = sampler.stop()
+    t_total = sum(times)
+    cell_iters = nt * sum(iters)
+    if pg is not None:
+        tt = torch.tensor([t_total, cell_iters], dtype=torch.float64, device=dev)
+        import torch.distributed as dist
+        gathered = [torch.zeros_like(tt) for _ in range(world)]
+        dist.all_gather(gathered, tt)
+        t_max = max(float(g[0]) for g in gathered)
+        total_cell_iters = sum(float(g[1]) for g in gathered)
+    else:
+        t_max, total_cell_iters = t_total, cell_iters
+    value = total_cell_iters / t_max
+
+    # ---- e2e: host buffers in, host result out, through the public API
+    e2e_times = []
+    for _ in range(max(2, min(args.steps, 3))):
+        flush.zero_()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        src = {k: v.to(dev, non_blocking=True) for k, v in host.items()}
+        st, _ = step(src)
+        x_host.copy_(x, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_times.append((e0.elapsed_time(e1) / 1e3, st.iters))
+    e2e_value = world * nt * sum(i for _, i in e2e_times) / sum(t for t, _ in e2e_times)
+
+    # ---- iteration roofline: time the solve loop alone (matrix assembled)
+    s = ctx.assemble(d["xy"], d["tri"], d["dir"], d["eps"], d["kinv"], cps.PER_VERTEX,
+                     cps.KIND_CP2, p.nu, p.dt)
+    roof = {}
+    mixed = {}
+    for prec, bpc in ((cps.FP64, BYTES_PER_CELL_ITER_FP64), (cps.MIXED, BYTES_PER_CELL_ITER_MIXED)):
+        ts = []
+        for _ in range(2):
+            x.zero_()
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, st = s.solve(d["b"], x=x, rtol=args.rtol, precision=prec)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append((e0.elapsed_time(e1) / 1e3, st))
+        t, st = min(ts, key=lambda v: v[0])
+        if prec == cps.FP64:
+            peak, peak_kind = measured_peaks()
+            achieved = bpc * nt * st.iters / t / 1e9
+            roof = {"bound": "hbm", "kernel": "pcg_iteration_fp64 (k_spmv_dot+k_update+k_pupdate)",
+                    "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "peak_kind": peak_kind,
+                    "bytes_per_cell_iter": bpc, "traffic": None,
+                    "fp64_time_to_rtol_s": t, "fp64_iters": st.iters}
+        else:
+            mixed = {"time_to_rtol_s": t, "iters": st.iters, "refinements": st.refinements,
+                     "rel_res": st.rel_res,
+                     "inner_gbs": bpc * nt * st.iters / t / 1e9}
+    s.free()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"channel-block-aniso lattice n={args.n} (CP2, Jacobi-PCG, "
+                               f"rtol {args.rtol:g})",
+                   "cells": nt, "iters_per_step": int(np.mean(iters)),
+                   "l2": "256 MB buffer written between steps",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roof,
+        "mixed_precision": mixed,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d_bytes,
+                "d2h_bytes_per_step": d2h_bytes},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        iters_cpu = args.cpu_iters or max(20, int(1e9 / nt))
+        line["cpu_baseline"] = cpu_baseline(p, b_np, iters_cpu)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/*
+ * cps.h -- C ABI of the GB300 corrector-step solver library (libcps.so).
+ *
+ * The library assembles and solves the sparse symmetric positive definite
+ * M-matrix systems of the two corrector problems of the mesoscopic one-domain
+ * Navier-Stokes-Brinkman scheme of Aricò, Helmig, Puleo and Schneider
+ * (arXiv 2309.03543):
+ *
+ *   CP2 (Sec. 3.2.3, Eq. CS2_sys_coeff):  A_ee  =  sum_j l_j d_{j,n} / d_{e,ep}
+ *                                          A_e,ep = -l_j d_{j,n} / d_{e,ep}
+ *        with d_{j,n} = n_j . Xi_j n_j, Xi = eps M^-1 = eps dt (I + nu eps Kinv dt)^-1
+ *        (Eq. Cs2_4, M = M0/dt, M0 = I + nu eps Kinv dt from Sec. 3.1);
+ *   CP1 (Sec. 3.2.2, Eq. CS1_sys_coeff):  A_ee  = Mbar_kk A_e + nu sum_j l_j / d_{e,ep}
+ *                                          A_e,ep = -nu l_j / d_{e,ep}.
+ *
+ * One unknown per triangle (cell); at most three neighbours per cell.  The
+ * systems are solved by preconditioned conjugate gradients (Sec. 3.2.2:
+ * "PCG with an incomplete Cholesky factorization"), assembled and factored
+ * once and then solved for many right-hand sides (Sec. 3.1).
+ *
+ * Conventions for every entry point:
+ *   - Array arguments are DEVICE pointers on the context's device unless the
+ *     comment says "host".  The caller owns them; the library never frees or
+ *     keeps them after the call returns.
+ *   - Floating point arrays are IEEE binary64, row-major, contiguous.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *     enqueued on it; calls that return a result the host needs (assemble,
+ *     solve, adjoint) synchronise that stream before they return.
+ *   - The return value is a status: CPS_OK (0) or a negative CPS_ERR_* code.
+ *     No entry point aborts, traps or throws.  cps_last_error() gives a
+ *     human-readable message for the last failing call on a context.
+ *   - Handles are not thread-safe: use one handle from one host thread at a
+ *     time.
+ */
+#ifndef CPS_H
+#define CPS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define CPS_OK 0
+#define CPS_ERR_ARG (-1)            /* bad argument: NULL, size, range, kind */
+#define CPS_ERR_NONMANIFOLD (-2)    /* a side shared by more than two cells */
+#define CPS_ERR_NONDELAUNAY (-3)    /* some d_{e,ep} <= 1e-12 l_j (Sec. 3.1) */
+#define CPS_ERR_ORIENTATION (-4)    /* a triangle is not counter-clockwise */
+#define CPS_ERR_NOT_SPD (-5)        /* PCG saw p.Ap <= 0 or a NaN */
+#define CPS_ERR_NOT_CONVERGED (-6)  /* max_iter reached; x holds the last iterate */
+#define CPS_ERR_SINGULAR (-7)       /* CP2 without a Dirichlet side, or a zero row */
+#define CPS_ERR_NOMEM (-8)          /* device allocation failed */
+#define CPS_ERR_CUDA (-9)           /* a CUDA runtime call failed */
+#define CPS_ERR_TIMEOUT (-10)       /* a bounded device-side wait gave up */
+
+/* ------------------------------------------------------------- constants */
+#define CPS_KIND_CP2 0      /* pressure-increment system (Eq. CS2_sys_coeff) */
+#define CPS_KIND_CP1_X 1    /* viscous x-velocity system (Eq. CS1_sys_coeff) */
+#define CPS_KIND_CP1_Y 2    /* viscous y-velocity system */
+
+#define CPS_PER_VERTEX 0    /* eps, Kinv given at the mesh nodes (Sec. 3.2) */
+#define CPS_PER_CELL 1      /* eps, Kinv given per triangle */
+
+#define CPS_PC_JACOBI 1     /* diagonal preconditioner */
+#define CPS_PC_IC0 2        /* IC(0) in a multicolour order of the cells */
+
+#define CPS_FP64 0          /* all storage and arithmetic in binary64 */
+#define CPS_MIXED 1         /* binary32 matrix/vectors inside FP64 refinement */
+
+typedef struct cps_ctx_s* cps_ctx;
+typedef struct cps_sys_s* cps_sys;
+
+typedef struct {
+    int64_t iters;        /* PCG iterations run (summed over refinements) */
+    double rel_res;       /* true ||b - A x||_2 / ||b||_2 at return, in FP64 */
+    int32_t status;       /* same value as the call's return */
+    int32_t refinements;  /* outer FP64 residual steps (CPS_MIXED), else 1 */
+    int64_t launches;     /* kernels this call enqueued (graph nodes counted) */
+} cps_stats;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`.  *out receives the handle. */
+int cps_create(cps_ctx* out, int device);
+
+/* Destroy a context.  Systems made from it that are still live are freed
+ * with it; their handles become invalid. */
+int cps_destroy(cps_ctx ctx);
+
+/* Message of the last failing call on this context (never NULL; owned by
+ * the context, valid until the next call on it). */
+const char* cps_last_error(cps_ctx ctx);
+
+/* ------------------------------------------------------------- assembly */
+
+/* Build one corrector system from a counter-clockwise triangle mesh.
+ *
+ *   xy[nv*2]        vertex coordinates (x, y)
+ *   tri[nt*3]       vertex ids of each triangle, counter-clockwise; local
+ *                   side j joins vertices (j+1)%3 and (j+2)%3
+ *   dirichlet[nb]   boundary sides with eta = 0 at the side midpoint, given as
+ *                   tri*3 + j; all other boundary sides are no-flux.  May be
+ *                   NULL when nb = 0 (then CP2 is singular: CPS_ERR_SINGULAR)
+ *   eps[nf]         porosity, nf = nv (CPS_PER_VERTEX) or nt (CPS_PER_CELL)
+ *   kinv[nf*3]      inverse permeability tensor (xx, xy, yy), symmetric PSD
+ *   field_loc       CPS_PER_VERTEX: side tensor = mean of the tensors Xi at the
+ *                   side's two nodes (Sec. 3.2 side averages); CPS_PER_CELL:
+ *                   mean of the two cells' Xi, a boundary side uses its cell's
+ *   kind            CPS_KIND_CP2, CPS_KIND_CP1_X or CPS_KIND_CP1_Y
+ *   nu, dt          kinematic viscosity and time step (> 0)
+ *
+ * Geometry (Sec. 3.1, Eq. cs1_discr): circumcentres c_e, side lengths l_j,
+ * outward unit normals n_j, d_{e,ep} = (c_ep - c_e) . n_j.  A Dirichlet side
+ * adds l_j d_{j,n} / delta_j (CP1: nu l_j / delta_j) to the diagonal, with
+ * delta_j = (m_j - c_e) . n_j the distance from the circumcentre to the side.
+ * The Jacobi preconditioner is ready on return (cps_set_precond switches).
+ * Errors: CPS_ERR_ARG, _NONMANIFOLD, _NONDELAUNAY, _ORIENTATION, _SINGULAR,
+ * _NOMEM, _CUDA.  On error *out is NULL. */
+int cps_assemble(cps_ctx ctx, const double* xy, int64_t nv, const int32_t* tri, int64_t nt,
+                 const int32_t* dirichlet, int64_t nb, const double* eps,
+                 const double* kinv, int field_loc, int kind, double nu, double dt,
+                 cps_sys* out, void* stream);
+
+/* Select the preconditioner (Sec. 3.2.2 uses incomplete Cholesky):
+ * CPS_PC_JACOBI, or CPS_PC_IC0 = IC(0) factored once on the pattern of A in a
+ * multicolour order of the cells (two colours on the lattice's bipartite cell
+ * graph).  The factor is computed here, once, on the device. */
+int cps_set_precond(cps_sys sys, int precond, void* stream);
+
+/* Free a system and all device memory it owns.  A handle that was already
+ * freed (or whose context was destroyed) must not be passed again. */
+int cps_sys_free(cps_sys sys);
+
+/* Host outputs (any may be NULL): number of cells, number of interior sides,
+ * smallest diagonal entry, 1 if every row has a positive diagonal and
+ * non-positive off-diagonals (the M-matrix sign pattern), and the number of
+ * kernels the assembly (and preconditioner set-up) launched. */
+int cps_sys_info(cps_sys sys, int64_t* nt, int64_t* n_interior_sides, double* diag_min,
+                 int* is_mmatrix, int64_t* setup_launches);
+
+/* Copy the assembled matrix out in padded ELL form (device pointers):
+ * diag[nt]; col[3*nt], val[3*nt] slot-major (entry s*nt + e is slot s of row
+ * e; an unused slot has col = e, val = 0).  Row/column order is the mesh's. */
+int cps_export_matrix(cps_sys sys, double* diag, int32_t* col, double* val, void* stream);
+
+/* ---------------------------------------------------------------- solves */
+
+/* Solve A x = b by PCG.
+ *   b[nt]       right-hand side (not modified)
+ *   x[nt]       in: initial guess (warm start; zeros for a cold start),
+ *               out: solution
+ *   rtol        stop when ||b - A x||_2 <= rtol ||b||_2; the true residual is
+ *               recomputed in FP64 at the end and the solve continues if it is
+ *               still above rtol
+ *   max_iter    bound on PCG iterations (summed over refinements)
+ *   precision   CPS_FP64 or CPS_MIXED (binary32 matrix, vectors and SpMV in
+ *               the inner PCG; binary64 dot products, alpha/beta, and the
+ *               outer residual b - A x and update of x)
+ *   stats       host pointer, may be NULL
+ * b = 0 gives x = 0.  Errors: CPS_ERR_ARG, _NOT_SPD, _NOT_CONVERGED (x holds
+ * the last iterate), _CUDA. */
+int cps_solve(cps_sys sys, const double* b, double* x, double rtol, int64_t max_iter,
+              int precision, cps_stats* stats, void* stream);
+
+/* Solve nsys independent systems (each with its own matrix, b and x) in one
+ * launch sequence with per-system convergence.  systems, b, x and stats are
+ * HOST arrays of length nsys holding handles and device pointers.  All systems
+ * must come from the same context and use the Jacobi preconditioner.  The
+ * return value is the first non-OK per-system status, or CPS_OK. */
+int cps_solve_batch(const cps_sys* systems, int nsys, const double* const* b,
+                    double* const* x, double rtol, int64_t max_iter, int precision,
+                    cps_stats* stats, void* stream);
+
+/* Adjoint of one solve x = A^-1 b (A symmetric, so the same matrix and
+ * preconditioner serve): lambda = A^-1 g, then for every local side slot
+ * (slot-major, s*nt + e)
+ *   dT[s*nt+e] += -(lambda_e - lambda_ep)(x_e - x_ep)   interior side
+ *   dT[s*nt+e] += -lambda_e x_e                         Dirichlet side
+ * which is dL/dT for the side coefficient T of A (each interior side appears
+ * in both of its cells' slots with the same value).  If dtheta is not NULL
+ * (CP2, CPS_PER_CELL, isotropic Kinv = exp(-theta) I only) the chain rule
+ * through Xi_e = eps dt / (1 + nu eps dt exp(-theta_e)) is applied and
+ * dL/dtheta is ADDED to dtheta[nt].  dT may be NULL if only dtheta is wanted.
+ * lambda[nt] is overwritten (its input is the initial guess).
+ * Errors: as cps_solve, plus CPS_ERR_ARG for dtheta on an unsupported system. */
+int cps_adjoint(cps_sys sys, const double* x, const double* g, double* lambda, double* dT,
+                double* dtheta, double rtol, int64_t max_iter, cps_stats* stats,
+                void* stream);
+
+/* y = A x for the assembled matrix (device pointers, FP64). */
+int cps_matvec(cps_sys sys, const double* x, double* y, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CPS_H */

@@ -1,0 +1,16 @@
+"""GB300-native corrector-step solver (arXiv 2309.03543, Sec. 3.2.2-3.2.3).
+
+Assembly of the CP1/CP2 matrices on Delaunay triangle meshes and their
+preconditioned conjugate-gradient solves, as hand-written sm_103a CUDA kernels
+behind the C ABI of include/cps.h.  This package is the Python binding:
+``Context.assemble`` -> ``System.solve`` / ``System.adjoint`` /
+``solve_batch``, and the autograd wrapper ``CorrectorSolve``.
+"""
+from ._cps import (FP64, KIND_CP1_X, KIND_CP1_Y, KIND_CP2, MIXED, PC_IC0, PC_JACOBI,  # noqa: F401
+                   PER_CELL, PER_VERTEX, LIB_PATH)
+from .api import Context, CpsError, SolveStats, System, solve_batch  # noqa: F401
+
+
+def build(force: bool = False) -> str:
+    from .build import build as _b
+    return _b(force=force)

@@ -1,0 +1,209 @@
+"""Thin Python binding of libcps.so (argument marshalling only).
+
+Tensors are torch tensors; device tensors are passed straight through as
+device pointers on the current torch stream.  Host (CPU) tensors are copied to
+the device first and results copied back, so the same calls serve callers
+that hold their data in host memory.  Every step of the computation runs in
+the CUDA library; nothing here computes.
+"""
+from __future__ import annotations
+
+import ctypes
+import weakref
+from dataclasses import dataclass
+
+import torch
+
+from . import _cps
+
+P = ctypes.c_void_p
+
+
+class CpsError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"{_cps.ERROR_NAMES.get(code, code)}: {message}")
+        self.code = code
+
+
+@dataclass
+class SolveStats:
+    iters: int
+    rel_res: float
+    status: int
+    refinements: int
+    launches: int
+
+
+def _stats(s: _cps.Stats) -> SolveStats:
+    return SolveStats(int(s.iters), float(s.rel_res), int(s.status), int(s.refinements),
+                      int(s.launches))
+
+
+def _stream(device: torch.device) -> P:
+    return P(torch.cuda.current_stream(device).cuda_stream)
+
+
+class Context:
+    """A library context on one CUDA device."""
+
+    def __init__(self, device: int | torch.device = 0):
+        self.lib = _cps.load()
+        self.device = torch.device("cuda", device if isinstance(device, int) else device.index or 0)
+        h = P()
+        rc = self.lib.cps_create(ctypes.byref(h), self.device.index)
+        if rc != _cps.OK:
+            raise CpsError(rc, "cps_create failed")
+        self.handle = h
+        self._systems = weakref.WeakSet()
+
+    def last_error(self) -> str:
+        m = self.lib.cps_last_error(self.handle)
+        return m.decode() if m else ""
+
+    def check(self, rc: int, what: str):
+        if rc != _cps.OK:
+            raise CpsError(rc, f"{what}: {self.last_error()}")
+
+    def dev(self, t, dtype) -> torch.Tensor:
+        """The tensor on this device, contiguous, of dtype (copied if needed)."""
+        t = torch.as_tensor(t)
+        return t.to(device=self.device, dtype=dtype).contiguous()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            for s in list(self._systems):
+                s.handle = None          # freed by cps_destroy with the context
+            self.lib.cps_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ assembly
+    def assemble(self, xy, tri, dirichlet, eps, kinv, field_loc: int = _cps.PER_VERTEX,
+                 kind: int = _cps.KIND_CP2, nu: float = 1.5e-5, dt: float = 0.225) -> "System":
+        xy_d = self.dev(xy, torch.float64)
+        tri_d = self.dev(tri, torch.int32)
+        dir_d = self.dev(dirichlet, torch.int32)
+        eps_d = self.dev(eps, torch.float64)
+        kinv_d = self.dev(kinv, torch.float64)
+        nv = xy_d.numel() // 2
+        nt = tri_d.numel() // 3
+        h = P()
+        rc = self.lib.cps_assemble(self.handle, P(xy_d.data_ptr()), nv, P(tri_d.data_ptr()), nt,
+                                   P(dir_d.data_ptr()) if dir_d.numel() else None, dir_d.numel(),
+                                   P(eps_d.data_ptr()), P(kinv_d.data_ptr()), field_loc, kind,
+                                   nu, dt, ctypes.byref(h), _stream(self.device))
+        self.check(rc, "cps_assemble")
+        s = System(self, h, nt)
+        self._systems.add(s)
+        return s
+
+
+class System:
+    """One assembled corrector system (matrix, preconditioner, workspace)."""
+
+    def __init__(self, ctx: Context, handle: P, nt: int):
+        self.ctx = ctx
+        self.handle = handle
+        self.nt = nt
+
+    def free(self):
+        if self.handle and self.ctx.handle:
+            self.ctx.lib.cps_sys_free(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        nt, ne, sl = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        dmin, mm = ctypes.c_double(), ctypes.c_int()
+        self.ctx.check(self.ctx.lib.cps_sys_info(self.handle, ctypes.byref(nt), ctypes.byref(ne),
+                                                 ctypes.byref(dmin), ctypes.byref(mm),
+                                                 ctypes.byref(sl)),
+                       "cps_sys_info")
+        return {"nt": nt.value, "n_interior_sides": ne.value, "diag_min": dmin.value,
+                "is_mmatrix": bool(mm.value), "setup_launches": sl.value}
+
+    def set_precond(self, precond: int):
+        self.ctx.check(self.ctx.lib.cps_set_precond(self.handle, precond,
+                                                    _stream(self.ctx.device)), "cps_set_precond")
+
+    def export_matrix(self):
+        """(diag [nt], col [3, nt], val [3, nt]) on the device."""
+        d = torch.empty(self.nt, dtype=torch.float64, device=self.ctx.device)
+        c = torch.empty(3 * self.nt, dtype=torch.int32, device=self.ctx.device)
+        v = torch.empty(3 * self.nt, dtype=torch.float64, device=self.ctx.device)
+        self.ctx.check(self.ctx.lib.cps_export_matrix(self.handle, P(d.data_ptr()), P(c.data_ptr()),
+                                                      P(v.data_ptr()), _stream(self.ctx.device)),
+                       "cps_export_matrix")
+        return d, c.view(3, self.nt), v.view(3, self.nt)
+
+    def matvec(self, x) -> torch.Tensor:
+        xd = self.ctx.dev(x, torch.float64)
+        y = torch.empty_like(xd)
+        self.ctx.check(self.ctx.lib.cps_matvec(self.handle, P(xd.data_ptr()), P(y.data_ptr()),
+                                               _stream(self.ctx.device)), "cps_matvec")
+        return y
+
+    def solve(self, b, x=None, rtol: float = 1e-10, max_iter: int = 1_000_000,
+              precision: int = _cps.FP64, check: bool = True):
+        """Solve A x = b.  x (if given, a device tensor) is the initial guess
+        and is overwritten in place.  Host inputs are copied in and the result
+        copied back to the host.  Returns (x, SolveStats)."""
+        host = not (isinstance(b, torch.Tensor) and b.is_cuda)
+        bd = self.ctx.dev(b, torch.float64)
+        if x is None:
+            xd = torch.zeros_like(bd)
+        elif isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64 \
+                and x.is_contiguous():
+            xd = x
+        else:
+            xd = self.ctx.dev(x, torch.float64)
+        st = _cps.Stats()
+        rc = self.ctx.lib.cps_solve(self.handle, P(bd.data_ptr()), P(xd.data_ptr()), rtol,
+                                    max_iter, precision, ctypes.byref(st),
+                                    _stream(self.ctx.device))
+        if check:
+            self.ctx.check(rc, "cps_solve")
+        out = xd.cpu() if host else xd
+        return out, _stats(st)
+
+    def adjoint(self, x, g, lam=None, dT=None, dtheta=None, rtol: float = 1e-12,
+                max_iter: int = 1_000_000):
+        """lambda = A^-1 g; accumulates dL/dT into dT [3, nt] and dL/dtheta
+        into dtheta [nt] when those device tensors are given."""
+        xd = self.ctx.dev(x, torch.float64)
+        gd = self.ctx.dev(g, torch.float64)
+        lam = torch.zeros_like(gd) if lam is None else lam
+        st = _cps.Stats()
+        rc = self.ctx.lib.cps_adjoint(self.handle, P(xd.data_ptr()), P(gd.data_ptr()),
+                                      P(lam.data_ptr()),
+                                      P(dT.data_ptr()) if dT is not None else None,
+                                      P(dtheta.data_ptr()) if dtheta is not None else None,
+                                      rtol, max_iter, ctypes.byref(st), _stream(self.ctx.device))
+        self.ctx.check(rc, "cps_adjoint")
+        return lam, _stats(st)
+
+
+def solve_batch(systems, bs, xs, rtol: float = 1e-10, max_iter: int = 1_000_000,
+                precision: int = _cps.FP64, check: bool = True):
+    """Solve several systems (device tensors b, x per system) in one call."""
+    ctx = systems[0].ctx
+    n = len(systems)
+    hs = (P * n)(*[s.handle for s in systems])
+    bp = (P * n)(*[P(b.data_ptr()) for b in bs])
+    xp = (P * n)(*[P(x.data_ptr()) for x in xs])
+    st = (_cps.Stats * n)()
+    rc = ctx.lib.cps_solve_batch(hs, n, bp, xp, rtol, max_iter, precision, st,
+                                 _stream(ctx.device))
+    if check:
+        ctx.check(rc, "cps_solve_batch")
+    return [_stats(s) for s in st]

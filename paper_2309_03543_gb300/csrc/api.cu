@@ -1,0 +1,146 @@
+// C ABI entry points (declared in include/cps.h).  Argument checks, device
+// selection and handle bookkeeping; the work is in assemble.cu and pcg.cu.
+#include "cps_internal.cuh"
+
+#include <new>
+
+namespace {
+
+int set_device(cps_ctx ctx) {
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) {
+        ctx->last_error = std::string("cudaSetDevice: ") + cudaGetErrorString(e);
+        return CPS_ERR_CUDA;
+    }
+    return CPS_OK;
+}
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+extern "C" {
+
+int cps_create(cps_ctx* out, int device) {
+    if (!out) return CPS_ERR_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count)
+        return CPS_ERR_ARG;
+    cps_ctx c = new (std::nothrow) cps_ctx_s();
+    if (!c) return CPS_ERR_NOMEM;
+    c->device = device;
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->max_threads_per_sm, cudaDevAttrMaxThreadsPerMultiProcessor,
+                               device) != cudaSuccess) {
+        delete c;
+        return CPS_ERR_CUDA;
+    }
+    int l2 = 0;
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device);
+    c->l2_bytes = (size_t)l2;
+    *out = c;
+    return CPS_OK;
+}
+
+int cps_destroy(cps_ctx ctx) {
+    if (!ctx) return CPS_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    for (cps_sys s : ctx->systems) cps::free_sys(s);
+    ctx->systems.clear();
+    delete ctx;
+    return CPS_OK;
+}
+
+const char* cps_last_error(cps_ctx ctx) {
+    if (!ctx) return "null context";
+    return ctx->last_error.c_str();
+}
+
+int cps_assemble(cps_ctx ctx, const double* xy, int64_t nv, const int32_t* tri, int64_t nt,
+                 const int32_t* dirichlet, int64_t nb, const double* eps, const double* kinv,
+                 int field_loc, int kind, double nu, double dt, cps_sys* out, void* stream) {
+    if (!ctx || !out) return CPS_ERR_ARG;
+    *out = nullptr;
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    ctx->last_error.clear();
+    rc = cps::assemble_impl(ctx, xy, nv, tri, nt, dirichlet, nb, eps, kinv, field_loc, kind, nu,
+                            dt, out, as_stream(stream));
+    if (rc == CPS_OK) ctx->systems.insert(*out);
+    return rc;
+}
+
+int cps_set_precond(cps_sys sys, int precond, void* stream) {
+    if (!sys) return CPS_ERR_ARG;
+    int rc = set_device(sys->ctx);
+    if (rc) return rc;
+    return cps::precond_impl(sys, precond, as_stream(stream));
+}
+
+int cps_sys_free(cps_sys sys) {
+    if (!sys) return CPS_ERR_ARG;
+    cps_ctx ctx = sys->ctx;
+    if (!ctx || ctx->systems.erase(sys) == 0) return CPS_ERR_ARG;   // unknown or freed
+    set_device(ctx);
+    cps::free_sys(sys);
+    return CPS_OK;
+}
+
+int cps_sys_info(cps_sys sys, int64_t* nt, int64_t* n_interior_sides, double* diag_min,
+                 int* is_mmatrix, int64_t* setup_launches) {
+    if (!sys) return CPS_ERR_ARG;
+    if (setup_launches) *setup_launches = sys->assembly_launches;
+    if (nt) *nt = sys->nt;
+    if (n_interior_sides) *n_interior_sides = sys->n_interior;
+    if (diag_min) *diag_min = sys->diag_min;
+    if (is_mmatrix) *is_mmatrix = sys->is_mmatrix;
+    return CPS_OK;
+}
+
+int cps_export_matrix(cps_sys sys, double* diag, int32_t* col, double* val, void* stream) {
+    if (!sys) return CPS_ERR_ARG;
+    int rc = set_device(sys->ctx);
+    if (rc) return rc;
+    return cps::export_impl(sys, diag, col, val, as_stream(stream));
+}
+
+int cps_solve(cps_sys sys, const double* b, double* x, double rtol, int64_t max_iter,
+              int precision, cps_stats* stats, void* stream) {
+    if (!sys) return CPS_ERR_ARG;
+    int rc = set_device(sys->ctx);
+    if (rc) return rc;
+    return cps::solve_impl(sys, b, x, rtol, max_iter, precision, stats, as_stream(stream));
+}
+
+int cps_solve_batch(const cps_sys* systems, int nsys, const double* const* b, double* const* x,
+                    double rtol, int64_t max_iter, int precision, cps_stats* stats,
+                    void* stream) {
+    if (nsys < 0 || (nsys > 0 && (!systems || !b || !x))) return CPS_ERR_ARG;
+    if (nsys == 0) return CPS_OK;
+    for (int i = 0; i < nsys; ++i)
+        if (!systems[i] || systems[i]->ctx != systems[0]->ctx) return CPS_ERR_ARG;
+    int rc = set_device(systems[0]->ctx);
+    if (rc) return rc;
+    return cps::solve_batch_impl(systems, nsys, b, x, rtol, max_iter, precision, stats,
+                                 as_stream(stream));
+}
+
+int cps_adjoint(cps_sys sys, const double* x, const double* g, double* lambda, double* dT,
+                double* dtheta, double rtol, int64_t max_iter, cps_stats* stats, void* stream) {
+    if (!sys) return CPS_ERR_ARG;
+    int rc = set_device(sys->ctx);
+    if (rc) return rc;
+    return cps::adjoint_impl(sys, x, g, lambda, dT, dtheta, rtol, max_iter, stats,
+                             as_stream(stream));
+}
+
+int cps_matvec(cps_sys sys, const double* x, double* y, void* stream) {
+    if (!sys) return CPS_ERR_ARG;
+    int rc = set_device(sys->ctx);
+    if (rc) return rc;
+    return cps::matvec_impl(sys, x, y, as_stream(stream));
+}
+
+}  // extern "C"

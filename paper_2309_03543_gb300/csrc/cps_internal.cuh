@@ -1,0 +1,218 @@
+// Internal definitions of the corrector-step solver library (not part of the
+// C ABI).  Device data layout, handle structs, launch helpers and the
+// deterministic grid reduction shared by the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <unordered_set>
+
+#include "cps.h"
+
+namespace cps {
+
+constexpr int kBlock = 256;          // threads per block for streaming kernels
+constexpr int kMaxGrid = 4096;       // bound on blocks (size of partial buffers)
+constexpr int kNumPartials = 4;      // doubles reduced per kernel at most
+
+// Scalar state of one conjugate-gradient run, kept on the device so that the
+// iteration never waits for the host.  Written only by the last block of a
+// reduction kernel; read by every block of later kernels.
+struct CgState {
+    double rho;        // r^T z of the current residual
+    double alpha;      // step length of the current iteration
+    double beta;       // p-update coefficient of the current iteration
+    double bnorm2;     // ||b||^2 of the outer system (unscaled)
+    double thresh2;    // stop threshold on the residual norm squared
+    double rnorm2;     // last evaluated residual norm squared (unscaled)
+    double gamma;      // p^T A p of the current iteration
+    long long iter;    // iterations completed in this run
+    long long max_iter;
+    int done;          // 1: stop (converged, breakdown or max_iter)
+    int status;        // CPS_OK or an error code set on the device
+    unsigned int arrive[4];   // arrival counters of the grid reductions
+    int pad[4];
+};
+
+// Device error flag written by the assembly kernels (first error wins).
+__device__ __forceinline__ void set_error(int* err, int code) {
+    atomicCAS(err, 0, code);
+}
+
+// Deterministic sum over the grid: every block writes its partial sums, the
+// last block to arrive adds them up in a fixed order.  Returns true only in
+// the last block, where out[] then holds the totals in every thread.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double (*sh)[NV]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    }
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sh[warp][k] = v[k];
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double t = lane < nw ? sh[lane][k] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            v[k] = t;
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) sh[0][k] = v[k];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = sh[0][k];
+    __syncthreads();
+}
+
+template <int NV>
+__device__ __forceinline__ bool grid_sum(double (&v)[NV], double* partials,
+                                         unsigned int* arrive) {
+    __shared__ double sh[32][NV];
+    __shared__ bool last;
+    block_sum<NV>(v, sh);
+    const int G = gridDim.x;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) partials[k * kMaxGrid + blockIdx.x] = v[k];
+        __threadfence();
+        unsigned int t = atomicAdd(arrive, 1u);
+        last = (t == (unsigned)G - 1u);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double acc = 0.0;
+        for (int i = threadIdx.x; i < G; i += blockDim.x) acc += __ldcg(&partials[k * kMaxGrid + i]);
+        v[k] = acc;
+    }
+    block_sum<NV>(v, sh);
+    if (threadIdx.x == 0) *arrive = 0u;
+    return true;
+}
+
+}  // namespace cps
+
+// Context and system handles (opaque in the C ABI).
+struct cps_ctx_s {
+    int device = 0;
+    int num_sms = 0;
+    int max_threads_per_sm = 2048;
+    size_t l2_bytes = 0;
+    std::string last_error;
+    std::unordered_set<cps_sys_s*> systems;   // live systems, freed with the context
+};
+
+struct cps_sys_s {
+    cps_ctx ctx = nullptr;
+    int64_t nt = 0, nv = 0;
+    int kind = CPS_KIND_CP2;
+    int field_loc = CPS_PER_VERTEX;
+    int precond = CPS_PC_JACOBI;
+    double nu = 0, dt = 0;
+    int64_t n_interior = 0;
+    double diag_min = 0;
+    int is_mmatrix = 0;
+    bool iso_cell = false;      // CPS_PER_CELL with isotropic Kinv (adjoint theta chain)
+    int64_t assembly_launches = 0;
+
+    // Matrix in symmetrically scaled padded-ELL form: A = S (I + Aoff) S with
+    // S = diag(s), s = sqrt(diag(A)); slot-major arrays [3][nt].
+    double* s = nullptr;        // [nt]
+    double* diag = nullptr;     // [nt] unscaled diagonal (export / info)
+    double* a = nullptr;        // [3*nt] scaled off-diagonals
+    int32_t* col = nullptr;     // [3*nt] column (= row for an unused slot)
+    float* a32 = nullptr;       // [3*nt] binary32 copy of a (mixed precision)
+    float* s32 = nullptr;       // [nt]
+    // Adjoint: per slot dT/dxi_e, per cell dxi/dtheta (CP2, cell fields).
+    double* gfac = nullptr;     // [3*nt]
+    double* dxi = nullptr;      // [nt]
+    int32_t* slot_kind = nullptr;   // [3*nt] 0 no-flux, 1 interior, 2 Dirichlet
+
+    // IC(0) in colour order (scaled matrix, unit diagonal).
+    int ncolours = 0;
+    int64_t colour_start[17] = {0};
+    int32_t* perm = nullptr;    // [nt] new -> old
+    int32_t* iperm = nullptr;   // [nt] old -> new
+    double* pa = nullptr;       // [3*nt] permuted scaled off-diagonals
+    int32_t* pcol = nullptr;    // [3*nt] permuted columns
+    double* pdinv = nullptr;    // [nt] inverse IC(0) pivots (permuted order)
+    float* pa32 = nullptr;
+    float* pdinv32 = nullptr;
+    double* ps = nullptr;       // [nt] s in permuted order
+    float* ps32 = nullptr;
+
+    // PCG workspace (allocated at assembly so that solves never allocate).
+    double* wy = nullptr;       // [nt] iterate (scaled)
+    double* wr = nullptr;       // [nt] residual
+    double* wp = nullptr;       // [nt] search direction
+    double* wq = nullptr;       // [nt] A p
+    double* wz = nullptr;       // [nt] preconditioned residual (IC0)
+    double* wb = nullptr;       // [nt] permuted right-hand side / staging
+    double* partials = nullptr; // [kNumPartials * kMaxGrid]
+    cps::CgState* st = nullptr; // device state
+    cps::CgState* hst = nullptr;  // pinned host mirror (2 slots)
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    int grid = 0;
+
+    // CUDA graphs of a chunk of iterations, per (precision, preconditioner).
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    int chunk = 0;
+};
+
+#define CPS_CUDA_TRY(ctx, call)                                                        \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            if (ctx) {                                                                 \
+                (ctx)->last_error = std::string(#call) + ": " + cudaGetErrorString(e_); \
+            }                                                                          \
+            return e_ == cudaErrorMemoryAllocation ? CPS_ERR_NOMEM : CPS_ERR_CUDA;     \
+        }                                                                              \
+    } while (0)
+
+namespace cps {
+
+inline int grid_for(const cps_ctx_s* ctx, int64_t n, int per_sm = 8) {
+    int64_t need = (n + kBlock - 1) / kBlock;
+    int64_t cap = (int64_t)ctx->num_sms * per_sm;
+    if (cap > kMaxGrid) cap = kMaxGrid;
+    if (need < 1) need = 1;
+    return (int)(need < cap ? need : cap);
+}
+
+int assemble_impl(cps_ctx ctx, const double* xy, int64_t nv, const int32_t* tri, int64_t nt,
+                  const int32_t* dirichlet, int64_t nb, const double* eps, const double* kinv,
+                  int field_loc, int kind, double nu, double dt, cps_sys* out,
+                  cudaStream_t stream);
+int precond_impl(cps_sys sys, int precond, cudaStream_t stream);
+int solve_impl(cps_sys sys, const double* b, double* x, double rtol, int64_t max_iter,
+               int precision, cps_stats* stats, cudaStream_t stream);
+int solve_batch_impl(const cps_sys* systems, int nsys, const double* const* b,
+                     double* const* x, double rtol, int64_t max_iter, int precision,
+                     cps_stats* stats, cudaStream_t stream);
+int adjoint_impl(cps_sys sys, const double* x, const double* g, double* lambda, double* dT,
+                 double* dtheta, double rtol, int64_t max_iter, cps_stats* stats,
+                 cudaStream_t stream);
+int matvec_impl(cps_sys sys, const double* x, double* y, cudaStream_t stream);
+int export_impl(cps_sys sys, double* diag, int32_t* col, double* val, cudaStream_t stream);
+void free_sys(cps_sys sys);
+
+}  // namespace cps

@@ -1,0 +1,221 @@
+"""CUDA path vs the CPU oracle, through the C ABI, element by element.
+
+Assembly: the exported ELL matrix against the oracle's CSR (FP64, 1e-13
+relative per entry).  Solves: relative L2 error of x against the oracle's
+solution at rtol 1e-13 -- 1e-9 for FP64 and 1e-8 for mixed precision.
+Sizes span several thread blocks and a ragged tail."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+cps = pytest.importorskip("paper_2309_03543_gb300")
+
+
+@pytest.fixture(scope="module")
+def ctx(cuda_device):
+    c = cps.Context(0)
+    yield c
+    c.close()
+
+
+def assemble(ctx, p, kind=cps.KIND_CP2):
+    m = p.mesh
+    return ctx.assemble(m.xy, m.tri, m.dirichlet, p.eps, p.kinv, p.field_loc, kind, p.nu, p.dt)
+
+
+def problems():
+    yield "block37", synth.centred_block_problem(37, seed=3)
+    yield "channel64", synth.channel_block_problem(64, seed=5)
+    yield "logperm29", synth.log_permeability_problem(29, seed=2)[0]
+    yield "ensemble", synth.ensemble_member_problem(3000, seed=11)
+
+
+PROBLEMS = dict(problems())
+
+
+def csr_rows(A):
+    rows = []
+    for i in range(A.n):
+        d = {}
+        for k in range(A.rowptr[i], A.rowptr[i + 1]):
+            d[int(A.col[k])] = d.get(int(A.col[k]), 0.0) + A.val[k]
+        rows.append(d)
+    return rows
+
+
+def ell_rows(diag, col, val):
+    diag = diag.cpu().numpy()
+    col = col.cpu().numpy()
+    val = val.cpu().numpy()
+    rows = []
+    for e in range(diag.shape[0]):
+        d = {e: diag[e]}
+        for j in range(3):
+            if col[j, e] != e:
+                d[int(col[j, e])] = d.get(int(col[j, e]), 0.0) + val[j, e]
+            else:
+                assert val[j, e] == 0.0
+        rows.append(d)
+    return rows
+
+
+@pytest.mark.parametrize("name", sorted(PROBLEMS))
+@pytest.mark.parametrize("kind", [cps.KIND_CP2, cps.KIND_CP1_X, cps.KIND_CP1_Y])
+def test_assembly_matches_oracle(ctx, name, kind):
+    p = PROBLEMS[name]
+    s = assemble(ctx, p, kind)
+    A = oracle.assemble_problem(p, kind)
+    got = ell_rows(*s.export_matrix())
+    want = csr_rows(A)
+    scale = np.abs(A.val).max()
+    for e, (g, w) in enumerate(zip(got, want)):
+        assert g.keys() == w.keys(), e
+        for c in w:
+            assert abs(g[c] - w[c]) <= 1e-13 * max(abs(w[c]), 1e-300) + 1e-15 * scale, (e, c)
+    info = s.info()
+    assert info["is_mmatrix"] and info["nt"] == p.mesh.nt
+    g = oracle.geometry(p.mesh.xy, p.mesh.tri)
+    assert info["n_interior_sides"] == int((g.nbr >= 0).sum()) // 2
+    s.free()
+
+
+@pytest.mark.parametrize("name", sorted(PROBLEMS))
+@pytest.mark.parametrize("precision,tol", [(cps.FP64, 1e-9), (cps.MIXED, 1e-8)])
+def test_solve_matches_oracle(ctx, name, precision, tol):
+    p = PROBLEMS[name]
+    s = assemble(ctx, p)
+    b = synth.rhs(p.mesh, 17)
+    xo, sto, A = oracle.solve_problem(p, b, rtol=1e-13)
+    x, st = s.solve(torch.as_tensor(b, device="cuda"), rtol=1e-12, precision=precision)
+    x = x.cpu().numpy()
+    err = np.linalg.norm(x - xo) / np.linalg.norm(xo)
+    assert err < tol, err
+    assert st.rel_res <= 1e-12
+    # the GPU's own residual claim, checked with the oracle's matrix
+    r = b - A.matvec(x)
+    assert np.linalg.norm(r) / np.linalg.norm(b) < 2e-12
+    s.free()
+
+
+def test_two_solves_one_matrix_warm_start(ctx):
+    """CP2 solves twice per step on one matrix (Eq. Cs2_7); the second can
+    start from the first solution."""
+    p = PROBLEMS["channel64"]
+    s = assemble(ctx, p)
+    b1 = synth.rhs(p.mesh, 1)
+    b2 = b1 + 1e-3 * synth.rhs(p.mesh, 2)
+    x1, st1 = s.solve(torch.as_tensor(b1, device="cuda"), rtol=1e-11)
+    x2 = x1.clone()
+    _, st2 = s.solve(torch.as_tensor(b2, device="cuda"), x=x2, rtol=1e-11)
+    assert st2.iters < st1.iters
+    xo, _, _ = oracle.solve_problem(p, b2, rtol=1e-13)
+    assert np.linalg.norm(x2.cpu().numpy() - xo) / np.linalg.norm(xo) < 1e-8
+    # solving again from the solution needs no iteration
+    _, st3 = s.solve(torch.as_tensor(b2, device="cuda"), x=x2.clone(), rtol=1e-6)
+    assert st3.iters == 0
+    s.free()
+
+
+def test_zero_rhs_and_max_iter(ctx):
+    p = PROBLEMS["block37"]
+    s = assemble(ctx, p)
+    x = torch.ones(p.mesh.nt, dtype=torch.float64, device="cuda")
+    _, st = s.solve(torch.zeros_like(x), x=x)
+    assert st.iters == 0 and torch.all(x == 0)
+    b = torch.as_tensor(synth.rhs(p.mesh, 1), device="cuda")
+    with pytest.raises(cps.CpsError) as ei:
+        s.solve(b, rtol=1e-12, max_iter=5)
+    assert ei.value.code == cps._cps.ERR_NOT_CONVERGED
+    x, st = s.solve(b, rtol=1e-12, max_iter=5, check=False)
+    assert st.iters == 5 and st.status == cps._cps.ERR_NOT_CONVERGED
+    s.free()
+
+
+def test_host_buffers_round_trip(ctx):
+    p = PROBLEMS["block37"]
+    s = assemble(ctx, p)
+    b = synth.rhs(p.mesh, 4)
+    x, st = s.solve(torch.as_tensor(b), rtol=1e-12)     # CPU tensor in, CPU tensor out
+    assert x.device.type == "cpu"
+    xo, _, _ = oracle.solve_problem(p, b, rtol=1e-13)
+    assert np.linalg.norm(x.numpy() - xo) / np.linalg.norm(xo) < 1e-9
+    s.free()
+
+
+def test_matvec_matches_oracle(ctx):
+    p = PROBLEMS["channel64"]
+    s = assemble(ctx, p)
+    A = oracle.assemble_problem(p)
+    v = np.random.default_rng(3).standard_normal(p.mesh.nt)
+    y = s.matvec(torch.as_tensor(v, device="cuda")).cpu().numpy()
+    np.testing.assert_allclose(y, A.matvec(v), rtol=1e-12, atol=1e-14 * np.abs(A.val).max())
+    s.free()
+
+
+def test_invalid_meshes_are_rejected(ctx):
+    m = synth.lattice(8, seed=0)
+    one = np.ones(m.nv)
+    zero = np.zeros((m.nv, 3))
+    E = cps._cps
+    with pytest.raises(cps.CpsError) as ei:        # CP2 without Dirichlet sides
+        ctx.assemble(m.xy, m.tri, np.zeros(0, np.int32), one, zero)
+    assert ei.value.code == E.ERR_SINGULAR
+    with pytest.raises(cps.CpsError) as ei:        # clockwise triangle
+        tri = m.tri.copy()
+        tri[5] = tri[5][[0, 2, 1]]
+        ctx.assemble(m.xy, tri, m.dirichlet, one, zero)
+    assert ei.value.code in (E.ERR_ORIENTATION, E.ERR_NONMANIFOLD, E.ERR_NONDELAUNAY)
+    with pytest.raises(cps.CpsError) as ei:        # non-Delaunay vertex move
+        xy = m.xy.copy()
+        xy[2 * 8 + 2] += [0.0, 0.6]
+        ctx.assemble(xy, m.tri, m.dirichlet, one, zero)
+    assert ei.value.code in (E.ERR_NONDELAUNAY, E.ERR_ORIENTATION)
+    with pytest.raises(cps.CpsError) as ei:        # a side of three triangles
+        tri = np.concatenate([m.tri, m.tri[:1, [1, 0, 2]]])
+        ctx.assemble(m.xy, tri, m.dirichlet, one, zero)
+    assert ei.value.code in (E.ERR_NONMANIFOLD, E.ERR_ORIENTATION)
+    with pytest.raises(cps.CpsError) as ei:        # vertex id out of range
+        tri = m.tri.copy()
+        tri[0, 0] = m.nv + 5
+        ctx.assemble(m.xy, tri, m.dirichlet, one, zero)
+    assert ei.value.code == E.ERR_ARG
+    with pytest.raises(cps.CpsError) as ei:        # Dirichlet side that is interior
+        ctx.assemble(m.xy, m.tri, np.array([3 * 40 + 0], np.int32), one, zero)
+    assert ei.value.code == E.ERR_ARG
+    with pytest.raises(cps.CpsError) as ei:        # zero porosity
+        ctx.assemble(m.xy, m.tri, m.dirichlet, np.zeros(m.nv), zero)
+    assert ei.value.code == E.ERR_ARG
+    # the context still works after every rejection
+    s = ctx.assemble(m.xy, m.tri, m.dirichlet, one, zero)
+    s.free()
+
+
+def test_adjoint_matches_oracle(ctx):
+    p, theta = synth.log_permeability_problem(24, seed=4)
+    s = assemble(ctx, p)
+    b = synth.rhs(p.mesh, 5)
+    x, _ = s.solve(torch.as_tensor(b, device="cuda"), rtol=1e-12)
+    target = 0.5 * torch.as_tensor(synth.rhs(p.mesh, 6), device="cuda") * 1e3
+    g = 2 * (x - target)
+    nt = p.mesh.nt
+    dT = torch.zeros(3, nt, dtype=torch.float64, device="cuda")
+    dth = torch.zeros(nt, dtype=torch.float64, device="cuda")
+    lam, st = s.adjoint(x, g, dT=dT, dtheta=dth, rtol=1e-12)
+    A = oracle.assemble_problem(p)
+    lam_o, _ = oracle.pcg(A, g.cpu().numpy(), rtol=1e-13, raise_on_error=False)
+    assert np.linalg.norm(lam.cpu().numpy() - lam_o) / np.linalg.norm(lam_o) < 1e-9
+    T, sigma, isd, nbr = oracle.side_coefficients(p.mesh.xy, p.mesh.tri, p.mesh.dirichlet,
+                                                  p.eps, p.kinv, p.field_loc, oracle.CP2, p.nu,
+                                                  p.dt)
+    dT_o = oracle.side_gradient(nbr, isd, lam_o, x.cpu().numpy())
+    np.testing.assert_allclose(dT.cpu().numpy().T, dT_o, rtol=1e-7,
+                               atol=1e-9 * np.abs(dT_o).max())
+    dth_o = oracle.theta_gradient(p.mesh.xy, p.mesh.tri, nbr, isd, p.eps, theta, p.nu, p.dt, dT_o)
+    np.testing.assert_allclose(dth.cpu().numpy(), dth_o, rtol=1e-7,
+                               atol=1e-9 * np.abs(dth_o).max())
+    s.free()
