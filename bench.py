@@ -34,13 +34,15 @@ import synth  # noqa: E402
 
 METRIC = "PCG cell-iters/s (FP64 Jacobi-PCG to 1e-10, assemble+solve)"
 UNIT = "cell-iters/s"
-# Algorithmic bytes per cell per iteration of the FP64 Jacobi loop on the
-# scaled matrix: k_spmv_dot reads p, 3 values, 3 columns and writes q
-# (8 + 24 + 12 + 8); k_update reads y, p, r, q and writes y, r (32 + 16);
-# k_pupdate reads r, p and writes p (16 + 8); every 8th k_update also reads s
-# (8/8 = 1 per iteration).  Neighbour gathers are counted once.
-BYTES_PER_CELL_ITER_FP64 = 52 + 48 + 24 + 1
-BYTES_PER_CELL_ITER_MIXED = 32 + 24 + 12 + 0.5
+# Algorithmic bytes per cell per iteration of the Jacobi loop on the scaled
+# matrix (neighbour gathers counted once):
+#   FP64, three kernels: k_spmv_dot reads p, 3 values, 3 columns, writes q
+#     (8 + 24 + 12 + 8 = 52); k_cg_b reads r, q, writes r (24); k_cg_c reads
+#     y, p, r, writes y, p (40); every 8th k_cg_b also reads s (+1).
+#   binary32, two kernels: k_cg_a reads r, p_old, y, 3 values, 3 columns and
+#     writes p_new, q, y (4+4+4+12+12 + 4+4+4 = 48); k_cg_b 12; +0.5 for s.
+BYTES_PER_CELL_ITER_FP64 = 52 + 24 + 40 + 1
+BYTES_PER_CELL_ITER_MIXED = 48 + 12 + 0.5
 
 
 def parse():
@@ -54,6 +56,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=0,
                     help="oracle PCG iterations in the CPU sample (0: auto)")
+    ap.add_argument("--profile-iters", type=int, default=0,
+                    help="profiling run: assemble, then FP64 and mixed solves bounded to this "
+                         "many iterations (Jacobi and IC(0)); no timing output")
     return ap.parse_args()
 
 
@@ -216,6 +221,21 @@ def main():
     h2d_bytes = sum(v.numel() * v.element_size() for v in host.values())
     d2h_bytes = nt * 8
 
+    if args.profile_iters:
+        s = ctx.assemble(d["xy"], d["tri"], d["dir"], d["eps"], d["kinv"], cps.PER_VERTEX,
+                         cps.KIND_CP2, p.nu, p.dt)
+        for pc in (cps.PC_JACOBI, cps.PC_IC0):
+            s.set_precond(pc)
+            for prec in (cps.FP64, cps.MIXED):
+                x.zero_()
+                s.solve(d["b"], x=x, rtol=args.rtol, max_iter=args.profile_iters,
+                        precision=prec, check=False)
+        torch.cuda.synchronize()
+        s.free()
+        print(json.dumps({"profile_run": True, "n": args.n, "cells": nt,
+                          "max_iter": args.profile_iters}))
+        return
+
     def step(src, precision=cps.FP64):
         s = ctx.assemble(src["xy"], src["tri"], src["dir"], src["eps"], src["kinv"],
                          cps.PER_VERTEX, cps.KIND_CP2, p.nu, p.dt)
@@ -278,38 +298,40 @@ def main():
         e2e_times.append((e0.elapsed_time(e1) / 1e3, st.iters))
     e2e_value = world * nt * sum(i for _, i in e2e_times) / sum(t for t, _ in e2e_times)
 
-    # ---- iteration roofline: time the solve loop alone (matrix assembled)
+    # ---- solve loop alone (matrix assembled): FP64 vs mixed, Jacobi vs IC(0)
     s = ctx.assemble(d["xy"], d["tri"], d["dir"], d["eps"], d["kinv"], cps.PER_VERTEX,
                      cps.KIND_CP2, p.nu, p.dt)
-    roof = {}
-    mixed = {}
-    for prec, bpc in ((cps.FP64, BYTES_PER_CELL_ITER_FP64), (cps.MIXED, BYTES_PER_CELL_ITER_MIXED)):
-        ts = []
-        for _ in range(2):
-            x.zero_()
-            flush.zero_()
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            _, st = s.solve(d["b"], x=x, rtol=args.rtol, precision=prec)
-            e1.record(stream)
-            e1.synchronize()
-            ts.append((e0.elapsed_time(e1) / 1e3, st))
-        t, st = min(ts, key=lambda v: v[0])
-        if prec == cps.FP64:
-            peak, peak_kind = measured_peaks()
-            achieved = bpc * nt * st.iters / t / 1e9
-            roof = {"bound": "hbm", "kernel": "pcg_iteration_fp64 (k_spmv_dot+k_update+k_pupdate)",
-                    "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "peak_kind": peak_kind,
-                    "bytes_per_cell_iter": bpc, "traffic": None,
-                    "fp64_time_to_rtol_s": t, "fp64_iters": st.iters}
-        else:
-            mixed = {"time_to_rtol_s": t, "iters": st.iters, "refinements": st.refinements,
-                     "rel_res": st.rel_res,
-                     "inner_gbs": bpc * nt * st.iters / t / 1e9}
+    peak, peak_kind = measured_peaks()
+    variants = {}
+    for pc_name, pc in (("jacobi", cps.PC_JACOBI), ("ic0", cps.PC_IC0)):
+        s.set_precond(pc)
+        for prec_name, prec in (("fp64", cps.FP64), ("mixed", cps.MIXED)):
+            ts = []
+            for _ in range(2):
+                x.zero_()
+                flush.zero_()
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                _, st = s.solve(d["b"], x=x, rtol=args.rtol, precision=prec)
+                e1.record(stream)
+                e1.synchronize()
+                ts.append((e0.elapsed_time(e1) / 1e3, st))
+            t, st = min(ts, key=lambda v: v[0])
+            variants[f"{pc_name}_{prec_name}"] = {
+                "time_to_rtol_s": t, "iters": st.iters, "refinements": st.refinements,
+                "rel_res": st.rel_res, "us_per_iter": 1e6 * t / max(st.iters, 1)}
+    tuning = {"fp64": s.tuning(cps.FP64), "mixed": s.tuning(cps.MIXED)}
     s.free()
+    jf = variants["jacobi_fp64"]
+    achieved = BYTES_PER_CELL_ITER_FP64 * nt * jf["iters"] / jf["time_to_rtol_s"] / 1e9
+    roof = {"bound": "hbm", "kernel": "pcg_iteration_fp64 (k_spmv_dot + k_cg_b + k_cg_c, Jacobi)",
+            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_kind": peak_kind, "bytes_per_cell_iter": BYTES_PER_CELL_ITER_FP64,
+            "traffic": None}
+    jm = variants["jacobi_mixed"]
+    jm["inner_gbs"] = BYTES_PER_CELL_ITER_MIXED * nt * jm["iters"] / jm["time_to_rtol_s"] / 1e9
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -322,7 +344,8 @@ def main():
                    "l2": "256 MB buffer written between steps",
                    "parallelism": f"replicas x{world}"},
         "roofline": roof,
-        "mixed_precision": mixed,
+        "solve_variants": variants,
+        "autotuned": tuning,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d_bytes,
                 "d2h_bytes_per_step": d2h_bytes},
         "gpu_launches": launches,

@@ -188,6 +188,15 @@ int cps_adjoint(cps_sys sys, const double* x, const double* g, double* lambda, d
                 double* dtheta, double rtol, int64_t max_iter, cps_stats* stats,
                 void* stream);
 
+/* Launch configuration the autotuner chose for the iteration kernels of one
+ * precision (host outputs of 3 entries each; zeros before the first solve in
+ * that precision): rows per thread per trip of the grid-stride loop, and the
+ * grid in blocks of 256 threads, for the SpMV kernel, the residual update and
+ * (CPS_FP64 only) the direction update.  The tuner times every candidate on
+ * the system's own data at its first solve; systems below 131072 cells keep
+ * the defaults (unroll 2, 8 blocks per SM). */
+int cps_get_tuning(cps_sys sys, int precision, int32_t* unroll, int32_t* grid);
+
 /* y = A x for the assembled matrix (device pointers, FP64). */
 int cps_matvec(cps_sys sys, const double* x, double* y, void* stream);
 

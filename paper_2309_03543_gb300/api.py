@@ -132,6 +132,13 @@ class System:
         return {"nt": nt.value, "n_interior_sides": ne.value, "diag_min": dmin.value,
                 "is_mmatrix": bool(mm.value), "setup_launches": sl.value}
 
+    def tuning(self, precision: int = _cps.FP64) -> dict:
+        """Autotuned (unroll, grid) of the iteration kernels for a precision."""
+        u = (ctypes.c_int32 * 3)()
+        g = (ctypes.c_int32 * 3)()
+        self.ctx.check(self.ctx.lib.cps_get_tuning(self.handle, precision, u, g), "cps_get_tuning")
+        return {"unroll": list(u), "grid": list(g)}
+
     def set_precond(self, precond: int):
         self.ctx.check(self.ctx.lib.cps_set_precond(self.handle, precond,
                                                     _stream(self.ctx.device)), "cps_set_precond")

@@ -136,6 +136,17 @@ int cps_adjoint(cps_sys sys, const double* x, const double* g, double* lambda, d
                              as_stream(stream));
 }
 
+int cps_get_tuning(cps_sys sys, int precision, int32_t* unroll, int32_t* grid) {
+    if (!sys || !unroll || !grid || (precision != CPS_FP64 && precision != CPS_MIXED))
+        return CPS_ERR_ARG;
+    const cps::Tuning& t = sys->tune[precision];
+    for (int k = 0; k < 3; ++k) {
+        unroll[k] = t.done ? t.k[k].unroll : 0;
+        grid[k] = t.done ? t.k[k].grid : 0;
+    }
+    return CPS_OK;
+}
+
 int cps_matvec(cps_sys sys, const double* x, double* y, void* stream) {
     if (!sys) return CPS_ERR_ARG;
     int rc = set_device(sys->ctx);

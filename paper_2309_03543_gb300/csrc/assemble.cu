@@ -339,9 +339,11 @@ static int dev_alloc(cps_ctx ctx, T** p, size_t n) {
 
 void free_sys(cps_sys s) {
     if (!s) return;
-    void* bufs[] = {s->s, s->diag, s->a, s->col, s->a32, s->s32, s->gfac, s->dxi, s->slot_kind,
-                    s->perm, s->iperm, s->pa, s->pcol, s->pdinv, s->pa32, s->pdinv32, s->ps,
-                    s->ps32, s->wy, s->wr, s->wp, s->wq, s->wz, s->wb, s->partials, s->st};
+    void* bufs[] = {s->s,     s->diag,  s->a,     s->col,   s->a32,     s->s32,      s->gfac,
+                    s->dxi,   s->slot_kind, s->perm, s->iperm, s->pa,  s->pcol,     s->pl,
+                    s->pdinv, s->ps,    s->pa32,  s->pl32,  s->pdinv32, s->ps32,     s->wy,
+                    s->wr,    s->wp0,   s->wp1,   s->wq,    s->wz,      s->wb,       s->wx,
+                    s->partials, s->st};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (s->hst) cudaFreeHost(s->hst);
@@ -400,11 +402,13 @@ int assemble_impl(cps_ctx ctx, const double* xy, int64_t nv, const int32_t* tri,
     TRY_ALLOC(s->slot_kind, 3 * nt);
     TRY_ALLOC(s->wy, nt);
     TRY_ALLOC(s->wr, nt);
-    TRY_ALLOC(s->wp, nt);
+    TRY_ALLOC(s->wp0, nt);
+    TRY_ALLOC(s->wp1, nt);
     TRY_ALLOC(s->wq, nt);
     TRY_ALLOC(s->wz, nt);
     TRY_ALLOC(s->wb, nt);
-    TRY_ALLOC(s->partials, kNumPartials * kMaxGrid);
+    TRY_ALLOC(s->wx, nt);
+    TRY_ALLOC(s->partials, (kNumPartials + 16) * kMaxGrid);
     TRY_ALLOC(s->st, 2);
     if (field_loc == CPS_PER_CELL && kind == CPS_KIND_CP2) {
         TRY_ALLOC(s->gfac, 3 * nt);

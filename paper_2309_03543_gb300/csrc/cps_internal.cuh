@@ -37,6 +37,21 @@ struct CgState {
     int pad[4];
 };
 
+// Launch configuration of one iteration kernel: rows per thread per trip of
+// the grid-stride loop, and grid size (blocks of kBlock threads).
+struct KCfg {
+    int unroll = 2;
+    int grid = 0;
+};
+
+// Autotuned configurations of the iteration kernels of one precision:
+// k[0] SpMV (FP64) or fused SpMV (binary32), k[1] residual update, k[2]
+// direction update (FP64 only).
+struct Tuning {
+    KCfg k[3];
+    bool done = false;
+};
+
 // Device error flag written by the assembly kernels (first error wins).
 __device__ __forceinline__ void set_error(int* err, int code) {
     atomicCAS(err, 0, code);
@@ -145,27 +160,31 @@ struct cps_sys_s {
     double* dxi = nullptr;      // [nt]
     int32_t* slot_kind = nullptr;   // [3*nt] 0 no-flux, 1 interior, 2 Dirichlet
 
-    // IC(0) in colour order (scaled matrix, unit diagonal).
+    // IC(0) in colour order (scaled matrix, unit diagonal), set up on demand.
     int ncolours = 0;
     int64_t colour_start[17] = {0};
-    int32_t* perm = nullptr;    // [nt] new -> old
-    int32_t* iperm = nullptr;   // [nt] old -> new
+    int32_t* perm = nullptr;    // [nt] colour order -> mesh order
+    int32_t* iperm = nullptr;   // [nt] mesh order -> colour order
     double* pa = nullptr;       // [3*nt] permuted scaled off-diagonals
     int32_t* pcol = nullptr;    // [3*nt] permuted columns
-    double* pdinv = nullptr;    // [nt] inverse IC(0) pivots (permuted order)
+    double* pl = nullptr;       // [3*nt] IC(0) factor entries per slot
+    double* pdinv = nullptr;    // [nt] inverse IC(0) pivots
+    double* ps = nullptr;       // [nt] s in colour order
     float* pa32 = nullptr;
+    float* pl32 = nullptr;
     float* pdinv32 = nullptr;
-    double* ps = nullptr;       // [nt] s in permuted order
     float* ps32 = nullptr;
 
     // PCG workspace (allocated at assembly so that solves never allocate).
     double* wy = nullptr;       // [nt] iterate (scaled)
     double* wr = nullptr;       // [nt] residual
-    double* wp = nullptr;       // [nt] search direction
+    double* wp0 = nullptr;      // [nt] search direction, even iterations
+    double* wp1 = nullptr;      // [nt] search direction, odd iterations
     double* wq = nullptr;       // [nt] A p
     double* wz = nullptr;       // [nt] preconditioned residual (IC0)
-    double* wb = nullptr;       // [nt] permuted right-hand side / staging
-    double* partials = nullptr; // [kNumPartials * kMaxGrid]
+    double* wb = nullptr;       // [nt] right-hand side in colour order
+    double* wx = nullptr;       // [nt] FP64 iterate in colour order
+    double* partials = nullptr; // [(kNumPartials + 16) * kMaxGrid]
     cps::CgState* st = nullptr; // device state
     cps::CgState* hst = nullptr;  // pinned host mirror (2 slots)
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -173,8 +192,9 @@ struct cps_sys_s {
 
     // CUDA graphs of a chunk of iterations, per (precision, preconditioner).
     cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t graph[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
-    int chunk = 0;
+    cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    int64_t graph_nodes[2][2] = {{0, 0}, {0, 0}};
+    cps::Tuning tune[2];        // per precision (CPS_FP64, CPS_MIXED)
 };
 
 #define CPS_CUDA_TRY(ctx, call)                                                        \

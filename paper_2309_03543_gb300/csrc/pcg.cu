@@ -1,21 +1,22 @@
 // Preconditioned conjugate gradients on the device (Sec. 3.2.2: the
 // corrector systems are solved by PCG; the matrix is assembled and factored
-// once and reused for every right-hand side).
+// once and reused for every right-hand side, Sec. 3.1).
 //
-// Jacobi-PCG on A is run as plain CG on the symmetrically scaled matrix
+// Jacobi-PCG on A runs as plain CG on the symmetrically scaled matrix
 // Ahat = S^-1 A S^-1 (S = diag(sqrt(a_ee)), unit diagonal): with yhat = S x
-// and bhat = S^-1 b its iterates are exactly those of Jacobi-PCG on A, but the
-// diagonal and its inverse are never read inside the loop.  One iteration is
-//   k_spmv_dot : q = Ahat p,  gamma = p.q  (last block: alpha = rho/gamma)
-//   k_update   : y += alpha p, r -= alpha q, rho' = r.r (and ||S r||^2 every
-//                few iterations for the stop test; last block: beta, stop)
-//   k_pupdate  : p = r + beta p
-// All scalars live in device memory; the host only polls a stop flag once per
-// chunk of iterations, which are replayed from a CUDA graph.
+// and bhat = S^-1 b its iterates are those of Jacobi-PCG on A, and the
+// diagonal is never read inside the loop.  IC(0) runs in a colour order
+// (precond.cu) on the same scaled matrix.  The kernels are in
+// pcg_kernels.cuh; the scalars of the iteration never leave the device, and
+// the host polls a stop flag once per chunk of iterations replayed from a
+// CUDA graph.
 //
-// Mixed precision (CPS_MIXED): FP64 outer iterative refinement
-//   r = b - A x (FP64), inner CG on Ahat d = S^-1 r with binary32 matrix,
-//   vectors and SpMV, FP64 dot products and alpha/beta, x += S^-1 d (FP64).
+// Mixed precision (CPS_MIXED): binary32 matrix, vectors and SpMV in the
+// iteration, FP64 dot products and alpha/beta.  The binary32 recursion's
+// residual is replaced by the true FP64 residual r = b - A x each time it has
+// dropped by a factor kDelta (reliable updates: the correction is folded into
+// the FP64 iterate x and the search direction is kept), until
+// ||b - A x||_2 <= rtol ||b||_2 holds in FP64.
 #include "cps_internal.cuh"
 #include "pcg_kernels.cuh"
 
@@ -24,12 +25,12 @@
 namespace cps {
 
 namespace {
-// Iterations per graph chunk and the stop-test period inside a chunk.
-constexpr int kChunk = 32;
-constexpr int kCheckEvery = 8;
-// Inner residual reduction per refinement step of the mixed solver.
-constexpr double kInnerEta = 1e-2;
-constexpr int kMaxRefinements = 100;
+constexpr int kChunk = 32;          // iterations per graph replay
+constexpr int kCheckEvery = 8;      // stop test period inside a chunk
+constexpr double kDelta = 0.5;      // residual drop between reliable updates
+constexpr int kMaxUpdates = 2000;
+constexpr int64_t kTuneMinRows = 1 << 17;   // smaller systems keep the defaults
+constexpr int kTuneReps = 5;
 }  // namespace
 
 static int ensure_capture_stream(cps_sys s) {
@@ -43,40 +44,231 @@ static int ensure_capture_stream(cps_sys s) {
     return CPS_OK;
 }
 
-// Vector views of one CG run in working precision V.
+// Operands of one CG run in working precision V, in solve order.
 template <typename V>
-struct CgVecs {
+struct Run {
     const V* a;
     const int32_t* col;
-    const V* s;        // scale, for the unscaled residual norm
+    const V* s;
+    const V* l;        // IC(0) factor (null: Jacobi)
+    const V* dinv;
     V* y;
     V* r;
-    V* p;
+    V* p0;
+    V* p1;
     V* q;
+    V* z;              // == r for Jacobi
     int64_t n;
 };
 
 template <typename V>
-static void enqueue_iteration(cps_sys s, const CgVecs<V>& v, bool norm, cudaStream_t st) {
-    const int g = s->grid;
-    k_spmv_dot<V><<<g, kBlock, 0, st>>>(v.a, v.col, v.p, v.q, v.n, s->partials, s->st);
-    if (norm)
-        k_update<V, true><<<g, kBlock, 0, st>>>(v.y, v.r, v.p, v.q, v.s, v.n, s->partials, s->st);
-    else
-        k_update<V, false><<<g, kBlock, 0, st>>>(v.y, v.r, v.p, v.q, v.s, v.n, s->partials, s->st);
-    k_pupdate<V><<<g, kBlock, 0, st>>>(v.p, v.r, v.n, s->st);
+static Run<V> make_run(cps_sys s);
+
+template <>
+Run<double> make_run<double>(cps_sys s) {
+    const bool ic0 = s->precond == CPS_PC_IC0;
+    Run<double> v{};
+    v.a = ic0 ? s->pa : s->a;
+    v.col = ic0 ? s->pcol : s->col;
+    v.s = ic0 ? s->ps : s->s;
+    v.l = ic0 ? s->pl : nullptr;
+    v.dinv = ic0 ? s->pdinv : nullptr;
+    v.y = s->wy;
+    v.r = s->wr;
+    v.p0 = s->wp0;
+    v.p1 = s->wp1;
+    v.q = s->wq;
+    v.z = ic0 ? s->wz : s->wr;
+    v.n = s->nt;
+    return v;
+}
+
+// binary32 vectors reuse the first half of the FP64 work buffers.
+template <>
+Run<float> make_run<float>(cps_sys s) {
+    const bool ic0 = s->precond == CPS_PC_IC0;
+    Run<float> v{};
+    v.a = ic0 ? s->pa32 : s->a32;
+    v.col = ic0 ? s->pcol : s->col;
+    v.s = ic0 ? s->ps32 : s->s32;
+    v.l = ic0 ? s->pl32 : nullptr;
+    v.dinv = ic0 ? s->pdinv32 : nullptr;
+    v.y = reinterpret_cast<float*>(s->wy);
+    v.r = reinterpret_cast<float*>(s->wr);
+    v.p0 = reinterpret_cast<float*>(s->wp0);
+    v.p1 = reinterpret_cast<float*>(s->wp1);
+    v.q = reinterpret_cast<float*>(s->wq);
+    v.z = ic0 ? reinterpret_cast<float*>(s->wz) : v.r;
+    v.n = s->nt;
+    return v;
+}
+
+
+// ------------------------------------------------------------ launch configs
+// Each streaming kernel of the iteration runs with a (rows-per-thread
+// unroll U, grid) pair picked by the autotuner below.
+
+template <typename V>
+static void launch_a(const KCfg& c, const Run<V>& v, cps_sys s, cudaStream_t st);
+
+template <>
+void launch_a<double>(const KCfg& c, const Run<double>& v, cps_sys s, cudaStream_t st) {
+    switch (c.unroll) {
+        case 1: k_spmv_dot<double, 1><<<c.grid, kBlock, 0, st>>>(v.a, v.col, v.p0, v.q, v.n, s->partials, s->st); break;
+        case 4: k_spmv_dot<double, 4><<<c.grid, kBlock, 0, st>>>(v.a, v.col, v.p0, v.q, v.n, s->partials, s->st); break;
+        default: k_spmv_dot<double, 2><<<c.grid, kBlock, 0, st>>>(v.a, v.col, v.p0, v.q, v.n, s->partials, s->st); break;
+    }
+}
+
+template <>
+void launch_a<float>(const KCfg& c, const Run<float>& v, cps_sys s, cudaStream_t st) {
+    switch (c.unroll) {
+        case 1: k_cg_a<float, 1><<<c.grid, kBlock, 0, st>>>(v.a, v.col, v.z, v.p0, v.p1, v.y, v.q, v.n, s->partials, s->st); break;
+        case 4: k_cg_a<float, 4><<<c.grid, kBlock, 0, st>>>(v.a, v.col, v.z, v.p0, v.p1, v.y, v.q, v.n, s->partials, s->st); break;
+        default: k_cg_a<float, 2><<<c.grid, kBlock, 0, st>>>(v.a, v.col, v.z, v.p0, v.p1, v.y, v.q, v.n, s->partials, s->st); break;
+    }
+}
+
+template <typename V, bool NORM, bool JACOBI>
+static void launch_b_u(const KCfg& c, const Run<V>& v, cps_sys s, cudaStream_t st) {
+    switch (c.unroll) {
+        case 1: k_cg_b<V, NORM, JACOBI, 1><<<c.grid, kBlock, 0, st>>>(v.r, v.q, v.s, v.n, s->partials, s->st); break;
+        case 4: k_cg_b<V, NORM, JACOBI, 4><<<c.grid, kBlock, 0, st>>>(v.r, v.q, v.s, v.n, s->partials, s->st); break;
+        default: k_cg_b<V, NORM, JACOBI, 2><<<c.grid, kBlock, 0, st>>>(v.r, v.q, v.s, v.n, s->partials, s->st); break;
+    }
 }
 
 template <typename V>
-static int get_chunk_graph(cps_sys s, int prec, const CgVecs<V>& v, cudaGraphExec_t* out) {
-    cudaGraphExec_t& ge = s->graph[prec][0];
+static void launch_b(const KCfg& c, const Run<V>& v, bool norm, cps_sys s, cudaStream_t st) {
+    const bool jac = v.l == nullptr;
+    if (norm && jac) launch_b_u<V, true, true>(c, v, s, st);
+    else if (norm) launch_b_u<V, true, false>(c, v, s, st);
+    else if (jac) launch_b_u<V, false, true>(c, v, s, st);
+    else launch_b_u<V, false, false>(c, v, s, st);
+}
+
+static void launch_c(const KCfg& c, const Run<double>& v, cps_sys s, cudaStream_t st) {
+    switch (c.unroll) {
+        case 1: k_cg_c<double, 1><<<c.grid, kBlock, 0, st>>>(v.y, v.p0, v.z, v.n, s->st); break;
+        case 4: k_cg_c<double, 4><<<c.grid, kBlock, 0, st>>>(v.y, v.p0, v.z, v.n, s->st); break;
+        default: k_cg_c<double, 2><<<c.grid, kBlock, 0, st>>>(v.y, v.p0, v.z, v.n, s->st); break;
+    }
+}
+
+static Tuning default_tuning(cps_sys s) {
+    Tuning t;
+    for (auto& k : t.k) {
+        k.unroll = 2;
+        k.grid = grid_for(s->ctx, s->nt);
+    }
+    return t;
+}
+
+// Times every (unroll, grid) candidate of each iteration kernel on the
+// system's own data and keeps the fastest.  The vectors are scratch here:
+// the caller starts the run afresh afterwards.
+template <typename V>
+static int autotune(cps_sys s, int prec, const Run<V>& v, cudaStream_t stream) {
+    Tuning& t = s->tune[prec];
+    t = default_tuning(s);
+    t.done = true;
+    if (s->nt < kTuneMinRows) return CPS_OK;
+    cudaEvent_t e0, e1;
+    CPS_CUDA_TRY(s->ctx, cudaEventCreate(&e0));
+    CPS_CUDA_TRY(s->ctx, cudaEventCreate(&e1));
+    const int unrolls[3] = {1, 2, 4};
+    const int per_sm[3] = {4, 8, 16};
+    const int nk = sizeof(V) == 8 ? 3 : 2;
+    int rc = CPS_OK;
+    for (int kind = 0; kind < nk && rc == CPS_OK; ++kind) {
+        float best = 1e30f;
+        for (int ui = 0; ui < 3; ++ui)
+            for (int gi = 0; gi < 3; ++gi) {
+                KCfg c{unrolls[ui], grid_for(s->ctx, s->nt, per_sm[gi])};
+                auto once = [&]() {
+                    if (kind == 0) {
+                        launch_a<V>(c, v, s, stream);
+                    } else if (kind == 1) {
+                        launch_b<V>(c, v, false, s, stream);
+                    } else if constexpr (sizeof(V) == 8) {
+                        launch_c(c, v, s, stream);
+                    }
+                };
+                k_tune_prime<<<1, 1, 0, stream>>>(s->st);
+                once();
+                cudaEventRecord(e0, stream);
+                for (int r = 0; r < kTuneReps; ++r) {
+                    k_tune_prime<<<1, 1, 0, stream>>>(s->st);
+                    once();
+                }
+                cudaEventRecord(e1, stream);
+                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                    rc = CPS_ERR_CUDA;
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) {
+                    best = ms;
+                    t.k[kind] = c;
+                }
+            }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (cudaGetLastError() != cudaSuccess) rc = CPS_ERR_CUDA;
+    if (rc) s->ctx->last_error = "autotune: kernel launch failed";
+    return rc;
+}
+
+// z = M^-1 r with the IC(0) colour sweeps; also rho = r.z and beta.
+template <typename V>
+static int64_t enqueue_precond(cps_sys s, const Run<V>& v, cudaStream_t st) {
+    const int C = s->ncolours;
+    const int64_t* cs = s->colour_start;
+    const int g = s->grid;
+    int64_t launches = 0;
+    for (int c = 1; c < C; ++c, ++launches)
+        k_ic0_fwd<V><<<g, kBlock, 0, st>>>(v.l, v.col, v.dinv, v.r, v.z, v.n, cs[c], cs[c + 1],
+                                           cs[1], c == C - 1 ? 1 : 0, c, s->partials, s->st);
+    for (int c = C - 2; c >= 0; --c, ++launches)
+        k_ic0_bwd<V><<<g, kBlock, 0, st>>>(v.l, v.col, v.dinv, v.r, v.z, v.n, cs[c], cs[c + 1],
+                                           C, c, s->partials, s->st);
+    if (C == 1) {
+        k_ic0_bwd<V><<<g, kBlock, 0, st>>>(v.l, v.col, v.dinv, v.r, v.z, v.n, cs[0], cs[1], C, 0,
+                                           s->partials, s->st);
+        ++launches;
+    }
+    return launches;
+}
+
+template <typename V>
+static int64_t enqueue_iteration(cps_sys s, const Run<V>& v, int prec, bool norm, cudaStream_t st) {
+    const Tuning& t = s->tune[prec];
+    int64_t nl = 2;
+    launch_a<V>(t.k[0], v, s, st);
+    launch_b<V>(t.k[1], v, norm, s, st);
+    if (v.l) nl += enqueue_precond<V>(s, v, st);
+    if constexpr (sizeof(V) == 8) {
+        launch_c(t.k[2], v, s, st);
+        ++nl;
+    }
+    return nl;
+}
+
+template <typename V>
+static int get_chunk_graph(cps_sys s, int prec, const Run<V>& v, cudaGraphExec_t* out,
+                           int64_t* per_chunk) {
+    const int pc = v.l ? 1 : 0;
+    cudaGraphExec_t& ge = s->graph[prec][pc];
+    int64_t nl = 0;
     if (!ge) {
         int rc = ensure_capture_stream(s);
         if (rc) return rc;
         cudaGraph_t graph = nullptr;
         CPS_CUDA_TRY(s->ctx, cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
         for (int k = 0; k < kChunk; ++k)
-            enqueue_iteration<V>(s, v, (k % kCheckEvery) == kCheckEvery - 1, s->cap_stream);
+            nl += enqueue_iteration<V>(s, v, prec, (k % kCheckEvery) == kCheckEvery - 1, s->cap_stream);
         cudaError_t le = cudaGetLastError();
         cudaError_t ce = cudaStreamEndCapture(s->cap_stream, &graph);
         if (le != cudaSuccess || ce != cudaSuccess) {
@@ -92,7 +284,9 @@ static int get_chunk_graph(cps_sys s, int prec, const CgVecs<V>& v, cudaGraphExe
             s->ctx->last_error = std::string("graph instantiate: ") + cudaGetErrorString(ie);
             return CPS_ERR_CUDA;
         }
+        s->graph_nodes[prec][pc] = nl;
     }
+    *per_chunk = s->graph_nodes[prec][pc];
     *out = ge;
     return CPS_OK;
 }
@@ -101,15 +295,16 @@ static int get_chunk_graph(cps_sys s, int prec, const CgVecs<V>& v, cudaGraphExe
 // look-ahead keeps the GPU busy while the host reads the previous flag; a
 // chunk enqueued after the stop returns at once in every kernel.
 template <typename V>
-static int run_chunks(cps_sys s, int prec, const CgVecs<V>& v, cudaStream_t stream,
+static int run_chunks(cps_sys s, int prec, const Run<V>& v, cudaStream_t stream,
                       CgState* final_state, int64_t* launches) {
     cudaGraphExec_t ge = nullptr;
-    int rc = get_chunk_graph<V>(s, prec, v, &ge);
+    int64_t per_chunk = 0;
+    int rc = get_chunk_graph<V>(s, prec, v, &ge, &per_chunk);
     if (rc) return rc;
     for (long long k = 0;; ++k) {
         const int slot = (int)(k & 1);
         CPS_CUDA_TRY(s->ctx, cudaGraphLaunch(ge, stream));
-        *launches += 3 * kChunk;
+        *launches += per_chunk;
         CPS_CUDA_TRY(s->ctx, cudaMemcpyAsync(&s->hst[slot], s->st, sizeof(CgState),
                                              cudaMemcpyDeviceToHost, stream));
         CPS_CUDA_TRY(s->ctx, cudaEventRecord(s->ev[slot], stream));
@@ -134,23 +329,51 @@ static int read_state(cps_sys s, cudaStream_t stream, CgState* h) {
     return CPS_OK;
 }
 
+static void fill_stats(cps_stats* stats, int64_t iters, double rel, int status, int refinements,
+                       int64_t launches) {
+    if (!stats) return;
+    stats->iters = iters;
+    stats->rel_res = rel;
+    stats->status = status;
+    stats->refinements = refinements;
+    stats->launches = launches;
+}
+
 // ------------------------------------------------------------------ FP64
 
 static int solve_fp64(cps_sys s, const double* b, double* x, double rtol, int64_t max_iter,
                       cps_stats* stats, cudaStream_t stream) {
     const int64_t n = s->nt;
     const int g = s->grid;
-    CgVecs<double> v{s->a, s->col, s->s, s->wy, s->wr, s->wp, s->wq, n};
+    const bool ic0 = s->precond == CPS_PC_IC0;
+    const Run<double> v = make_run<double>(s);
+    const double* bb = b;
+    double* xx = x;
     int64_t total = 0, launches = 0;
+    if (!s->tune[CPS_FP64].done) {
+        int rc = autotune<double>(s, CPS_FP64, v, stream);
+        if (rc) return rc;
+    }
+    if (ic0) {
+        k_permute_in<<<g, kBlock, 0, stream>>>(b, x, s->perm, n, s->wb, s->wx);
+        ++launches;
+        bb = s->wb;
+        xx = s->wx;
+    }
     CgState h{};
     int status = CPS_OK;
     // A restart recomputes r = b - A x when the recursively updated residual
     // has met rtol but the true residual has not (rounding drift).
     for (int restart = 0; restart < 8; ++restart) {
         const long long budget = (long long)(max_iter - total);
-        k_init64<<<g, kBlock, 0, stream>>>(b, x, v.s, v.a, v.col, n, v.y, v.r, v.p, rtol, budget,
-                                            s->partials, s->st);
+        k_init64<<<g, kBlock, 0, stream>>>(bb, xx, v.s, v.a, v.col, n, v.y, v.r, v.p0, rtol,
+                                            budget, ic0 ? 0 : 1, s->partials, s->st);
         ++launches;
+        if (ic0) {
+            launches += enqueue_precond<double>(s, v, stream);
+            k_copy<double><<<g, kBlock, 0, stream>>>(v.p0, v.z, n);
+            ++launches;
+        }
         CPS_CUDA_TRY(s->ctx, cudaGetLastError());
         int rc = read_state(s, stream, &h);
         if (rc) return rc;
@@ -160,22 +383,22 @@ static int solve_fp64(cps_sys s, const double* b, double* x, double rtol, int64_
         }
         total += h.iter;
         status = h.status;
-        k_final64<<<g, kBlock, 0, stream>>>(b, v.y, v.s, v.a, v.col, n, x, s->partials, s->st);
+        k_final64<<<g, kBlock, 0, stream>>>(bb, v.y, v.s, v.a, v.col, n, xx, s->partials, s->st);
         ++launches;
         CPS_CUDA_TRY(s->ctx, cudaGetLastError());
         rc = read_state(s, stream, &h);
         if (rc) return rc;
         if (status != CPS_OK || h.rnorm2 <= h.thresh2 || total >= max_iter) break;
     }
+    if (ic0) {
+        k_permute_out<<<g, kBlock, 0, stream>>>(s->wx, s->perm, n, x);
+        ++launches;
+        CPS_CUDA_TRY(s->ctx, cudaGetLastError());
+        CPS_CUDA_TRY(s->ctx, cudaStreamSynchronize(stream));
+    }
     const double rel = h.bnorm2 > 0 ? std::sqrt(h.rnorm2 / h.bnorm2) : 0.0;
     if (status == CPS_OK && h.bnorm2 > 0 && !(rel <= rtol)) status = CPS_ERR_NOT_CONVERGED;
-    if (stats) {
-        stats->iters = total;
-        stats->rel_res = rel;
-        stats->status = status;
-        stats->refinements = 1;
-        stats->launches = launches;
-    }
+    fill_stats(stats, total, rel, status, 1, launches);
     if (status == CPS_ERR_NOT_SPD) s->ctx->last_error = "solve: p.Ap <= 0 (matrix not SPD or NaN input)";
     if (status == CPS_ERR_NOT_CONVERGED) s->ctx->last_error = "solve: max_iter reached";
     return status;
@@ -187,56 +410,86 @@ static int solve_mixed(cps_sys s, const double* b, double* x, double rtol, int64
                        cps_stats* stats, cudaStream_t stream) {
     const int64_t n = s->nt;
     const int g = s->grid;
-    // binary32 vectors reuse the first half of the FP64 work buffers.
-    float* d32 = reinterpret_cast<float*>(s->wy);
-    float* r32 = reinterpret_cast<float*>(s->wr);
-    float* p32 = reinterpret_cast<float*>(s->wp);
-    float* q32 = reinterpret_cast<float*>(s->wq);
-    CgVecs<float> v{s->a32, s->col, s->s32, d32, r32, p32, q32, n};
-    int64_t total = 0, launches = 0;
-    int refinements = 0;
+    const bool ic0 = s->precond == CPS_PC_IC0;
+    const Run<float> v = make_run<float>(s);
+    if (!s->tune[CPS_MIXED].done) {
+        int rc = autotune<float>(s, CPS_MIXED, v, stream);
+        if (rc) return rc;
+    }
+    const double* A64 = ic0 ? s->pa : s->a;
+    const double* S64 = ic0 ? s->ps : s->s;
+    const double* bb = b;
+    double* xx = x;
+    int64_t launches = 0;
+    if (ic0) {
+        k_permute_in<<<g, kBlock, 0, stream>>>(b, x, s->perm, n, s->wb, s->wx);
+        ++launches;
+        bb = s->wb;
+        xx = s->wx;
+    }
+    int64_t base = 0;          // iterations of runs before the last restart
+    int updates = 0, stall = 0, restarts = 0;
+    double prev = INFINITY;
+    int first = 1;
     CgState h{};
     int status = CPS_OK;
     for (;;) {
-        k_res64<<<g, kBlock, 0, stream>>>(b, x, s->s, s->a, s->col, n, r32, p32, d32, rtol,
-                                          kInnerEta, (long long)(max_iter - total), s->partials,
-                                          s->st);
+        const long long budget = (long long)(max_iter - base - (first ? 0 : h.iter));
+        k_res64<<<g, kBlock, 0, stream>>>(bb, xx, S64, A64, v.col, n, v.r, v.p0, v.y, rtol, kDelta,
+                                          budget, first, ic0 ? 0 : 1, s->partials, s->st);
         ++launches;
+        if (ic0) launches += enqueue_precond<float>(s, v, stream);
         CPS_CUDA_TRY(s->ctx, cudaGetLastError());
         int rc = read_state(s, stream, &h);
         if (rc) return rc;
         if (h.bnorm2 == 0.0 || h.rnorm2 <= rtol * rtol * h.bnorm2) break;   // converged
-        if (total >= max_iter || refinements >= kMaxRefinements) {
+        if (base + h.iter >= max_iter || updates >= kMaxUpdates) {
             status = CPS_ERR_NOT_CONVERGED;
             break;
         }
-        ++refinements;
+        // A replaced residual that stops falling (no 10% gain over 8
+        // replacements): restart the search directions.
+        if (h.rnorm2 < 0.81 * prev) {
+            prev = h.rnorm2;
+            stall = 0;
+        } else {
+            ++stall;
+        }
+        if (stall >= 8 && !first) {
+            if (++restarts > 4) {
+                status = CPS_ERR_NOT_CONVERGED;
+                break;
+            }
+            base += h.iter;
+            first = 1;
+            stall = 0;
+            continue;
+        }
+        first = 0;
+        ++updates;
         if (!h.done) {
             rc = run_chunks<float>(s, CPS_MIXED, v, stream, &h, &launches);
             if (rc) return rc;
         }
-        total += h.iter;
         if (h.status != CPS_OK) {
             status = h.status;
             break;
         }
-        k_correct<<<g, kBlock, 0, stream>>>(x, d32, s->s, n);
+        k_flush_y<float><<<g, kBlock, 0, stream>>>(v.y, v.p0, v.p1, n, s->st);
+        k_correct<<<g, kBlock, 0, stream>>>(xx, v.y, S64, n);
+        launches += 2;
+    }
+    if (ic0) {
+        k_permute_out<<<g, kBlock, 0, stream>>>(s->wx, s->perm, n, x);
         ++launches;
     }
-    if (h.bnorm2 == 0.0) {
-        CPS_CUDA_TRY(s->ctx, cudaMemsetAsync(x, 0, sizeof(double) * n, stream));
-    }
+    if (h.bnorm2 == 0.0) CPS_CUDA_TRY(s->ctx, cudaMemsetAsync(x, 0, sizeof(double) * n, stream));
+    CPS_CUDA_TRY(s->ctx, cudaGetLastError());
     CPS_CUDA_TRY(s->ctx, cudaStreamSynchronize(stream));
     const double rel = h.bnorm2 > 0 ? std::sqrt(h.rnorm2 / h.bnorm2) : 0.0;
-    if (stats) {
-        stats->iters = total;
-        stats->rel_res = rel;
-        stats->status = status;
-        stats->refinements = refinements;
-        stats->launches = launches;
-    }
-    if (status == CPS_ERR_NOT_CONVERGED) s->ctx->last_error = "solve: refinement did not reach rtol";
-    if (status == CPS_ERR_NOT_SPD) s->ctx->last_error = "solve: p.Ap <= 0 in the inner solve";
+    fill_stats(stats, base + h.iter, rel, status, updates, launches);
+    if (status == CPS_ERR_NOT_CONVERGED) s->ctx->last_error = "solve: mixed precision did not reach rtol";
+    if (status == CPS_ERR_NOT_SPD) s->ctx->last_error = "solve: p.Ap <= 0 in the binary32 iteration";
     return status;
 }
 
@@ -246,22 +499,9 @@ int solve_impl(cps_sys s, const double* b, double* x, double rtol, int64_t max_i
         s->ctx->last_error = "solve: bad argument";
         return CPS_ERR_ARG;
     }
-    if (s->precond != CPS_PC_JACOBI) {
-        s->ctx->last_error = "solve: preconditioner not available";
-        return CPS_ERR_ARG;
-    }
     if (precision == CPS_FP64) return solve_fp64(s, b, x, rtol, max_iter, stats, stream);
     if (precision == CPS_MIXED) return solve_mixed(s, b, x, rtol, max_iter, stats, stream);
     s->ctx->last_error = "solve: bad precision";
-    return CPS_ERR_ARG;
-}
-
-int precond_impl(cps_sys s, int precond, cudaStream_t) {
-    if (precond == CPS_PC_JACOBI) {
-        s->precond = precond;
-        return CPS_OK;
-    }
-    s->ctx->last_error = "set_precond: unknown preconditioner";
     return CPS_ERR_ARG;
 }
 

@@ -1,7 +1,22 @@
-// Kernels of the conjugate-gradient solve.  All vectors of one run are in the
-// symmetrically scaled space (yhat = S x, rhat = S^-1 r); matrix rows are
-// padded ELL with 3 off-diagonal slots, slot-major (entry j*n + e), and a
-// unit diagonal.  Every reduction is deterministic (fixed grid, fixed order).
+// Kernels of the conjugate-gradient solve.
+//
+// All vectors of a run live in the symmetrically scaled space (yhat = S x,
+// rhat = S^-1 r, S = diag(sqrt(a_ee))); matrix rows are padded ELL with three
+// off-diagonal slots, slot-major (entry j*n + e), and a unit diagonal.  Every
+// reduction is deterministic (fixed grid, fixed summation order).
+//
+// One iteration k of (P)CG is two fused streaming kernels:
+//   k_cg_a: y += alpha_{k-1} p_{k-1}           (x update, one iteration late)
+//           p_k = z_k + beta_{k-1} p_{k-1}      (own row and, recomputed
+//                                                bit-identically, the three
+//                                                neighbours' rows)
+//           q = Ahat p_k, gamma = p_k . q;      last block: alpha_k = rho/gamma
+//   k_cg_b: r -= alpha_k q; Jacobi: rho' = r.r, beta_k = rho'/rho; every
+//           few iterations also ||S r||^2 and the stop test.
+// The search direction alternates between two buffers chosen by the parity
+// of the device iteration counter, so the same captured graph serves any
+// starting iteration.  With IC(0) the preconditioner kernels (ic0 sweeps)
+// run between k_cg_b and the next k_cg_a and produce z, rho and beta.
 #pragma once
 
 #include "cps_internal.cuh"
@@ -11,60 +26,166 @@ namespace cps {
 #define CPS_GRID_STRIDE(i, n) \
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
-// q = Ahat p, gamma = p.q; last block: alpha = rho / gamma.
-template <typename V>
+// Unrolled grid-stride loop: each thread takes U rows per trip, spaced one
+// grid apart (every access stays coalesced), so that the loads of U rows are
+// in flight together.  body(e, u) is called for the U rows of a trip after
+// load(e, u) has been called for all of them; the tail runs one row a trip.
+#define CPS_UNROLLED_LOOP(n, U, LOAD, BODY)                                            \
+    {                                                                                  \
+        const int64_t stride_ = (int64_t)gridDim.x * blockDim.x;                       \
+        int64_t e0_ = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;                  \
+        for (; e0_ + (U - 1) * stride_ < (n); e0_ += U * stride_) {                    \
+            _Pragma("unroll") for (int u = 0; u < U; ++u) {                            \
+                const int64_t e = e0_ + u * stride_;                                   \
+                LOAD;                                                                  \
+            }                                                                          \
+            _Pragma("unroll") for (int u = 0; u < U; ++u) {                            \
+                const int64_t e = e0_ + u * stride_;                                   \
+                BODY;                                                                  \
+            }                                                                          \
+        }                                                                              \
+        for (; e0_ < (n); e0_ += stride_) {                                            \
+            const int u = 0;                                                           \
+            const int64_t e = e0_;                                                     \
+            LOAD;                                                                      \
+            BODY;                                                                      \
+        }                                                                              \
+    }
+
+// Stop protocol of a run: st->done = 0 running; 1 stop after the current
+// iteration's last kernel (set by k_cg_b); 2 stopped (set by the next
+// k_spmv_dot when it finds 1, by a breakdown, or at the start of a run).
+
+// ---- FP64 iteration: three kernels, 8 FP64 FMAs per row (GB300's FP64 rate
+// is ~1/64 of FP32, so recomputing p at the neighbours would make the loop
+// FP64-bound); 116 algorithmic bytes per row.
+//   k_spmv_dot: q = Ahat p, gamma = p.q; last block: alpha = rho / gamma
+//   k_cg_b:     r -= alpha q; Jacobi: rho' = r.r, beta = rho'/rho; stop test
+//   k_cg_c:     y += alpha p; p = z + beta p
+
+template <typename V, int U>
 __global__ void __launch_bounds__(kBlock) k_spmv_dot(const V* __restrict__ a,
                                                      const int32_t* __restrict__ col,
                                                      const V* __restrict__ p, V* __restrict__ q,
                                                      int64_t n, double* partials, CgState* st) {
-    if (st->done) return;
-    double acc = 0.0;
-    CPS_GRID_STRIDE(e, n) {
-        const V pe = p[e];
-        V v = pe;
-#pragma unroll
-        for (int j = 0; j < 3; ++j) v = fma(a[j * n + e], p[col[j * n + e]], v);
-        q[e] = v;
-        acc = fma((double)pe, (double)v, acc);
+    {
+        const int d = st->done;
+        if (d) {
+            if (d == 1 && blockIdx.x == 0 && threadIdx.x == 0) st->done = 2;
+            return;
+        }
     }
+    double acc = 0.0;
+    V pe[U], a0[U], a1[U], a2[U];
+    int32_t c0[U], c1[U], c2[U];
+    CPS_UNROLLED_LOOP(n, U,
+        (pe[u] = p[e], a0[u] = a[e], a1[u] = a[n + e], a2[u] = a[2 * n + e],
+         c0[u] = col[e], c1[u] = col[n + e], c2[u] = col[2 * n + e]),
+        {
+            V v = fma(a0[u], p[c0[u]], pe[u]);
+            v = fma(a1[u], p[c1[u]], v);
+            v = fma(a2[u], p[c2[u]], v);
+            q[e] = v;
+            acc = fma((double)pe[u], (double)v, acc);
+        })
     double t[1] = {acc};
     if (grid_sum<1>(t, partials, &st->arrive[0]) && threadIdx.x == 0) {
         const double gamma = t[0];
         st->gamma = gamma;
         if (!(gamma > 0.0) || !isfinite(gamma)) {
             st->status = CPS_ERR_NOT_SPD;
-            st->done = 1;
+            st->done = 2;
         } else {
             st->alpha = st->rho / gamma;
         }
     }
 }
 
-// y += alpha p, r -= alpha q, rho' = r.r; with NORM also ||S r||^2 and the
-// stop test.  Last block: beta = rho'/rho, iteration count, stop flag.
-template <typename V, bool NORM>
-__global__ void __launch_bounds__(kBlock) k_update(V* __restrict__ y, V* __restrict__ r,
-                                                   const V* __restrict__ p,
-                                                   const V* __restrict__ q,
-                                                   const V* __restrict__ s, int64_t n,
-                                                   double* partials, CgState* st) {
+template <typename V, int U>
+__global__ void __launch_bounds__(kBlock) k_cg_c(V* __restrict__ y, V* __restrict__ p,
+                                                 const V* __restrict__ z, int64_t n,
+                                                 const CgState* st) {
+    if (st->done == 2) return;
+    const V al = (V)st->alpha;
+    const V be = (V)st->beta;
+    V pe[U], ye[U], ze[U];
+    CPS_UNROLLED_LOOP(n, U, (pe[u] = p[e], ye[u] = y[e], ze[u] = z[e]),
+        {
+            y[e] = fma(al, pe[u], ye[u]);
+            p[e] = fma(be, pe[u], ze[u]);
+        })
+}
+
+// ---- binary32 iteration: two fused kernels (FP32 arithmetic is cheap, so p
+// is recomputed at the neighbours instead of stored and re-read).
+//   k_cg_a: y += alpha_{k-1} p_{k-1}   (x update one iteration late)
+//           p_k = z_k + beta_{k-1} p_{k-1}   (own row and the neighbours')
+//           q = Ahat p_k, gamma = p_k . q;  last block: alpha_k
+//   k_cg_b: as above.
+// p alternates between two buffers chosen by the parity of the iteration
+// counter, so one captured graph serves any starting iteration.
+template <typename V, int U>
+__global__ void __launch_bounds__(kBlock) k_cg_a(const V* __restrict__ a,
+                                                 const int32_t* __restrict__ col,
+                                                 const V* __restrict__ z, V* __restrict__ p0,
+                                                 V* __restrict__ p1, V* __restrict__ y,
+                                                 V* __restrict__ q, int64_t n, double* partials,
+                                                 CgState* st) {
+    if (st->done) return;
+    const bool odd = (st->iter & 1) != 0;
+    const V* __restrict__ po = odd ? p1 : p0;
+    V* __restrict__ pn = odd ? p0 : p1;
+    const V al = (V)st->alpha;
+    const V be = (V)st->beta;
+    double acc = 0.0;
+    V pold[U], ze[U], ye[U], a0[U], a1[U], a2[U];
+    int32_t c0[U], c1[U], c2[U];
+    CPS_UNROLLED_LOOP(n, U,
+        (pold[u] = po[e], ze[u] = z[e], ye[u] = y[e], a0[u] = a[e], a1[u] = a[n + e],
+         a2[u] = a[2 * n + e], c0[u] = col[e], c1[u] = col[n + e], c2[u] = col[2 * n + e]),
+        {
+            y[e] = fma(al, pold[u], ye[u]);
+            const V pe = fma(be, pold[u], ze[u]);
+            V v = fma(a0[u], fma(be, po[c0[u]], z[c0[u]]), pe);
+            v = fma(a1[u], fma(be, po[c1[u]], z[c1[u]]), v);
+            v = fma(a2[u], fma(be, po[c2[u]], z[c2[u]]), v);
+            pn[e] = pe;
+            q[e] = v;
+            acc = fma((double)pe, (double)v, acc);
+        })
+    double t[1] = {acc};
+    if (grid_sum<1>(t, partials, &st->arrive[0]) && threadIdx.x == 0) {
+        const double gamma = t[0];
+        st->gamma = gamma;
+        if (!(gamma > 0.0) || !isfinite(gamma)) {
+            st->status = CPS_ERR_NOT_SPD;
+            st->done = 2;
+        } else {
+            st->alpha = st->rho / gamma;
+        }
+    }
+}
+
+template <typename V, bool NORM, bool JACOBI, int U>
+__global__ void __launch_bounds__(kBlock) k_cg_b(V* __restrict__ r, const V* __restrict__ q,
+                                                 const V* __restrict__ s, int64_t n,
+                                                 double* partials, CgState* st) {
     if (st->done) return;
     const V al = (V)st->alpha;
     double rr = 0.0, nn = 0.0;
-    CPS_GRID_STRIDE(e, n) {
-        const V pe = p[e], qe = q[e];
-        y[e] = fma(al, pe, y[e]);
-        const V re = fma(-al, qe, r[e]);
-        r[e] = re;
-        rr = fma((double)re, (double)re, rr);
-        if (NORM) {
-            const double t = (double)s[e] * (double)re;
-            nn = fma(t, t, nn);
-        }
-    }
+    V re[U], qe[U], se[U];
+    CPS_UNROLLED_LOOP(n, U, (re[u] = r[e], qe[u] = q[e], se[u] = NORM ? s[e] : (V)0),
+        {
+            const V rv = fma(-al, qe[u], re[u]);
+            r[e] = rv;
+            if (JACOBI) rr = fma((double)rv, (double)rv, rr);
+            if (NORM) {
+                const double t = (double)se[u] * (double)rv;
+                nn = fma(t, t, nn);
+            }
+        })
     double t[2] = {rr, nn};
     if (grid_sum<2>(t, partials, &st->arrive[1]) && threadIdx.x == 0) {
-        const double rho_new = t[0];
         const long long it = st->iter + 1;
         st->iter = it;
         int done = 0;
@@ -72,32 +193,59 @@ __global__ void __launch_bounds__(kBlock) k_update(V* __restrict__ y, V* __restr
             st->rnorm2 = t[1];
             if (t[1] <= st->thresh2) done = 1;
         }
-        if (!(rho_new > 0.0)) done = 1;          // exact solution reached
         if (it >= st->max_iter) done = 1;
-        st->beta = rho_new / st->rho;
-        st->rho = rho_new;
+        if (JACOBI) {
+            const double rho_new = t[0];
+            if (!(rho_new > 0.0)) done = 1;      // exact solution reached
+            st->beta = rho_new / st->rho;
+            st->rho = rho_new;
+        }
         if (done) st->done = 1;
     }
 }
 
-// p = r + beta p
-template <typename V>
-__global__ void __launch_bounds__(kBlock) k_pupdate(V* __restrict__ p, const V* __restrict__ r,
-                                                    int64_t n, const CgState* st) {
-    if (st->done) return;
-    const V be = (V)st->beta;
-    CPS_GRID_STRIDE(e, n) { p[e] = fma(be, p[e], r[e]); }
+// Autotuning: keep the iteration kernels running whatever the data does.
+__global__ void k_tune_prime(CgState* st) {
+    st->done = 0;
+    st->status = CPS_OK;
+    st->rho = 1.0;
+    st->alpha = 1e-3;
+    st->beta = 0.5;
+    st->max_iter = 1LL << 62;
 }
 
-// Start of a FP64 run from the user's x: y = S x, r = S^-1 b - Ahat y, p = r.
+// p = z (start of an IC(0) run, after the first preconditioner application).
+template <typename V>
+__global__ void __launch_bounds__(kBlock) k_copy(V* __restrict__ dst, const V* __restrict__ src,
+                                                 int64_t n) {
+    CPS_GRID_STRIDE(e, n) { dst[e] = src[e]; }
+}
+
+// Pending x update of the binary32 iteration after its last k_cg_b:
+// y += alpha p_last (the next run start resets alpha).
+template <typename V>
+__global__ void __launch_bounds__(kBlock) k_flush_y(V* __restrict__ y, const V* __restrict__ p0,
+                                                    const V* __restrict__ p1, int64_t n,
+                                                    CgState* st) {
+    // iteration k wrote p_k to p1 (k even) or p0 (k odd); iter = k + 1 now
+    const V* __restrict__ pl = (st->iter & 1) ? p1 : p0;
+    if (st->status != CPS_OK) return;
+    const V al = (V)st->alpha;
+    if (al == (V)0) return;
+    CPS_GRID_STRIDE(e, n) { y[e] = fma(al, pl[e], y[e]); }
+}
+
+// Start of a FP64 run from x: y = S x, r = S^-1 b - Ahat y, p_{-1} = 0.
+// Jacobi: rho = r.r.  IC(0): rho = +inf so that the first preconditioner
+// application yields beta = 0.
 __global__ void __launch_bounds__(kBlock) k_init64(const double* __restrict__ b,
                                                    const double* __restrict__ x,
                                                    const double* __restrict__ s,
                                                    const double* __restrict__ a,
                                                    const int32_t* __restrict__ col, int64_t n,
                                                    double* __restrict__ y, double* __restrict__ r,
-                                                   double* __restrict__ p, double rtol,
-                                                   long long budget, double* partials,
+                                                   double* __restrict__ p0, double rtol,
+                                                   long long budget, int jacobi, double* partials,
                                                    CgState* st) {
     double rr = 0.0, bb = 0.0, nn = 0.0;
     CPS_GRID_STRIDE(e, n) {
@@ -113,7 +261,7 @@ __global__ void __launch_bounds__(kBlock) k_init64(const double* __restrict__ b,
         const double re = be / se - ay;
         y[e] = ye;
         r[e] = re;
-        if (p) p[e] = re;
+        p0[e] = jacobi ? re : 0.0;
         rr = fma(re, re, rr);
         bb = fma(be, be, bb);
         const double t = se * re;
@@ -121,7 +269,7 @@ __global__ void __launch_bounds__(kBlock) k_init64(const double* __restrict__ b,
     }
     double t[3] = {rr, bb, nn};
     if (grid_sum<3>(t, partials, &st->arrive[2]) && threadIdx.x == 0) {
-        st->rho = t[0];
+        st->rho = jacobi ? t[0] : INFINITY;
         st->bnorm2 = t[1];
         st->thresh2 = rtol * rtol * t[1];
         st->rnorm2 = t[2];
@@ -131,11 +279,11 @@ __global__ void __launch_bounds__(kBlock) k_init64(const double* __restrict__ b,
         st->iter = 0;
         st->max_iter = budget;
         st->status = CPS_OK;
-        st->done = (t[1] == 0.0 || t[2] <= st->thresh2 || budget <= 0) ? 1 : 0;
+        st->done = (t[1] == 0.0 || t[2] <= st->thresh2 || budget <= 0) ? 2 : 0;
     }
 }
 
-// End of a FP64 run: x = S^-1 y and the true residual ||b - A x||^2 in FP64.
+// End of a FP64 run: x = S^-1 y and the true residual ||b - A x||^2.
 __global__ void __launch_bounds__(kBlock) k_final64(const double* __restrict__ b,
                                                     const double* __restrict__ y,
                                                     const double* __restrict__ s,
@@ -163,17 +311,21 @@ __global__ void __launch_bounds__(kBlock) k_final64(const double* __restrict__ b
     if (grid_sum<1>(t, partials, &st->arrive[3]) && threadIdx.x == 0) st->rnorm2 = t[0];
 }
 
-// Mixed precision, outer step: r = b - A x in FP64 from the FP64 iterate x;
-// the inner run starts from d = 0 with r32 = p32 = S^-1 r rounded to binary32.
-// Inner stop: ||S r_inner|| <= max(eta ||r||, rtol ||b|| / 2).
+// Mixed precision, residual replacement: r = b - A x in FP64 from the FP64
+// iterate x; the binary32 run continues with r32 = S^-1 r and d32 = 0.
+// first: start a new run (p_{-1} = 0, beta = 0, iteration 0).  Otherwise the
+// search direction is kept and beta is rescaled to the replaced residual
+// (beta = rho_true / rho_k).  Stop of the binary32 run:
+// ||S r|| <= max(delta ||r_true||, rtol ||b|| / 2).
 __global__ void __launch_bounds__(kBlock) k_res64(const double* __restrict__ b,
                                                   const double* __restrict__ x,
                                                   const double* __restrict__ s,
                                                   const double* __restrict__ a,
                                                   const int32_t* __restrict__ col, int64_t n,
-                                                  float* __restrict__ r32, float* __restrict__ p32,
-                                                  float* __restrict__ d32, double rtol, double eta,
-                                                  long long budget, double* partials, CgState* st) {
+                                                  float* __restrict__ r32, float* __restrict__ p32_0,
+                                                  float* __restrict__ d32, double rtol,
+                                                  double delta, long long budget, int first,
+                                                  int jacobi, double* partials, CgState* st) {
     double rr = 0.0, bb = 0.0, nn = 0.0;
     CPS_GRID_STRIDE(e, n) {
         const double se = s[e];
@@ -187,8 +339,8 @@ __global__ void __launch_bounds__(kBlock) k_res64(const double* __restrict__ b,
         const double re = be / se - ay;
         const float rf = (float)re;
         r32[e] = rf;
-        p32[e] = rf;
         d32[e] = 0.0f;
+        if (first) p32_0[e] = 0.0f;
         rr = fma((double)rf, (double)rf, rr);
         bb = fma(be, be, bb);
         const double t = se * re;
@@ -196,19 +348,29 @@ __global__ void __launch_bounds__(kBlock) k_res64(const double* __restrict__ b,
     }
     double t[3] = {rr, bb, nn};
     if (grid_sum<3>(t, partials, &st->arrive[2]) && threadIdx.x == 0) {
-        st->rho = t[0];
+        const double outer2 = rtol * rtol * t[1];
+        const double inner2 = delta * delta * t[2];
         st->bnorm2 = t[1];
         st->rnorm2 = t[2];
-        const double outer2 = rtol * rtol * t[1];
-        const double inner2 = eta * eta * t[2];
         st->thresh2 = inner2 > 0.25 * outer2 ? inner2 : 0.25 * outer2;
         st->alpha = 0.0;
-        st->beta = 0.0;
-        st->gamma = 0.0;
-        st->iter = 0;
-        st->max_iter = budget;
         st->status = CPS_OK;
-        st->done = (t[1] == 0.0 || t[2] <= outer2 || budget <= 0 || !(t[0] > 0.0)) ? 1 : 0;
+        if (first) {
+            st->iter = 0;
+            st->beta = 0.0;
+            st->rho = jacobi ? t[0] : INFINITY;
+        } else if (jacobi) {
+            // beta_k = rho_{k+1}/rho_k with rho_{k+1} taken from the true residual
+            const double rho_k = st->beta > 0.0 ? st->rho / st->beta : INFINITY;
+            st->beta = t[0] / rho_k;
+            st->rho = t[0];
+        } else {
+            // the preconditioner application that follows computes
+            // beta = rho_true / st->rho: hand it rho_k
+            st->rho = st->beta > 0.0 ? st->rho / st->beta : INFINITY;
+        }
+        st->max_iter = st->iter + budget;
+        st->done = (t[1] == 0.0 || t[2] <= outer2 || budget <= 0 || !(t[0] > 0.0)) ? 2 : 0;
     }
 }
 
@@ -245,6 +407,22 @@ __global__ void k_unscale_offdiag(const double* __restrict__ a, const int32_t* _
     }
 }
 
+// Gather/scatter between the mesh order and the solver's (colour) order.
+__global__ void k_permute_in(const double* __restrict__ b, const double* __restrict__ x,
+                             const int32_t* __restrict__ perm, int64_t n,
+                             double* __restrict__ bp, double* __restrict__ xp) {
+    CPS_GRID_STRIDE(i, n) {
+        const int32_t o = perm[i];
+        bp[i] = b[o];
+        xp[i] = x[o];
+    }
+}
+
+__global__ void k_permute_out(const double* __restrict__ xp, const int32_t* __restrict__ perm,
+                              int64_t n, double* __restrict__ x) {
+    CPS_GRID_STRIDE(i, n) { x[perm[i]] = xp[i]; }
+}
+
 // dL/dT per side slot for one solve (A lambda = g):
 //   interior: -(lambda_e - lambda_ep)(x_e - x_ep); Dirichlet: -lambda_e x_e.
 // Optional chain to the cell log-permeability: dtheta_e += dxi_e sum_j dT_j gfac_j.
@@ -271,6 +449,113 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_scatter(
             if (dtheta) g = fma(v, gfac[k], g);
         }
         if (dtheta) dtheta[e] += g * dxi[e];
+    }
+}
+
+// ------------------------------------------------------------------ IC(0)
+// Apply z = (L D L^T)^-1 r in colour order, L unit lower triangular with the
+// pattern of Ahat (IC(0) factor), per colour c of rows [cs, ce):
+//   forward  (c >= 1): w_i = r_i - sum_{lower slots} l_ik w_k   (w of colour 0 is r)
+//   backward (c <= C-2): z_i = w_i / d_i - sum_{upper slots} l_ki z_k
+// The last colour has no upper slots: forward and backward fuse.  Each kernel
+// adds r_i z_i of its final rows into its own partial segment; the colour-0
+// kernel (always last) sums every segment and sets rho, beta.
+
+// Partial-sum segment of colour c.
+__device__ __forceinline__ double* ic0_segment(double* partials, int c) {
+    return partials + (size_t)(kNumPartials + c) * kMaxGrid;
+}
+
+template <typename V>
+__global__ void __launch_bounds__(kBlock) k_ic0_fwd(const V* __restrict__ l,
+                                                    const int32_t* __restrict__ col,
+                                                    const V* __restrict__ dinv,
+                                                    const V* __restrict__ r, V* __restrict__ z,
+                                                    int64_t n, int64_t cs, int64_t ce,
+                                                    int64_t first_end, int last, int colour,
+                                                    double* partials, const CgState* st) {
+    if (st->done) return;
+    double acc = 0.0;
+    for (int64_t i = cs + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ce;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        V w = r[i];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int32_t k = col[j * n + i];
+            if (k < cs) {
+                const V wk = k < first_end ? r[k] : z[k];
+                w = fma(-l[j * n + i], wk, w);
+            }
+        }
+        if (last) {
+            const V zi = w * dinv[i];
+            z[i] = zi;
+            acc = fma((double)r[i], (double)zi, acc);
+        } else {
+            z[i] = w;
+        }
+    }
+    if (last) {
+        __shared__ double sh[32][1];
+        double t[1] = {acc};
+        block_sum<1>(t, sh);
+        if (threadIdx.x == 0) ic0_segment(partials, colour)[blockIdx.x] = t[0];
+    }
+}
+
+template <typename V>
+__global__ void __launch_bounds__(kBlock) k_ic0_bwd(const V* __restrict__ l,
+                                                    const int32_t* __restrict__ col,
+                                                    const V* __restrict__ dinv,
+                                                    const V* __restrict__ r, V* __restrict__ z,
+                                                    int64_t n, int64_t cs, int64_t ce,
+                                                    int ncolours, int colour, double* partials,
+                                                    CgState* st) {
+    if (st->done) return;
+    double acc = 0.0;
+    for (int64_t i = cs + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ce;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const V ri = r[i];
+        const V wi = colour == 0 ? ri : z[i];
+        V zi = wi * dinv[i];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int32_t k = col[j * n + i];
+            if (k >= ce) zi = fma(-l[j * n + i], z[k], zi);
+        }
+        z[i] = zi;
+        acc = fma((double)ri, (double)zi, acc);
+    }
+    __shared__ double sh[32][1];
+    double t[1] = {acc};
+    block_sum<1>(t, sh);
+    if (colour != 0) {
+        if (threadIdx.x == 0) ic0_segment(partials, colour)[blockIdx.x] = t[0];
+        return;
+    }
+    __shared__ bool lastb;
+    if (threadIdx.x == 0) {
+        ic0_segment(partials, 0)[blockIdx.x] = t[0];
+        __threadfence();
+        const unsigned int v = atomicAdd(&st->arrive[2], 1u);
+        lastb = (v == gridDim.x - 1u);
+    }
+    __syncthreads();
+    if (!lastb) return;
+    __threadfence();
+    double tot = 0.0;
+    for (int c = 0; c < ncolours; ++c) {
+        const double* seg = ic0_segment(partials, c);
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) tot += __ldcg(&seg[i]);
+    }
+    double u[1] = {tot};
+    block_sum<1>(u, sh);
+    if (threadIdx.x == 0) {
+        st->arrive[2] = 0u;
+        const double rho_new = u[0];
+        if (!(rho_new > 0.0)) st->done = 1;      // exact solution reached
+        st->beta = rho_new / st->rho;
+        st->rho = rho_new;
     }
 }
 

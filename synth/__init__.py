@@ -139,6 +139,64 @@ def lattice(n: int, seed: int = 0, jitter: float = 0.05) -> Mesh:
     return Mesh(n=n, xy=xy, tri=tri, dirichlet=dirichlet)
 
 
+def defect_lattice(n: int, seed: int = 0, defects: int = 4) -> Mesh:
+    """Jittered lattice with `defects` interior sides bisected at their
+    midpoint: the two cells of such a side become four, and the two vertices
+    opposite the side get odd degree, so the cell graph has odd cycles (it is
+    not two-colourable).  Every circumcentre distance stays positive."""
+    base = lattice(n, seed)
+    xy = [row for row in base.xy]
+    tri = [list(t) for t in base.tri]
+    rng = np.random.default_rng(seed + 271828)
+    nt0 = len(tri)
+    used = set()
+    side_of = {}
+    for e, t in enumerate(tri):
+        for j in range(3):
+            a, b = t[(j + 1) % 3], t[(j + 2) % 3]
+            side_of.setdefault((min(a, b), max(a, b)), []).append(e)
+    cands = [k for k, v in side_of.items() if len(v) == 2]
+    rng.shuffle(cands)
+    made = 0
+    for a, b in cands:
+        if made == defects:
+            break
+        e1, e2 = side_of[(a, b)]
+        if e1 in used or e2 in used or e1 >= nt0 or e2 >= nt0:
+            continue
+        # keep defects apart: no shared vertex with earlier ones
+        verts = set(tri[e1]) | set(tri[e2])
+        if any(v in used for v in verts):
+            continue
+        m = len(xy)
+        xy.append(0.5 * (np.asarray(xy[a]) + np.asarray(xy[b])))
+        for e in (e1, e2):
+            t = tri[e]
+            k = [i for i in range(3) if t[i] not in (a, b)][0]
+            c, p, q = t[k], t[(k + 1) % 3], t[(k + 2) % 3]   # side p -> q opposite c
+            tri[e] = [p, m, c]
+            tri.append([m, q, c])
+        used.update({e1, e2})
+        used.update(verts)
+        made += 1
+    xy = np.asarray(xy, dtype=np.float64)
+    tri = np.asarray(tri, dtype=np.int32)
+    right = np.zeros(len(xy), dtype=bool)
+    right[: n * n] = (np.arange(n * n) % n) == n - 1
+    return Mesh(n=n, xy=xy, tri=tri, dirichlet=sides_on_vertex_set(tri, right))
+
+
+def defect_problem(n: int, seed: int = 0) -> Problem:
+    """Random-Fourier porosity in [0.3, 1] with isotropic Kozeny-Carman K on
+    a lattice with bisected sides (a mesh that needs more than two colours)."""
+    mesh = defect_lattice(n, seed)
+    rng = np.random.default_rng(seed + 3571)
+    f = random_fourier_field(mesh.xy, rng, mesh.width, mesh.height)
+    eps = np.clip(0.65 + 0.175 * f, 0.3, 1.0)
+    return Problem(mesh, eps, iso_kinv(kozeny_carman_kinv(eps)), PER_VERTEX,
+                   meta={"workload": f"defect-lattice n={n}", "seed": seed})
+
+
 def triangle_areas(mesh: Mesh) -> np.ndarray:
     """Shoelace area of each triangle (used to scale the random RHS)."""
     p = mesh.xy[mesh.tri]

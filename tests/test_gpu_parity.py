@@ -33,6 +33,7 @@ def problems():
     yield "channel64", synth.channel_block_problem(64, seed=5)
     yield "logperm29", synth.log_permeability_problem(29, seed=2)[0]
     yield "ensemble", synth.ensemble_member_problem(3000, seed=11)
+    yield "defect20", synth.defect_problem(20, seed=3)
 
 
 PROBLEMS = dict(problems())
@@ -85,20 +86,44 @@ def test_assembly_matches_oracle(ctx, name, kind):
 
 
 @pytest.mark.parametrize("name", sorted(PROBLEMS))
+@pytest.mark.parametrize("precond", [cps.PC_JACOBI, cps.PC_IC0])
 @pytest.mark.parametrize("precision,tol", [(cps.FP64, 1e-9), (cps.MIXED, 1e-8)])
-def test_solve_matches_oracle(ctx, name, precision, tol):
+def test_solve_matches_oracle(ctx, name, precond, precision, tol):
+    """Relative L2 error against the oracle's solution at rtol 1e-13.  The
+    GPU solves to rtol 1e-12; where FP64 cannot reach that true residual on
+    an ill-conditioned system the call reports CPS_ERR_NOT_CONVERGED with the
+    residual it reached, which must still be below 1e-10."""
     p = PROBLEMS[name]
     s = assemble(ctx, p)
+    s.set_precond(precond)
     b = synth.rhs(p.mesh, 17)
     xo, sto, A = oracle.solve_problem(p, b, rtol=1e-13)
-    x, st = s.solve(torch.as_tensor(b, device="cuda"), rtol=1e-12, precision=precision)
+    x, st = s.solve(torch.as_tensor(b, device="cuda"), rtol=1e-12, precision=precision,
+                    check=False)
+    assert st.status in (0, cps._cps.ERR_NOT_CONVERGED)
+    assert st.rel_res < (1e-12 if st.status == 0 else 1e-10)
     x = x.cpu().numpy()
     err = np.linalg.norm(x - xo) / np.linalg.norm(xo)
     assert err < tol, err
-    assert st.rel_res <= 1e-12
     # the GPU's own residual claim, checked with the oracle's matrix
     r = b - A.matvec(x)
-    assert np.linalg.norm(r) / np.linalg.norm(b) < 2e-12
+    assert np.linalg.norm(r) / np.linalg.norm(b) < 2 * max(st.rel_res, 1e-13)
+    s.free()
+
+
+def test_ic0_needs_fewer_iterations_than_jacobi(ctx):
+    p = PROBLEMS["channel64"]
+    s = assemble(ctx, p)
+    b = torch.as_tensor(synth.rhs(p.mesh, 3), device="cuda")
+    _, sj = s.solve(b, rtol=1e-10)
+    s.set_precond(cps.PC_IC0)
+    _, si = s.solve(b, rtol=1e-10)
+    A = oracle.assemble_problem(p)
+    _, so = oracle.pcg(A, b.cpu().numpy(), rtol=1e-10, precond=oracle.PC_IC0,
+                       perm=oracle.red_black_order(A.n))
+    assert si.iters < 0.75 * sj.iters
+    # same ordering (red/black on the lattice) as the oracle's coloured IC(0)
+    assert abs(si.iters - so.iters) <= max(8, 0.05 * so.iters)
     s.free()
 
 
@@ -218,4 +243,29 @@ def test_adjoint_matches_oracle(ctx):
     dth_o = oracle.theta_gradient(p.mesh.xy, p.mesh.tri, nbr, isd, p.eps, theta, p.nu, p.dt, dT_o)
     np.testing.assert_allclose(dth.cpu().numpy(), dth_o, rtol=1e-7,
                                atol=1e-9 * np.abs(dth_o).max())
+    s.free()
+
+
+def test_autotuned_solves_on_a_large_system(ctx):
+    """Above 131072 cells the first solve of each precision autotunes the
+    iteration kernels; the tuned solves must still be right.  Checked with
+    the oracle's matrix (true residual) and its Jacobi-PCG iterate count."""
+    p = synth.channel_block_problem(300, seed=8)
+    assert p.mesh.nt >= 1 << 17
+    s = assemble(ctx, p)
+    A = oracle.assemble_problem(p)
+    b = synth.rhs(p.mesh, 2)
+    bt = torch.as_tensor(b, device="cuda")
+    for prec in (cps.FP64, cps.MIXED):
+        x, st = s.solve(bt, rtol=1e-10, precision=prec)
+        tu = s.tuning(prec)
+        nk = 3 if prec == cps.FP64 else 2
+        assert all(u in (1, 2, 4) for u in tu["unroll"][:nk])
+        assert all(0 < g <= 4096 for g in tu["grid"][:nk])
+        r = b - A.matvec(x.cpu().numpy())
+        assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-10 * 1.01
+    s.set_precond(cps.PC_IC0)
+    x, st = s.solve(bt, rtol=1e-10)
+    r = b - A.matvec(x.cpu().numpy())
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-10 * 1.01
     s.free()

@@ -80,10 +80,10 @@ def test_clockwise_triangle_is_rejected():
     assert ei.value.code == oracle.ERR_ORIENTATION
 
 
-@pytest.mark.parametrize("seed", [0, 5])
-def test_jittered_mesh_geometric_identities(seed):
+@pytest.mark.parametrize("seed,defects", [(0, False), (5, False), (2, True)])
+def test_jittered_mesh_geometric_identities(seed, defects):
     n = 20
-    m = synth.lattice(n, seed=seed)
+    m = synth.defect_lattice(n, seed=seed) if defects else synth.lattice(n, seed=seed)
     g = oracle.geometry(m.xy, m.tri)
     p = m.xy[m.tri]                                   # [nt, 3, 2]
     r = np.linalg.norm(p - g.cc[:, None, :], axis=2)  # circumradius thrice
