@@ -61,6 +61,8 @@ extern "C" {
 
 #define CPS_PER_VERTEX 0    /* eps, Kinv given at the mesh nodes (Sec. 3.2) */
 #define CPS_PER_CELL 1      /* eps, Kinv given per triangle */
+#define CPS_PER_CELL_LOGK 2 /* eps per triangle; kinv[nt] holds the log-permeability
+                               theta, K = exp(theta) I (isotropic), Kinv = exp(-theta) I */
 
 #define CPS_PC_JACOBI 1     /* diagonal preconditioner */
 #define CPS_PC_IC0 2        /* IC(0) in a multicolour order of the cells */
@@ -102,8 +104,10 @@ const char* cps_last_error(cps_ctx ctx);
  *   dirichlet[nb]   boundary sides with eta = 0 at the side midpoint, given as
  *                   tri*3 + j; all other boundary sides are no-flux.  May be
  *                   NULL when nb = 0 (then CP2 is singular: CPS_ERR_SINGULAR)
- *   eps[nf]         porosity, nf = nv (CPS_PER_VERTEX) or nt (CPS_PER_CELL)
- *   kinv[nf*3]      inverse permeability tensor (xx, xy, yy), symmetric PSD
+ *   eps[nf]         porosity, nf = nv (CPS_PER_VERTEX) or nt (CPS_PER_CELL,
+ *                   CPS_PER_CELL_LOGK)
+ *   kinv[nf*3]      inverse permeability tensor (xx, xy, yy), symmetric PSD;
+ *                   kinv[nt] = theta for CPS_PER_CELL_LOGK
  *   field_loc       CPS_PER_VERTEX: side tensor = mean of the tensors Xi at the
  *                   side's two nodes (Sec. 3.2 side averages); CPS_PER_CELL:
  *                   mean of the two cells' Xi, a boundary side uses its cell's
@@ -163,11 +167,16 @@ int cps_export_matrix(cps_sys sys, double* diag, int32_t* col, double* val, void
 int cps_solve(cps_sys sys, const double* b, double* x, double rtol, int64_t max_iter,
               int precision, cps_stats* stats, void* stream);
 
-/* Solve nsys independent systems (each with its own matrix, b and x) in one
- * launch sequence with per-system convergence.  systems, b, x and stats are
- * HOST arrays of length nsys holding handles and device pointers.  All systems
- * must come from the same context and use the Jacobi preconditioner.  The
- * return value is the first non-OK per-system status, or CPS_OK. */
+/* Solve nsys independent systems (each with its own matrix, b and x) together.
+ * systems, b, x and stats are HOST arrays of length nsys holding handles and
+ * device pointers (b[i], x[i] of system i's size; x[i] is the initial guess
+ * and receives the solution).  All systems must come from the same context.
+ * CPS_FP64: one launch per phase for all systems (Jacobi, whatever each
+ * system's preconditioner setting), a per-system convergence mask, and
+ * iteration chunks replayed from a CUDA graph; a system of more than
+ * 8,388,608 cells is rejected (CPS_ERR_ARG) -- solve it alone.  CPS_MIXED
+ * solves the systems one after the other.  The return value is the first
+ * non-OK per-system status, or CPS_OK. */
 int cps_solve_batch(const cps_sys* systems, int nsys, const double* const* b,
                     double* const* x, double rtol, int64_t max_iter, int precision,
                     cps_stats* stats, void* stream);
@@ -179,7 +188,8 @@ int cps_solve_batch(const cps_sys* systems, int nsys, const double* const* b,
  *   dT[s*nt+e] += -lambda_e x_e                         Dirichlet side
  * which is dL/dT for the side coefficient T of A (each interior side appears
  * in both of its cells' slots with the same value).  If dtheta is not NULL
- * (CP2, CPS_PER_CELL, isotropic Kinv = exp(-theta) I only) the chain rule
+ * (CP2 with CPS_PER_CELL_LOGK, or CPS_PER_CELL with isotropic Kinv, read as
+ * Kinv = exp(-theta) I) the chain rule
  * through Xi_e = eps dt / (1 + nu eps dt exp(-theta_e)) is applied and
  * dL/dtheta is ADDED to dtheta[nt].  dT may be NULL if only dtheta is wanted.
  * lambda[nt] is overwritten (its input is the initial guess).

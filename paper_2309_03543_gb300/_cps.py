@@ -24,7 +24,7 @@ ERR_CUDA = -9
 ERR_TIMEOUT = -10
 
 KIND_CP2, KIND_CP1_X, KIND_CP1_Y = 0, 1, 2
-PER_VERTEX, PER_CELL = 0, 1
+PER_VERTEX, PER_CELL, PER_CELL_LOGK = 0, 1, 2
 PC_JACOBI, PC_IC0 = 1, 2
 FP64, MIXED = 0, 1
 

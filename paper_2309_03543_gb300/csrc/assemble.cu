@@ -124,13 +124,22 @@ __global__ void k_cell_geometry(const double* __restrict__ xy, const int32_t* __
     }
 }
 
+// Component comp (0 xx, 1 xy, 2 yy) of K^-1 at field point i: stored, or
+// exp(-theta_i) I for a log-permeability field.
+__device__ __forceinline__ double kinv_at(const double* __restrict__ kinv, int64_t i, int comp,
+                                          bool logk) {
+    if (logk) return comp == 1 ? 0.0 : exp(-kinv[i]);
+    return kinv[3 * i + comp];
+}
+
 // Xi = eps dt (I + c Kinv)^-1, c = nu eps dt, explicit 2x2 inverse.
 __global__ void k_xi(const double* __restrict__ eps, const double* __restrict__ kinv, int64_t nf,
-                     double nu, double dt, double* __restrict__ xi, int* err) {
+                     double nu, double dt, bool logk, double* __restrict__ xi, int* err) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nf;
          i += (int64_t)gridDim.x * blockDim.x) {
         const double ep = eps[i];
-        const double kxx = kinv[3 * i], kxy = kinv[3 * i + 1], kyy = kinv[3 * i + 2];
+        const double kxx = kinv_at(kinv, i, 0, logk), kxy = kinv_at(kinv, i, 1, logk),
+                     kyy = kinv_at(kinv, i, 2, logk);
         const double c = nu * ep * dt;
         const double m00 = 1.0 + c * kxx, m01 = c * kxy, m11 = 1.0 + c * kyy;
         const double det = m00 * m11 - m01 * m01;
@@ -181,7 +190,8 @@ struct TransArgs {
     unsigned long long* n_interior;
     int64_t nt;
     int kind;
-    int field_loc;
+    int field_loc;     // CPS_PER_VERTEX or CPS_PER_CELL (log-permeability maps to cells)
+    bool logk;
     double nu, dt;
     int* err;
 };
@@ -203,7 +213,7 @@ __global__ void k_transmissibility(TransArgs A) {
                     mkk += (1.0 + A.nu * A.eps[v[k]] * A.kinv[3 * (int64_t)v[k] + comp] * A.dt) / A.dt;
                 mkk /= 3.0;
             } else {
-                mkk = (1.0 + A.nu * A.eps[e] * A.kinv[3 * e + comp] * A.dt) / A.dt;
+                mkk = (1.0 + A.nu * A.eps[e] * kinv_at(A.kinv, e, comp, A.logk) * A.dt) / A.dt;
             }
             diag = mkk * A.area[e];
         }
@@ -312,12 +322,12 @@ __global__ void k_scale_offdiag(const double* __restrict__ off, const int32_t* _
 // Xi = eps dt / (1 + s), s = nu eps dt Kinv, dXi/dtheta = Xi s / (1 + s).
 // Flags a non-isotropic field by clearing *iso.
 __global__ void k_dxi_dtheta(const double* __restrict__ eps, const double* __restrict__ kinv,
-                             int64_t nt, double nu, double dt, double* __restrict__ dxi,
-                             int* iso) {
+                             int64_t nt, double nu, double dt, bool logk,
+                             double* __restrict__ dxi, int* iso) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nt;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const double k = kinv[3 * e];
-        if (kinv[3 * e + 1] != 0.0 || kinv[3 * e + 2] != k) atomicExch(iso, 0);
+        const double k = kinv_at(kinv, e, 0, logk);
+        if (!logk && (kinv[3 * e + 1] != 0.0 || kinv[3 * e + 2] != k)) atomicExch(iso, 0);
         const double sv = nu * eps[e] * dt * k;
         const double xi = eps[e] * dt / (1.0 + sv);
         dxi[e] = xi * sv / (1.0 + sv);
@@ -370,8 +380,10 @@ int assemble_impl(cps_ctx ctx, const double* xy, int64_t nv, const int32_t* tri,
         return fail(ctx, CPS_ERR_ARG, "assemble: null pointer or bad size");
     if (nt > (int64_t)INT32_MAX / 3 || nv > (int64_t)INT32_MAX)
         return fail(ctx, CPS_ERR_ARG, "assemble: mesh too large for 32-bit indices");
-    if (field_loc != CPS_PER_VERTEX && field_loc != CPS_PER_CELL)
+    if (field_loc != CPS_PER_VERTEX && field_loc != CPS_PER_CELL && field_loc != CPS_PER_CELL_LOGK)
         return fail(ctx, CPS_ERR_ARG, "assemble: bad field_loc");
+    const bool logk = field_loc == CPS_PER_CELL_LOGK;
+    if (logk) field_loc = CPS_PER_CELL;
     if (kind != CPS_KIND_CP2 && kind != CPS_KIND_CP1_X && kind != CPS_KIND_CP1_Y)
         return fail(ctx, CPS_ERR_ARG, "assemble: bad kind");
     if (!(nu > 0.0) || !(dt > 0.0)) return fail(ctx, CPS_ERR_ARG, "assemble: nu and dt must be > 0");
@@ -470,7 +482,7 @@ int assemble_impl(cps_ctx ctx, const double* xy, int64_t nv, const int32_t* tri,
             k_side_insert<<<g3, kBlock, 0, stream>>>(tri, nt, nv, keys, id0, id1, cap - 1, err);
             k_side_lookup<<<g3, kBlock, 0, stream>>>(tri, nt, nv, keys, id0, id1, cap - 1, nbr);
             k_cell_geometry<<<g1, kBlock, 0, stream>>>(xy, tri, nt, nv, area, ccx, ccy, err);
-            k_xi<<<gf, kBlock, 0, stream>>>(eps, kinv, nf, nu, dt, xi, err);
+            k_xi<<<gf, kBlock, 0, stream>>>(eps, kinv, nf, nu, dt, logk, xi, err);
             if (nb > 0)
                 k_mark_dirichlet<<<grid_for(ctx, nb), kBlock, 0, stream>>>(dirichlet, nb, nt, nbr,
                                                                          s->slot_kind, err);
@@ -479,11 +491,11 @@ int assemble_impl(cps_ctx ctx, const double* xy, int64_t nv, const int32_t* tri,
             ta.xi = xi; ta.eps = eps; ta.kinv = kinv; ta.slot_kind = s->slot_kind;
             ta.diag = s->diag; ta.off = off; ta.col = s->col; ta.gfac = s->gfac;
             ta.n_interior = counters; ta.nt = nt; ta.kind = kind; ta.field_loc = field_loc;
-            ta.nu = nu; ta.dt = dt; ta.err = err;
+            ta.nu = nu; ta.dt = dt; ta.err = err; ta.logk = logk;
             k_transmissibility<<<g1, kBlock, 0, stream>>>(ta);
             k_sqrt_diag<<<g1, kBlock, 0, stream>>>(s->diag, nt, s->s, s->s32, counters + 1, err);
             k_scale_offdiag<<<g3, kBlock, 0, stream>>>(off, s->col, s->s, nt, s->a, s->a32);
-            if (s->dxi) k_dxi_dtheta<<<g1, kBlock, 0, stream>>>(eps, kinv, nt, nu, dt, s->dxi, iso);
+            if (s->dxi) k_dxi_dtheta<<<g1, kBlock, 0, stream>>>(eps, kinv, nt, nu, dt, logk, s->dxi, iso);
             s->assembly_launches = 8 + (nb > 0 ? 1 : 0) + (s->dxi ? 1 : 0);
             ce = cudaGetLastError();
             if (ce == cudaSuccess) ce = cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, stream);

@@ -553,16 +553,4 @@ int adjoint_impl(cps_sys s, const double* x, const double* g, double* lambda, do
     return CPS_OK;
 }
 
-int solve_batch_impl(const cps_sys* systems, int nsys, const double* const* b,
-                     double* const* x, double rtol, int64_t max_iter, int precision,
-                     cps_stats* stats, cudaStream_t stream) {
-    int first = CPS_OK;
-    for (int i = 0; i < nsys; ++i) {
-        int rc = solve_impl(systems[i], b[i], x[i], rtol, max_iter, precision,
-                            stats ? &stats[i] : nullptr, stream);
-        if (rc != CPS_OK && first == CPS_OK) first = rc;
-    }
-    return first;
-}
-
 }  // namespace cps

@@ -269,3 +269,34 @@ def test_autotuned_solves_on_a_large_system(ctx):
     r = b - A.matvec(x.cpu().numpy())
     assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-10 * 1.01
     s.free()
+
+
+def test_batched_solve_matches_oracle_per_system(ctx):
+    """Uneven ensemble solved together (one launch per phase, per-system
+    convergence): every member against its own oracle solve; a zero RHS
+    member returns zeros; the result equals the loop of single solves."""
+    sizes = [600, 2500, 9000, 1200, 30000]
+    probs = [synth.ensemble_member_problem(nt, seed=40 + i) for i, nt in enumerate(sizes)]
+    systems = [assemble(ctx, p) for p in probs]
+    bs = [torch.as_tensor(synth.rhs(p.mesh, 90 + i), device="cuda") for i, p in enumerate(probs)]
+    bs[3] = torch.zeros_like(bs[3])
+    xs = [torch.zeros_like(b) for b in bs]
+    stats = cps.solve_batch(systems, bs, xs, rtol=1e-12, check=False)
+    for i, (p, b, x, st) in enumerate(zip(probs, bs, xs, stats)):
+        if i == 3:
+            assert torch.all(x == 0) and st.iters == 0
+            continue
+        assert st.status in (0, cps._cps.ERR_NOT_CONVERGED) and st.rel_res < 1e-10
+        xo, _, _ = oracle.solve_problem(p, b.cpu().numpy(), rtol=1e-13)
+        err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
+        assert err < 1e-9, (i, err)
+        x1, st1 = systems[i].solve(b, rtol=1e-12, check=False)
+        assert abs(st1.iters - st.iters) <= max(4, 0.02 * st1.iters)
+    # a second batched call on the same handles (state reuse) and mixed mode
+    xs2 = [torch.zeros_like(b) for b in bs]
+    stats2 = cps.solve_batch(systems, bs, xs2, rtol=1e-10, precision=cps.MIXED, check=False)
+    for i, (x, st) in enumerate(zip(xs2, stats2)):
+        if i != 3:
+            assert st.rel_res <= 1e-10
+    for s in systems:
+        s.free()
