@@ -56,6 +56,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=0,
                     help="oracle PCG iterations in the CPU sample (0: auto)")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="ensemble mode: this many systems of log-uniform 2k-500k cells, "
+                         "batched solve vs a loop of single solves (prints its own line)")
+    ap.add_argument("--chain", type=int, default=0,
+                    help="adjoint mode: this many chained log-permeability solves on the "
+                         "--n lattice with checkpointed adjoint backward (own line)")
+    ap.add_argument("--chain-rtol", type=float, default=1e-8,
+                    help="relative residual of the chained forward and adjoint solves")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiling run: assemble, then FP64 and mixed solves bounded to this "
                          "many iterations (Jacobi and IC(0)); no timing output")
@@ -178,10 +186,146 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def timed(fn, stream):
+    import torch
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3, out
+
+
+def run_batch(args):
+    """Uneven ensemble: sizes log-uniform in [2k, 500k] cells, random-Fourier
+    porosity in [0.3, 1], isotropic Kozeny-Carman K; FP64 Jacobi to rtol."""
+    import torch
+    import paper_2309_03543_gb300 as cps
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    ctx = cps.Context(0)
+    sizes = synth.ensemble_sizes(args.batch, 2000, 500000, seed=2024)
+    systems, bs = [], []
+    t0 = time.perf_counter()
+    for i, nt in enumerate(sizes):
+        p = synth.ensemble_member_problem(int(nt), seed=5000 + i)
+        m = p.mesh
+        systems.append(ctx.assemble(m.xy, m.tri, m.dirichlet, p.eps, p.kinv, p.field_loc,
+                                    cps.KIND_CP2, p.nu, p.dt))
+        bs.append(torch.as_tensor(synth.rhs(m, 9000 + i), device=dev))
+    setup = time.perf_counter() - t0
+    cells = sum(s.nt for s in systems)
+    xs = [torch.zeros_like(b) for b in bs]
+
+    def loop(prec):
+        its = 0
+        for s, b, x in zip(systems, bs, xs):
+            x.zero_()
+            _, st = s.solve(b, x=x, rtol=args.rtol, precision=prec)
+            its += st.iters * s.nt
+        return its
+
+    def batch(prec):
+        for x in xs:
+            x.zero_()
+        st = cps.solve_batch(systems, bs, xs, rtol=args.rtol, precision=prec)
+        return sum(t.iters * s.nt for t, s in zip(st, systems))
+
+    loop(cps.FP64)
+    batch(cps.FP64)   # warm-up (autotuning, graph capture)
+    res = {}
+    for name, fn in (("loop_fp64", lambda: loop(cps.FP64)), ("batch_fp64", lambda: batch(cps.FP64)),
+                     ("loop_mixed", lambda: loop(cps.MIXED))):
+        best = None
+        for _ in range(max(1, args.steps)):
+            t, ci = timed(fn, stream)
+            best = (t, ci) if best is None or t < best[0] else best
+        res[name] = {"seconds": best[0], "cell_iters": best[1],
+                     "cell_iters_per_s": best[1] / best[0]}
+    line = {"metric": "ensemble corrector solves: batched vs loop (FP64 Jacobi-PCG to rtol)",
+            "value": res["batch_fp64"]["cell_iters_per_s"], "unit": UNIT,
+            "config": {"workload": f"{args.batch} systems, log-uniform 2k-500k cells",
+                       "cells": cells, "rtol": args.rtol, "host_setup_s": setup},
+            "variants": res,
+            "batch_speedup_vs_loop": res["loop_fp64"]["seconds"] / res["batch_fp64"]["seconds"]}
+    print(json.dumps(line), flush=True)
+
+
+def run_chain(args):
+    """Chained corrector solves x_t = A(theta)^-1 (n_t + 0.1 |n_t|/|x_{t-1}| x_{t-1}),
+    n_t = area N(0,1); loss = sum_t |x_t - x*_t|^2 with targets from theta*
+    (seed + 1000); gradient by the adjoint with checkpoints every 10 steps.
+    (With the unnormalised feedback 0.1 x_{t-1} the chain grows by
+    0.1 / lambda_min(A) ~ 1e7 per step on this matrix and overflows.)"""
+    import torch
+    import paper_2309_03543_gb300 as cps
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    ctx = cps.Context(0)
+    p, theta_np = synth.log_permeability_problem(args.n, seed=0)
+    _, theta_star = synth.log_permeability_problem(args.n, seed=1000)
+    m = p.mesh
+    area = synth.triangle_areas(m)
+    rhs = [torch.as_tensor(area * synth.normal_noise(m.nt, 100 + t), device=dev)
+           for t in range(args.chain)]
+    model = cps.LogPermeabilityCorrector(ctx, m.xy, m.tri, m.dirichlet, p.eps, p.nu, p.dt,
+                                         rtol=args.chain_rtol)
+    with torch.no_grad():
+        targets = [x.clone() for x in cps.chained_solve(
+            model, torch.as_tensor(theta_star, device=dev), rhs, checkpoint_every=0,
+            normalized=True)]
+    theta = torch.as_tensor(theta_np, device=dev).requires_grad_(True)
+
+    def fwd_only():
+        with torch.no_grad():
+            return cps.chained_solve(model, theta, rhs, checkpoint_every=0, normalized=True)
+
+    def fwd_bwd():
+        theta.grad = None
+        xs = cps.chained_solve(model, theta, rhs, checkpoint_every=10, normalized=True)
+        loss = sum(((x - t) ** 2).sum() for x, t in zip(xs, targets))
+        loss.backward()
+        return float(loss)
+
+    sys_ = model.system(theta)
+
+    def plain():
+        its = 0
+        x = torch.zeros(m.nt, dtype=torch.float64, device=dev)
+        for t in range(args.chain):
+            x.zero_()
+            _, st = sys_.solve(rhs[t], x=x, rtol=args.chain_rtol)
+            its += st.iters
+        return its
+
+    fwd_only()
+    fwd_bwd()
+    t_plain, its = timed(plain, stream)
+    t_fwd, _ = timed(fwd_only, stream)
+    t_fb, loss = timed(fwd_bwd, stream)
+    line = {"metric": "differentiable chained corrector solves (adjoint backward, checkpoint 10)",
+            "value": t_fb, "unit": "s per forward+backward", "higher_is_better": False,
+            "config": {"workload": f"log-permeability lattice n={args.n}", "cells": m.nt,
+                       "steps": args.chain, "rtol": args.chain_rtol},
+            "plain_fp64_solves_s": t_plain, "plain_iters": its, "forward_s": t_fwd,
+            "forward_backward_s": t_fb, "backward_s": t_fb - t_fwd,
+            "ratio_forward_backward_vs_plain": t_fb / t_plain, "loss": loss,
+            "grad_norm": float(theta.grad.norm())}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.batch:
+        run_batch(args)
+        return
+    if args.chain:
+        run_chain(args)
         return
     import torch
     import paper_2309_03543_gb300 as cps
@@ -323,6 +467,20 @@ def main():
                 "time_to_rtol_s": t, "iters": st.iters, "refinements": st.refinements,
                 "rel_res": st.rel_res, "us_per_iter": 1e6 * t / max(st.iters, 1)}
     tuning = {"fp64": s.tuning(cps.FP64), "mixed": s.tuning(cps.MIXED)}
+    # small systems: the one-launch cluster solve against the streaming path
+    s.set_precond(cps.PC_JACOBI)
+    for path_name, path in (("stream", cps.PATH_STREAM), ("cluster", cps.PATH_CLUSTER)):
+        try:
+            s.set_solver_path(path)
+        except cps.CpsError:
+            continue
+        ts = []
+        for _ in range(3):
+            x.zero_()
+            ts.append(timed(lambda: s.solve(d["b"], x=x, rtol=args.rtol)[1], stream))
+        t, st = min(ts, key=lambda v: v[0])
+        variants[f"jacobi_fp64_{path_name}_path"] = {
+            "time_to_rtol_s": t, "iters": st.iters, "us_per_iter": 1e6 * t / max(st.iters, 1)}
     s.free()
     jf = variants["jacobi_fp64"]
     achieved = BYTES_PER_CELL_ITER_FP64 * nt * jf["iters"] / jf["time_to_rtol_s"] / 1e9

@@ -198,6 +198,17 @@ int cps_adjoint(cps_sys sys, const double* x, const double* g, double* lambda, d
                 double* dtheta, double rtol, int64_t max_iter, cps_stats* stats,
                 void* stream);
 
+/* Choose how FP64 Jacobi solves run: CPS_PATH_AUTO (default: the autotuner
+ * times both on the system's first FP64 solve), CPS_PATH_STREAM (the
+ * graph-replayed streaming kernels, any size), CPS_PATH_CLUSTER (the whole
+ * solve in one launch of a single thread-block cluster whose shared memory
+ * holds the system; CPS_ERR_ARG if the system does not fit, see
+ * cps_sys_info).  IC(0) and mixed precision always stream. */
+#define CPS_PATH_AUTO 0
+#define CPS_PATH_STREAM 1
+#define CPS_PATH_CLUSTER 2
+int cps_set_solver_path(cps_sys sys, int path);
+
 /* Launch configuration the autotuner chose for the iteration kernels of one
  * precision (host outputs of 3 entries each; zeros before the first solve in
  * that precision): rows per thread per trip of the grid-stride loop, and the

@@ -27,6 +27,7 @@ KIND_CP2, KIND_CP1_X, KIND_CP1_Y = 0, 1, 2
 PER_VERTEX, PER_CELL, PER_CELL_LOGK = 0, 1, 2
 PC_JACOBI, PC_IC0 = 1, 2
 FP64, MIXED = 0, 1
+PATH_AUTO, PATH_STREAM, PATH_CLUSTER = 0, 1, 2
 
 ERROR_NAMES = {
     ERR_ARG: "CPS_ERR_ARG", ERR_NONMANIFOLD: "CPS_ERR_NONMANIFOLD",
@@ -65,6 +66,7 @@ SIGNATURES = {
     "cps_adjoint": (_I, [_P, _P, _P, _P, _P, _P, _D, _I64, ctypes.POINTER(Stats), _P]),
     "cps_matvec": (_I, [_P, _P, _P, _P]),
     "cps_get_tuning": (_I, [_P, _I, _P, _P]),
+    "cps_set_solver_path": (_I, [_P, _I]),
 }
 
 _lib = None

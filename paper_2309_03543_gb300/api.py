@@ -139,6 +139,10 @@ class System:
         self.ctx.check(self.ctx.lib.cps_get_tuning(self.handle, precision, u, g), "cps_get_tuning")
         return {"unroll": list(u), "grid": list(g)}
 
+    def set_solver_path(self, path: int):
+        """PATH_AUTO, PATH_STREAM or PATH_CLUSTER for FP64 Jacobi solves."""
+        self.ctx.check(self.ctx.lib.cps_set_solver_path(self.handle, path), "cps_set_solver_path")
+
     def set_precond(self, precond: int):
         self.ctx.check(self.ctx.lib.cps_set_precond(self.handle, precond,
                                                     _stream(self.ctx.device)), "cps_set_precond")

@@ -80,18 +80,29 @@ class CorrectorSolve(torch.autograd.Function):
 
 
 def chained_solve(model: LogPermeabilityCorrector, theta: torch.Tensor, rhs,
-                  coupling: float = 0.1, checkpoint_every: int = 10):
-    """x_t = A(theta)^-1 (rhs[t] + coupling * x_{t-1}), x_0 = 0 before the
-    first step; returns the list of x_t.  With checkpoint_every > 0 the
-    autograd graph keeps only every segment's input state."""
+                  coupling: float = 0.1, checkpoint_every: int = 10, normalized: bool = False):
+    """x_t = A(theta)^-1 (rhs[t] + coupling * f(x_{t-1})), x_0 = 0 before the
+    first step; returns the list of x_t.  f(x) = x, or with normalized=True
+    f(x) = x * |rhs[t]| / |x| (the previous solution rescaled to the norm of
+    the new data, which keeps long chains bounded: with f(x) = x the feedback
+    grows by coupling / lambda_min(A) per step).  With checkpoint_every > 0
+    the autograd graph keeps only every segment's input state."""
     steps = len(rhs)
     x_prev = torch.zeros_like(rhs[0])
     xs = []
 
+    def feed(b, xp):
+        if not normalized:
+            return b + coupling * xp
+        nx = torch.linalg.vector_norm(xp)
+        if float(nx) == 0.0:
+            return b.clone()
+        return b + coupling * (torch.linalg.vector_norm(b) / nx) * xp
+
     def segment(th, xp, *bs):
         out = []
         for b in bs:
-            xp = CorrectorSolve.apply(th, b + coupling * xp, model)
+            xp = CorrectorSolve.apply(th, feed(b, xp), model)
             out.append(xp)
         return tuple(out)
 

@@ -136,6 +136,28 @@ int cps_adjoint(cps_sys sys, const double* x, const double* g, double* lambda, d
                              as_stream(stream));
 }
 
+int cps_set_solver_path(cps_sys sys, int path) {
+    if (!sys) return CPS_ERR_ARG;
+    cps::Tuning& t = sys->tune[CPS_FP64];
+    if (path == CPS_PATH_AUTO) {
+        t.path_done = false;
+        t.path = 0;
+    } else if (path == CPS_PATH_STREAM) {
+        t.path_done = true;
+        t.path = 0;
+    } else if (path == CPS_PATH_CLUSTER) {
+        if (sys->nt > cps::cluster_max_rows(sys->ctx)) {
+            sys->ctx->last_error = "set_solver_path: system too large for one cluster";
+            return CPS_ERR_ARG;
+        }
+        t.path_done = true;
+        t.path = 1;
+    } else {
+        return CPS_ERR_ARG;
+    }
+    return CPS_OK;
+}
+
 int cps_get_tuning(cps_sys sys, int precision, int32_t* unroll, int32_t* grid) {
     if (!sys || !unroll || !grid || (precision != CPS_FP64 && precision != CPS_MIXED))
         return CPS_ERR_ARG;

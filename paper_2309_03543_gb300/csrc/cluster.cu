@@ -1,0 +1,290 @@
+// Persistent solve of a small system inside one thread-block cluster.
+//
+// For meshes of up to a few tens of thousands of cells every kernel launch of
+// the streaming loop costs more than its work, so the whole Jacobi-PCG run is
+// one launch of a single cluster of C CTAs (C = 16 where the GPU allows it).
+// CTA k owns rows [k R, (k+1) R): its slice of the scaled matrix and of the
+// vectors y, r, p, q, s stay in its shared memory for the whole run.  The
+// SpMV reads a neighbour's p from the owning CTA's shared memory through the
+// cluster's distributed shared memory; dot products are summed per CTA, then
+// every CTA adds the C partials in rank order after a cluster barrier (the
+// same order everywhere, so all CTAs hold bit-identical alpha, beta and stop
+// decisions).  The cluster barrier is the hardware one: all CTAs of a
+// cluster are resident together, and no CTA waits on a software flag.
+//
+// Iteration (3 cluster barriers):
+//   q = Ahat p, gamma = p.q | alpha = rho/gamma; r -= alpha q; y += alpha p;
+//   rho' = r.r (and ||S r||^2) | beta = rho'/rho; stop test; p = r + beta p |
+#include "cps_internal.cuh"
+
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cmath>
+
+namespace cg = cooperative_groups;
+
+namespace cps {
+namespace {
+
+constexpr int kClusterThreads = 1024;
+constexpr int kCheck = 8;
+
+struct ClusterArgs {
+    const double* a;        // scaled off-diagonals [3][n]
+    const int32_t* col;     // [3][n]
+    const double* s;        // [n]
+    const double* b;        // [n]
+    const double* x;        // [n] initial guess
+    double* y_out;          // [n] final scaled iterate
+    CgState* st;
+    int64_t n;
+    int rows;               // R, rows per CTA
+    double rtol;
+    long long max_iter;
+};
+
+// Shared-memory layout of one CTA (R rows).
+__host__ __device__ inline size_t cluster_smem_bytes(int R) {
+    return (size_t)R * (3 * sizeof(double) + 3 * sizeof(int32_t) + 5 * sizeof(double)) + 256;
+}
+
+__global__ void __launch_bounds__(kClusterThreads, 1) k_cluster_cg(ClusterArgs A) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int C = (int)cluster.num_blocks();
+    const int rank = (int)cluster.block_rank();
+    const int R = A.rows;
+    const int64_t n = A.n;
+    const int64_t r0 = (int64_t)rank * R;
+    const int nloc = (int)((r0 + R <= n) ? R : (n > r0 ? n - r0 : 0));
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    double* a_s = reinterpret_cast<double*>(smem);          // [3][R]
+    double* p_s = a_s + 3 * R;
+    double* r_s = p_s + R;
+    double* y_s = r_s + R;
+    double* q_s = y_s + R;
+    double* s_s = q_s + R;
+    int32_t* c_s = reinterpret_cast<int32_t*>(s_s + R);      // [3][R] packed (rank << 16) | local
+    __shared__ double red[4];
+    __shared__ double sh3[32][3];
+    __shared__ double sh2[32][2];
+    __shared__ double sh1[32][1];
+
+    const int tid = threadIdx.x;
+    for (int i = tid; i < nloc; i += blockDim.x) {
+        const int64_t e = r0 + i;
+        for (int j = 0; j < 3; ++j) {
+            a_s[j * R + i] = A.a[j * n + e];
+            const int32_t c = A.col[j * n + e];
+            const int cr = c / R;
+            c_s[j * R + i] = (cr << 16) | (c - cr * R);
+        }
+        const double se = A.s[e];
+        s_s[i] = se;
+        y_s[i] = se * A.x[e];
+    }
+    cluster.sync();
+
+    auto gather = [&](double* base, int32_t packed) -> double {
+        const int cr = packed >> 16, li = packed & 0xFFFF;
+        if (cr == rank) return base[li];
+        return cluster.map_shared_rank(base, cr)[li];
+    };
+    // Sum of per-CTA partials red[0..nv) over the cluster, rank order.
+    auto cluster_sum = [&](int k) -> double {
+        double t = 0.0;
+        for (int c = 0; c < C; ++c) t += cluster.map_shared_rank(red, c)[k];
+        return t;
+    };
+
+    // r = S^-1 b - Ahat y, p = r
+    double v3[3] = {0.0, 0.0, 0.0};
+    for (int i = tid; i < nloc; i += blockDim.x) {
+        double ay = y_s[i];
+        for (int j = 0; j < 3; ++j) ay = fma(a_s[j * R + i], gather(y_s, c_s[j * R + i]), ay);
+        const double be = A.b[r0 + i];
+        const double re = be / s_s[i] - ay;
+        r_s[i] = re;
+        p_s[i] = re;
+        v3[0] = fma(re, re, v3[0]);
+        v3[1] = fma(be, be, v3[1]);
+        const double t = s_s[i] * re;
+        v3[2] = fma(t, t, v3[2]);
+    }
+    block_sum<3>(v3, sh3);
+    if (tid == 0) {
+        red[0] = v3[0];
+        red[1] = v3[1];
+        red[2] = v3[2];
+    }
+    cluster.sync();
+    double rho = cluster_sum(0);
+    const double bnorm2 = cluster_sum(1);
+    double rnorm2 = cluster_sum(2);
+    const double thresh2 = A.rtol * A.rtol * bnorm2;
+    int status = CPS_OK;
+    long long it = 0;
+    bool stop = (bnorm2 == 0.0 || rnorm2 <= thresh2 || A.max_iter <= 0);
+    while (!stop) {
+        cluster.sync();     // p complete everywhere; partials of the last step read
+        double g1[1] = {0.0};
+        for (int i = tid; i < nloc; i += blockDim.x) {
+            const double pe = p_s[i];
+            double v = pe;
+            for (int j = 0; j < 3; ++j) v = fma(a_s[j * R + i], gather(p_s, c_s[j * R + i]), v);
+            q_s[i] = v;
+            g1[0] = fma(pe, v, g1[0]);
+        }
+        block_sum<1>(g1, sh1);
+        if (tid == 0) red[0] = g1[0];
+        cluster.sync();
+        const double gamma = cluster_sum(0);
+        if (!(gamma > 0.0) || !isfinite(gamma)) {
+            status = CPS_ERR_NOT_SPD;
+            break;
+        }
+        const double alpha = rho / gamma;
+        const bool check = ((it + 1) % kCheck) == 0;
+        double g2[2] = {0.0, 0.0};
+        for (int i = tid; i < nloc; i += blockDim.x) {
+            y_s[i] = fma(alpha, p_s[i], y_s[i]);
+            const double re = fma(-alpha, q_s[i], r_s[i]);
+            r_s[i] = re;
+            g2[0] = fma(re, re, g2[0]);
+            if (check) {
+                const double t = s_s[i] * re;
+                g2[1] = fma(t, t, g2[1]);
+            }
+        }
+        block_sum<2>(g2, sh2);
+        if (tid == 0) {
+            red[1] = g2[0];
+            red[2] = g2[1];
+        }
+        cluster.sync();
+        const double rho_new = cluster_sum(1);
+        ++it;
+        if (check) {
+            rnorm2 = cluster_sum(2);
+            if (rnorm2 <= thresh2) stop = true;
+        }
+        if (!(rho_new > 0.0) || it >= A.max_iter) stop = true;
+        const double beta = rho_new / rho;
+        rho = rho_new;
+        if (!stop)
+            for (int i = tid; i < nloc; i += blockDim.x) p_s[i] = fma(beta, p_s[i], r_s[i]);
+    }
+    for (int i = tid; i < nloc; i += blockDim.x) A.y_out[r0 + i] = y_s[i];
+    if (rank == 0 && tid == 0) {
+        CgState* st = A.st;
+        st->rho = rho;
+        st->bnorm2 = bnorm2;
+        st->thresh2 = thresh2;
+        st->rnorm2 = rnorm2;
+        st->iter = it;
+        st->max_iter = A.max_iter;
+        st->status = status;
+        st->done = 2;
+        st->alpha = 0.0;
+        st->beta = 0.0;
+    }
+    cluster.sync();         // no CTA leaves while others may still read its memory
+}
+
+}  // namespace
+
+// Dynamic shared memory a CTA of k_cluster_cg may use on this device: the
+// opt-in limit minus the kernel's static shared memory.
+static size_t cluster_dyn_smem_limit(int dev) {
+    int smem_optin = 0;
+    if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_cluster_cg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return (size_t)smem_optin > fa.sharedSizeBytes ? (size_t)smem_optin - fa.sharedSizeBytes : 0;
+}
+
+// Largest system the cluster path takes on this GPU (0: not available).
+int64_t cluster_max_rows(cps_ctx ctx) {
+    const size_t lim = cluster_dyn_smem_limit(ctx->device);
+    const size_t per_row = cluster_smem_bytes(1) - 256;
+    if (lim <= 256) return 0;
+    const int64_t R = (int64_t)((lim - 256) / per_row);
+    return std::min<int64_t>(R, 0xFFFF) * 16;
+}
+
+// Runs a whole FP64 Jacobi solve (from x) in one cluster launch; leaves the
+// scaled iterate in y and the final scalars in s->st (done = 2).
+int cluster_solve(cps_sys s, const double* b, const double* x, double* y, double rtol,
+                  long long max_iter, cudaStream_t stream) {
+    static bool configured[64] = {false};
+    const int64_t n = s->nt;
+    int csize = 16;
+    cudaError_t e = cudaSuccess;
+    const int dev = s->ctx->device;
+    const size_t lim = cluster_dyn_smem_limit(dev);
+    if (!configured[dev & 63]) {
+        e = cudaFuncSetAttribute(k_cluster_cg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_cluster_cg, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            s->ctx->last_error = std::string("cluster path: ") + cudaGetErrorString(e);
+            return CPS_ERR_ARG;
+        }
+        configured[dev & 63] = true;
+    }
+    ClusterArgs A;
+    A.a = s->a;
+    A.col = s->col;
+    A.s = s->s;
+    A.b = b;
+    A.x = x;
+    A.y_out = y;
+    A.st = s->st;
+    A.n = n;
+    A.rtol = rtol;
+    A.max_iter = max_iter;
+    for (; csize >= 2; csize /= 2) {
+        const int R = (int)((n + csize - 1) / csize);
+        if (R > 0xFFFF || cluster_smem_bytes(R) > lim) continue;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(csize, 1, 1);
+        cfg.blockDim = dim3(kClusterThreads, 1, 1);
+        cfg.dynamicSmemBytes = cluster_smem_bytes(R);
+        cfg.stream = stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = csize;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, k_cluster_cg, &cfg) != cudaSuccess ||
+            nclusters < 1) {
+            cudaGetLastError();
+            continue;
+        }
+        A.rows = R;
+        e = cudaLaunchKernelEx(&cfg, k_cluster_cg, A);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            s->ctx->last_error = std::string("cluster launch: ") + cudaGetErrorString(e);
+            return CPS_ERR_CUDA;
+        }
+        s->cluster_size = csize;
+        return CPS_OK;
+    }
+    s->ctx->last_error = "cluster path: no cluster shape fits this system";
+    return CPS_ERR_ARG;
+}
+
+}  // namespace cps

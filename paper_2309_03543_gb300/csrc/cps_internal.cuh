@@ -50,6 +50,8 @@ struct KCfg {
 struct Tuning {
     KCfg k[3];
     bool done = false;
+    int path = 0;            // FP64 Jacobi: 0 graph-replayed kernels, 1 one-cluster launch
+    bool path_done = false;
 };
 
 // Device error flag written by the assembly kernels (first error wins).
@@ -195,6 +197,7 @@ struct cps_sys_s {
     cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     int64_t graph_nodes[2][2] = {{0, 0}, {0, 0}};
     cps::Tuning tune[2];        // per precision (CPS_FP64, CPS_MIXED)
+    int cluster_size = 0;       // CTAs of the last one-cluster solve
 };
 
 #define CPS_CUDA_TRY(ctx, call)                                                        \
@@ -232,6 +235,9 @@ int adjoint_impl(cps_sys sys, const double* x, const double* g, double* lambda, 
                  double* dtheta, double rtol, int64_t max_iter, cps_stats* stats,
                  cudaStream_t stream);
 int matvec_impl(cps_sys sys, const double* x, double* y, cudaStream_t stream);
+int64_t cluster_max_rows(cps_ctx ctx);
+int cluster_solve(cps_sys s, const double* b, const double* x, double* y, double rtol,
+                  long long max_iter, cudaStream_t stream);
 int export_impl(cps_sys sys, double* diag, int32_t* col, double* val, cudaStream_t stream);
 void free_sys(cps_sys sys);
 

@@ -341,6 +341,51 @@ static void fill_stats(cps_stats* stats, int64_t iters, double rel, int status, 
 
 // ------------------------------------------------------------------ FP64
 
+// For Jacobi solves of systems that fit one cluster's shared memory, times a
+// 64-iteration run of each path (graph-replayed streaming kernels, and the
+// one-launch cluster solve) from x = 0 and keeps the faster one.
+static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
+                            cudaStream_t stream) {
+    Tuning& t = s->tune[CPS_FP64];
+    t.path_done = true;
+    t.path = 0;
+    if (s->precond != CPS_PC_JACOBI || s->nt > cluster_max_rows(s->ctx)) return CPS_OK;
+    const long long probe = 64;
+    cudaEvent_t e0, e1;
+    CPS_CUDA_TRY(s->ctx, cudaEventCreate(&e0));
+    CPS_CUDA_TRY(s->ctx, cudaEventCreate(&e1));
+    double per_iter[2] = {0.0, 0.0};
+    int rc = CPS_OK;
+    cudaGraphExec_t ge = nullptr;
+    int64_t per_chunk = 0, dummy = 0;
+    rc = get_chunk_graph<double>(s, CPS_FP64, v, &ge, &per_chunk);
+    for (int path = 0; path < 2 && rc == CPS_OK; ++path) {
+        for (int rep = 0; rep < 2 && rc == CPS_OK; ++rep) {   // first one warms up
+            CPS_CUDA_TRY(s->ctx, cudaMemsetAsync(s->wx, 0, sizeof(double) * s->nt, stream));
+            CgState h{};
+            CPS_CUDA_TRY(s->ctx, cudaEventRecord(e0, stream));
+            if (path == 0) {
+                k_init64<<<s->grid, kBlock, 0, stream>>>(b, s->wx, v.s, v.a, v.col, s->nt, v.y, v.r,
+                                                         v.p0, 0.0, probe, 1, s->partials, s->st);
+                rc = run_chunks<double>(s, CPS_FP64, v, stream, &h, &dummy);
+            } else {
+                rc = cluster_solve(s, b, s->wx, v.y, 0.0, probe, stream);
+                if (rc == CPS_OK) rc = read_state(s, stream, &h);
+            }
+            CPS_CUDA_TRY(s->ctx, cudaEventRecord(e1, stream));
+            CPS_CUDA_TRY(s->ctx, cudaEventSynchronize(e1));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            per_iter[path] = ms / (double)(h.iter > 0 ? h.iter : 1);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc == CPS_ERR_ARG) rc = CPS_OK;        // no cluster shape: keep the graph path
+    else if (rc == CPS_OK && per_iter[1] > 0.0 && per_iter[1] < per_iter[0]) t.path = 1;
+    return rc;
+}
+
 static int solve_fp64(cps_sys s, const double* b, double* x, double rtol, int64_t max_iter,
                       cps_stats* stats, cudaStream_t stream) {
     const int64_t n = s->nt;
@@ -354,6 +399,11 @@ static int solve_fp64(cps_sys s, const double* b, double* x, double rtol, int64_
         int rc = autotune<double>(s, CPS_FP64, v, stream);
         if (rc) return rc;
     }
+    if (!ic0 && !s->tune[CPS_FP64].path_done) {
+        int rc = choose_fp64_path(s, v, b, stream);
+        if (rc) return rc;
+    }
+    const bool cluster = !ic0 && s->tune[CPS_FP64].path == 1;
     if (ic0) {
         k_permute_in<<<g, kBlock, 0, stream>>>(b, x, s->perm, n, s->wb, s->wx);
         ++launches;
@@ -366,6 +416,23 @@ static int solve_fp64(cps_sys s, const double* b, double* x, double rtol, int64_
     // has met rtol but the true residual has not (rounding drift).
     for (int restart = 0; restart < 8; ++restart) {
         const long long budget = (long long)(max_iter - total);
+        if (cluster) {
+            int rc = cluster_solve(s, bb, xx, v.y, rtol, budget, stream);
+            if (rc) return rc;
+            ++launches;
+            CgState hc{};
+            rc = read_state(s, stream, &hc);
+            if (rc) return rc;
+            total += hc.iter;
+            status = hc.status;
+            k_final64<<<g, kBlock, 0, stream>>>(bb, v.y, v.s, v.a, v.col, n, xx, s->partials, s->st);
+            ++launches;
+            CPS_CUDA_TRY(s->ctx, cudaGetLastError());
+            rc = read_state(s, stream, &h);
+            if (rc) return rc;
+            if (status != CPS_OK || h.rnorm2 <= h.thresh2 || total >= max_iter) break;
+            continue;
+        }
         k_init64<<<g, kBlock, 0, stream>>>(bb, xx, v.s, v.a, v.col, n, v.y, v.r, v.p0, rtol,
                                             budget, ic0 ? 0 : 1, s->partials, s->st);
         ++launches;

@@ -300,3 +300,43 @@ def test_batched_solve_matches_oracle_per_system(ctx):
             assert st.rel_res <= 1e-10
     for s in systems:
         s.free()
+
+
+@pytest.mark.parametrize("name", ["block37", "channel64", "defect20"])
+def test_cluster_path_matches_oracle(ctx, name):
+    """The one-launch cluster solve (system held in the cluster's shared
+    memory, neighbours read through distributed shared memory) against the
+    oracle, and against the streaming path on the same system."""
+    p = PROBLEMS[name]
+    s = assemble(ctx, p)
+    b = synth.rhs(p.mesh, 23)
+    bt = torch.as_tensor(b, device="cuda")
+    s.set_solver_path(cps.PATH_CLUSTER)
+    x, st = s.solve(bt, rtol=1e-12, check=False)
+    assert st.status in (0, cps._cps.ERR_NOT_CONVERGED) and st.rel_res < 1e-10
+    xo, _, _ = oracle.solve_problem(p, b, rtol=1e-13)
+    err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
+    assert err < 1e-9, err
+    s.set_solver_path(cps.PATH_STREAM)
+    x2, st2 = s.solve(bt, rtol=1e-12, check=False)
+    assert abs(st2.iters - st.iters) <= max(8, 0.02 * st.iters)
+    # warm start and zero right-hand side on the cluster path
+    s.set_solver_path(cps.PATH_CLUSTER)
+    x3 = x.clone()
+    _, st3 = s.solve(bt, x=x3, rtol=1e-8)
+    assert st3.iters == 0
+    z = torch.ones_like(bt)
+    _, st4 = s.solve(torch.zeros_like(bt), x=z)
+    assert torch.all(z == 0)
+    s.set_solver_path(cps.PATH_AUTO)
+    x5, st5 = s.solve(bt, rtol=1e-10)
+    assert st5.rel_res <= 1e-10
+    s.free()
+
+
+def test_cluster_path_rejects_oversized_systems(ctx):
+    p = synth.channel_block_problem(300, seed=1)
+    s = assemble(ctx, p)
+    with pytest.raises(cps.CpsError):
+        s.set_solver_path(cps.PATH_CLUSTER)
+    s.free()
