@@ -218,6 +218,39 @@ int cps_set_solver_path(cps_sys sys, int path);
  * the defaults (unroll 2, 8 blocks per SM). */
 int cps_get_tuning(cps_sys sys, int precision, int32_t* unroll, int32_t* grid);
 
+/* Allocation-free solve of a matrix the caller already holds in the padded
+ * ELL form that cps_export_matrix writes (no counterpart in the paper; it is
+ * an interface for callers that cannot allocate device memory).  Such callers
+ * exist: code running inside a host that owns all device memory through its
+ * own pool, code that must not call cudaMalloc/cudaFree because those calls
+ * synchronise the device, and code whose memory budget is already spent.
+ * This call needs no handle and allocates nothing (no cudaMalloc, cudaFree,
+ * pinned host memory, events or graphs): its working vectors live in one
+ * fixed device array inside libcps.so (about 4.3 MB, held on every device
+ * that loads the library until the process exits).
+ *   n                 rows, 0 <= n <= 65536; a larger n returns CPS_ERR_ARG
+ *                     before any work is enqueued
+ *   diag[n], col[3n], val[3n]   device arrays: diagonal, then slot-major
+ *                     neighbour columns and values (s*n + e is slot s of row
+ *                     e; an unused slot has col = e, val = 0); A must be
+ *                     symmetric with a positive diagonal
+ *   b[n], x[n]        device arrays: right-hand side; initial guess in,
+ *                     solution out
+ *   rtol, max_iter    as cps_solve (FP64 Jacobi-PCG, true-residual stop)
+ *   stats             host pointer, may be NULL
+ *   stream            cudaStream_t on the current device
+ * The first call on a device looks up the device address of the array
+ * (cudaGetSymbolAddress) for that device, which is the current device of the
+ * calling thread; make that first call before any stream capture.  Every
+ * call on a device shares the same array and resets the parts that must
+ * start at zero, so calls whose work overlaps on the GPU (different streams
+ * or host threads at the same time) race with each other: serialise them.
+ * Errors: CPS_ERR_ARG (size, NULL, column out of range), CPS_ERR_NOT_SPD
+ * (diagonal <= 0 or p.Ap <= 0), CPS_ERR_NOT_CONVERGED, CPS_ERR_CUDA. */
+int cps_solve_ell_noalloc(int64_t n, const double* diag, const int32_t* col, const double* val,
+                          const double* b, double* x, double rtol, int64_t max_iter,
+                          cps_stats* stats, void* stream);
+
 /* y = A x for the assembled matrix (device pointers, FP64). */
 int cps_matvec(cps_sys sys, const double* x, double* y, void* stream);
 

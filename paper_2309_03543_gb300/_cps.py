@@ -67,6 +67,8 @@ SIGNATURES = {
     "cps_matvec": (_I, [_P, _P, _P, _P]),
     "cps_get_tuning": (_I, [_P, _I, _P, _P]),
     "cps_set_solver_path": (_I, [_P, _I]),
+    "cps_solve_ell_noalloc": (_I, [_I64, _P, _P, _P, _P, _P, _D, _I64, ctypes.POINTER(Stats),
+                                   _P]),
 }
 
 _lib = None
