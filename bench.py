@@ -415,15 +415,8 @@ def main():
     clocks = sampler.stop()
     t_total = sum(times)
     cell_iters = nt * sum(iters)
-    if pg is not None:
-        tt = torch.tensor([t_total, cell_iters], dtype=torch.float64, device=dev)
-        import torch.distributed as dist
-        gathered = [torch.zeros_like(tt) for _ in range(world)]
-        dist.all_gather(gathered, tt)
-        t_max = max(float(g[0]) for g in gathered)
-        total_cell_iters = sum(float(g[1]) for g in gathered)
-    else:
-        t_max, total_cell_iters = t_total, cell_iters
+    from paper_2309_03543_gb300.dist import aggregate
+    t_max, total_cell_iters = aggregate(t_total, cell_iters, device=dev)
     value = total_cell_iters / t_max
 
     # ---- e2e: host buffers in, host result out, through the public API

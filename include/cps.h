@@ -66,6 +66,8 @@ extern "C" {
 
 #define CPS_PC_JACOBI 1     /* diagonal preconditioner */
 #define CPS_PC_IC0 2        /* IC(0) in a multicolour order of the cells */
+#define CPS_PC_REDUCED 3    /* two-colourable cell graphs: eliminate one colour
+                               exactly, CG on the other colour's Schur complement */
 
 #define CPS_FP64 0          /* all storage and arithmetic in binary64 */
 #define CPS_MIXED 1         /* binary32 matrix/vectors inside FP64 refinement */
@@ -129,7 +131,13 @@ int cps_assemble(cps_ctx ctx, const double* xy, int64_t nv, const int32_t* tri, 
 /* Select the preconditioner (Sec. 3.2.2 uses incomplete Cholesky):
  * CPS_PC_JACOBI, or CPS_PC_IC0 = IC(0) factored once on the pattern of A in a
  * multicolour order of the cells (two colours on the lattice's bipartite cell
- * graph).  The factor is computed here, once, on the device. */
+ * graph).  The factor is computed here, once, on the device.
+ * CPS_PC_REDUCED (FP64 solves only): for a cell graph with two colours R, B
+ * (no two neighbours share a colour), the R unknowns are eliminated exactly
+ * from the diagonally scaled system and CG runs on S = I - E^T E over the B
+ * cells (E = the scaled R-B couplings); x_R is recovered afterwards.  The
+ * solution is that of A x = b; CPS_ERR_ARG if the graph needs more than two
+ * colours. */
 int cps_set_precond(cps_sys sys, int precond, void* stream);
 
 /* Free a system and all device memory it owns.  A handle that was already
@@ -215,8 +223,14 @@ int cps_set_solver_path(cps_sys sys, int path);
  * grid in blocks of 256 threads, for the SpMV kernel, the residual update and
  * (CPS_FP64 only) the direction update.  The tuner times every candidate on
  * the system's own data at its first solve; systems below 131072 cells keep
- * the defaults (unroll 2, 8 blocks per SM). */
-int cps_get_tuning(cps_sys sys, int precision, int32_t* unroll, int32_t* grid);
+ * the defaults (unroll 2, 8 blocks per SM).  For CPS_FP64 Jacobi solves it
+ * also times the ways of running the loop: flags (may be NULL) receives
+ * {one-cluster launch chosen, matrix held in persisting L2, programmatic
+ * dependent launch}, probe_us (may be NULL) the microseconds per iteration
+ * measured for {streaming, one cluster, streaming + L2 window, streaming +
+ * programmatic launch} (0 where not tried). */
+int cps_get_tuning(cps_sys sys, int precision, int32_t* unroll, int32_t* grid, int32_t* flags,
+                   double* probe_us);
 
 /* Allocation-free solve of a matrix the caller already holds in the padded
  * ELL form that cps_export_matrix writes (no counterpart in the paper; it is

@@ -40,6 +40,9 @@ int cps_create(cps_ctx* out, int device) {
     int l2 = 0;
     cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device);
     c->l2_bytes = (size_t)l2;
+    int lp = 0;
+    cudaDeviceGetAttribute(&lp, cudaDevAttrMaxPersistingL2CacheSize, device);
+    c->l2_persist_max = (size_t)lp;
     *out = c;
     return CPS_OK;
 }
@@ -158,7 +161,8 @@ int cps_set_solver_path(cps_sys sys, int path) {
     return CPS_OK;
 }
 
-int cps_get_tuning(cps_sys sys, int precision, int32_t* unroll, int32_t* grid) {
+int cps_get_tuning(cps_sys sys, int precision, int32_t* unroll, int32_t* grid, int32_t* flags,
+                   double* probe_us) {
     if (!sys || !unroll || !grid || (precision != CPS_FP64 && precision != CPS_MIXED))
         return CPS_ERR_ARG;
     const cps::Tuning& t = sys->tune[precision];
@@ -166,6 +170,13 @@ int cps_get_tuning(cps_sys sys, int precision, int32_t* unroll, int32_t* grid) {
         unroll[k] = t.done ? t.k[k].unroll : 0;
         grid[k] = t.done ? t.k[k].grid : 0;
     }
+    if (flags) {
+        flags[0] = t.path_done && t.path == 1;
+        flags[1] = t.path_done && t.l2win;
+        flags[2] = t.path_done && t.pdl;
+    }
+    if (probe_us)
+        for (int k = 0; k < 4; ++k) probe_us[k] = t.probe_us[k];
     return CPS_OK;
 }
 

@@ -349,7 +349,8 @@ static int dev_alloc(cps_ctx ctx, T** p, size_t n) {
 
 void free_sys(cps_sys s) {
     if (!s) return;
-    void* bufs[] = {s->s,     s->diag,  s->a,     s->col,   s->a32,     s->s32,      s->gfac,
+    // s->col lives inside s->a's allocation (one range for the L2 window)
+    void* bufs[] = {s->s,     s->diag,  s->a,     s->a32,     s->s32,      s->gfac,
                     s->dxi,   s->slot_kind, s->perm, s->iperm, s->pa,  s->pcol,     s->pl,
                     s->pdinv, s->ps,    s->pa32,  s->pl32,  s->pdinv32, s->ps32,     s->wy,
                     s->wr,    s->wp0,   s->wp1,   s->wq,    s->wz,      s->wb,       s->wx,
@@ -407,8 +408,16 @@ int assemble_impl(cps_ctx ctx, const double* xy, int64_t nv, const int32_t* tri,
     } while (0)
     TRY_ALLOC(s->s, nt);
     TRY_ALLOC(s->diag, nt);
-    TRY_ALLOC(s->a, 3 * nt);
-    TRY_ALLOC(s->col, 3 * nt);
+    // Off-diagonal values and columns in one allocation: a [3 nt] doubles,
+    // then col [3 nt] int32 (256-byte aligned), so that one L2 access-policy
+    // window covers the whole matrix the iteration streams.
+    {
+        const size_t a_elems = ((size_t)3 * nt + 31) / 32 * 32;
+        const size_t col_elems = ((size_t)3 * nt * sizeof(int32_t) + sizeof(double) - 1) / sizeof(double);
+        TRY_ALLOC(s->a, a_elems + col_elems);
+        s->col = reinterpret_cast<int32_t*>(s->a + a_elems);
+        s->mat_bytes = (a_elems + col_elems) * sizeof(double);
+    }
     TRY_ALLOC(s->a32, 3 * nt);
     TRY_ALLOC(s->s32, nt);
     TRY_ALLOC(s->slot_kind, 3 * nt);

@@ -6,10 +6,11 @@
 // CTA k owns rows [k R, (k+1) R): its slice of the scaled matrix and of the
 // vectors y, r, p, q, s stay in its shared memory for the whole run.  The
 // SpMV reads a neighbour's p from the owning CTA's shared memory through the
-// cluster's distributed shared memory; dot products are summed per CTA, then
-// every CTA adds the C partials in rank order after a cluster barrier (the
-// same order everywhere, so all CTAs hold bit-identical alpha, beta and stop
-// decisions).  The cluster barrier is the hardware one: all CTAs of a
+// cluster's distributed shared memory.  A dot product is summed per CTA and
+// the CTA's partial is stored into a slot of every CTA's shared memory (C
+// remote stores, one per lane); after the cluster barrier each CTA adds the C
+// slots in rank order from its own shared memory (the same order everywhere,
+// so all CTAs hold bit-identical alpha, beta and stop decisions).  The cluster barrier is the hardware one: all CTAs of a
 // cluster are resident together, and no CTA waits on a software flag.
 //
 // Iteration (3 cluster barriers):
@@ -66,7 +67,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_cluster_cg(ClusterArgs A
     double* q_s = y_s + R;
     double* s_s = q_s + R;
     int32_t* c_s = reinterpret_cast<int32_t*>(s_s + R);      // [3][R] packed (rank << 16) | local
-    __shared__ double red[4];
+    __shared__ double red[3][16];   // red[k][c]: partial k of CTA c
     __shared__ double sh3[32][3];
     __shared__ double sh2[32][2];
     __shared__ double sh1[32][1];
@@ -91,10 +92,14 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_cluster_cg(ClusterArgs A
         if (cr == rank) return base[li];
         return cluster.map_shared_rank(base, cr)[li];
     };
-    // Sum of per-CTA partials red[0..nv) over the cluster, rank order.
+    // This CTA's partial k (held by every thread after block_sum) goes to slot
+    // [k][rank] of every CTA; lane c of warp 0 stores to CTA c.
+    auto push = [&](int k, double v) {
+        if (tid < C) cluster.map_shared_rank(&red[k][0], tid)[rank] = v;
+    };
     auto cluster_sum = [&](int k) -> double {
         double t = 0.0;
-        for (int c = 0; c < C; ++c) t += cluster.map_shared_rank(red, c)[k];
+        for (int c = 0; c < C; ++c) t += red[k][c];
         return t;
     };
 
@@ -113,11 +118,9 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_cluster_cg(ClusterArgs A
         v3[2] = fma(t, t, v3[2]);
     }
     block_sum<3>(v3, sh3);
-    if (tid == 0) {
-        red[0] = v3[0];
-        red[1] = v3[1];
-        red[2] = v3[2];
-    }
+    push(0, v3[0]);
+    push(1, v3[1]);
+    push(2, v3[2]);
     cluster.sync();
     double rho = cluster_sum(0);
     const double bnorm2 = cluster_sum(1);
@@ -137,7 +140,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_cluster_cg(ClusterArgs A
             g1[0] = fma(pe, v, g1[0]);
         }
         block_sum<1>(g1, sh1);
-        if (tid == 0) red[0] = g1[0];
+        push(0, g1[0]);
         cluster.sync();
         const double gamma = cluster_sum(0);
         if (!(gamma > 0.0) || !isfinite(gamma)) {
@@ -158,10 +161,8 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_cluster_cg(ClusterArgs A
             }
         }
         block_sum<2>(g2, sh2);
-        if (tid == 0) {
-            red[1] = g2[0];
-            red[2] = g2[1];
-        }
+        push(1, g2[0]);
+        push(2, g2[1]);
         cluster.sync();
         const double rho_new = cluster_sum(1);
         ++it;

@@ -52,6 +52,9 @@ struct Tuning {
     bool done = false;
     int path = 0;            // FP64 Jacobi: 0 graph-replayed kernels, 1 one-cluster launch
     bool path_done = false;
+    bool l2win = false;      // FP64 Jacobi stream path: matrix held in persisting L2
+    bool pdl = false;        // FP64 Jacobi stream path: programmatic dependent launch
+    double probe_us[4] = {0, 0, 0, 0};   // us/iteration: stream, cluster, +L2, +PDL
 };
 
 // Device error flag written by the assembly kernels (first error wins).
@@ -132,6 +135,8 @@ struct cps_ctx_s {
     int num_sms = 0;
     int max_threads_per_sm = 2048;
     size_t l2_bytes = 0;
+    size_t l2_persist_max = 0;   // cudaDevAttrMaxPersistingL2CacheSize
+    size_t l2_persist_set = 0;   // persisting L2 limit this process has set
     std::string last_error;
     std::unordered_set<cps_sys_s*> systems;   // live systems, freed with the context
 };
@@ -153,8 +158,9 @@ struct cps_sys_s {
     // S = diag(s), s = sqrt(diag(A)); slot-major arrays [3][nt].
     double* s = nullptr;        // [nt]
     double* diag = nullptr;     // [nt] unscaled diagonal (export / info)
-    double* a = nullptr;        // [3*nt] scaled off-diagonals
+    double* a = nullptr;        // [3*nt] scaled off-diagonals (allocation also holds col)
     int32_t* col = nullptr;     // [3*nt] column (= row for an unused slot)
+    size_t mat_bytes = 0;       // bytes of the a + col allocation
     float* a32 = nullptr;       // [3*nt] binary32 copy of a (mixed precision)
     float* s32 = nullptr;       // [nt]
     // Adjoint: per slot dT/dxi_e, per cell dxi/dtheta (CP2, cell fields).
@@ -194,8 +200,11 @@ struct cps_sys_s {
 
     // CUDA graphs of a chunk of iterations, per (precision, preconditioner).
     cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
-    int64_t graph_nodes[2][2] = {{0, 0}, {0, 0}};
+    // [precision][0 Jacobi, 1 IC(0), 2 reduced system]
+    cudaGraphExec_t graph[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    int64_t graph_nodes[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    bool graph_l2win[2][3] = {{false, false, false}, {false, false, false}};
+    bool graph_pdl[2][3] = {{false, false, false}, {false, false, false}};
     cps::Tuning tune[2];        // per precision (CPS_FP64, CPS_MIXED)
     int cluster_size = 0;       // CTAs of the last one-cluster solve
 };

@@ -106,7 +106,28 @@ Run<float> make_run<float>(cps_sys s) {
 
 // ------------------------------------------------------------ launch configs
 // Each streaming kernel of the iteration runs with a (rows-per-thread
-// unroll U, grid) pair picked by the autotuner below.
+// unroll U, grid) pair picked by the autotuner below, and is launched with
+// programmatic stream serialisation so that it can be scheduled during its
+// predecessor's reduction tail (see pdl_wait / pdl_trigger).
+
+// Whether the launches being enqueued use programmatic serialisation (set
+// around a graph capture from the system's tuning; off for direct launches).
+static thread_local bool g_pdl = false;
+
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*kernel)(KArgs...), int grid, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid, 1, 1);
+    cfg.blockDim = dim3(kBlock, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = g_pdl ? at : nullptr;
+    cfg.numAttrs = g_pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
 
 template <typename V>
 static void launch_a(const KCfg& c, const Run<V>& v, cps_sys s, cudaStream_t st);
@@ -114,27 +135,27 @@ static void launch_a(const KCfg& c, const Run<V>& v, cps_sys s, cudaStream_t st)
 template <>
 void launch_a<double>(const KCfg& c, const Run<double>& v, cps_sys s, cudaStream_t st) {
     switch (c.unroll) {
-        case 1: k_spmv_dot<double, 1><<<c.grid, kBlock, 0, st>>>(v.a, v.col, v.p0, v.q, v.n, s->partials, s->st); break;
-        case 4: k_spmv_dot<double, 4><<<c.grid, kBlock, 0, st>>>(v.a, v.col, v.p0, v.q, v.n, s->partials, s->st); break;
-        default: k_spmv_dot<double, 2><<<c.grid, kBlock, 0, st>>>(v.a, v.col, v.p0, v.q, v.n, s->partials, s->st); break;
+        case 1: launch_pdl(k_spmv_dot<double, 1>, c.grid, st, v.a, v.col, v.p0, v.q, v.n, s->partials, s->st); break;
+        case 4: launch_pdl(k_spmv_dot<double, 4>, c.grid, st, v.a, v.col, v.p0, v.q, v.n, s->partials, s->st); break;
+        default: launch_pdl(k_spmv_dot<double, 2>, c.grid, st, v.a, v.col, v.p0, v.q, v.n, s->partials, s->st); break;
     }
 }
 
 template <>
 void launch_a<float>(const KCfg& c, const Run<float>& v, cps_sys s, cudaStream_t st) {
     switch (c.unroll) {
-        case 1: k_cg_a<float, 1><<<c.grid, kBlock, 0, st>>>(v.a, v.col, v.z, v.p0, v.p1, v.y, v.q, v.n, s->partials, s->st); break;
-        case 4: k_cg_a<float, 4><<<c.grid, kBlock, 0, st>>>(v.a, v.col, v.z, v.p0, v.p1, v.y, v.q, v.n, s->partials, s->st); break;
-        default: k_cg_a<float, 2><<<c.grid, kBlock, 0, st>>>(v.a, v.col, v.z, v.p0, v.p1, v.y, v.q, v.n, s->partials, s->st); break;
+        case 1: launch_pdl(k_cg_a<float, 1>, c.grid, st, v.a, v.col, v.z, v.p0, v.p1, v.y, v.q, v.n, s->partials, s->st); break;
+        case 4: launch_pdl(k_cg_a<float, 4>, c.grid, st, v.a, v.col, v.z, v.p0, v.p1, v.y, v.q, v.n, s->partials, s->st); break;
+        default: launch_pdl(k_cg_a<float, 2>, c.grid, st, v.a, v.col, v.z, v.p0, v.p1, v.y, v.q, v.n, s->partials, s->st); break;
     }
 }
 
 template <typename V, bool NORM, bool JACOBI>
 static void launch_b_u(const KCfg& c, const Run<V>& v, cps_sys s, cudaStream_t st) {
     switch (c.unroll) {
-        case 1: k_cg_b<V, NORM, JACOBI, 1><<<c.grid, kBlock, 0, st>>>(v.r, v.q, v.s, v.n, s->partials, s->st); break;
-        case 4: k_cg_b<V, NORM, JACOBI, 4><<<c.grid, kBlock, 0, st>>>(v.r, v.q, v.s, v.n, s->partials, s->st); break;
-        default: k_cg_b<V, NORM, JACOBI, 2><<<c.grid, kBlock, 0, st>>>(v.r, v.q, v.s, v.n, s->partials, s->st); break;
+        case 1: launch_pdl(k_cg_b<V, NORM, JACOBI, 1>, c.grid, st, v.r, v.q, v.s, v.n, s->partials, s->st); break;
+        case 4: launch_pdl(k_cg_b<V, NORM, JACOBI, 4>, c.grid, st, v.r, v.q, v.s, v.n, s->partials, s->st); break;
+        default: launch_pdl(k_cg_b<V, NORM, JACOBI, 2>, c.grid, st, v.r, v.q, v.s, v.n, s->partials, s->st); break;
     }
 }
 
@@ -149,9 +170,9 @@ static void launch_b(const KCfg& c, const Run<V>& v, bool norm, cps_sys s, cudaS
 
 static void launch_c(const KCfg& c, const Run<double>& v, cps_sys s, cudaStream_t st) {
     switch (c.unroll) {
-        case 1: k_cg_c<double, 1><<<c.grid, kBlock, 0, st>>>(v.y, v.p0, v.z, v.n, s->st); break;
-        case 4: k_cg_c<double, 4><<<c.grid, kBlock, 0, st>>>(v.y, v.p0, v.z, v.n, s->st); break;
-        default: k_cg_c<double, 2><<<c.grid, kBlock, 0, st>>>(v.y, v.p0, v.z, v.n, s->st); break;
+        case 1: launch_pdl(k_cg_c<double, 1>, c.grid, st, v.y, v.p0, v.z, v.n, s->st); break;
+        case 4: launch_pdl(k_cg_c<double, 4>, c.grid, st, v.y, v.p0, v.z, v.n, s->st); break;
+        default: launch_pdl(k_cg_c<double, 2>, c.grid, st, v.y, v.p0, v.z, v.n, s->st); break;
     }
 }
 
@@ -229,14 +250,14 @@ static int64_t enqueue_precond(cps_sys s, const Run<V>& v, cudaStream_t st) {
     const int g = s->grid;
     int64_t launches = 0;
     for (int c = 1; c < C; ++c, ++launches)
-        k_ic0_fwd<V><<<g, kBlock, 0, st>>>(v.l, v.col, v.dinv, v.r, v.z, v.n, cs[c], cs[c + 1],
-                                           cs[1], c == C - 1 ? 1 : 0, c, s->partials, s->st);
+        launch_pdl(k_ic0_fwd<V>, g, st, v.l, v.col, v.dinv, v.r, v.z, v.n, cs[c], cs[c + 1], cs[1],
+                   c == C - 1 ? 1 : 0, c, s->partials, s->st);
     for (int c = C - 2; c >= 0; --c, ++launches)
-        k_ic0_bwd<V><<<g, kBlock, 0, st>>>(v.l, v.col, v.dinv, v.r, v.z, v.n, cs[c], cs[c + 1],
-                                           C, c, s->partials, s->st);
+        launch_pdl(k_ic0_bwd<V>, g, st, v.l, v.col, v.dinv, v.r, v.z, v.n, cs[c], cs[c + 1], C, c,
+                   s->partials, s->st);
     if (C == 1) {
-        k_ic0_bwd<V><<<g, kBlock, 0, st>>>(v.l, v.col, v.dinv, v.r, v.z, v.n, cs[0], cs[1], C, 0,
-                                           s->partials, s->st);
+        launch_pdl(k_ic0_bwd<V>, g, st, v.l, v.col, v.dinv, v.r, v.z, v.n, cs[0], cs[1], C, 0,
+                   s->partials, s->st);
         ++launches;
     }
     return launches;
@@ -256,19 +277,60 @@ static int64_t enqueue_iteration(cps_sys s, const Run<V>& v, int prec, bool norm
     return nl;
 }
 
+// The matrix of a FP64 Jacobi run (values and columns, one allocation) as a
+// persisting L2 access-policy window: the iteration re-reads it every time,
+// and at up to ~100 MB it fits GB300's 129 MB L2 next to the streamed
+// vectors.  The context's persisting-L2 limit is raised once to cover it.
+static bool l2_window_fits(cps_sys s) {
+    return s->ctx->l2_persist_max > 0 && s->mat_bytes <= s->ctx->l2_persist_max;
+}
+
+static int set_l2_window(cps_sys s, cudaStream_t st, bool on) {
+    cudaStreamAttrValue v = {};
+    if (on) {
+        if (s->ctx->l2_persist_set < s->mat_bytes) {
+            CPS_CUDA_TRY(s->ctx, cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, s->mat_bytes));
+            s->ctx->l2_persist_set = s->mat_bytes;
+        }
+        v.accessPolicyWindow.base_ptr = s->a;
+        v.accessPolicyWindow.num_bytes = s->mat_bytes;
+        v.accessPolicyWindow.hitRatio = 1.0f;
+        v.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    } else {
+        v.accessPolicyWindow.num_bytes = 0;
+        v.accessPolicyWindow.hitProp = cudaAccessPropertyNormal;
+        v.accessPolicyWindow.missProp = cudaAccessPropertyNormal;
+    }
+    CPS_CUDA_TRY(s->ctx, cudaStreamSetAttribute(st, cudaStreamAttributeAccessPolicyWindow, &v));
+    return CPS_OK;
+}
+
 template <typename V>
 static int get_chunk_graph(cps_sys s, int prec, const Run<V>& v, cudaGraphExec_t* out,
                            int64_t* per_chunk) {
     const int pc = v.l ? 1 : 0;
+    const bool win = prec == CPS_FP64 && pc == 0 && s->tune[CPS_FP64].l2win;
+    const bool pdl = prec == CPS_FP64 && pc == 0 && s->tune[CPS_FP64].pdl;
+    if (s->graph[prec][pc] && (s->graph_l2win[prec][pc] != win || s->graph_pdl[prec][pc] != pdl)) {
+        cudaGraphExecDestroy(s->graph[prec][pc]);
+        s->graph[prec][pc] = nullptr;
+    }
     cudaGraphExec_t& ge = s->graph[prec][pc];
     int64_t nl = 0;
     if (!ge) {
         int rc = ensure_capture_stream(s);
         if (rc) return rc;
+        rc = set_l2_window(s, s->cap_stream, win);
+        if (rc) return rc;
+        s->graph_l2win[prec][pc] = win;
+        s->graph_pdl[prec][pc] = pdl;
         cudaGraph_t graph = nullptr;
         CPS_CUDA_TRY(s->ctx, cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+        g_pdl = pdl;
         for (int k = 0; k < kChunk; ++k)
             nl += enqueue_iteration<V>(s, v, prec, (k % kCheckEvery) == kCheckEvery - 1, s->cap_stream);
+        g_pdl = false;
         cudaError_t le = cudaGetLastError();
         cudaError_t ce = cudaStreamEndCapture(s->cap_stream, &graph);
         if (le != cudaSuccess || ce != cudaSuccess) {
@@ -285,6 +347,10 @@ static int get_chunk_graph(cps_sys s, int prec, const Run<V>& v, cudaGraphExec_t
             return CPS_ERR_CUDA;
         }
         s->graph_nodes[prec][pc] = nl;
+        if (win) {
+            rc = set_l2_window(s, s->cap_stream, false);
+            if (rc) return rc;
+        }
     }
     *per_chunk = s->graph_nodes[prec][pc];
     *out = ge;
@@ -349,22 +415,30 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
     Tuning& t = s->tune[CPS_FP64];
     t.path_done = true;
     t.path = 0;
-    if (s->precond != CPS_PC_JACOBI || s->nt > cluster_max_rows(s->ctx)) return CPS_OK;
-    const long long probe = 64;
+    t.l2win = false;
+    if (s->precond != CPS_PC_JACOBI) return CPS_OK;
+    const bool try_cluster = s->nt <= cluster_max_rows(s->ctx);
+    const bool try_win = !try_cluster && l2_window_fits(s) && s->nt >= kTuneMinRows;
+    const long long probe = s->nt >= kTuneMinRows ? 256 : 64;
     cudaEvent_t e0, e1;
     CPS_CUDA_TRY(s->ctx, cudaEventCreate(&e0));
     CPS_CUDA_TRY(s->ctx, cudaEventCreate(&e1));
-    double per_iter[2] = {0.0, 0.0};
+    // candidates: 0 streaming, 1 one-cluster launch, 2 streaming with the
+    // matrix in persisting L2, 3 streaming with programmatic dependent launch
+    double per_iter[4] = {0.0, 0.0, 0.0, 0.0};
     int rc = CPS_OK;
     cudaGraphExec_t ge = nullptr;
     int64_t per_chunk = 0, dummy = 0;
-    rc = get_chunk_graph<double>(s, CPS_FP64, v, &ge, &per_chunk);
-    for (int path = 0; path < 2 && rc == CPS_OK; ++path) {
+    for (int path = 0; path < 4 && rc == CPS_OK; ++path) {
+        if ((path == 1 && !try_cluster) || (path == 2 && !try_win)) continue;
+        t.l2win = path == 2;
+        t.pdl = path == 3;
+        rc = get_chunk_graph<double>(s, CPS_FP64, v, &ge, &per_chunk);
         for (int rep = 0; rep < 2 && rc == CPS_OK; ++rep) {   // first one warms up
             CPS_CUDA_TRY(s->ctx, cudaMemsetAsync(s->wx, 0, sizeof(double) * s->nt, stream));
             CgState h{};
             CPS_CUDA_TRY(s->ctx, cudaEventRecord(e0, stream));
-            if (path == 0) {
+            if (path != 1) {
                 k_init64<<<s->grid, kBlock, 0, stream>>>(b, s->wx, v.s, v.a, v.col, s->nt, v.y, v.r,
                                                          v.p0, 0.0, probe, 1, s->partials, s->st);
                 rc = run_chunks<double>(s, CPS_FP64, v, stream, &h, &dummy);
@@ -381,8 +455,20 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (rc == CPS_ERR_ARG) rc = CPS_OK;        // no cluster shape: keep the graph path
-    else if (rc == CPS_OK && per_iter[1] > 0.0 && per_iter[1] < per_iter[0]) t.path = 1;
+    if (try_win) cudaCtxResetPersistingL2Cache();
+    t.l2win = false;
+    t.pdl = false;
+    if (rc == CPS_ERR_ARG) {
+        rc = CPS_OK;        // no cluster shape: keep the graph path
+    } else if (rc == CPS_OK) {
+        int best = 0;
+        for (int c = 1; c < 4; ++c)
+            if (per_iter[c] > 0.0 && per_iter[c] < per_iter[best]) best = c;
+        t.path = best == 1 ? 1 : 0;
+        t.l2win = best == 2;
+        t.pdl = best == 3;
+    }
+    for (int c = 0; c < 4; ++c) t.probe_us[c] = 1e3 * per_iter[c];
     return rc;
 }
 
@@ -463,10 +549,124 @@ static int solve_fp64(cps_sys s, const double* b, double* x, double rtol, int64_
         CPS_CUDA_TRY(s->ctx, cudaGetLastError());
         CPS_CUDA_TRY(s->ctx, cudaStreamSynchronize(stream));
     }
+    if (!ic0 && s->tune[CPS_FP64].l2win) {
+        // release the persisting lines: later work gets the whole L2 back
+        CPS_CUDA_TRY(s->ctx, cudaStreamSynchronize(stream));
+        CPS_CUDA_TRY(s->ctx, cudaCtxResetPersistingL2Cache());
+    }
     const double rel = h.bnorm2 > 0 ? std::sqrt(h.rnorm2 / h.bnorm2) : 0.0;
     if (status == CPS_OK && h.bnorm2 > 0 && !(rel <= rtol)) status = CPS_ERR_NOT_CONVERGED;
     fill_stats(stats, total, rel, status, 1, launches);
     if (status == CPS_ERR_NOT_SPD) s->ctx->last_error = "solve: p.Ap <= 0 (matrix not SPD or NaN input)";
+    if (status == CPS_ERR_NOT_CONVERGED) s->ctx->last_error = "solve: max_iter reached";
+    return status;
+}
+
+// ------------------------------------------------------------ reduced system
+
+// CG on the black-cell Schur complement of the two-coloured scaled system
+// (kernels at the end of pcg_kernels.cuh); the red unknowns are recovered
+// exactly at the end, and the true residual of the full system decides.
+static int solve_reduced(cps_sys s, const double* b, double* x, double rtol, int64_t max_iter,
+                         cps_stats* stats, cudaStream_t stream) {
+    const int64_t n = s->nt, nR = s->colour_start[1], nB = n - nR;
+    const int g = s->grid;
+    const double* A = s->pa;
+    const int32_t* col = s->pcol;
+    const double* S = s->ps;
+    double *y = s->wy, *r = s->wr, *p = s->wp0, *q = s->wq, *t = s->wz;
+    int64_t total = 0, launches = 0;
+    k_permute_in<<<g, kBlock, 0, stream>>>(b, x, s->perm, n, s->wb, s->wx);
+    ++launches;
+    const double* bb = s->wb;
+    double* xx = s->wx;
+    // black-range views for the shared update kernels
+    Run<double> vb{};
+    vb.s = S + nR;
+    vb.y = y + nR;
+    vb.r = r + nR;
+    vb.p0 = p + nR;
+    vb.q = q + nR;
+    vb.z = r + nR;
+    vb.n = nB;
+    KCfg cb{2, grid_for(s->ctx, nB)};
+    cudaGraphExec_t& ge = s->graph[CPS_FP64][2];
+    if (!ge) {
+        int rc = ensure_capture_stream(s);
+        if (rc) return rc;
+        cudaGraph_t graph = nullptr;
+        int64_t nl = 0;
+        CPS_CUDA_TRY(s->ctx, cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+        for (int k = 0; k < kChunk; ++k) {
+            launch_pdl(k_schur_red, g, s->cap_stream, A, col, (const double*)p, t, n, nR, s->st);
+            launch_pdl(k_schur_black, g, s->cap_stream, A, col, (const double*)p,
+                       (const double*)t, q, n, nR, s->partials, s->st);
+            launch_b<double>(cb, vb, (k % kCheckEvery) == kCheckEvery - 1, s, s->cap_stream);
+            launch_c(cb, vb, s, s->cap_stream);
+            nl += 4;
+        }
+        cudaError_t le = cudaGetLastError();
+        cudaError_t ce = cudaStreamEndCapture(s->cap_stream, &graph);
+        if (le != cudaSuccess || ce != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            s->ctx->last_error = std::string("graph capture: ") +
+                                 cudaGetErrorString(le != cudaSuccess ? le : ce);
+            return CPS_ERR_CUDA;
+        }
+        cudaError_t ie = cudaGraphInstantiate(&ge, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) {
+            ge = nullptr;
+            s->ctx->last_error = std::string("graph instantiate: ") + cudaGetErrorString(ie);
+            return CPS_ERR_CUDA;
+        }
+        s->graph_nodes[CPS_FP64][2] = nl;
+    }
+    CgState h{};
+    int status = CPS_OK;
+    for (int restart = 0; restart < 8; ++restart) {
+        const long long budget = (long long)(max_iter - total);
+        k_red_recover<<<g, kBlock, 0, stream>>>(bb, xx, S, A, col, n, nR, 1, y);
+        k_black_init<<<g, kBlock, 0, stream>>>(bb, xx, S, A, col, n, nR, y, r, p, rtol, budget,
+                                               s->partials, s->st);
+        launches += 2;
+        CPS_CUDA_TRY(s->ctx, cudaGetLastError());
+        int rc = read_state(s, stream, &h);
+        if (rc) return rc;
+        if (!h.done && budget > 0) {
+            for (long long k = 0;; ++k) {
+                const int slot = (int)(k & 1);
+                CPS_CUDA_TRY(s->ctx, cudaGraphLaunch(ge, stream));
+                launches += s->graph_nodes[CPS_FP64][2];
+                CPS_CUDA_TRY(s->ctx, cudaMemcpyAsync(&s->hst[slot], s->st, sizeof(CgState),
+                                                     cudaMemcpyDeviceToHost, stream));
+                CPS_CUDA_TRY(s->ctx, cudaEventRecord(s->ev[slot], stream));
+                if (k >= 1) {
+                    CPS_CUDA_TRY(s->ctx, cudaEventSynchronize(s->ev[1 - slot]));
+                    if (s->hst[1 - slot].done) break;
+                }
+            }
+            rc = read_state(s, stream, &h);
+            if (rc) return rc;
+        }
+        total += h.iter;
+        status = h.status;
+        k_red_recover<<<g, kBlock, 0, stream>>>(bb, y, S, A, col, n, nR, 0, y);
+        k_final64<<<g, kBlock, 0, stream>>>(bb, y, S, A, col, n, xx, s->partials, s->st);
+        launches += 2;
+        CPS_CUDA_TRY(s->ctx, cudaGetLastError());
+        rc = read_state(s, stream, &h);
+        if (rc) return rc;
+        if (status != CPS_OK || h.rnorm2 <= h.thresh2 || total >= max_iter) break;
+    }
+    k_permute_out<<<g, kBlock, 0, stream>>>(s->wx, s->perm, n, x);
+    ++launches;
+    CPS_CUDA_TRY(s->ctx, cudaGetLastError());
+    CPS_CUDA_TRY(s->ctx, cudaStreamSynchronize(stream));
+    const double rel = h.bnorm2 > 0 ? std::sqrt(h.rnorm2 / h.bnorm2) : 0.0;
+    if (status == CPS_OK && h.bnorm2 > 0 && !(rel <= rtol)) status = CPS_ERR_NOT_CONVERGED;
+    fill_stats(stats, total, rel, status, 1, launches);
+    if (status == CPS_ERR_NOT_SPD) s->ctx->last_error = "solve: p.Sp <= 0 (reduced system)";
     if (status == CPS_ERR_NOT_CONVERGED) s->ctx->last_error = "solve: max_iter reached";
     return status;
 }
@@ -565,6 +765,13 @@ int solve_impl(cps_sys s, const double* b, double* x, double rtol, int64_t max_i
     if (!b || !x || !(rtol >= 0.0) || max_iter < 0) {
         s->ctx->last_error = "solve: bad argument";
         return CPS_ERR_ARG;
+    }
+    if (s->precond == CPS_PC_REDUCED) {
+        if (precision != CPS_FP64) {
+            s->ctx->last_error = "solve: the reduced-system solve is FP64 only";
+            return CPS_ERR_ARG;
+        }
+        return solve_reduced(s, b, x, rtol, max_iter, stats, stream);
     }
     if (precision == CPS_FP64) return solve_fp64(s, b, x, rtol, max_iter, stats, stream);
     if (precision == CPS_MIXED) return solve_mixed(s, b, x, rtol, max_iter, stats, stream);

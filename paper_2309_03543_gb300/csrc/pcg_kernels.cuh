@@ -23,6 +23,15 @@
 
 namespace cps {
 
+// Programmatic dependent launch: the iteration kernels are launched so that
+// the next one may start while this one finishes.  Each waits for its
+// predecessor grid (completion and memory) before touching anything the
+// predecessor writes, and lets its successor be scheduled once its own main
+// loop is done (the successor's blocks then wait on the same instruction).
+// Launched without the attribute, both instructions do nothing.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 #define CPS_GRID_STRIDE(i, n) \
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
@@ -68,6 +77,7 @@ __global__ void __launch_bounds__(kBlock) k_spmv_dot(const V* __restrict__ a,
                                                      const int32_t* __restrict__ col,
                                                      const V* __restrict__ p, V* __restrict__ q,
                                                      int64_t n, double* partials, CgState* st) {
+    pdl_wait();
     {
         const int d = st->done;
         if (d) {
@@ -88,6 +98,7 @@ __global__ void __launch_bounds__(kBlock) k_spmv_dot(const V* __restrict__ a,
             q[e] = v;
             acc = fma((double)pe[u], (double)v, acc);
         })
+    pdl_trigger();
     double t[1] = {acc};
     if (grid_sum<1>(t, partials, &st->arrive[0]) && threadIdx.x == 0) {
         const double gamma = t[0];
@@ -105,6 +116,7 @@ template <typename V, int U>
 __global__ void __launch_bounds__(kBlock) k_cg_c(V* __restrict__ y, V* __restrict__ p,
                                                  const V* __restrict__ z, int64_t n,
                                                  const CgState* st) {
+    pdl_wait();
     if (st->done == 2) return;
     const V al = (V)st->alpha;
     const V be = (V)st->beta;
@@ -131,6 +143,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_a(const V* __restrict__ a,
                                                  V* __restrict__ p1, V* __restrict__ y,
                                                  V* __restrict__ q, int64_t n, double* partials,
                                                  CgState* st) {
+    pdl_wait();
     if (st->done) return;
     const bool odd = (st->iter & 1) != 0;
     const V* __restrict__ po = odd ? p1 : p0;
@@ -153,6 +166,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_a(const V* __restrict__ a,
             q[e] = v;
             acc = fma((double)pe, (double)v, acc);
         })
+    pdl_trigger();
     double t[1] = {acc};
     if (grid_sum<1>(t, partials, &st->arrive[0]) && threadIdx.x == 0) {
         const double gamma = t[0];
@@ -170,6 +184,7 @@ template <typename V, bool NORM, bool JACOBI, int U>
 __global__ void __launch_bounds__(kBlock) k_cg_b(V* __restrict__ r, const V* __restrict__ q,
                                                  const V* __restrict__ s, int64_t n,
                                                  double* partials, CgState* st) {
+    pdl_wait();
     if (st->done) return;
     const V al = (V)st->alpha;
     double rr = 0.0, nn = 0.0;
@@ -184,6 +199,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_b(V* __restrict__ r, const V* __r
                 nn = fma(t, t, nn);
             }
         })
+    pdl_trigger();
     double t[2] = {rr, nn};
     if (grid_sum<2>(t, partials, &st->arrive[1]) && threadIdx.x == 0) {
         const long long it = st->iter + 1;
@@ -474,6 +490,7 @@ __global__ void __launch_bounds__(kBlock) k_ic0_fwd(const V* __restrict__ l,
                                                     int64_t n, int64_t cs, int64_t ce,
                                                     int64_t first_end, int last, int colour,
                                                     double* partials, const CgState* st) {
+    pdl_wait();
     if (st->done) return;
     double acc = 0.0;
     for (int64_t i = cs + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ce;
@@ -511,6 +528,7 @@ __global__ void __launch_bounds__(kBlock) k_ic0_bwd(const V* __restrict__ l,
                                                     int64_t n, int64_t cs, int64_t ce,
                                                     int ncolours, int colour, double* partials,
                                                     CgState* st) {
+    pdl_wait();
     if (st->done) return;
     double acc = 0.0;
     for (int64_t i = cs + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ce;
@@ -556,6 +574,155 @@ __global__ void __launch_bounds__(kBlock) k_ic0_bwd(const V* __restrict__ l,
         if (!(rho_new > 0.0)) st->done = 1;      // exact solution reached
         st->beta = rho_new / st->rho;
         st->rho = rho_new;
+    }
+}
+
+// ------------------------------------------------------- reduced system
+// Two-coloured cell graph, colour order: red rows [0, nR), black rows
+// [nR, n); red rows couple only to black ones and vice versa, and Ahat has a
+// unit diagonal.  Eliminating the red unknowns, y_R = bhat_R - E y_B, leaves
+// the Schur complement system on the black cells
+//   S y_B = bhat_B - E^T bhat_R,   S = I - E^T E,
+// whose residual is exactly the black part of the full residual (the red part
+// is zero by construction).  S p is applied as t_R = E p_B, q_B = p_B - E^T t_R.
+
+// y_R = S_R^-1 b_R - E y_B with y_B given (from_x = 0) or taken as S_B x_B.
+__global__ void __launch_bounds__(kBlock) k_red_recover(const double* __restrict__ b,
+                                                        const double* __restrict__ xy,
+                                                        const double* __restrict__ s,
+                                                        const double* __restrict__ a,
+                                                        const int32_t* __restrict__ col,
+                                                        int64_t n, int64_t nR, int from_x,
+                                                        double* __restrict__ y) {
+    CPS_GRID_STRIDE(i, nR) {
+        double acc = b[i] / s[i];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int32_t c = col[j * n + i];
+            if (c == (int32_t)i) continue;             // unused slot
+            const double v = from_x ? s[c] * xy[c] : xy[c];
+            acc = fma(-a[j * n + i], v, acc);
+        }
+        y[i] = acc;
+    }
+}
+
+// Black rows: y_B = S_B x_B, r_B = bhat_B - y_B - E^T y_R, p_B = r_B; per run
+// rho = r.r, ||b||^2 over all rows, ||S r||^2.
+__global__ void __launch_bounds__(kBlock) k_black_init(const double* __restrict__ b,
+                                                       const double* __restrict__ x,
+                                                       const double* __restrict__ s,
+                                                       const double* __restrict__ a,
+                                                       const int32_t* __restrict__ col,
+                                                       int64_t n, int64_t nR,
+                                                       double* __restrict__ y,
+                                                       double* __restrict__ r,
+                                                       double* __restrict__ p, double rtol,
+                                                       long long budget, double* partials,
+                                                       CgState* st) {
+    double rr = 0.0, bb = 0.0, nn = 0.0;
+    CPS_GRID_STRIDE(k, n) {
+        const double bk = b[k];
+        bb = fma(bk, bk, bb);
+    }
+    CPS_GRID_STRIDE(k, n - nR) {
+        const int64_t i = nR + k;
+        const double se = s[i];
+        const double ye = se * x[i];
+        double ay = ye;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int32_t c = col[j * n + i];
+            if (c == (int32_t)i) continue;
+            ay = fma(a[j * n + i], y[c], ay);
+        }
+        const double re = b[i] / se - ay;
+        y[i] = ye;
+        r[i] = re;
+        p[i] = re;
+        rr = fma(re, re, rr);
+        const double t = se * re;
+        nn = fma(t, t, nn);
+    }
+    double t[3] = {rr, bb, nn};
+    if (grid_sum<3>(t, partials, &st->arrive[2]) && threadIdx.x == 0) {
+        st->rho = t[0];
+        st->bnorm2 = t[1];
+        st->thresh2 = rtol * rtol * t[1];
+        st->rnorm2 = t[2];
+        st->alpha = 0.0;
+        st->beta = 0.0;
+        st->gamma = 0.0;
+        st->iter = 0;
+        st->max_iter = budget;
+        st->status = CPS_OK;
+        st->done = (t[1] == 0.0 || t[2] <= st->thresh2 || budget <= 0) ? 2 : 0;
+    }
+}
+
+// t_R = E p_B (red rows).  First kernel of a reduced iteration: it also
+// turns "stop after this iteration" into "stopped".
+__global__ void __launch_bounds__(kBlock) k_schur_red(const double* __restrict__ a,
+                                                      const int32_t* __restrict__ col,
+                                                      const double* __restrict__ p,
+                                                      double* __restrict__ t, int64_t n,
+                                                      int64_t nR, CgState* st) {
+    pdl_wait();
+    {
+        const int d = st->done;
+        if (d) {
+            if (d == 1 && blockIdx.x == 0 && threadIdx.x == 0) st->done = 2;
+            return;
+        }
+    }
+    CPS_GRID_STRIDE(i, nR) {
+        double acc = 0.0;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int32_t c = col[j * n + i];
+            if (c == (int32_t)i) continue;
+            acc = fma(a[j * n + i], p[c], acc);
+        }
+        t[i] = acc;
+    }
+    pdl_trigger();
+}
+
+// q_B = p_B - E^T t_R (black rows), gamma = p_B . q_B; last block: alpha.
+__global__ void __launch_bounds__(kBlock) k_schur_black(const double* __restrict__ a,
+                                                        const int32_t* __restrict__ col,
+                                                        const double* __restrict__ p,
+                                                        const double* __restrict__ t,
+                                                        double* __restrict__ q, int64_t n,
+                                                        int64_t nR, double* partials,
+                                                        CgState* st) {
+    pdl_wait();
+    if (st->done) return;
+    double acc = 0.0;
+    CPS_GRID_STRIDE(k, n - nR) {
+        const int64_t i = nR + k;
+        const double pe = p[i];
+        double v = pe;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int32_t c = col[j * n + i];
+            if (c == (int32_t)i) continue;
+            v = fma(-a[j * n + i], t[c], v);
+        }
+        q[i] = v;
+        acc = fma(pe, v, acc);
+    }
+    pdl_trigger();
+    double g[1] = {acc};
+    if (grid_sum<1>(g, partials, &st->arrive[0]) && threadIdx.x == 0) {
+        const double gamma = g[0];
+        st->gamma = gamma;
+        if (!(gamma > 0.0) || !isfinite(gamma)) {
+            st->status = CPS_ERR_NOT_SPD;
+            st->done = 2;
+        } else {
+            st->alpha = st->rho / gamma;
+        }
     }
 }
 

@@ -399,11 +399,15 @@ int precond_impl(cps_sys s, int precond, cudaStream_t stream) {
         s->precond = precond;
         return CPS_OK;
     }
-    if (precond != CPS_PC_IC0) {
+    if (precond != CPS_PC_IC0 && precond != CPS_PC_REDUCED) {
         s->ctx->last_error = "set_precond: unknown preconditioner";
         return CPS_ERR_ARG;
     }
-    if (s->ncolours > 0) {   // factored already (matrix is fixed)
+    if (s->ncolours > 0) {   // ordered and factored already (the matrix is fixed)
+        if (precond == CPS_PC_REDUCED && s->ncolours != 2) {
+            s->ctx->last_error = "set_precond: the cell graph is not two-colourable";
+            return CPS_ERR_ARG;
+        }
         s->precond = precond;
         return CPS_OK;
     }
@@ -475,7 +479,12 @@ int precond_impl(cps_sys s, int precond, cudaStream_t stream) {
         return rc;
     }
     s->ncolours = ncol;
-    s->precond = CPS_PC_IC0;
+    if (precond == CPS_PC_REDUCED && ncol != 2) {
+        s->precond = CPS_PC_JACOBI;
+        s->ctx->last_error = "set_precond: the cell graph is not two-colourable";
+        return CPS_ERR_ARG;
+    }
+    s->precond = precond;
     return CPS_OK;
 }
 

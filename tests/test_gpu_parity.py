@@ -340,3 +340,44 @@ def test_cluster_path_rejects_oversized_systems(ctx):
     with pytest.raises(cps.CpsError):
         s.set_solver_path(cps.PATH_CLUSTER)
     s.free()
+
+
+@pytest.mark.parametrize("name", ["block37", "channel64", "logperm29", "ensemble"])
+def test_reduced_system_solve_matches_oracle(ctx, name):
+    """Two-coloured lattices: exact elimination of one colour, CG on the Schur
+    complement of the other; the full solution against the oracle."""
+    p = PROBLEMS[name]
+    s = assemble(ctx, p)
+    s.set_precond(cps.PC_REDUCED)
+    b = synth.rhs(p.mesh, 29)
+    x, st = s.solve(torch.as_tensor(b, device="cuda"), rtol=1e-12, check=False)
+    assert st.status in (0, cps._cps.ERR_NOT_CONVERGED) and st.rel_res < 1e-10
+    xo, sto, A = oracle.solve_problem(p, b, rtol=1e-13)
+    err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
+    assert err < 1e-9, err
+    r = b - A.matvec(x.cpu().numpy())
+    assert np.linalg.norm(r) / np.linalg.norm(b) < 2 * max(st.rel_res, 1e-13)
+    # fewer iterations than Jacobi on the full system
+    s.set_precond(cps.PC_JACOBI)
+    _, sj = s.solve(torch.as_tensor(b, device="cuda"), rtol=1e-10)
+    s.set_precond(cps.PC_REDUCED)
+    _, sr = s.solve(torch.as_tensor(b, device="cuda"), rtol=1e-10)
+    assert sr.iters < 0.75 * sj.iters
+    # warm start from the solution: nothing to do
+    _, sw = s.solve(torch.as_tensor(b, device="cuda"), x=x.clone(), rtol=1e-8)
+    assert sw.iters == 0
+    with pytest.raises(cps.CpsError):
+        s.solve(torch.as_tensor(b, device="cuda"), precision=cps.MIXED)
+    s.free()
+
+
+def test_reduced_system_needs_two_colours(ctx):
+    p = PROBLEMS["defect20"]
+    s = assemble(ctx, p)
+    with pytest.raises(cps.CpsError) as ei:
+        s.set_precond(cps.PC_REDUCED)
+    assert ei.value.code == cps._cps.ERR_ARG
+    s.set_precond(cps.PC_IC0)            # the same ordering serves IC(0)
+    _, st = s.solve(torch.as_tensor(synth.rhs(p.mesh, 1), device="cuda"), rtol=1e-10)
+    assert st.rel_res <= 1e-10
+    s.free()
