@@ -285,13 +285,22 @@ static bool l2_window_fits(cps_sys s) {
     return s->ctx->l2_persist_max > 0 && s->mat_bytes <= s->ctx->l2_persist_max;
 }
 
+// The persisting set-aside is a context-wide reservation that shrinks the L2
+// every other kernel sees, so it is held only for the duration of a solve
+// that uses the window and given back (set to 0) right after.
+static int l2_set_aside(cps_sys s, bool on, cudaStream_t st) {
+    const size_t want = on ? s->mat_bytes : 0;
+    if (s->ctx->l2_persist_set == want) return CPS_OK;
+    CPS_CUDA_TRY(s->ctx, cudaStreamSynchronize(st));
+    if (!on) CPS_CUDA_TRY(s->ctx, cudaCtxResetPersistingL2Cache());
+    CPS_CUDA_TRY(s->ctx, cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want));
+    s->ctx->l2_persist_set = want;
+    return CPS_OK;
+}
+
 static int set_l2_window(cps_sys s, cudaStream_t st, bool on) {
     cudaStreamAttrValue v = {};
     if (on) {
-        if (s->ctx->l2_persist_set < s->mat_bytes) {
-            CPS_CUDA_TRY(s->ctx, cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, s->mat_bytes));
-            s->ctx->l2_persist_set = s->mat_bytes;
-        }
         v.accessPolicyWindow.base_ptr = s->a;
         v.accessPolicyWindow.num_bytes = s->mat_bytes;
         v.accessPolicyWindow.hitRatio = 1.0f;
@@ -433,7 +442,8 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
         if ((path == 1 && !try_cluster) || (path == 2 && !try_win)) continue;
         t.l2win = path == 2;
         t.pdl = path == 3;
-        rc = get_chunk_graph<double>(s, CPS_FP64, v, &ge, &per_chunk);
+        rc = l2_set_aside(s, t.l2win, stream);
+        if (rc == CPS_OK) rc = get_chunk_graph<double>(s, CPS_FP64, v, &ge, &per_chunk);
         for (int rep = 0; rep < 2 && rc == CPS_OK; ++rep) {   // first one warms up
             CPS_CUDA_TRY(s->ctx, cudaMemsetAsync(s->wx, 0, sizeof(double) * s->nt, stream));
             CgState h{};
@@ -455,7 +465,10 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (try_win) cudaCtxResetPersistingL2Cache();
+    {
+        const int rc2 = l2_set_aside(s, false, stream);
+        if (rc == CPS_OK) rc = rc2;
+    }
     t.l2win = false;
     t.pdl = false;
     if (rc == CPS_ERR_ARG) {
@@ -490,6 +503,11 @@ static int solve_fp64(cps_sys s, const double* b, double* x, double rtol, int64_
         if (rc) return rc;
     }
     const bool cluster = !ic0 && s->tune[CPS_FP64].path == 1;
+    const bool window = !ic0 && !cluster && s->tune[CPS_FP64].l2win;
+    if (window) {
+        int rc = l2_set_aside(s, true, stream);
+        if (rc) return rc;
+    }
     if (ic0) {
         k_permute_in<<<g, kBlock, 0, stream>>>(b, x, s->perm, n, s->wb, s->wx);
         ++launches;
@@ -549,10 +567,10 @@ static int solve_fp64(cps_sys s, const double* b, double* x, double rtol, int64_
         CPS_CUDA_TRY(s->ctx, cudaGetLastError());
         CPS_CUDA_TRY(s->ctx, cudaStreamSynchronize(stream));
     }
-    if (!ic0 && s->tune[CPS_FP64].l2win) {
-        // release the persisting lines: later work gets the whole L2 back
-        CPS_CUDA_TRY(s->ctx, cudaStreamSynchronize(stream));
-        CPS_CUDA_TRY(s->ctx, cudaCtxResetPersistingL2Cache());
+    if (window) {
+        // release the lines and the set-aside: later work gets the whole L2
+        int rc = l2_set_aside(s, false, stream);
+        if (rc) return rc;
     }
     const double rel = h.bnorm2 > 0 ? std::sqrt(h.rnorm2 / h.bnorm2) : 0.0;
     if (status == CPS_OK && h.bnorm2 > 0 && !(rel <= rtol)) status = CPS_ERR_NOT_CONVERGED;
@@ -773,7 +791,11 @@ int solve_impl(cps_sys s, const double* b, double* x, double rtol, int64_t max_i
         }
         return solve_reduced(s, b, x, rtol, max_iter, stats, stream);
     }
-    if (precision == CPS_FP64) return solve_fp64(s, b, x, rtol, max_iter, stats, stream);
+    if (precision == CPS_FP64) {
+        const int rc = solve_fp64(s, b, x, rtol, max_iter, stats, stream);
+        if (s->ctx->l2_persist_set != 0) l2_set_aside(s, false, stream);   // error paths
+        return rc;
+    }
     if (precision == CPS_MIXED) return solve_mixed(s, b, x, rtol, max_iter, stats, stream);
     s->ctx->last_error = "solve: bad precision";
     return CPS_ERR_ARG;
