@@ -440,9 +440,15 @@ def main():
                      cps.KIND_CP2, p.nu, p.dt)
     peak, peak_kind = measured_peaks()
     variants = {}
-    for pc_name, pc in (("jacobi", cps.PC_JACOBI), ("ic0", cps.PC_IC0)):
-        s.set_precond(pc)
+    for pc_name, pc in (("jacobi", cps.PC_JACOBI), ("ic0", cps.PC_IC0),
+                        ("reduced", cps.PC_REDUCED)):
+        try:
+            s.set_precond(pc)
+        except cps.CpsError:
+            continue
         for prec_name, prec in (("fp64", cps.FP64), ("mixed", cps.MIXED)):
+            if pc == cps.PC_REDUCED and prec != cps.FP64:
+                continue
             ts = []
             for _ in range(2):
                 x.zero_()

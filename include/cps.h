@@ -224,11 +224,10 @@ int cps_set_solver_path(cps_sys sys, int path);
  * (CPS_FP64 only) the direction update.  The tuner times every candidate on
  * the system's own data at its first solve; systems below 131072 cells keep
  * the defaults (unroll 2, 8 blocks per SM).  For CPS_FP64 Jacobi solves it
- * also times the ways of running the loop: flags (may be NULL) receives
- * {one-cluster launch chosen, matrix held in persisting L2, programmatic
- * dependent launch}, probe_us (may be NULL) the microseconds per iteration
- * measured for {streaming, one cluster, streaming + L2 window, streaming +
- * programmatic launch} (0 where not tried). */
+ * also times the ways of running the loop: flags (may be NULL, 2 entries)
+ * receives {one-cluster launch chosen, matrix held in persisting L2},
+ * probe_us (may be NULL, 3 entries) the microseconds per iteration measured
+ * for {streaming, one cluster, streaming + L2 window} (0 where not tried). */
 int cps_get_tuning(cps_sys sys, int precision, int32_t* unroll, int32_t* grid, int32_t* flags,
                    double* probe_us);
 

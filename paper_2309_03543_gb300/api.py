@@ -136,14 +136,13 @@ class System:
         """Autotuned (unroll, grid) of the iteration kernels for a precision."""
         u = (ctypes.c_int32 * 3)()
         g = (ctypes.c_int32 * 3)()
-        f = (ctypes.c_int32 * 3)()
-        pr = (ctypes.c_double * 4)()
+        f = (ctypes.c_int32 * 2)()
+        pr = (ctypes.c_double * 3)()
         self.ctx.check(self.ctx.lib.cps_get_tuning(self.handle, precision, u, g, f, pr),
                        "cps_get_tuning")
         return {"unroll": list(u), "grid": list(g),
-                "cluster": bool(f[0]), "l2_window": bool(f[1]), "pdl": bool(f[2]),
-                "probe_us_per_iter": {"stream": pr[0], "cluster": pr[1], "stream_l2_window": pr[2],
-                                      "stream_pdl": pr[3]}}
+                "cluster": bool(f[0]), "l2_window": bool(f[1]),
+                "probe_us_per_iter": {"stream": pr[0], "cluster": pr[1], "stream_l2_window": pr[2]}}
 
     def set_solver_path(self, path: int):
         """PATH_AUTO, PATH_STREAM or PATH_CLUSTER for FP64 Jacobi solves."""

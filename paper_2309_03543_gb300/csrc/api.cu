@@ -173,10 +173,9 @@ int cps_get_tuning(cps_sys sys, int precision, int32_t* unroll, int32_t* grid, i
     if (flags) {
         flags[0] = t.path_done && t.path == 1;
         flags[1] = t.path_done && t.l2win;
-        flags[2] = t.path_done && t.pdl;
     }
     if (probe_us)
-        for (int k = 0; k < 4; ++k) probe_us[k] = t.probe_us[k];
+        for (int k = 0; k < 3; ++k) probe_us[k] = t.probe_us[k];
     return CPS_OK;
 }
 

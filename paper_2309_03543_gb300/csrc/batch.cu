@@ -22,9 +22,6 @@ namespace {
 constexpr int kTileRows = 512;
 constexpr int kBatchChunk = 32;
 constexpr int kBatchCheck = 8;
-// Programmatic dependent launch measured slower than plain graph edges for
-// the large single-system loop; the batch keeps plain launches.
-constexpr bool kBatchPdl = false;
 
 struct BatchDesc {
     const double* a;
@@ -48,25 +45,6 @@ struct TileRef {
     int32_t tile;
 };
 
-// Programmatic dependent launch of the iteration kernels (as in the single-
-// system loop): wait for the predecessor grid before reading anything it
-// writes; let the successor be scheduled once this grid's tiles are done.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
-template <typename... KArgs, typename... Args>
-void launch_pdl(void (*kernel)(KArgs...), int grid, cudaStream_t st, Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid, 1, 1);
-    cfg.blockDim = dim3(kBlock, 1, 1);
-    cfg.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = kBatchPdl ? at : nullptr;
-    cfg.numAttrs = kBatchPdl ? 1 : 0;
-    cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
-}
 
 // Sum of a per-tile partial over the block; returns true in the block that
 // completed the system's last tile, with the system's totals in v[].
@@ -221,7 +199,6 @@ __global__ void __launch_bounds__(kBlock) kb_spmv(const BatchDesc* __restrict__ 
                                                   const int* ntile) {
     __shared__ double sh[32][1];
     __shared__ bool last;
-    pdl_wait();
     CPS_TILE_LOOP(tiles, ntile) {
         const TileRef tr = tiles[ti_];
         const BatchDesc d = dd[tr.sys];
@@ -262,7 +239,6 @@ __global__ void __launch_bounds__(kBlock) kb_update(const BatchDesc* __restrict_
                                                     const int* ntile) {
     __shared__ double sh[32][2];
     __shared__ bool last;
-    pdl_wait();
     CPS_TILE_LOOP(tiles, ntile) {
         const TileRef tr = tiles[ti_];
         const BatchDesc d = dd[tr.sys];
@@ -303,7 +279,6 @@ __global__ void __launch_bounds__(kBlock) kb_update(const BatchDesc* __restrict_
 __global__ void __launch_bounds__(kBlock) kb_direction(const BatchDesc* __restrict__ dd,
                                                        const TileRef* __restrict__ tiles,
                                                        const int* ntile) {
-    pdl_wait();
     CPS_TILE_LOOP(tiles, ntile) {
         const TileRef tr = tiles[ti_];
         const BatchDesc d = dd[tr.sys];
@@ -446,15 +421,12 @@ int solve_batch_impl(const cps_sys* systems, int nsys, const double* const* b,
         cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         kb_compact<<<1, cblock, 0, cap>>>(dd, nsys, tiles, counts);
         for (int k = 0; k < kBatchChunk; ++k) {
-            const BatchDesc* cdd = dd;
-            const TileRef* ctl = tiles;
-            const int* ccn = counts;
-            launch_pdl(kb_spmv, grid, cap, cdd, ctl, ccn);
+            kb_spmv<<<grid, kBlock, 0, cap>>>(dd, tiles, counts);
             if (k % kBatchCheck == kBatchCheck - 1)
-                launch_pdl(kb_update<true>, grid, cap, cdd, ctl, ccn);
+                kb_update<true><<<grid, kBlock, 0, cap>>>(dd, tiles, counts);
             else
-                launch_pdl(kb_update<false>, grid, cap, cdd, ctl, ccn);
-            launch_pdl(kb_direction, grid, cap, cdd, ctl, ccn);
+                kb_update<false><<<grid, kBlock, 0, cap>>>(dd, tiles, counts);
+            kb_direction<<<grid, kBlock, 0, cap>>>(dd, tiles, counts);
         }
         kb_count_running<<<1, cblock, 0, cap>>>(dd, nsys, counts + 1);
         cudaError_t ce = cudaStreamEndCapture(cap, &g);

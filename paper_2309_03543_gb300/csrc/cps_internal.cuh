@@ -53,8 +53,7 @@ struct Tuning {
     int path = 0;            // FP64 Jacobi: 0 graph-replayed kernels, 1 one-cluster launch
     bool path_done = false;
     bool l2win = false;      // FP64 Jacobi stream path: matrix held in persisting L2
-    bool pdl = false;        // FP64 Jacobi stream path: programmatic dependent launch
-    double probe_us[4] = {0, 0, 0, 0};   // us/iteration: stream, cluster, +L2, +PDL
+    double probe_us[3] = {0, 0, 0};      // us/iteration: stream, cluster, stream + L2 window
 };
 
 // Device error flag written by the assembly kernels (first error wins).
@@ -204,7 +203,6 @@ struct cps_sys_s {
     cudaGraphExec_t graph[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
     int64_t graph_nodes[2][3] = {{0, 0, 0}, {0, 0, 0}};
     bool graph_l2win[2][3] = {{false, false, false}, {false, false, false}};
-    bool graph_pdl[2][3] = {{false, false, false}, {false, false, false}};
     cps::Tuning tune[2];        // per precision (CPS_FP64, CPS_MIXED)
     int cluster_size = 0;       // CTAs of the last one-cluster solve
 };

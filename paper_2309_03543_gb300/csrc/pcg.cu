@@ -106,27 +106,14 @@ Run<float> make_run<float>(cps_sys s) {
 
 // ------------------------------------------------------------ launch configs
 // Each streaming kernel of the iteration runs with a (rows-per-thread
-// unroll U, grid) pair picked by the autotuner below, and is launched with
-// programmatic stream serialisation so that it can be scheduled during its
-// predecessor's reduction tail (see pdl_wait / pdl_trigger).
-
-// Whether the launches being enqueued use programmatic serialisation (set
-// around a graph capture from the system's tuning; off for direct launches).
-static thread_local bool g_pdl = false;
+// unroll U, grid) pair picked by the autotuner below.  (Programmatic
+// dependent launch between the iteration kernels was measured slower than
+// plain graph edges on GB300 -- 65.6 against 55 us per iteration at 2.1M
+// cells -- and is not used.)
 
 template <typename... KArgs, typename... Args>
-static void launch_pdl(void (*kernel)(KArgs...), int grid, cudaStream_t st, Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid, 1, 1);
-    cfg.blockDim = dim3(kBlock, 1, 1);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = g_pdl ? at : nullptr;
-    cfg.numAttrs = g_pdl ? 1 : 0;
-    cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+static void launch_k(void (*kernel)(KArgs...), int grid, cudaStream_t st, Args... args) {
+    kernel<<<grid, kBlock, 0, st>>>(static_cast<KArgs>(args)...);
 }
 
 template <typename V>
@@ -135,27 +122,27 @@ static void launch_a(const KCfg& c, const Run<V>& v, cps_sys s, cudaStream_t st)
 template <>
 void launch_a<double>(const KCfg& c, const Run<double>& v, cps_sys s, cudaStream_t st) {
     switch (c.unroll) {
-        case 1: launch_pdl(k_spmv_dot<double, 1>, c.grid, st, v.a, v.col, v.p0, v.q, v.n, s->partials, s->st); break;
-        case 4: launch_pdl(k_spmv_dot<double, 4>, c.grid, st, v.a, v.col, v.p0, v.q, v.n, s->partials, s->st); break;
-        default: launch_pdl(k_spmv_dot<double, 2>, c.grid, st, v.a, v.col, v.p0, v.q, v.n, s->partials, s->st); break;
+        case 1: launch_k(k_spmv_dot<double, 1>, c.grid, st, v.a, v.col, v.p0, v.q, v.n, s->partials, s->st); break;
+        case 4: launch_k(k_spmv_dot<double, 4>, c.grid, st, v.a, v.col, v.p0, v.q, v.n, s->partials, s->st); break;
+        default: launch_k(k_spmv_dot<double, 2>, c.grid, st, v.a, v.col, v.p0, v.q, v.n, s->partials, s->st); break;
     }
 }
 
 template <>
 void launch_a<float>(const KCfg& c, const Run<float>& v, cps_sys s, cudaStream_t st) {
     switch (c.unroll) {
-        case 1: launch_pdl(k_cg_a<float, 1>, c.grid, st, v.a, v.col, v.z, v.p0, v.p1, v.y, v.q, v.n, s->partials, s->st); break;
-        case 4: launch_pdl(k_cg_a<float, 4>, c.grid, st, v.a, v.col, v.z, v.p0, v.p1, v.y, v.q, v.n, s->partials, s->st); break;
-        default: launch_pdl(k_cg_a<float, 2>, c.grid, st, v.a, v.col, v.z, v.p0, v.p1, v.y, v.q, v.n, s->partials, s->st); break;
+        case 1: launch_k(k_cg_a<float, 1>, c.grid, st, v.a, v.col, v.z, v.p0, v.p1, v.y, v.q, v.n, s->partials, s->st); break;
+        case 4: launch_k(k_cg_a<float, 4>, c.grid, st, v.a, v.col, v.z, v.p0, v.p1, v.y, v.q, v.n, s->partials, s->st); break;
+        default: launch_k(k_cg_a<float, 2>, c.grid, st, v.a, v.col, v.z, v.p0, v.p1, v.y, v.q, v.n, s->partials, s->st); break;
     }
 }
 
 template <typename V, bool NORM, bool JACOBI>
 static void launch_b_u(const KCfg& c, const Run<V>& v, cps_sys s, cudaStream_t st) {
     switch (c.unroll) {
-        case 1: launch_pdl(k_cg_b<V, NORM, JACOBI, 1>, c.grid, st, v.r, v.q, v.s, v.n, s->partials, s->st); break;
-        case 4: launch_pdl(k_cg_b<V, NORM, JACOBI, 4>, c.grid, st, v.r, v.q, v.s, v.n, s->partials, s->st); break;
-        default: launch_pdl(k_cg_b<V, NORM, JACOBI, 2>, c.grid, st, v.r, v.q, v.s, v.n, s->partials, s->st); break;
+        case 1: launch_k(k_cg_b<V, NORM, JACOBI, 1>, c.grid, st, v.r, v.q, v.s, v.n, s->partials, s->st); break;
+        case 4: launch_k(k_cg_b<V, NORM, JACOBI, 4>, c.grid, st, v.r, v.q, v.s, v.n, s->partials, s->st); break;
+        default: launch_k(k_cg_b<V, NORM, JACOBI, 2>, c.grid, st, v.r, v.q, v.s, v.n, s->partials, s->st); break;
     }
 }
 
@@ -170,9 +157,9 @@ static void launch_b(const KCfg& c, const Run<V>& v, bool norm, cps_sys s, cudaS
 
 static void launch_c(const KCfg& c, const Run<double>& v, cps_sys s, cudaStream_t st) {
     switch (c.unroll) {
-        case 1: launch_pdl(k_cg_c<double, 1>, c.grid, st, v.y, v.p0, v.z, v.n, s->st); break;
-        case 4: launch_pdl(k_cg_c<double, 4>, c.grid, st, v.y, v.p0, v.z, v.n, s->st); break;
-        default: launch_pdl(k_cg_c<double, 2>, c.grid, st, v.y, v.p0, v.z, v.n, s->st); break;
+        case 1: launch_k(k_cg_c<double, 1>, c.grid, st, v.y, v.p0, v.z, v.n, s->st); break;
+        case 4: launch_k(k_cg_c<double, 4>, c.grid, st, v.y, v.p0, v.z, v.n, s->st); break;
+        default: launch_k(k_cg_c<double, 2>, c.grid, st, v.y, v.p0, v.z, v.n, s->st); break;
     }
 }
 
@@ -250,13 +237,13 @@ static int64_t enqueue_precond(cps_sys s, const Run<V>& v, cudaStream_t st) {
     const int g = s->grid;
     int64_t launches = 0;
     for (int c = 1; c < C; ++c, ++launches)
-        launch_pdl(k_ic0_fwd<V>, g, st, v.l, v.col, v.dinv, v.r, v.z, v.n, cs[c], cs[c + 1], cs[1],
+        launch_k(k_ic0_fwd<V>, g, st, v.l, v.col, v.dinv, v.r, v.z, v.n, cs[c], cs[c + 1], cs[1],
                    c == C - 1 ? 1 : 0, c, s->partials, s->st);
     for (int c = C - 2; c >= 0; --c, ++launches)
-        launch_pdl(k_ic0_bwd<V>, g, st, v.l, v.col, v.dinv, v.r, v.z, v.n, cs[c], cs[c + 1], C, c,
+        launch_k(k_ic0_bwd<V>, g, st, v.l, v.col, v.dinv, v.r, v.z, v.n, cs[c], cs[c + 1], C, c,
                    s->partials, s->st);
     if (C == 1) {
-        launch_pdl(k_ic0_bwd<V>, g, st, v.l, v.col, v.dinv, v.r, v.z, v.n, cs[0], cs[1], C, 0,
+        launch_k(k_ic0_bwd<V>, g, st, v.l, v.col, v.dinv, v.r, v.z, v.n, cs[0], cs[1], C, 0,
                    s->partials, s->st);
         ++launches;
     }
@@ -320,8 +307,7 @@ static int get_chunk_graph(cps_sys s, int prec, const Run<V>& v, cudaGraphExec_t
                            int64_t* per_chunk) {
     const int pc = v.l ? 1 : 0;
     const bool win = prec == CPS_FP64 && pc == 0 && s->tune[CPS_FP64].l2win;
-    const bool pdl = prec == CPS_FP64 && pc == 0 && s->tune[CPS_FP64].pdl;
-    if (s->graph[prec][pc] && (s->graph_l2win[prec][pc] != win || s->graph_pdl[prec][pc] != pdl)) {
+    if (s->graph[prec][pc] && s->graph_l2win[prec][pc] != win) {
         cudaGraphExecDestroy(s->graph[prec][pc]);
         s->graph[prec][pc] = nullptr;
     }
@@ -333,13 +319,10 @@ static int get_chunk_graph(cps_sys s, int prec, const Run<V>& v, cudaGraphExec_t
         rc = set_l2_window(s, s->cap_stream, win);
         if (rc) return rc;
         s->graph_l2win[prec][pc] = win;
-        s->graph_pdl[prec][pc] = pdl;
         cudaGraph_t graph = nullptr;
         CPS_CUDA_TRY(s->ctx, cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
-        g_pdl = pdl;
         for (int k = 0; k < kChunk; ++k)
             nl += enqueue_iteration<V>(s, v, prec, (k % kCheckEvery) == kCheckEvery - 1, s->cap_stream);
-        g_pdl = false;
         cudaError_t le = cudaGetLastError();
         cudaError_t ce = cudaStreamEndCapture(s->cap_stream, &graph);
         if (le != cudaSuccess || ce != cudaSuccess) {
@@ -433,15 +416,14 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
     CPS_CUDA_TRY(s->ctx, cudaEventCreate(&e0));
     CPS_CUDA_TRY(s->ctx, cudaEventCreate(&e1));
     // candidates: 0 streaming, 1 one-cluster launch, 2 streaming with the
-    // matrix in persisting L2, 3 streaming with programmatic dependent launch
+    // matrix in persisting L2
     double per_iter[4] = {0.0, 0.0, 0.0, 0.0};
     int rc = CPS_OK;
     cudaGraphExec_t ge = nullptr;
     int64_t per_chunk = 0, dummy = 0;
-    for (int path = 0; path < 4 && rc == CPS_OK; ++path) {
+    for (int path = 0; path < 3 && rc == CPS_OK; ++path) {
         if ((path == 1 && !try_cluster) || (path == 2 && !try_win)) continue;
         t.l2win = path == 2;
-        t.pdl = path == 3;
         rc = l2_set_aside(s, t.l2win, stream);
         if (rc == CPS_OK) rc = get_chunk_graph<double>(s, CPS_FP64, v, &ge, &per_chunk);
         for (int rep = 0; rep < 2 && rc == CPS_OK; ++rep) {   // first one warms up
@@ -470,16 +452,14 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
         if (rc == CPS_OK) rc = rc2;
     }
     t.l2win = false;
-    t.pdl = false;
     if (rc == CPS_ERR_ARG) {
         rc = CPS_OK;        // no cluster shape: keep the graph path
     } else if (rc == CPS_OK) {
         int best = 0;
-        for (int c = 1; c < 4; ++c)
+        for (int c = 1; c < 3; ++c)
             if (per_iter[c] > 0.0 && per_iter[c] < per_iter[best]) best = c;
         t.path = best == 1 ? 1 : 0;
         t.l2win = best == 2;
-        t.pdl = best == 3;
     }
     for (int c = 0; c < 4; ++c) t.probe_us[c] = 1e3 * per_iter[c];
     return rc;
@@ -616,8 +596,8 @@ static int solve_reduced(cps_sys s, const double* b, double* x, double rtol, int
         int64_t nl = 0;
         CPS_CUDA_TRY(s->ctx, cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
         for (int k = 0; k < kChunk; ++k) {
-            launch_pdl(k_schur_red, g, s->cap_stream, A, col, (const double*)p, t, n, nR, s->st);
-            launch_pdl(k_schur_black, g, s->cap_stream, A, col, (const double*)p,
+            launch_k(k_schur_red, g, s->cap_stream, A, col, (const double*)p, t, n, nR, s->st);
+            launch_k(k_schur_black, g, s->cap_stream, A, col, (const double*)p,
                        (const double*)t, q, n, nR, s->partials, s->st);
             launch_b<double>(cb, vb, (k % kCheckEvery) == kCheckEvery - 1, s, s->cap_stream);
             launch_c(cb, vb, s, s->cap_stream);

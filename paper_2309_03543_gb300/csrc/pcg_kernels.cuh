@@ -23,15 +23,6 @@
 
 namespace cps {
 
-// Programmatic dependent launch: the iteration kernels are launched so that
-// the next one may start while this one finishes.  Each waits for its
-// predecessor grid (completion and memory) before touching anything the
-// predecessor writes, and lets its successor be scheduled once its own main
-// loop is done (the successor's blocks then wait on the same instruction).
-// Launched without the attribute, both instructions do nothing.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
 #define CPS_GRID_STRIDE(i, n) \
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
@@ -77,7 +68,6 @@ __global__ void __launch_bounds__(kBlock) k_spmv_dot(const V* __restrict__ a,
                                                      const int32_t* __restrict__ col,
                                                      const V* __restrict__ p, V* __restrict__ q,
                                                      int64_t n, double* partials, CgState* st) {
-    pdl_wait();
     {
         const int d = st->done;
         if (d) {
@@ -98,7 +88,6 @@ __global__ void __launch_bounds__(kBlock) k_spmv_dot(const V* __restrict__ a,
             q[e] = v;
             acc = fma((double)pe[u], (double)v, acc);
         })
-    pdl_trigger();
     double t[1] = {acc};
     if (grid_sum<1>(t, partials, &st->arrive[0]) && threadIdx.x == 0) {
         const double gamma = t[0];
@@ -116,7 +105,6 @@ template <typename V, int U>
 __global__ void __launch_bounds__(kBlock) k_cg_c(V* __restrict__ y, V* __restrict__ p,
                                                  const V* __restrict__ z, int64_t n,
                                                  const CgState* st) {
-    pdl_wait();
     if (st->done == 2) return;
     const V al = (V)st->alpha;
     const V be = (V)st->beta;
@@ -143,7 +131,6 @@ __global__ void __launch_bounds__(kBlock) k_cg_a(const V* __restrict__ a,
                                                  V* __restrict__ p1, V* __restrict__ y,
                                                  V* __restrict__ q, int64_t n, double* partials,
                                                  CgState* st) {
-    pdl_wait();
     if (st->done) return;
     const bool odd = (st->iter & 1) != 0;
     const V* __restrict__ po = odd ? p1 : p0;
@@ -166,7 +153,6 @@ __global__ void __launch_bounds__(kBlock) k_cg_a(const V* __restrict__ a,
             q[e] = v;
             acc = fma((double)pe, (double)v, acc);
         })
-    pdl_trigger();
     double t[1] = {acc};
     if (grid_sum<1>(t, partials, &st->arrive[0]) && threadIdx.x == 0) {
         const double gamma = t[0];
@@ -184,7 +170,6 @@ template <typename V, bool NORM, bool JACOBI, int U>
 __global__ void __launch_bounds__(kBlock) k_cg_b(V* __restrict__ r, const V* __restrict__ q,
                                                  const V* __restrict__ s, int64_t n,
                                                  double* partials, CgState* st) {
-    pdl_wait();
     if (st->done) return;
     const V al = (V)st->alpha;
     double rr = 0.0, nn = 0.0;
@@ -199,7 +184,6 @@ __global__ void __launch_bounds__(kBlock) k_cg_b(V* __restrict__ r, const V* __r
                 nn = fma(t, t, nn);
             }
         })
-    pdl_trigger();
     double t[2] = {rr, nn};
     if (grid_sum<2>(t, partials, &st->arrive[1]) && threadIdx.x == 0) {
         const long long it = st->iter + 1;
@@ -490,7 +474,6 @@ __global__ void __launch_bounds__(kBlock) k_ic0_fwd(const V* __restrict__ l,
                                                     int64_t n, int64_t cs, int64_t ce,
                                                     int64_t first_end, int last, int colour,
                                                     double* partials, const CgState* st) {
-    pdl_wait();
     if (st->done) return;
     double acc = 0.0;
     for (int64_t i = cs + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ce;
@@ -528,7 +511,6 @@ __global__ void __launch_bounds__(kBlock) k_ic0_bwd(const V* __restrict__ l,
                                                     int64_t n, int64_t cs, int64_t ce,
                                                     int ncolours, int colour, double* partials,
                                                     CgState* st) {
-    pdl_wait();
     if (st->done) return;
     double acc = 0.0;
     for (int64_t i = cs + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ce;
@@ -667,7 +649,6 @@ __global__ void __launch_bounds__(kBlock) k_schur_red(const double* __restrict__
                                                       const double* __restrict__ p,
                                                       double* __restrict__ t, int64_t n,
                                                       int64_t nR, CgState* st) {
-    pdl_wait();
     {
         const int d = st->done;
         if (d) {
@@ -685,7 +666,6 @@ __global__ void __launch_bounds__(kBlock) k_schur_red(const double* __restrict__
         }
         t[i] = acc;
     }
-    pdl_trigger();
 }
 
 // q_B = p_B - E^T t_R (black rows), gamma = p_B . q_B; last block: alpha.
@@ -696,7 +676,6 @@ __global__ void __launch_bounds__(kBlock) k_schur_black(const double* __restrict
                                                         double* __restrict__ q, int64_t n,
                                                         int64_t nR, double* partials,
                                                         CgState* st) {
-    pdl_wait();
     if (st->done) return;
     double acc = 0.0;
     CPS_GRID_STRIDE(k, n - nR) {
@@ -712,7 +691,6 @@ __global__ void __launch_bounds__(kBlock) k_schur_black(const double* __restrict
         q[i] = v;
         acc = fma(pe, v, acc);
     }
-    pdl_trigger();
     double g[1] = {acc};
     if (grid_sum<1>(g, partials, &st->arrive[0]) && threadIdx.x == 0) {
         const double gamma = g[0];
