@@ -43,6 +43,10 @@ UNIT = "cell-iters/s"
 #     writes p_new, q, y (4+4+4+12+12 + 4+4+4 = 48); k_cg_b 12; +0.5 for s.
 BYTES_PER_CELL_ITER_FP64 = 52 + 24 + 40 + 1
 BYTES_PER_CELL_ITER_MIXED = 48 + 12 + 0.5
+# DRAM bytes (read + write) of one FP64 Jacobi iteration (k_spmv_dot + k_cg_b
+# + k_cg_c) on the 1024 x 1024 channel lattice, from one ncu capture of the
+# current kernels (profiles/pcg_iteration_traffic_channel1024.md).
+TRAFFIC_PER_ITER_N1024 = (96.9 + 33.5 + 50.2) * 1e6
 
 
 def parse():
@@ -486,7 +490,9 @@ def main():
     roof = {"bound": "hbm", "kernel": "pcg_iteration_fp64 (k_spmv_dot + k_cg_b + k_cg_c, Jacobi)",
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "peak_kind": peak_kind, "bytes_per_cell_iter": BYTES_PER_CELL_ITER_FP64,
-            "traffic": None}
+            "traffic": TRAFFIC_PER_ITER_N1024 if args.n == 1024 else None,
+            "traffic_unit": "bytes per iteration (DRAM read + write, ncu)",
+            "algorithmic_bytes_per_iter": BYTES_PER_CELL_ITER_FP64 * nt}
     jm = variants["jacobi_mixed"]
     jm["inner_gbs"] = BYTES_PER_CELL_ITER_MIXED * nt * jm["iters"] / jm["time_to_rtol_s"] / 1e9
 

@@ -182,7 +182,7 @@ int cps_solve(cps_sys sys, const double* b, double* x, double rtol, int64_t max_
  * CPS_FP64: one launch per phase for all systems (Jacobi, whatever each
  * system's preconditioner setting), a per-system convergence mask, and
  * iteration chunks replayed from a CUDA graph; a system of more than
- * 8,388,608 cells is rejected (CPS_ERR_ARG) -- solve it alone.  CPS_MIXED
+ * 33,554,432 cells is rejected (CPS_ERR_ARG) -- solve it alone.  CPS_MIXED
  * solves the systems one after the other.  The return value is the first
  * non-OK per-system status, or CPS_OK. */
 int cps_solve_batch(const cps_sys* systems, int nsys, const double* const* b,

@@ -19,7 +19,7 @@
 namespace cps {
 namespace {
 
-constexpr int kTileRows = 512;
+constexpr int kTileRows = 2048;   // 8 rows per thread per tile
 constexpr int kBatchChunk = 32;
 constexpr int kBatchCheck = 8;
 
@@ -156,6 +156,7 @@ __global__ void __launch_bounds__(kBlock) kb_init(const BatchDesc* __restrict__ 
         const int64_t n = d.n;
         double rr = 0.0, bb = 0.0, nn = 0.0;
         const int64_t r0 = (int64_t)tr.tile * kTileRows;
+#pragma unroll 4
         for (int64_t e = r0 + threadIdx.x; e < r0 + kTileRows && e < n; e += blockDim.x) {
             const double se = d.s[e];
             const double ye = se * d.x[e];
@@ -210,6 +211,7 @@ __global__ void __launch_bounds__(kBlock) kb_spmv(const BatchDesc* __restrict__ 
         const int64_t n = d.n;
         double acc = 0.0;
         const int64_t r0 = (int64_t)tr.tile * kTileRows;
+#pragma unroll 4
         for (int64_t e = r0 + threadIdx.x; e < r0 + kTileRows && e < n; e += blockDim.x) {
             const double pe = d.p[e];
             double v = pe;
@@ -247,6 +249,7 @@ __global__ void __launch_bounds__(kBlock) kb_update(const BatchDesc* __restrict_
         const double al = d.st->alpha;
         double rr = 0.0, nn = 0.0;
         const int64_t r0 = (int64_t)tr.tile * kTileRows;
+#pragma unroll 4
         for (int64_t e = r0 + threadIdx.x; e < r0 + kTileRows && e < n; e += blockDim.x) {
             const double re = fma(-al, d.q[e], d.r[e]);
             d.r[e] = re;
@@ -286,6 +289,7 @@ __global__ void __launch_bounds__(kBlock) kb_direction(const BatchDesc* __restri
         const int64_t n = d.n;
         const double al = d.st->alpha, be = d.st->beta;
         const int64_t r0 = (int64_t)tr.tile * kTileRows;
+#pragma unroll 4
         for (int64_t e = r0 + threadIdx.x; e < r0 + kTileRows && e < n; e += blockDim.x) {
             const double pe = d.p[e];
             d.y[e] = fma(al, pe, d.y[e]);
@@ -307,6 +311,7 @@ __global__ void __launch_bounds__(kBlock) kb_final(const BatchDesc* __restrict__
         const bool zero = d.st->bnorm2 == 0.0;
         double nn = 0.0;
         const int64_t r0 = (int64_t)tr.tile * kTileRows;
+#pragma unroll 4
         for (int64_t e = r0 + threadIdx.x; e < r0 + kTileRows && e < n; e += blockDim.x) {
             if (zero) {
                 d.x[e] = 0.0;
