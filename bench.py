@@ -470,27 +470,44 @@ def main():
                 "time_to_rtol_s": t, "iters": st.iters, "refinements": st.refinements,
                 "rel_res": st.rel_res, "us_per_iter": 1e6 * t / max(st.iters, 1)}
     tuning = {"fp64": s.tuning(cps.FP64), "mixed": s.tuning(cps.MIXED)}
-    # small systems: the one-launch cluster solve against the streaming path
-    s.set_precond(cps.PC_JACOBI)
-    for path_name, path in (("stream", cps.PATH_STREAM), ("cluster", cps.PATH_CLUSTER)):
+    # each way of running the loop, forced: streaming kernels, the one-launch
+    # cluster solve (small systems), the persistent grid-synchronised launch
+    for pc_name, pc in (("jacobi", cps.PC_JACOBI), ("reduced", cps.PC_REDUCED)):
         try:
-            s.set_solver_path(path)
+            s.set_precond(pc)
         except cps.CpsError:
             continue
-        ts = []
-        for _ in range(3):
-            x.zero_()
-            ts.append(timed(lambda: s.solve(d["b"], x=x, rtol=args.rtol)[1], stream))
-        t, st = min(ts, key=lambda v: v[0])
-        variants[f"jacobi_fp64_{path_name}_path"] = {
-            "time_to_rtol_s": t, "iters": st.iters, "us_per_iter": 1e6 * t / max(st.iters, 1)}
+        for path_name, path in (("stream", cps.PATH_STREAM), ("cluster", cps.PATH_CLUSTER),
+                                ("persistent", cps.PATH_PERSISTENT)):
+            if pc == cps.PC_REDUCED and path == cps.PATH_CLUSTER:
+                continue
+            try:
+                s.set_solver_path(path)
+            except cps.CpsError:
+                continue
+            ts = []
+            for _ in range(3):
+                x.zero_()
+                ts.append(timed(lambda: s.solve(d["b"], x=x, rtol=args.rtol)[1], stream))
+            t, st = min(ts, key=lambda v: v[0])
+            variants[f"{pc_name}_fp64_{path_name}_path"] = {
+                "time_to_rtol_s": t, "iters": st.iters, "us_per_iter": 1e6 * t / max(st.iters, 1)}
+        s.set_solver_path(cps.PATH_AUTO)
     s.free()
     jf = variants["jacobi_fp64"]
     achieved = BYTES_PER_CELL_ITER_FP64 * nt * jf["iters"] / jf["time_to_rtol_s"] / 1e9
-    roof = {"bound": "hbm", "kernel": "pcg_iteration_fp64 (k_spmv_dot + k_cg_b + k_cg_c, Jacobi)",
+    tf = tuning["fp64"]
+    if tf["persistent"]:
+        kname = "k_persistent_cg (whole Jacobi-PCG solve in one cooperative launch)"
+    elif tf["cluster"]:
+        kname = "k_cluster_cg (whole Jacobi-PCG solve in one thread-block cluster)"
+    else:
+        kname = "pcg_iteration_fp64 (k_spmv_dot + k_cg_b + k_cg_c, Jacobi)"
+    streaming = not (tf["persistent"] or tf["cluster"] or tf["l2_window"] != "none")
+    roof = {"bound": "hbm", "kernel": kname,
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "peak_kind": peak_kind, "bytes_per_cell_iter": BYTES_PER_CELL_ITER_FP64,
-            "traffic": TRAFFIC_PER_ITER_N1024 if args.n == 1024 else None,
+            "traffic": TRAFFIC_PER_ITER_N1024 if (args.n == 1024 and streaming) else None,
             "traffic_unit": "bytes per iteration (DRAM read + write, ncu)",
             "algorithmic_bytes_per_iter": BYTES_PER_CELL_ITER_FP64 * nt}
     jm = variants["jacobi_mixed"]

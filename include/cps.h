@@ -206,30 +206,45 @@ int cps_adjoint(cps_sys sys, const double* x, const double* g, double* lambda, d
                 double* dtheta, double rtol, int64_t max_iter, cps_stats* stats,
                 void* stream);
 
-/* Choose how FP64 Jacobi solves run: CPS_PATH_AUTO (default: the autotuner
- * times both on the system's first FP64 solve), CPS_PATH_STREAM (the
- * graph-replayed streaming kernels, any size), CPS_PATH_CLUSTER (the whole
- * solve in one launch of a single thread-block cluster whose shared memory
- * holds the system; CPS_ERR_ARG if the system does not fit, see
- * cps_sys_info).  IC(0) and mixed precision always stream. */
+/* Choose how FP64 Jacobi and reduced-system solves run:
+ *   CPS_PATH_AUTO (default): the autotuner times the applicable paths on the
+ *     system's first solve of that kind and keeps the fastest;
+ *   CPS_PATH_STREAM: graph-replayed streaming kernels, any size;
+ *   CPS_PATH_CLUSTER (FP64 Jacobi only): the whole solve in one launch of a
+ *     single thread-block cluster whose shared memory holds the system;
+ *     CPS_ERR_ARG if the system does not fit, see cps_sys_info;
+ *   CPS_PATH_PERSISTENT: the whole solve in one cooperative launch of one
+ *     resident grid, iterations separated by software grid barriers (every
+ *     wait bounded: a wait that runs out ends the solve with
+ *     CPS_ERR_TIMEOUT).
+ * IC(0) and mixed precision always stream. */
 #define CPS_PATH_AUTO 0
 #define CPS_PATH_STREAM 1
 #define CPS_PATH_CLUSTER 2
+#define CPS_PATH_PERSISTENT 3
 int cps_set_solver_path(cps_sys sys, int path);
 
 /* Launch configuration the autotuner chose for the iteration kernels of one
  * precision (host outputs of 3 entries each; zeros before the first solve in
- * that precision): rows per thread per trip of the grid-stride loop, and the
- * grid in blocks of 256 threads, for the SpMV kernel, the residual update and
+ * that precision): rows per thread per trip of the grid-stride loop, the
+ * grid in blocks and the threads per block (block may be NULL; 256, or 1024
+ * for the FP64 kernels), for the SpMV kernel, the residual update and
  * (CPS_FP64 only) the direction update.  The tuner times every candidate on
  * the system's own data at its first solve; systems below 131072 cells keep
  * the defaults (unroll 2, 8 blocks per SM).  For CPS_FP64 Jacobi solves it
- * also times the ways of running the loop: flags (may be NULL, 2 entries)
- * receives {one-cluster launch chosen, matrix held in persisting L2},
- * probe_us (may be NULL, 3 entries) the microseconds per iteration measured
- * for {streaming, one cluster, streaming + L2 window} (0 where not tried). */
-int cps_get_tuning(cps_sys sys, int precision, int32_t* unroll, int32_t* grid, int32_t* flags,
-                   double* probe_us);
+ * also times the ways of running the loop: flags (may be NULL, 4 entries)
+ * receives {one-cluster launch chosen, persisting-L2 window (0 none, 1 the
+ * matrix, 2 the vectors r, p, q), persistent launch chosen, persistent
+ * launch chosen for the reduced system}, probe_us (may be NULL, 7 entries)
+ * the microseconds per iteration measured for {streaming, one cluster,
+ * streaming + matrix in L2, persistent, reduced system streaming, reduced
+ * system persistent, streaming + vectors in L2} (0 where not tried).
+ * The context remembers what the tuner chose per mesh size (cells,
+ * vertices): a system assembled later on the same context with the same
+ * sizes starts from those choices and is not timed again.  A path forced by
+ * cps_set_solver_path applies to that system only. */
+int cps_get_tuning(cps_sys sys, int precision, int32_t* unroll, int32_t* grid, int32_t* block,
+                   int32_t* flags, double* probe_us);
 
 /* Allocation-free solve of a matrix the caller already holds in the padded
  * ELL form that cps_export_matrix writes (no counterpart in the paper; it is

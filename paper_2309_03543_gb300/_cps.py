@@ -27,7 +27,7 @@ KIND_CP2, KIND_CP1_X, KIND_CP1_Y = 0, 1, 2
 PER_VERTEX, PER_CELL, PER_CELL_LOGK = 0, 1, 2
 PC_JACOBI, PC_IC0, PC_REDUCED = 1, 2, 3
 FP64, MIXED = 0, 1
-PATH_AUTO, PATH_STREAM, PATH_CLUSTER = 0, 1, 2
+PATH_AUTO, PATH_STREAM, PATH_CLUSTER, PATH_PERSISTENT = 0, 1, 2, 3
 
 ERROR_NAMES = {
     ERR_ARG: "CPS_ERR_ARG", ERR_NONMANIFOLD: "CPS_ERR_NONMANIFOLD",
@@ -65,7 +65,7 @@ SIGNATURES = {
     "cps_solve_batch": (_I, [_P, _I, _P, _P, _D, _I64, _I, ctypes.POINTER(Stats), _P]),
     "cps_adjoint": (_I, [_P, _P, _P, _P, _P, _P, _D, _I64, ctypes.POINTER(Stats), _P]),
     "cps_matvec": (_I, [_P, _P, _P, _P]),
-    "cps_get_tuning": (_I, [_P, _I, _P, _P, _P, _P]),
+    "cps_get_tuning": (_I, [_P, _I, _P, _P, _P, _P, _P]),
     "cps_set_solver_path": (_I, [_P, _I]),
     "cps_solve_ell_noalloc": (_I, [_I64, _P, _P, _P, _P, _P, _D, _I64, ctypes.POINTER(Stats),
                                    _P]),

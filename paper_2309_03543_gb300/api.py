@@ -133,19 +133,26 @@ class System:
                 "is_mmatrix": bool(mm.value), "setup_launches": sl.value}
 
     def tuning(self, precision: int = _cps.FP64) -> dict:
-        """Autotuned (unroll, grid) of the iteration kernels for a precision."""
+        """Autotuned (unroll, grid) of the iteration kernels for a precision,
+        and which way of running the loop the tuner chose (with the measured
+        microseconds per iteration of each candidate; 0 where not tried)."""
         u = (ctypes.c_int32 * 3)()
         g = (ctypes.c_int32 * 3)()
-        f = (ctypes.c_int32 * 2)()
-        pr = (ctypes.c_double * 3)()
-        self.ctx.check(self.ctx.lib.cps_get_tuning(self.handle, precision, u, g, f, pr),
+        bl = (ctypes.c_int32 * 3)()
+        f = (ctypes.c_int32 * 4)()
+        pr = (ctypes.c_double * 7)()
+        self.ctx.check(self.ctx.lib.cps_get_tuning(self.handle, precision, u, g, bl, f, pr),
                        "cps_get_tuning")
-        return {"unroll": list(u), "grid": list(g),
-                "cluster": bool(f[0]), "l2_window": bool(f[1]),
-                "probe_us_per_iter": {"stream": pr[0], "cluster": pr[1], "stream_l2_window": pr[2]}}
+        return {"unroll": list(u), "grid": list(g), "block": list(bl),
+                "cluster": bool(f[0]), "l2_window": ("none", "matrix", "vectors")[f[1]],
+                "persistent": bool(f[2]), "reduced_persistent": bool(f[3]),
+                "probe_us_per_iter": {"stream": pr[0], "cluster": pr[1], "stream_l2_matrix": pr[2],
+                                      "persistent": pr[3], "reduced_stream": pr[4],
+                                      "reduced_persistent": pr[5], "stream_l2_vectors": pr[6]}}
 
     def set_solver_path(self, path: int):
-        """PATH_AUTO, PATH_STREAM or PATH_CLUSTER for FP64 Jacobi solves."""
+        """PATH_AUTO, PATH_STREAM, PATH_CLUSTER or PATH_PERSISTENT for FP64
+        Jacobi and reduced-system solves."""
         self.ctx.check(self.ctx.lib.cps_set_solver_path(self.handle, path), "cps_set_solver_path")
 
     def set_precond(self, precond: int):

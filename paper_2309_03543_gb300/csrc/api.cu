@@ -71,7 +71,12 @@ int cps_assemble(cps_ctx ctx, const double* xy, int64_t nv, const int32_t* tri, 
     ctx->last_error.clear();
     rc = cps::assemble_impl(ctx, xy, nv, tri, nt, dirichlet, nb, eps, kinv, field_loc, kind, nu,
                             dt, out, as_stream(stream));
-    if (rc == CPS_OK) ctx->systems.insert(*out);
+    if (rc == CPS_OK) {
+        ctx->systems.insert(*out);
+        auto it = ctx->tune_cache.find({(*out)->nt, (*out)->nv});
+        if (it != ctx->tune_cache.end())
+            for (int p = 0; p < 2; ++p) (*out)->tune[p] = it->second[p];
+    }
     return rc;
 }
 
@@ -145,9 +150,20 @@ int cps_set_solver_path(cps_sys sys, int path) {
     if (path == CPS_PATH_AUTO) {
         t.path_done = false;
         t.path = 0;
+        t.red_done = false;
+        t.red_path = 0;
     } else if (path == CPS_PATH_STREAM) {
         t.path_done = true;
         t.path = 0;
+        t.l2win = 0;
+        t.red_done = true;
+        t.red_path = 0;
+    } else if (path == CPS_PATH_PERSISTENT) {
+        t.path_done = true;
+        t.path = 2;
+        t.l2win = 0;
+        t.red_done = true;
+        t.red_path = 1;
     } else if (path == CPS_PATH_CLUSTER) {
         if (sys->nt > cps::cluster_max_rows(sys->ctx)) {
             sys->ctx->last_error = "set_solver_path: system too large for one cluster";
@@ -155,27 +171,35 @@ int cps_set_solver_path(cps_sys sys, int path) {
         }
         t.path_done = true;
         t.path = 1;
+        t.l2win = 0;
     } else {
         return CPS_ERR_ARG;
     }
     return CPS_OK;
 }
 
-int cps_get_tuning(cps_sys sys, int precision, int32_t* unroll, int32_t* grid, int32_t* flags,
-                   double* probe_us) {
+int cps_get_tuning(cps_sys sys, int precision, int32_t* unroll, int32_t* grid, int32_t* block,
+                   int32_t* flags, double* probe_us) {
     if (!sys || !unroll || !grid || (precision != CPS_FP64 && precision != CPS_MIXED))
         return CPS_ERR_ARG;
     const cps::Tuning& t = sys->tune[precision];
     for (int k = 0; k < 3; ++k) {
         unroll[k] = t.done ? t.k[k].unroll : 0;
         grid[k] = t.done ? t.k[k].grid : 0;
+        if (block) block[k] = t.done ? t.k[k].block : 0;
     }
     if (flags) {
         flags[0] = t.path_done && t.path == 1;
-        flags[1] = t.path_done && t.l2win;
+        flags[1] = t.path_done ? t.l2win : 0;
+        flags[2] = t.path_done && t.path == 2;
+        flags[3] = t.red_done && t.red_path == 1;
     }
-    if (probe_us)
-        for (int k = 0; k < 3; ++k) probe_us[k] = t.probe_us[k];
+    if (probe_us) {
+        for (int k = 0; k < 4; ++k) probe_us[k] = t.probe_us[k];
+        probe_us[4] = t.red_probe_us[0];
+        probe_us[5] = t.red_probe_us[1];
+        probe_us[6] = t.probe_us[4];
+    }
     return CPS_OK;
 }
 

@@ -352,9 +352,8 @@ void free_sys(cps_sys s) {
     // s->col lives inside s->a's allocation (one range for the L2 window)
     void* bufs[] = {s->s,     s->diag,  s->a,     s->a32,     s->s32,      s->gfac,
                     s->dxi,   s->slot_kind, s->perm, s->iperm, s->pa,  s->pcol,     s->pl,
-                    s->pdinv, s->ps,    s->pa32,  s->pl32,  s->pdinv32, s->ps32,     s->wy,
-                    s->wr,    s->wp0,   s->wp1,   s->wq,    s->wz,      s->wb,       s->wx,
-                    s->partials, s->st};
+                    s->pdinv, s->ps,    s->pa32,  s->pl32,  s->pdinv32, s->ps32,     s->wvec,
+                    s->partials, s->st, s->gsync};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (s->hst) cudaFreeHost(s->hst);
@@ -421,14 +420,20 @@ int assemble_impl(cps_ctx ctx, const double* xy, int64_t nv, const int32_t* tri,
     TRY_ALLOC(s->a32, 3 * nt);
     TRY_ALLOC(s->s32, nt);
     TRY_ALLOC(s->slot_kind, 3 * nt);
-    TRY_ALLOC(s->wy, nt);
-    TRY_ALLOC(s->wr, nt);
-    TRY_ALLOC(s->wp0, nt);
-    TRY_ALLOC(s->wp1, nt);
-    TRY_ALLOC(s->wq, nt);
-    TRY_ALLOC(s->wz, nt);
-    TRY_ALLOC(s->wb, nt);
-    TRY_ALLOC(s->wx, nt);
+    {
+        const int64_t vs = (nt + 31) / 32 * 32;     // 256-byte aligned slices
+        TRY_ALLOC(s->wvec, 8 * vs);
+        s->vec_stride = vs;
+        double* w = s->wvec;
+        s->wr = w;
+        s->wp0 = w + vs;
+        s->wq = w + 2 * vs;
+        s->wy = w + 3 * vs;
+        s->wp1 = w + 4 * vs;
+        s->wz = w + 5 * vs;
+        s->wb = w + 6 * vs;
+        s->wx = w + 7 * vs;
+    }
     TRY_ALLOC(s->partials, (kNumPartials + 16) * kMaxGrid);
     TRY_ALLOC(s->st, 2);
     if (field_loc == CPS_PER_CELL && kind == CPS_KIND_CP2) {

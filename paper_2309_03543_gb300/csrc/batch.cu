@@ -50,8 +50,8 @@ struct TileRef {
 // completed the system's last tile, with the system's totals in v[].
 template <int NV>
 __device__ __forceinline__ bool tile_sum(double (&v)[NV], const BatchDesc& d, int tile,
-                                         unsigned int* arrive, double (*sh)[NV], bool* last) {
-    block_sum<NV>(v, sh);
+                                         unsigned int* arrive, bool* last) {
+    block_sum<NV>(v);
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) d.partials[k * kMaxGrid * 4 + tile] = v[k];
@@ -69,7 +69,7 @@ __device__ __forceinline__ bool tile_sum(double (&v)[NV], const BatchDesc& d, in
             acc += __ldcg(&d.partials[k * kMaxGrid * 4 + i]);
         v[k] = acc;
     }
-    block_sum<NV>(v, sh);
+    block_sum<NV>(v);
     if (threadIdx.x == 0) *arrive = 0u;
     return true;
 }
@@ -148,7 +148,6 @@ __global__ void __launch_bounds__(kBlock) kb_init(const BatchDesc* __restrict__ 
                                                   const TileRef* __restrict__ tiles,
                                                   const int* ntile, double rtol,
                                                   long long budget) {
-    __shared__ double sh[32][3];
     __shared__ bool last;
     CPS_TILE_LOOP(tiles, ntile) {
         const TileRef tr = tiles[ti_];
@@ -177,7 +176,7 @@ __global__ void __launch_bounds__(kBlock) kb_init(const BatchDesc* __restrict__ 
             nn = fma(t, t, nn);
         }
         double v[3] = {rr, bb, nn};
-        if (tile_sum<3>(v, d, tr.tile, &d.st->arrive[2], sh, &last) && threadIdx.x == 0) {
+        if (tile_sum<3>(v, d, tr.tile, &d.st->arrive[2], &last) && threadIdx.x == 0) {
             CgState* st = d.st;
             st->rho = v[0];
             st->bnorm2 = v[1];
@@ -198,7 +197,6 @@ __global__ void __launch_bounds__(kBlock) kb_init(const BatchDesc* __restrict__ 
 __global__ void __launch_bounds__(kBlock) kb_spmv(const BatchDesc* __restrict__ dd,
                                                   const TileRef* __restrict__ tiles,
                                                   const int* ntile) {
-    __shared__ double sh[32][1];
     __shared__ bool last;
     CPS_TILE_LOOP(tiles, ntile) {
         const TileRef tr = tiles[ti_];
@@ -221,7 +219,7 @@ __global__ void __launch_bounds__(kBlock) kb_spmv(const BatchDesc* __restrict__ 
             acc = fma(pe, v, acc);
         }
         double t[1] = {acc};
-        if (tile_sum<1>(t, d, tr.tile, &d.st->arrive[0], sh, &last) && threadIdx.x == 0) {
+        if (tile_sum<1>(t, d, tr.tile, &d.st->arrive[0], &last) && threadIdx.x == 0) {
             CgState* st = d.st;
             st->gamma = t[0];
             if (!(t[0] > 0.0) || !isfinite(t[0])) {
@@ -239,7 +237,6 @@ template <bool NORM>
 __global__ void __launch_bounds__(kBlock) kb_update(const BatchDesc* __restrict__ dd,
                                                     const TileRef* __restrict__ tiles,
                                                     const int* ntile) {
-    __shared__ double sh[32][2];
     __shared__ bool last;
     CPS_TILE_LOOP(tiles, ntile) {
         const TileRef tr = tiles[ti_];
@@ -260,7 +257,7 @@ __global__ void __launch_bounds__(kBlock) kb_update(const BatchDesc* __restrict_
             }
         }
         double t[2] = {rr, nn};
-        if (tile_sum<2>(t, d, tr.tile, &d.st->arrive[1], sh, &last) && threadIdx.x == 0) {
+        if (tile_sum<2>(t, d, tr.tile, &d.st->arrive[1], &last) && threadIdx.x == 0) {
             CgState* st = d.st;
             const long long it = st->iter + 1;
             st->iter = it;
@@ -302,7 +299,6 @@ __global__ void __launch_bounds__(kBlock) kb_direction(const BatchDesc* __restri
 __global__ void __launch_bounds__(kBlock) kb_final(const BatchDesc* __restrict__ dd,
                                                    const TileRef* __restrict__ tiles,
                                                    const int* ntile) {
-    __shared__ double sh[32][1];
     __shared__ bool last;
     CPS_TILE_LOOP(tiles, ntile) {
         const TileRef tr = tiles[ti_];
@@ -326,7 +322,7 @@ __global__ void __launch_bounds__(kBlock) kb_final(const BatchDesc* __restrict__
             nn = fma(res, res, nn);
         }
         double t[1] = {nn};
-        if (tile_sum<1>(t, d, tr.tile, &d.st->arrive[3], sh, &last) && threadIdx.x == 0)
+        if (tile_sum<1>(t, d, tr.tile, &d.st->arrive[3], &last) && threadIdx.x == 0)
             d.st->rnorm2 = t[0];
         __syncthreads();
     }

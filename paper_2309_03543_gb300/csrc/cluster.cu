@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_cluster_cg(ClusterArgs A
         const double t = s_s[i] * re;
         v3[2] = fma(t, t, v3[2]);
     }
-    block_sum<3>(v3, sh3);
+    block_sum_shfl<3>(v3, sh3);
     push(0, v3[0]);
     push(1, v3[1]);
     push(2, v3[2]);
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_cluster_cg(ClusterArgs A
             q_s[i] = v;
             g1[0] = fma(pe, v, g1[0]);
         }
-        block_sum<1>(g1, sh1);
+        block_sum_shfl<1>(g1, sh1);
         push(0, g1[0]);
         cluster.sync();
         const double gamma = cluster_sum(0);
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_cluster_cg(ClusterArgs A
                 g2[1] = fma(t, t, g2[1]);
             }
         }
-        block_sum<2>(g2, sh2);
+        block_sum_shfl<2>(g2, sh2);
         push(1, g2[0]);
         push(2, g2[1]);
         cluster.sync();

@@ -6,8 +6,11 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <array>
 #include <cstdio>
+#include <map>
 #include <string>
+#include <utility>
 #include <unordered_set>
 
 #include "cps.h"
@@ -42,6 +45,7 @@ struct CgState {
 struct KCfg {
     int unroll = 2;
     int grid = 0;
+    int block = kBlock;      // threads per block (FP64 iteration kernels: 256 or 1024)
 };
 
 // Autotuned configurations of the iteration kernels of one precision:
@@ -50,10 +54,16 @@ struct KCfg {
 struct Tuning {
     KCfg k[3];
     bool done = false;
-    int path = 0;            // FP64 Jacobi: 0 graph-replayed kernels, 1 one-cluster launch
+    int path = 0;            // FP64 Jacobi: 0 graph-replayed kernels, 1 one-cluster launch,
+                             // 2 one persistent grid-synchronised launch
+    int red_path = 0;        // reduced system: 0 graph-replayed kernels, 1 persistent launch
+    bool red_done = false;
     bool path_done = false;
-    bool l2win = false;      // FP64 Jacobi stream path: matrix held in persisting L2
-    double probe_us[3] = {0, 0, 0};      // us/iteration: stream, cluster, stream + L2 window
+    int l2win = 0;           // FP64 Jacobi stream path, persisting L2 window: 0 none,
+                             // 1 the matrix, 2 the vectors r, p, q
+    double probe_us[5] = {0, 0, 0, 0, 0};   // us/iteration: stream, cluster, stream + matrix
+                                            // in L2, persistent, stream + vectors in L2
+    double red_probe_us[2] = {0, 0};     // reduced system: stream, persistent
 };
 
 // Device error flag written by the assembly kernels (first error wins).
@@ -61,11 +71,39 @@ __device__ __forceinline__ void set_error(int* err, int code) {
     atomicCAS(err, 0, code);
 }
 
-// Deterministic sum over the grid: every block writes its partial sums, the
-// last block to arrive adds them up in a fixed order.  Returns true only in
-// the last block, where out[] then holds the totals in every thread.
+// Block-wide sum of v[0..NV) over BS threads (BS = blockDim.x); on return
+// every thread holds the totals.  GB300 issues FP64 adds at 1/64 of the FP32
+// rate, so the adds are kept few: every thread stores its values to shared
+// memory and warp k alone adds the BS values of quantity k (BS/32 serial adds
+// per lane, then a 5-step shuffle tree), NV (BS/32 + 5) warp-wide FP64 adds
+// per block instead of the (BS/32 + 1) 5 of a shuffle tree in every warp.  The
+// order is fixed, so the result is deterministic.
+template <int NV, int BS = kBlock>
+__device__ __forceinline__ void block_sum(double (&v)[NV]) {
+    static_assert(BS % 32 == 0 && BS <= 1024 && NV <= BS / 32, "block shape");
+    __shared__ double buf[NV][BS];
+    __shared__ double tot[NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) buf[k][threadIdx.x] = v[k];
+    __syncthreads();
+    if (warp < NV) {
+        double t = buf[warp][lane];
+#pragma unroll
+        for (int j = lane + 32; j < BS; j += 32) t += buf[warp][j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) tot[warp] = t;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = tot[k];
+}
+
+// Older form (a shuffle tree in every warp, then one over the warp sums), for
+// kernels whose shared memory is spoken for; sh holds 32 x NV doubles.
 template <int NV>
-__device__ __forceinline__ void block_sum(double (&v)[NV], double (*sh)[NV]) {
+__device__ __forceinline__ void block_sum_shfl(double (&v)[NV], double (*sh)[NV]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
@@ -98,12 +136,14 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double (*sh)[NV]) {
     __syncthreads();
 }
 
-template <int NV>
+// Deterministic sum over the grid: every block writes its partial sums, the
+// last block to arrive adds them up in a fixed order.  Returns true only in
+// the last block, where v[] then holds the totals in every thread.
+template <int NV, int BS = kBlock>
 __device__ __forceinline__ bool grid_sum(double (&v)[NV], double* partials,
                                          unsigned int* arrive) {
-    __shared__ double sh[32][NV];
     __shared__ bool last;
-    block_sum<NV>(v, sh);
+    block_sum<NV, BS>(v);
     const int G = gridDim.x;
     if (threadIdx.x == 0) {
 #pragma unroll
@@ -121,7 +161,7 @@ __device__ __forceinline__ bool grid_sum(double (&v)[NV], double* partials,
         for (int i = threadIdx.x; i < G; i += blockDim.x) acc += __ldcg(&partials[k * kMaxGrid + i]);
         v[k] = acc;
     }
-    block_sum<NV>(v, sh);
+    block_sum<NV, BS>(v);
     if (threadIdx.x == 0) *arrive = 0u;
     return true;
 }
@@ -138,6 +178,9 @@ struct cps_ctx_s {
     size_t l2_persist_set = 0;   // persisting L2 limit this process has set
     std::string last_error;
     std::unordered_set<cps_sys_s*> systems;   // live systems, freed with the context
+    // Tuned launch choices by mesh size (cells, vertices): a system assembled
+    // later on a mesh of the same size starts from them instead of re-timing.
+    std::map<std::pair<int64_t, int64_t>, std::array<cps::Tuning, 2>> tune_cache;
 };
 
 struct cps_sys_s {
@@ -182,7 +225,12 @@ struct cps_sys_s {
     float* pdinv32 = nullptr;
     float* ps32 = nullptr;
 
-    // PCG workspace (allocated at assembly so that solves never allocate).
+    // PCG workspace (allocated at assembly so that solves never allocate), one
+    // allocation of 8 vectors of vec_stride doubles in the order r, p0, q, y,
+    // p1, z, b, x: r, p0 and q, the vectors every iteration reads and writes,
+    // are one contiguous range for an L2 access-policy window.
+    double* wvec = nullptr;
+    int64_t vec_stride = 0;
     double* wy = nullptr;       // [nt] iterate (scaled)
     double* wr = nullptr;       // [nt] residual
     double* wp0 = nullptr;      // [nt] search direction, even iterations
@@ -202,9 +250,10 @@ struct cps_sys_s {
     // [precision][0 Jacobi, 1 IC(0), 2 reduced system]
     cudaGraphExec_t graph[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
     int64_t graph_nodes[2][3] = {{0, 0, 0}, {0, 0, 0}};
-    bool graph_l2win[2][3] = {{false, false, false}, {false, false, false}};
+    int graph_l2win[2][3] = {{0, 0, 0}, {0, 0, 0}};
     cps::Tuning tune[2];        // per precision (CPS_FP64, CPS_MIXED)
     int cluster_size = 0;       // CTAs of the last one-cluster solve
+    void* gsync = nullptr;      // grid-barrier state of the persistent solves
 };
 
 #define CPS_CUDA_TRY(ctx, call)                                                        \
@@ -245,6 +294,9 @@ int matvec_impl(cps_sys sys, const double* x, double* y, cudaStream_t stream);
 int64_t cluster_max_rows(cps_ctx ctx);
 int cluster_solve(cps_sys s, const double* b, const double* x, double* y, double rtol,
                   long long max_iter, cudaStream_t stream);
+int persistent_solve(cps_sys s, int reduced, const double* a, const int32_t* col,
+                     const double* sc, double* y, double* r, double* p, double* q, double* t,
+                     int64_t n, int64_t nR, cudaStream_t stream);
 int export_impl(cps_sys sys, double* diag, int32_t* col, double* val, cudaStream_t stream);
 void free_sys(cps_sys sys);
 

@@ -30,7 +30,7 @@ constexpr int kCheckEvery = 8;      // stop test period inside a chunk
 constexpr double kDelta = 0.5;      // residual drop between reliable updates
 constexpr int kMaxUpdates = 2000;
 constexpr int64_t kTuneMinRows = 1 << 17;   // smaller systems keep the defaults
-constexpr int kTuneReps = 5;
+constexpr int kTuneIters = 32;               // iterations per timed candidate
 }  // namespace
 
 static int ensure_capture_stream(cps_sys s) {
@@ -116,16 +116,42 @@ static void launch_k(void (*kernel)(KArgs...), int grid, cudaStream_t st, Args..
     kernel<<<grid, kBlock, 0, st>>>(static_cast<KArgs>(args)...);
 }
 
+template <typename... KArgs, typename... Args>
+static void launch_kb(void (*kernel)(KArgs...), int grid, int block, cudaStream_t st,
+                      Args... args) {
+    kernel<<<grid, block, 0, st>>>(static_cast<KArgs>(args)...);
+}
+
 template <typename V>
 static void launch_a(const KCfg& c, const Run<V>& v, cps_sys s, cudaStream_t st);
 
+// FP64 iteration kernels: (unroll, block size) picks the instantiation.
+#define CPS_FP64_SHAPES(KERNEL_U_B, ...)                                                  \
+    switch (c.unroll * 2048 + c.block) {                                                  \
+        case 1 * 2048 + 1024:                                                             \
+            launch_kb(KERNEL_U_B(1, 1024), c.grid, 1024, __VA_ARGS__);                    \
+            break;                                                                        \
+        case 2 * 2048 + 1024:                                                             \
+            launch_kb(KERNEL_U_B(2, 1024), c.grid, 1024, __VA_ARGS__);                    \
+            break;                                                                        \
+        case 4 * 2048 + 1024:                                                             \
+            launch_kb(KERNEL_U_B(4, 1024), c.grid, 1024, __VA_ARGS__);                    \
+            break;                                                                        \
+        case 1 * 2048 + kBlock:                                                           \
+            launch_kb(KERNEL_U_B(1, kBlock), c.grid, kBlock, __VA_ARGS__);                \
+            break;                                                                        \
+        case 4 * 2048 + kBlock:                                                           \
+            launch_kb(KERNEL_U_B(4, kBlock), c.grid, kBlock, __VA_ARGS__);                \
+            break;                                                                        \
+        default:                                                                          \
+            launch_kb(KERNEL_U_B(2, kBlock), c.grid, kBlock, __VA_ARGS__);                \
+            break;                                                                        \
+    }
+
+#define CPS_SPMV64(U, B) k_spmv_dot<double, U, B>
 template <>
 void launch_a<double>(const KCfg& c, const Run<double>& v, cps_sys s, cudaStream_t st) {
-    switch (c.unroll) {
-        case 1: launch_k(k_spmv_dot<double, 1>, c.grid, st, v.a, v.col, v.p0, v.q, v.n, s->partials, s->st); break;
-        case 4: launch_k(k_spmv_dot<double, 4>, c.grid, st, v.a, v.col, v.p0, v.q, v.n, s->partials, s->st); break;
-        default: launch_k(k_spmv_dot<double, 2>, c.grid, st, v.a, v.col, v.p0, v.q, v.n, s->partials, s->st); break;
-    }
+    CPS_FP64_SHAPES(CPS_SPMV64, st, v.a, v.col, v.p0, v.q, v.n, s->partials, s->st)
 }
 
 template <>
@@ -139,10 +165,16 @@ void launch_a<float>(const KCfg& c, const Run<float>& v, cps_sys s, cudaStream_t
 
 template <typename V, bool NORM, bool JACOBI>
 static void launch_b_u(const KCfg& c, const Run<V>& v, cps_sys s, cudaStream_t st) {
-    switch (c.unroll) {
-        case 1: launch_k(k_cg_b<V, NORM, JACOBI, 1>, c.grid, st, v.r, v.q, v.s, v.n, s->partials, s->st); break;
-        case 4: launch_k(k_cg_b<V, NORM, JACOBI, 4>, c.grid, st, v.r, v.q, v.s, v.n, s->partials, s->st); break;
-        default: launch_k(k_cg_b<V, NORM, JACOBI, 2>, c.grid, st, v.r, v.q, v.s, v.n, s->partials, s->st); break;
+    if constexpr (sizeof(V) == 8) {
+#define CPS_CGB64(U, B) k_cg_b<double, NORM, JACOBI, U, B>
+        CPS_FP64_SHAPES(CPS_CGB64, st, v.r, v.q, v.s, v.n, s->partials, s->st)
+#undef CPS_CGB64
+    } else {
+        switch (c.unroll) {
+            case 1: launch_k(k_cg_b<V, NORM, JACOBI, 1>, c.grid, st, v.r, v.q, v.s, v.n, s->partials, s->st); break;
+            case 4: launch_k(k_cg_b<V, NORM, JACOBI, 4>, c.grid, st, v.r, v.q, v.s, v.n, s->partials, s->st); break;
+            default: launch_k(k_cg_b<V, NORM, JACOBI, 2>, c.grid, st, v.r, v.q, v.s, v.n, s->partials, s->st); break;
+        }
     }
 }
 
@@ -155,12 +187,9 @@ static void launch_b(const KCfg& c, const Run<V>& v, bool norm, cps_sys s, cudaS
     else launch_b_u<V, false, false>(c, v, s, st);
 }
 
+#define CPS_CGC64(U, B) k_cg_c<double, U, B>
 static void launch_c(const KCfg& c, const Run<double>& v, cps_sys s, cudaStream_t st) {
-    switch (c.unroll) {
-        case 1: launch_k(k_cg_c<double, 1>, c.grid, st, v.y, v.p0, v.z, v.n, s->st); break;
-        case 4: launch_k(k_cg_c<double, 4>, c.grid, st, v.y, v.p0, v.z, v.n, s->st); break;
-        default: launch_k(k_cg_c<double, 2>, c.grid, st, v.y, v.p0, v.z, v.n, s->st); break;
-    }
+    CPS_FP64_SHAPES(CPS_CGC64, st, v.y, v.p0, v.z, v.n, s->st)
 }
 
 static Tuning default_tuning(cps_sys s) {
@@ -172,61 +201,121 @@ static Tuning default_tuning(cps_sys s) {
     return t;
 }
 
-// Times every (unroll, grid) candidate of each iteration kernel on the
-// system's own data and keeps the fastest.  The vectors are scratch here:
-// the caller starts the run afresh afterwards.
+// The context's remembered choices for systems of this mesh size.
+static Tuning* cached_tuning(cps_sys s, int prec) {
+    return &s->ctx->tune_cache[{s->nt, s->nv}][prec];
+}
+
+template <typename V>
+static int64_t enqueue_iteration(cps_sys s, const Run<V>& v, int prec, bool norm, cudaStream_t st);
+
+// Picks the launch shape of every iteration kernel by timing whole
+// iterations on the system's own matrix: coordinate descent over the
+// kernels (SpMV, residual update, direction update), each candidate timed
+// as kTuneIters consecutive iterations with the other kernels at their
+// current choice.  Timing a kernel alone, with its operands warm in L2 from
+// the repetition before, ranks candidates differently from the loop.  The
+// vectors are scratch here (a CG run on positive constant data, primed so
+// that it never stops); the caller starts the run afresh afterwards.
 template <typename V>
 static int autotune(cps_sys s, int prec, const Run<V>& v, cudaStream_t stream) {
     Tuning& t = s->tune[prec];
-    t = default_tuning(s);
+    {
+        const Tuning d = default_tuning(s);     // kernel shapes only: a chosen path stays
+        for (int k = 0; k < 3; ++k) t.k[k] = d.k[k];
+    }
     t.done = true;
     if (s->nt < kTuneMinRows) return CPS_OK;
+    const size_t vb = sizeof(V) * (size_t)s->nt;
+    // 0x3F bytes: a small positive value in binary32 and in binary64
+    V* const scratch[4] = {v.r, v.p0, v.p1, v.z};
+    for (int k = 0; k < 4; ++k)
+        CPS_CUDA_TRY(s->ctx, cudaMemsetAsync(scratch[k], 0x3F, vb, stream));
+    CPS_CUDA_TRY(s->ctx, cudaMemsetAsync(v.y, 0, vb, stream));
+    CPS_CUDA_TRY(s->ctx, cudaMemsetAsync(v.q, 0, vb, stream));
     cudaEvent_t e0, e1;
     CPS_CUDA_TRY(s->ctx, cudaEventCreate(&e0));
     CPS_CUDA_TRY(s->ctx, cudaEventCreate(&e1));
-    const int unrolls[3] = {1, 2, 4};
-    const int per_sm[3] = {4, 8, 16};
-    const int nk = sizeof(V) == 8 ? 3 : 2;
-    int rc = CPS_OK;
-    for (int kind = 0; kind < nk && rc == CPS_OK; ++kind) {
+    int rc = ensure_capture_stream(s);
+    if (rc) return rc;
+    // kTuneIters iterations as one graph (as the solve replays them), timed
+    // three times; the first run warms up
+    auto time_loop = [&]() -> float {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        if (cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal) !=
+            cudaSuccess) {
+            rc = CPS_ERR_CUDA;
+            return 1e30f;
+        }
+        for (int k = 0; k < kTuneIters; ++k)
+            enqueue_iteration<V>(s, v, prec, (k % kCheckEvery) == kCheckEvery - 1, s->cap_stream);
+        const cudaError_t le = cudaGetLastError();
+        const cudaError_t ce = cudaStreamEndCapture(s->cap_stream, &graph);
+        if (le != cudaSuccess || ce != cudaSuccess ||
+            cudaGraphInstantiate(&ge, graph, 0) != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            rc = CPS_ERR_CUDA;
+            return 1e30f;
+        }
+        cudaGraphDestroy(graph);
         float best = 1e30f;
-        for (int ui = 0; ui < 3; ++ui)
-            for (int gi = 0; gi < 3; ++gi) {
-                KCfg c{unrolls[ui], grid_for(s->ctx, s->nt, per_sm[gi])};
-                auto once = [&]() {
-                    if (kind == 0) {
-                        launch_a<V>(c, v, s, stream);
-                    } else if (kind == 1) {
-                        launch_b<V>(c, v, false, s, stream);
-                    } else if constexpr (sizeof(V) == 8) {
-                        launch_c(c, v, s, stream);
-                    }
-                };
-                k_tune_prime<<<1, 1, 0, stream>>>(s->st);
-                once();
-                cudaEventRecord(e0, stream);
-                for (int r = 0; r < kTuneReps; ++r) {
-                    k_tune_prime<<<1, 1, 0, stream>>>(s->st);
-                    once();
-                }
-                cudaEventRecord(e1, stream);
-                if (cudaEventSynchronize(e1) != cudaSuccess) {
-                    rc = CPS_ERR_CUDA;
-                    break;
-                }
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
+        for (int rep = 0; rep < 3 && rc == CPS_OK; ++rep) {
+            k_tune_prime<<<1, 1, 0, stream>>>(s->st);
+            cudaEventRecord(e0, stream);
+            cudaGraphLaunch(ge, stream);
+            cudaEventRecord(e1, stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = CPS_ERR_CUDA;
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) best = ms < best ? ms : best;
+        }
+        cudaGraphExecDestroy(ge);
+        return best;
+    };
+    // candidates: rows per thread per trip x (block size, blocks per SM)
+    const int unrolls[3] = {1, 2, 4};
+    struct Shape {
+        int block, per_sm;
+    };
+    const Shape shapes64[5] = {{kBlock, 4}, {kBlock, 8}, {kBlock, 16}, {1024, 1}, {1024, 2}};
+    const int nshapes = sizeof(V) == 8 ? 5 : 3;       // binary32 kernels: 256 threads
+    const int nk = sizeof(V) == 8 ? 3 : 2;
+    for (int kind = 0; kind < nk && rc == CPS_OK; ++kind) {
+        KCfg keep = t.k[kind];
+        float best = time_loop();
+        for (int ui = 0; ui < 3 && rc == CPS_OK; ++ui)
+            for (int gi = 0; gi < nshapes && rc == CPS_OK; ++gi) {
+                const Shape sh = shapes64[gi];
+                KCfg c;
+                c.unroll = unrolls[ui];
+                c.block = sh.block;
+                c.grid = grid_for(s->ctx, s->nt * kBlock / sh.block, sh.per_sm);
+                if (c.unroll == keep.unroll && c.block == keep.block && c.grid == keep.grid)
+                    continue;
+                t.k[kind] = c;
+                const float ms = time_loop();
                 if (ms < best) {
                     best = ms;
-                    t.k[kind] = c;
+                    keep = c;
                 }
             }
+        t.k[kind] = keep;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (cudaGetLastError() != cudaSuccess) rc = CPS_ERR_CUDA;
-    if (rc) s->ctx->last_error = "autotune: kernel launch failed";
-    return rc;
+    if (rc) {
+        s->ctx->last_error = "autotune: kernel launch failed";
+        return rc;
+    }
+    Tuning* c = cached_tuning(s, prec);
+    for (int k = 0; k < 3; ++k) c->k[k] = t.k[k];
+    c->done = true;
+    return CPS_OK;
 }
 
 // z = M^-1 r with the IC(0) colour sweeps; also rho = r.z and beta.
@@ -264,32 +353,39 @@ static int64_t enqueue_iteration(cps_sys s, const Run<V>& v, int prec, bool norm
     return nl;
 }
 
-// The matrix of a FP64 Jacobi run (values and columns, one allocation) as a
-// persisting L2 access-policy window: the iteration re-reads it every time,
-// and at up to ~100 MB it fits GB300's 129 MB L2 next to the streamed
-// vectors.  The context's persisting-L2 limit is raised once to cover it.
-static bool l2_window_fits(cps_sys s) {
-    return s->ctx->l2_persist_max > 0 && s->mat_bytes <= s->ctx->l2_persist_max;
+// Persisting L2 access-policy windows of a FP64 Jacobi run: mode 1 holds
+// the matrix (values and columns, one allocation; re-read every iteration),
+// mode 2 the vectors r, p and q (one contiguous range; each is read and
+// written every iteration, 64 of the 117 bytes a row moves).  At a few
+// million cells either fits GB300's 129 MB L2 next to the streamed rest.
+static void* l2_window_base(cps_sys s, int mode) {
+    return mode == 1 ? (void*)s->a : (void*)s->wr;
+}
+static size_t l2_window_bytes(cps_sys s, int mode) {
+    return mode == 1 ? s->mat_bytes : (size_t)3 * s->vec_stride * sizeof(double);
+}
+static bool l2_window_fits(cps_sys s, int mode) {
+    return s->ctx->l2_persist_max > 0 && l2_window_bytes(s, mode) <= s->ctx->l2_persist_max;
 }
 
 // The persisting set-aside is a context-wide reservation that shrinks the L2
 // every other kernel sees, so it is held only for the duration of a solve
 // that uses the window and given back (set to 0) right after.
-static int l2_set_aside(cps_sys s, bool on, cudaStream_t st) {
-    const size_t want = on ? s->mat_bytes : 0;
+static int l2_set_aside(cps_sys s, int mode, cudaStream_t st) {
+    const size_t want = mode ? l2_window_bytes(s, mode) : 0;
     if (s->ctx->l2_persist_set == want) return CPS_OK;
     CPS_CUDA_TRY(s->ctx, cudaStreamSynchronize(st));
-    if (!on) CPS_CUDA_TRY(s->ctx, cudaCtxResetPersistingL2Cache());
+    if (s->ctx->l2_persist_set) CPS_CUDA_TRY(s->ctx, cudaCtxResetPersistingL2Cache());
     CPS_CUDA_TRY(s->ctx, cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want));
     s->ctx->l2_persist_set = want;
     return CPS_OK;
 }
 
-static int set_l2_window(cps_sys s, cudaStream_t st, bool on) {
+static int set_l2_window(cps_sys s, cudaStream_t st, int mode) {
     cudaStreamAttrValue v = {};
-    if (on) {
-        v.accessPolicyWindow.base_ptr = s->a;
-        v.accessPolicyWindow.num_bytes = s->mat_bytes;
+    if (mode) {
+        v.accessPolicyWindow.base_ptr = l2_window_base(s, mode);
+        v.accessPolicyWindow.num_bytes = l2_window_bytes(s, mode);
         v.accessPolicyWindow.hitRatio = 1.0f;
         v.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
         v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
@@ -306,7 +402,7 @@ template <typename V>
 static int get_chunk_graph(cps_sys s, int prec, const Run<V>& v, cudaGraphExec_t* out,
                            int64_t* per_chunk) {
     const int pc = v.l ? 1 : 0;
-    const bool win = prec == CPS_FP64 && pc == 0 && s->tune[CPS_FP64].l2win;
+    const int win = (prec == CPS_FP64 && pc == 0) ? s->tune[CPS_FP64].l2win : 0;
     if (s->graph[prec][pc] && s->graph_l2win[prec][pc] != win) {
         cudaGraphExecDestroy(s->graph[prec][pc]);
         s->graph[prec][pc] = nullptr;
@@ -340,7 +436,7 @@ static int get_chunk_graph(cps_sys s, int prec, const Run<V>& v, cudaGraphExec_t
         }
         s->graph_nodes[prec][pc] = nl;
         if (win) {
-            rc = set_l2_window(s, s->cap_stream, false);
+            rc = set_l2_window(s, s->cap_stream, 0);
             if (rc) return rc;
         }
     }
@@ -399,38 +495,52 @@ static void fill_stats(cps_stats* stats, int64_t iters, double rel, int status, 
 
 // ------------------------------------------------------------------ FP64
 
-// For Jacobi solves of systems that fit one cluster's shared memory, times a
-// 64-iteration run of each path (graph-replayed streaming kernels, and the
-// one-launch cluster solve) from x = 0 and keeps the faster one.
+// For Jacobi solves, times a short run (64 iterations; 256 on large systems)
+// of each path that applies from x = 0 and keeps the fastest: graph-replayed
+// streaming kernels, the one-launch cluster solve (systems that fit one
+// cluster's shared memory), streaming with the matrix or with the vectors
+// r, p, q held in persisting L2 (large systems whose window fits the
+// set-aside), and the persistent grid-synchronised launch.
 static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
                             cudaStream_t stream) {
     Tuning& t = s->tune[CPS_FP64];
     t.path_done = true;
     t.path = 0;
-    t.l2win = false;
+    t.l2win = 0;
     if (s->precond != CPS_PC_JACOBI) return CPS_OK;
     const bool try_cluster = s->nt <= cluster_max_rows(s->ctx);
-    const bool try_win = !try_cluster && l2_window_fits(s) && s->nt >= kTuneMinRows;
+    const bool big = !try_cluster && s->nt >= kTuneMinRows;
     const long long probe = s->nt >= kTuneMinRows ? 256 : 64;
+    // candidate 3 (persistent grid-synchronised launch) is always tried
     cudaEvent_t e0, e1;
     CPS_CUDA_TRY(s->ctx, cudaEventCreate(&e0));
     CPS_CUDA_TRY(s->ctx, cudaEventCreate(&e1));
     // candidates: 0 streaming, 1 one-cluster launch, 2 streaming with the
-    // matrix in persisting L2
-    double per_iter[4] = {0.0, 0.0, 0.0, 0.0};
+    // matrix in persisting L2, 3 one persistent grid-synchronised launch,
+    // 4 streaming with the vectors r, p, q in persisting L2
+    double per_iter[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     int rc = CPS_OK;
     cudaGraphExec_t ge = nullptr;
     int64_t per_chunk = 0, dummy = 0;
-    for (int path = 0; path < 3 && rc == CPS_OK; ++path) {
-        if ((path == 1 && !try_cluster) || (path == 2 && !try_win)) continue;
-        t.l2win = path == 2;
+    for (int path = 0; path < 5 && rc == CPS_OK; ++path) {
+        if (path == 1 && !try_cluster) continue;
+        if (path == 2 && !(big && l2_window_fits(s, 1))) continue;
+        if (path == 4 && !(big && l2_window_fits(s, 2))) continue;
+        t.l2win = path == 2 ? 1 : (path == 4 ? 2 : 0);
         rc = l2_set_aside(s, t.l2win, stream);
         if (rc == CPS_OK) rc = get_chunk_graph<double>(s, CPS_FP64, v, &ge, &per_chunk);
         for (int rep = 0; rep < 2 && rc == CPS_OK; ++rep) {   // first one warms up
             CPS_CUDA_TRY(s->ctx, cudaMemsetAsync(s->wx, 0, sizeof(double) * s->nt, stream));
             CgState h{};
             CPS_CUDA_TRY(s->ctx, cudaEventRecord(e0, stream));
-            if (path != 1) {
+            if (path == 3) {
+                k_init64<<<s->grid, kBlock, 0, stream>>>(b, s->wx, v.s, v.a, v.col, s->nt, v.y, v.r,
+                                                         v.p0, 0.0, probe, 1, s->partials, s->st);
+                rc = persistent_solve(s, 0, v.a, v.col, v.s, v.y, v.r, v.p0, v.q, nullptr, s->nt,
+                                      0, stream);
+                if (rc == CPS_OK) rc = read_state(s, stream, &h);
+                if (rc == CPS_OK && h.status != CPS_OK) rc = CPS_ERR_ARG;   // not usable here
+            } else if (path != 1) {
                 k_init64<<<s->grid, kBlock, 0, stream>>>(b, s->wx, v.s, v.a, v.col, s->nt, v.y, v.r,
                                                          v.p0, 0.0, probe, 1, s->partials, s->st);
                 rc = run_chunks<double>(s, CPS_FP64, v, stream, &h, &dummy);
@@ -442,26 +552,32 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
             CPS_CUDA_TRY(s->ctx, cudaEventSynchronize(e1));
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
-            per_iter[path] = ms / (double)(h.iter > 0 ? h.iter : 1);
+            per_iter[path] = rc == CPS_OK ? ms / (double)(h.iter > 0 ? h.iter : 1) : 0.0;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     {
-        const int rc2 = l2_set_aside(s, false, stream);
+        const int rc2 = l2_set_aside(s, 0, stream);
         if (rc == CPS_OK) rc = rc2;
     }
-    t.l2win = false;
-    if (rc == CPS_ERR_ARG) {
-        rc = CPS_OK;        // no cluster shape: keep the graph path
-    } else if (rc == CPS_OK) {
+    t.l2win = 0;
+    if (rc == CPS_ERR_ARG) rc = CPS_OK;      // a candidate that cannot run here: skip it
+    if (rc == CPS_OK) {
         int best = 0;
-        for (int c = 1; c < 3; ++c)
+        for (int c = 1; c < 5; ++c)
             if (per_iter[c] > 0.0 && per_iter[c] < per_iter[best]) best = c;
-        t.path = best == 1 ? 1 : 0;
-        t.l2win = best == 2;
+        t.path = best == 1 ? 1 : (best == 3 ? 2 : 0);
+        t.l2win = best == 2 ? 1 : (best == 4 ? 2 : 0);
     }
-    for (int c = 0; c < 4; ++c) t.probe_us[c] = 1e3 * per_iter[c];
+    for (int c = 0; c < 5; ++c) t.probe_us[c] = 1e3 * per_iter[c];
+    if (rc == CPS_OK) {
+        Tuning* c = cached_tuning(s, CPS_FP64);
+        c->path_done = true;
+        c->path = t.path;
+        c->l2win = t.l2win;
+        for (int k = 0; k < 5; ++k) c->probe_us[k] = t.probe_us[k];
+    }
     return rc;
 }
 
@@ -483,9 +599,10 @@ static int solve_fp64(cps_sys s, const double* b, double* x, double rtol, int64_
         if (rc) return rc;
     }
     const bool cluster = !ic0 && s->tune[CPS_FP64].path == 1;
-    const bool window = !ic0 && !cluster && s->tune[CPS_FP64].l2win;
+    const bool persistent = !ic0 && s->tune[CPS_FP64].path == 2;
+    const int window = (!ic0 && !cluster && !persistent) ? s->tune[CPS_FP64].l2win : 0;
     if (window) {
-        int rc = l2_set_aside(s, true, stream);
+        int rc = l2_set_aside(s, window, stream);
         if (rc) return rc;
     }
     if (ic0) {
@@ -520,6 +637,25 @@ static int solve_fp64(cps_sys s, const double* b, double* x, double rtol, int64_
         k_init64<<<g, kBlock, 0, stream>>>(bb, xx, v.s, v.a, v.col, n, v.y, v.r, v.p0, rtol,
                                             budget, ic0 ? 0 : 1, s->partials, s->st);
         ++launches;
+        if (persistent) {
+            // one launch runs to the stop (it returns at once if init stopped)
+            int rc = persistent_solve(s, 0, v.a, v.col, v.s, v.y, v.r, v.p0, v.q, nullptr, n, 0,
+                                      stream);
+            if (rc) return rc;
+            ++launches;
+            rc = read_state(s, stream, &h);
+            if (rc) return rc;
+            total += h.iter;
+            status = h.status;
+            k_final64<<<g, kBlock, 0, stream>>>(bb, v.y, v.s, v.a, v.col, n, xx, s->partials,
+                                                s->st);
+            ++launches;
+            CPS_CUDA_TRY(s->ctx, cudaGetLastError());
+            rc = read_state(s, stream, &h);
+            if (rc) return rc;
+            if (status != CPS_OK || h.rnorm2 <= h.thresh2 || total >= max_iter) break;
+            continue;
+        }
         if (ic0) {
             launches += enqueue_precond<double>(s, v, stream);
             k_copy<double><<<g, kBlock, 0, stream>>>(v.p0, v.z, n);
@@ -549,13 +685,14 @@ static int solve_fp64(cps_sys s, const double* b, double* x, double rtol, int64_
     }
     if (window) {
         // release the lines and the set-aside: later work gets the whole L2
-        int rc = l2_set_aside(s, false, stream);
+        int rc = l2_set_aside(s, 0, stream);
         if (rc) return rc;
     }
     const double rel = h.bnorm2 > 0 ? std::sqrt(h.rnorm2 / h.bnorm2) : 0.0;
     if (status == CPS_OK && h.bnorm2 > 0 && !(rel <= rtol)) status = CPS_ERR_NOT_CONVERGED;
     fill_stats(stats, total, rel, status, 1, launches);
     if (status == CPS_ERR_NOT_SPD) s->ctx->last_error = "solve: p.Ap <= 0 (matrix not SPD or NaN input)";
+    if (status == CPS_ERR_TIMEOUT) s->ctx->last_error = "solve: a grid barrier wait ran out";
     if (status == CPS_ERR_NOT_CONVERGED) s->ctx->last_error = "solve: max_iter reached";
     return status;
 }
@@ -620,6 +757,71 @@ static int solve_reduced(cps_sys s, const double* b, double* x, double rtol, int
         }
         s->graph_nodes[CPS_FP64][2] = nl;
     }
+    // Runs CG from the state k_black_init left, on the graph-replayed kernels
+    // or (pers) in one persistent grid-synchronised launch; state into *hh.
+    auto run_cg = [&](bool pers, CgState* hh) -> int {
+        if (pers) {
+            int rc = persistent_solve(s, 1, A, col, S, y, r, p, q, t, n, nR, stream);
+            if (rc) return rc;
+            ++launches;
+            return read_state(s, stream, hh);
+        }
+        int rc = read_state(s, stream, hh);
+        if (rc || hh->done) return rc;
+        for (long long k = 0;; ++k) {
+            const int slot = (int)(k & 1);
+            CPS_CUDA_TRY(s->ctx, cudaGraphLaunch(ge, stream));
+            launches += s->graph_nodes[CPS_FP64][2];
+            CPS_CUDA_TRY(s->ctx, cudaMemcpyAsync(&s->hst[slot], s->st, sizeof(CgState),
+                                                 cudaMemcpyDeviceToHost, stream));
+            CPS_CUDA_TRY(s->ctx, cudaEventRecord(s->ev[slot], stream));
+            if (k >= 1) {
+                CPS_CUDA_TRY(s->ctx, cudaEventSynchronize(s->ev[1 - slot]));
+                if (s->hst[1 - slot].done) break;
+            }
+        }
+        return read_state(s, stream, hh);
+    };
+    Tuning& tu = s->tune[CPS_FP64];
+    if (!tu.red_done) {
+        // time a short run of each from x = 0 and keep the faster
+        const long long probe = nB >= kTuneMinRows ? 256 : 64;
+        cudaEvent_t e0, e1;
+        CPS_CUDA_TRY(s->ctx, cudaEventCreate(&e0));
+        CPS_CUDA_TRY(s->ctx, cudaEventCreate(&e1));
+        double per_iter[2] = {0.0, 0.0};
+        int rc = CPS_OK;
+        for (int c = 0; c < 2 && rc == CPS_OK; ++c) {
+            for (int rep = 0; rep < 2 && rc == CPS_OK; ++rep) {
+                CPS_CUDA_TRY(s->ctx, cudaMemsetAsync(xx, 0, sizeof(double) * n, stream));
+                CPS_CUDA_TRY(s->ctx, cudaEventRecord(e0, stream));
+                k_red_recover<<<g, kBlock, 0, stream>>>(bb, xx, S, A, col, n, nR, 1, y);
+                k_black_init<<<g, kBlock, 0, stream>>>(bb, xx, S, A, col, n, nR, y, r, p, 0.0,
+                                                       probe, s->partials, s->st);
+                CgState hp{};
+                rc = run_cg(c == 1, &hp);
+                if (rc == CPS_OK && hp.status != CPS_OK) rc = CPS_ERR_ARG;
+                CPS_CUDA_TRY(s->ctx, cudaEventRecord(e1, stream));
+                CPS_CUDA_TRY(s->ctx, cudaEventSynchronize(e1));
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                per_iter[c] = rc == CPS_OK ? ms / (double)(hp.iter > 0 ? hp.iter : 1) : 0.0;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (rc != CPS_OK && rc != CPS_ERR_ARG) return rc;
+        tu.red_done = true;
+        tu.red_path = (per_iter[1] > 0.0 && per_iter[1] < per_iter[0]) ? 1 : 0;
+        tu.red_probe_us[0] = 1e3 * per_iter[0];
+        tu.red_probe_us[1] = 1e3 * per_iter[1];
+        Tuning* c = cached_tuning(s, CPS_FP64);
+        c->red_done = true;
+        c->red_path = tu.red_path;
+        c->red_probe_us[0] = tu.red_probe_us[0];
+        c->red_probe_us[1] = tu.red_probe_us[1];
+    }
+    const bool pers = tu.red_path == 1;
     CgState h{};
     int status = CPS_OK;
     for (int restart = 0; restart < 8; ++restart) {
@@ -629,24 +831,8 @@ static int solve_reduced(cps_sys s, const double* b, double* x, double rtol, int
                                                s->partials, s->st);
         launches += 2;
         CPS_CUDA_TRY(s->ctx, cudaGetLastError());
-        int rc = read_state(s, stream, &h);
+        int rc = run_cg(pers, &h);
         if (rc) return rc;
-        if (!h.done && budget > 0) {
-            for (long long k = 0;; ++k) {
-                const int slot = (int)(k & 1);
-                CPS_CUDA_TRY(s->ctx, cudaGraphLaunch(ge, stream));
-                launches += s->graph_nodes[CPS_FP64][2];
-                CPS_CUDA_TRY(s->ctx, cudaMemcpyAsync(&s->hst[slot], s->st, sizeof(CgState),
-                                                     cudaMemcpyDeviceToHost, stream));
-                CPS_CUDA_TRY(s->ctx, cudaEventRecord(s->ev[slot], stream));
-                if (k >= 1) {
-                    CPS_CUDA_TRY(s->ctx, cudaEventSynchronize(s->ev[1 - slot]));
-                    if (s->hst[1 - slot].done) break;
-                }
-            }
-            rc = read_state(s, stream, &h);
-            if (rc) return rc;
-        }
         total += h.iter;
         status = h.status;
         k_red_recover<<<g, kBlock, 0, stream>>>(bb, y, S, A, col, n, nR, 0, y);
@@ -665,6 +851,7 @@ static int solve_reduced(cps_sys s, const double* b, double* x, double rtol, int
     if (status == CPS_OK && h.bnorm2 > 0 && !(rel <= rtol)) status = CPS_ERR_NOT_CONVERGED;
     fill_stats(stats, total, rel, status, 1, launches);
     if (status == CPS_ERR_NOT_SPD) s->ctx->last_error = "solve: p.Sp <= 0 (reduced system)";
+    if (status == CPS_ERR_TIMEOUT) s->ctx->last_error = "solve: a grid barrier wait ran out";
     if (status == CPS_ERR_NOT_CONVERGED) s->ctx->last_error = "solve: max_iter reached";
     return status;
 }
@@ -773,7 +960,7 @@ int solve_impl(cps_sys s, const double* b, double* x, double rtol, int64_t max_i
     }
     if (precision == CPS_FP64) {
         const int rc = solve_fp64(s, b, x, rtol, max_iter, stats, stream);
-        if (s->ctx->l2_persist_set != 0) l2_set_aside(s, false, stream);   // error paths
+        if (s->ctx->l2_persist_set != 0) l2_set_aside(s, 0, stream);   // error paths
         return rc;
     }
     if (precision == CPS_MIXED) return solve_mixed(s, b, x, rtol, max_iter, stats, stream);

@@ -63,8 +63,8 @@ namespace cps {
 //   k_cg_b:     r -= alpha q; Jacobi: rho' = r.r, beta = rho'/rho; stop test
 //   k_cg_c:     y += alpha p; p = z + beta p
 
-template <typename V, int U>
-__global__ void __launch_bounds__(kBlock) k_spmv_dot(const V* __restrict__ a,
+template <typename V, int U, int BS = kBlock>
+__global__ void __launch_bounds__(BS) k_spmv_dot(const V* __restrict__ a,
                                                      const int32_t* __restrict__ col,
                                                      const V* __restrict__ p, V* __restrict__ q,
                                                      int64_t n, double* partials, CgState* st) {
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kBlock) k_spmv_dot(const V* __restrict__ a,
             acc = fma((double)pe[u], (double)v, acc);
         })
     double t[1] = {acc};
-    if (grid_sum<1>(t, partials, &st->arrive[0]) && threadIdx.x == 0) {
+    if (grid_sum<1, BS>(t, partials, &st->arrive[0]) && threadIdx.x == 0) {
         const double gamma = t[0];
         st->gamma = gamma;
         if (!(gamma > 0.0) || !isfinite(gamma)) {
@@ -101,8 +101,8 @@ __global__ void __launch_bounds__(kBlock) k_spmv_dot(const V* __restrict__ a,
     }
 }
 
-template <typename V, int U>
-__global__ void __launch_bounds__(kBlock) k_cg_c(V* __restrict__ y, V* __restrict__ p,
+template <typename V, int U, int BS = kBlock>
+__global__ void __launch_bounds__(BS) k_cg_c(V* __restrict__ y, V* __restrict__ p,
                                                  const V* __restrict__ z, int64_t n,
                                                  const CgState* st) {
     if (st->done == 2) return;
@@ -166,8 +166,8 @@ __global__ void __launch_bounds__(kBlock) k_cg_a(const V* __restrict__ a,
     }
 }
 
-template <typename V, bool NORM, bool JACOBI, int U>
-__global__ void __launch_bounds__(kBlock) k_cg_b(V* __restrict__ r, const V* __restrict__ q,
+template <typename V, bool NORM, bool JACOBI, int U, int BS = kBlock>
+__global__ void __launch_bounds__(BS) k_cg_b(V* __restrict__ r, const V* __restrict__ q,
                                                  const V* __restrict__ s, int64_t n,
                                                  double* partials, CgState* st) {
     if (st->done) return;
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_b(V* __restrict__ r, const V* __r
             }
         })
     double t[2] = {rr, nn};
-    if (grid_sum<2>(t, partials, &st->arrive[1]) && threadIdx.x == 0) {
+    if (grid_sum<2, BS>(t, partials, &st->arrive[1]) && threadIdx.x == 0) {
         const long long it = st->iter + 1;
         st->iter = it;
         int done = 0;
@@ -212,6 +212,7 @@ __global__ void k_tune_prime(CgState* st) {
     st->alpha = 1e-3;
     st->beta = 0.5;
     st->max_iter = 1LL << 62;
+    st->thresh2 = -1.0;
 }
 
 // p = z (start of an IC(0) run, after the first preconditioner application).
@@ -496,9 +497,8 @@ __global__ void __launch_bounds__(kBlock) k_ic0_fwd(const V* __restrict__ l,
         }
     }
     if (last) {
-        __shared__ double sh[32][1];
         double t[1] = {acc};
-        block_sum<1>(t, sh);
+        block_sum<1>(t);
         if (threadIdx.x == 0) ic0_segment(partials, colour)[blockIdx.x] = t[0];
     }
 }
@@ -526,9 +526,8 @@ __global__ void __launch_bounds__(kBlock) k_ic0_bwd(const V* __restrict__ l,
         z[i] = zi;
         acc = fma((double)ri, (double)zi, acc);
     }
-    __shared__ double sh[32][1];
     double t[1] = {acc};
-    block_sum<1>(t, sh);
+    block_sum<1>(t);
     if (colour != 0) {
         if (threadIdx.x == 0) ic0_segment(partials, colour)[blockIdx.x] = t[0];
         return;
@@ -549,7 +548,7 @@ __global__ void __launch_bounds__(kBlock) k_ic0_bwd(const V* __restrict__ l,
         for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) tot += __ldcg(&seg[i]);
     }
     double u[1] = {tot};
-    block_sum<1>(u, sh);
+    block_sum<1>(u);
     if (threadIdx.x == 0) {
         st->arrive[2] = 0u;
         const double rho_new = u[0];

@@ -262,6 +262,7 @@ def test_autotuned_solves_on_a_large_system(ctx):
         nk = 3 if prec == cps.FP64 else 2
         assert all(u in (1, 2, 4) for u in tu["unroll"][:nk])
         assert all(0 < g <= 4096 for g in tu["grid"][:nk])
+        assert all(b in ((256, 1024) if prec == cps.FP64 else (256,)) for b in tu["block"][:nk])
         r = b - A.matvec(x.cpu().numpy())
         assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-10 * 1.01
     s.set_precond(cps.PC_IC0)
@@ -380,4 +381,85 @@ def test_reduced_system_needs_two_colours(ctx):
     s.set_precond(cps.PC_IC0)            # the same ordering serves IC(0)
     _, st = s.solve(torch.as_tensor(synth.rhs(p.mesh, 1), device="cuda"), rtol=1e-10)
     assert st.rel_res <= 1e-10
+    s.free()
+
+
+@pytest.mark.parametrize("name", ["block37", "channel64", "defect20", "channel300"])
+def test_persistent_path_matches_oracle(ctx, name):
+    """One cooperative launch runs the whole Jacobi-PCG solve, iterations
+    separated by software grid barriers: against the oracle, and the iterate
+    count against the streaming path on the same system."""
+    p = PROBLEMS[name] if name in PROBLEMS else synth.channel_block_problem(300, seed=8)
+    s = assemble(ctx, p)
+    b = synth.rhs(p.mesh, 31)
+    bt = torch.as_tensor(b, device="cuda")
+    s.set_solver_path(cps.PATH_PERSISTENT)
+    x, st = s.solve(bt, rtol=1e-12, check=False)
+    assert st.status in (0, cps._cps.ERR_NOT_CONVERGED) and st.rel_res < 1e-10
+    assert s.tuning()["persistent"]
+    xo, sto, A = oracle.solve_problem(p, b, rtol=1e-13)
+    err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
+    assert err < 1e-9, err
+    r = b - A.matvec(x.cpu().numpy())
+    assert np.linalg.norm(r) / np.linalg.norm(b) < 2 * max(st.rel_res, 1e-13)
+    s.set_solver_path(cps.PATH_STREAM)
+    _, st2 = s.solve(bt, rtol=1e-12, check=False)
+    assert abs(st2.iters - st.iters) <= max(8, 0.02 * st.iters)
+    s.set_solver_path(cps.PATH_PERSISTENT)
+    # warm start from the solution, zero right-hand side, iteration cap
+    _, st3 = s.solve(bt, x=x.clone(), rtol=1e-8)
+    assert st3.iters == 0
+    z = torch.ones_like(bt)
+    s.solve(torch.zeros_like(bt), x=z)
+    assert torch.all(z == 0)
+    _, st4 = s.solve(bt, rtol=1e-14, max_iter=5, check=False)
+    assert st4.status == cps._cps.ERR_NOT_CONVERGED and st4.iters == 5
+    s.free()
+
+
+@pytest.mark.parametrize("name", ["block37", "channel64", "channel300"])
+def test_persistent_reduced_system_matches_oracle(ctx, name):
+    """The reduced (black-cell Schur complement) CG in one persistent launch."""
+    p = PROBLEMS[name] if name in PROBLEMS else synth.channel_block_problem(300, seed=8)
+    s = assemble(ctx, p)
+    s.set_precond(cps.PC_REDUCED)
+    s.set_solver_path(cps.PATH_PERSISTENT)
+    b = synth.rhs(p.mesh, 37)
+    bt = torch.as_tensor(b, device="cuda")
+    x, st = s.solve(bt, rtol=1e-12, check=False)
+    assert st.status in (0, cps._cps.ERR_NOT_CONVERGED) and st.rel_res < 1e-10
+    assert s.tuning()["reduced_persistent"]
+    xo, _, A = oracle.solve_problem(p, b, rtol=1e-13)
+    err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
+    assert err < 1e-9, err
+    s.set_solver_path(cps.PATH_STREAM)
+    x2, st2 = s.solve(bt, rtol=1e-12, check=False)
+    assert abs(st2.iters - st.iters) <= max(8, 0.02 * st.iters)
+    assert torch.allclose(x, x2, rtol=1e-9, atol=1e-12 * float(x.abs().max()))
+    s.free()
+
+
+def test_path_autotuner_reports_every_candidate(ctx):
+    """On a system above the tuning threshold the first Jacobi solve times
+    streaming, streaming with the matrix in persisting L2 (where it fits) and
+    the persistent launch, and keeps the fastest; the first reduced-system
+    solve times streaming against persistent."""
+    p = synth.channel_block_problem(300, seed=8)
+    s = assemble(ctx, p)
+    b = torch.as_tensor(synth.rhs(p.mesh, 4), device="cuda")
+    _, st = s.solve(b, rtol=1e-10)
+    tu = s.tuning()
+    pr = tu["probe_us_per_iter"]
+    assert pr["stream"] > 0 and pr["persistent"] > 0 and pr["cluster"] == 0
+    chosen = [k for k in ("stream", "stream_l2_matrix", "stream_l2_vectors", "persistent")
+              if pr[k] > 0]
+    best = min(chosen, key=lambda k: pr[k])
+    assert tu["persistent"] == (best == "persistent")
+    assert tu["l2_window"] == {"stream_l2_matrix": "matrix",
+                               "stream_l2_vectors": "vectors"}.get(best, "none")
+    s.set_precond(cps.PC_REDUCED)
+    _, st = s.solve(b, rtol=1e-10)
+    pr = s.tuning()["probe_us_per_iter"]
+    assert pr["reduced_stream"] > 0 and pr["reduced_persistent"] > 0
+    assert s.tuning()["reduced_persistent"] == (pr["reduced_persistent"] < pr["reduced_stream"])
     s.free()
