@@ -232,13 +232,16 @@ int cps_set_solver_path(cps_sys sys, int path);
  * (CPS_FP64 only) the direction update.  The tuner times every candidate on
  * the system's own data at its first solve; systems below 131072 cells keep
  * the defaults (unroll 2, 8 blocks per SM).  For CPS_FP64 Jacobi solves it
- * also times the ways of running the loop: flags (may be NULL, 4 entries)
+ * also times the ways of running the loop: flags (may be NULL, 5 entries)
  * receives {one-cluster launch chosen, persisting-L2 window (0 none, 1 the
- * matrix, 2 the vectors r, p, q), persistent launch chosen, persistent
- * launch chosen for the reduced system}, probe_us (may be NULL, 7 entries)
- * the microseconds per iteration measured for {streaming, one cluster,
- * streaming + matrix in L2, persistent, reduced system streaming, reduced
- * system persistent, streaming + vectors in L2} (0 where not tried).
+ * matrix, 2 the vectors r, p, q), persistent launch chosen, reduced system:
+ * persistent launch chosen, reduced system: window (0 or 2)}, probe_us (may
+ * be NULL, 10 entries) the microseconds per iteration measured for
+ * {streaming, one cluster, streaming + matrix in L2, persistent, streaming +
+ * vectors in L2, persistent + vectors in L2, reduced system: streaming,
+ * persistent, streaming + vectors in L2, persistent + vectors in L2} (0
+ * where not tried; the persistent figures are the best over the grid sizes
+ * tried).
  * The context remembers what the tuner chose per mesh size (cells,
  * vertices): a system assembled later on the same context with the same
  * sizes starts from those choices and is not timed again.  A path forced by

@@ -139,16 +139,19 @@ class System:
         u = (ctypes.c_int32 * 3)()
         g = (ctypes.c_int32 * 3)()
         bl = (ctypes.c_int32 * 3)()
-        f = (ctypes.c_int32 * 4)()
-        pr = (ctypes.c_double * 7)()
+        f = (ctypes.c_int32 * 5)()
+        pr = (ctypes.c_double * 10)()
         self.ctx.check(self.ctx.lib.cps_get_tuning(self.handle, precision, u, g, bl, f, pr),
                        "cps_get_tuning")
         return {"unroll": list(u), "grid": list(g), "block": list(bl),
                 "cluster": bool(f[0]), "l2_window": ("none", "matrix", "vectors")[f[1]],
                 "persistent": bool(f[2]), "reduced_persistent": bool(f[3]),
-                "probe_us_per_iter": {"stream": pr[0], "cluster": pr[1], "stream_l2_matrix": pr[2],
-                                      "persistent": pr[3], "reduced_stream": pr[4],
-                                      "reduced_persistent": pr[5], "stream_l2_vectors": pr[6]}}
+                "reduced_l2_window": ("none", "matrix", "vectors")[f[4]],
+                "probe_us_per_iter": {
+                    "stream": pr[0], "cluster": pr[1], "stream_l2_matrix": pr[2],
+                    "persistent": pr[3], "stream_l2_vectors": pr[4], "persistent_l2_vectors": pr[5],
+                    "reduced_stream": pr[6], "reduced_persistent": pr[7],
+                    "reduced_stream_l2_vectors": pr[8], "reduced_persistent_l2_vectors": pr[9]}}
 
     def set_solver_path(self, path: int):
         """PATH_AUTO, PATH_STREAM, PATH_CLUSTER or PATH_PERSISTENT for FP64

@@ -158,12 +158,16 @@ int cps_set_solver_path(cps_sys sys, int path) {
         t.l2win = 0;
         t.red_done = true;
         t.red_path = 0;
+        t.red_win = 0;
     } else if (path == CPS_PATH_PERSISTENT) {
         t.path_done = true;
         t.path = 2;
         t.l2win = 0;
         t.red_done = true;
         t.red_path = 1;
+        t.red_win = 0;
+        t.pgrid = 0;
+        t.red_pgrid = 0;
     } else if (path == CPS_PATH_CLUSTER) {
         if (sys->nt > cps::cluster_max_rows(sys->ctx)) {
             sys->ctx->last_error = "set_solver_path: system too large for one cluster";
@@ -193,12 +197,11 @@ int cps_get_tuning(cps_sys sys, int precision, int32_t* unroll, int32_t* grid, i
         flags[1] = t.path_done ? t.l2win : 0;
         flags[2] = t.path_done && t.path == 2;
         flags[3] = t.red_done && t.red_path == 1;
+        flags[4] = t.red_done ? t.red_win : 0;
     }
     if (probe_us) {
-        for (int k = 0; k < 4; ++k) probe_us[k] = t.probe_us[k];
-        probe_us[4] = t.red_probe_us[0];
-        probe_us[5] = t.red_probe_us[1];
-        probe_us[6] = t.probe_us[4];
+        for (int k = 0; k < 6; ++k) probe_us[k] = t.probe_us[k];
+        for (int k = 0; k < 4; ++k) probe_us[6 + k] = t.red_probe_us[k];
     }
     return CPS_OK;
 }

@@ -45,9 +45,38 @@ struct ClusterArgs {
     long long max_iter;
 };
 
-// Shared-memory layout of one CTA (R rows).
+// Shared-memory layout of one CTA (R rows): a [3][R], p, r, y, q, s [R]
+// doubles, col [3][R] int32, then (16-byte aligned) a reduction buffer of 3
+// doubles per thread.
+constexpr size_t kRowBytes = 3 * sizeof(double) + 3 * sizeof(int32_t) + 5 * sizeof(double);
+constexpr size_t kRedBufBytes = 3 * kClusterThreads * sizeof(double);
+__host__ __device__ inline size_t cluster_red_offset(int R) {
+    return ((size_t)R * kRowBytes + 15) / 16 * 16;
+}
 __host__ __device__ inline size_t cluster_smem_bytes(int R) {
-    return (size_t)R * (3 * sizeof(double) + 3 * sizeof(int32_t) + 5 * sizeof(double)) + 256;
+    return cluster_red_offset(R) + kRedBufBytes;
+}
+
+// Block sum of v[0..NV) through buf (NV x kClusterThreads doubles): warp k
+// adds the values of quantity k (few FP64 adds: GB300 issues FP64 at 1/64
+// of the FP32 rate); every thread then holds the totals.  Needs at least NV
+// warps.
+template <int NV>
+__device__ __forceinline__ void block_sum_buf(double (&v)[NV], double* buf, double* tot) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) buf[k * kClusterThreads + threadIdx.x] = v[k];
+    __syncthreads();
+    if (warp < NV) {
+        double a = buf[warp * kClusterThreads + lane];
+        for (int j = lane + 32; j < (int)blockDim.x; j += 32) a += buf[warp * kClusterThreads + j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) tot[warp] = a;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = tot[k];
 }
 
 __global__ void __launch_bounds__(kClusterThreads, 1) k_cluster_cg(ClusterArgs A) {
@@ -67,10 +96,11 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_cluster_cg(ClusterArgs A
     double* q_s = y_s + R;
     double* s_s = q_s + R;
     int32_t* c_s = reinterpret_cast<int32_t*>(s_s + R);      // [3][R] packed (rank << 16) | local
+    double* rbuf = reinterpret_cast<double*>(smem + cluster_red_offset(R));
     __shared__ double red[3][16];   // red[k][c]: partial k of CTA c
-    __shared__ double sh3[32][3];
-    __shared__ double sh2[32][2];
-    __shared__ double sh1[32][1];
+    __shared__ double tot[3];
+    __shared__ double sc[2];        // scalars derived once per CTA by thread 0
+    __shared__ int s_stop;
 
     const int tid = threadIdx.x;
     for (int i = tid; i < nloc; i += blockDim.x) {
@@ -97,6 +127,8 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_cluster_cg(ClusterArgs A
     auto push = [&](int k, double v) {
         if (tid < C) cluster.map_shared_rank(&red[k][0], tid)[rank] = v;
     };
+    // sum of slot k over the cluster, in rank order (thread 0 only: a FP64
+    // add per thread per slot would cost more than the iteration's work)
     auto cluster_sum = [&](int k) -> double {
         double t = 0.0;
         for (int c = 0; c < C; ++c) t += red[k][c];
@@ -117,18 +149,24 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_cluster_cg(ClusterArgs A
         const double t = s_s[i] * re;
         v3[2] = fma(t, t, v3[2]);
     }
-    block_sum_shfl<3>(v3, sh3);
+    block_sum_buf<3>(v3, rbuf, tot);
     push(0, v3[0]);
     push(1, v3[1]);
     push(2, v3[2]);
     cluster.sync();
-    double rho = cluster_sum(0);
-    const double bnorm2 = cluster_sum(1);
-    double rnorm2 = cluster_sum(2);
-    const double thresh2 = A.rtol * A.rtol * bnorm2;
+    // run scalars: kept by thread 0 of every CTA (identical everywhere)
+    double rho = 0.0, bnorm2 = 0.0, rnorm2 = 0.0, thresh2 = 0.0;
+    if (tid == 0) {
+        rho = cluster_sum(0);
+        bnorm2 = cluster_sum(1);
+        rnorm2 = cluster_sum(2);
+        thresh2 = A.rtol * A.rtol * bnorm2;
+        s_stop = (bnorm2 == 0.0 || rnorm2 <= thresh2 || A.max_iter <= 0) ? 1 : 0;
+    }
+    __syncthreads();
     int status = CPS_OK;
     long long it = 0;
-    bool stop = (bnorm2 == 0.0 || rnorm2 <= thresh2 || A.max_iter <= 0);
+    bool stop = s_stop != 0;
     while (!stop) {
         cluster.sync();     // p complete everywhere; partials of the last step read
         double g1[1] = {0.0};
@@ -139,15 +177,21 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_cluster_cg(ClusterArgs A
             q_s[i] = v;
             g1[0] = fma(pe, v, g1[0]);
         }
-        block_sum_shfl<1>(g1, sh1);
+        block_sum_buf<1>(g1, rbuf, tot);
         push(0, g1[0]);
         cluster.sync();
-        const double gamma = cluster_sum(0);
-        if (!(gamma > 0.0) || !isfinite(gamma)) {
+        if (tid == 0) {
+            const double gamma = cluster_sum(0);
+            const bool bad = !(gamma > 0.0) || !isfinite(gamma);
+            sc[0] = bad ? 0.0 : rho / gamma;
+            s_stop = bad ? 1 : 0;
+        }
+        __syncthreads();
+        if (s_stop) {
             status = CPS_ERR_NOT_SPD;
             break;
         }
-        const double alpha = rho / gamma;
+        const double alpha = sc[0];
         const bool check = ((it + 1) % kCheck) == 0;
         double g2[2] = {0.0, 0.0};
         for (int i = tid; i < nloc; i += blockDim.x) {
@@ -160,19 +204,25 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_cluster_cg(ClusterArgs A
                 g2[1] = fma(t, t, g2[1]);
             }
         }
-        block_sum_shfl<2>(g2, sh2);
+        block_sum_buf<2>(g2, rbuf, tot);
         push(1, g2[0]);
         push(2, g2[1]);
         cluster.sync();
-        const double rho_new = cluster_sum(1);
         ++it;
-        if (check) {
-            rnorm2 = cluster_sum(2);
-            if (rnorm2 <= thresh2) stop = true;
+        if (tid == 0) {
+            const double rho_new = cluster_sum(1);
+            bool halt = !(rho_new > 0.0) || it >= A.max_iter;
+            if (check) {
+                rnorm2 = cluster_sum(2);
+                if (rnorm2 <= thresh2) halt = true;
+            }
+            sc[1] = rho_new / rho;
+            rho = rho_new;
+            s_stop = halt ? 1 : 0;
         }
-        if (!(rho_new > 0.0) || it >= A.max_iter) stop = true;
-        const double beta = rho_new / rho;
-        rho = rho_new;
+        __syncthreads();
+        stop = s_stop != 0;
+        const double beta = sc[1];
         if (!stop)
             for (int i = tid; i < nloc; i += blockDim.x) p_s[i] = fma(beta, p_s[i], r_s[i]);
     }
@@ -215,9 +265,9 @@ static size_t cluster_dyn_smem_limit(int dev) {
 // Largest system the cluster path takes on this GPU (0: not available).
 int64_t cluster_max_rows(cps_ctx ctx) {
     const size_t lim = cluster_dyn_smem_limit(ctx->device);
-    const size_t per_row = cluster_smem_bytes(1) - 256;
-    if (lim <= 256) return 0;
-    const int64_t R = (int64_t)((lim - 256) / per_row);
+    const size_t fixed = kRedBufBytes + 16;
+    if (lim <= fixed) return 0;
+    const int64_t R = (int64_t)((lim - fixed) / kRowBytes);
     return std::min<int64_t>(R, 0xFFFF) * 16;
 }
 
@@ -258,7 +308,11 @@ int cluster_solve(cps_sys s, const double* b, const double* x, double* y, double
         if (R > 0xFFFF || cluster_smem_bytes(R) > lim) continue;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(csize, 1, 1);
-        cfg.blockDim = dim3(kClusterThreads, 1, 1);
+        // one row per thread where the rows allow (fewer threads: cheaper
+        // block reductions); at least 4 warps for the 3-quantity sums
+        const int threads =
+            R >= kClusterThreads ? kClusterThreads : (R < 128 ? 128 : (R + 31) / 32 * 32);
+        cfg.blockDim = dim3(threads, 1, 1);
         cfg.dynamicSmemBytes = cluster_smem_bytes(R);
         cfg.stream = stream;
         cudaLaunchAttribute attr[1];

@@ -61,9 +61,14 @@ struct Tuning {
     bool path_done = false;
     int l2win = 0;           // FP64 Jacobi stream path, persisting L2 window: 0 none,
                              // 1 the matrix, 2 the vectors r, p, q
-    double probe_us[5] = {0, 0, 0, 0, 0};   // us/iteration: stream, cluster, stream + matrix
-                                            // in L2, persistent, stream + vectors in L2
-    double red_probe_us[2] = {0, 0};     // reduced system: stream, persistent
+    double probe_us[6] = {0, 0, 0, 0, 0, 0};   // us/iteration: stream, cluster, stream +
+                                               // matrix in L2, persistent, stream + vectors
+                                               // in L2, persistent + vectors in L2
+    double red_probe_us[4] = {0, 0, 0, 0};   // reduced system: stream, persistent, and the
+                                             // same with r, p, q in persisting L2
+    int red_win = 0;         // reduced system: persisting L2 window (0 none, 2 r, p, q)
+    int pgrid = 0;           // blocks of the persistent launch (0: all that stay resident)
+    int red_pgrid = 0;       // the same for the reduced system
 };
 
 // Device error flag written by the assembly kernels (first error wins).
@@ -98,42 +103,6 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < NV; ++k) v[k] = tot[k];
-}
-
-// Older form (a shuffle tree in every warp, then one over the warp sums), for
-// kernels whose shared memory is spoken for; sh holds 32 x NV doubles.
-template <int NV>
-__device__ __forceinline__ void block_sum_shfl(double (&v)[NV], double (*sh)[NV]) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-    }
-    __syncthreads();
-    if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) sh[warp][k] = v[k];
-    }
-    __syncthreads();
-    if (warp == 0) {
-        const int nw = blockDim.x >> 5;
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            double t = lane < nw ? sh[lane][k] : 0.0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            v[k] = t;
-        }
-        if (lane == 0) {
-#pragma unroll
-            for (int k = 0; k < NV; ++k) sh[0][k] = v[k];
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = sh[0][k];
-    __syncthreads();
 }
 
 // Deterministic sum over the grid: every block writes its partial sums, the
@@ -296,7 +265,9 @@ int cluster_solve(cps_sys s, const double* b, const double* x, double* y, double
                   long long max_iter, cudaStream_t stream);
 int persistent_solve(cps_sys s, int reduced, const double* a, const int32_t* col,
                      const double* sc, double* y, double* r, double* p, double* q, double* t,
-                     int64_t n, int64_t nR, cudaStream_t stream);
+                     int64_t n, int64_t nR, const void* win_base, size_t win_bytes, int grid,
+                     cudaStream_t stream);
+int persistent_max_grid(cps_sys s, int reduced);
 int export_impl(cps_sys sys, double* diag, int32_t* col, double* val, cudaStream_t stream);
 void free_sys(cps_sys sys);
 

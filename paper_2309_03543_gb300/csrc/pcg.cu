@@ -507,40 +507,68 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
     t.path_done = true;
     t.path = 0;
     t.l2win = 0;
+    t.pgrid = 0;
     if (s->precond != CPS_PC_JACOBI) return CPS_OK;
     const bool try_cluster = s->nt <= cluster_max_rows(s->ctx);
     const bool big = !try_cluster && s->nt >= kTuneMinRows;
     const long long probe = s->nt >= kTuneMinRows ? 256 : 64;
-    // candidate 3 (persistent grid-synchronised launch) is always tried
+    // candidates (slot in probe_us): 0 streaming, 1 one-cluster launch,
+    // 2 streaming with the matrix in persisting L2, 3 one persistent
+    // grid-synchronised launch, 4 streaming with the vectors r, p, q in
+    // persisting L2, 5 persistent with the vectors in persisting L2.  The
+    // persistent launch is timed at a few grid sizes (fewer blocks
+    // synchronise faster; more blocks move more bytes).
+    struct Cand {
+        int slot, path, win, grid;
+    };
+    Cand cands[16];
+    int nc = 0;
+    cands[nc++] = {0, 0, 0, 0};
+    if (try_cluster) cands[nc++] = {1, 1, 0, 0};
+    if (big && l2_window_fits(s, 1)) cands[nc++] = {2, 0, 1, 0};
+    if (big && l2_window_fits(s, 2)) cands[nc++] = {4, 0, 2, 0};
+    {
+        const int gmax = persistent_max_grid(s, 0);
+        int grids[3] = {gmax, (int)((s->nt + 8191) / 8192), (int)((s->nt + 2047) / 2048)};
+        for (int i = 0; i < 3; ++i) {
+            const int gi = grids[i] < 1 ? 1 : (grids[i] > gmax ? gmax : grids[i]);
+            bool dup = gmax <= 0;
+            for (int j = 0; j < i; ++j) dup = dup || grids[j] == gi;
+            grids[i] = gi;
+            if (dup) continue;
+            cands[nc++] = {3, 2, 0, gi};
+            if (big && l2_window_fits(s, 2)) cands[nc++] = {5, 2, 2, gi};
+        }
+    }
     cudaEvent_t e0, e1;
     CPS_CUDA_TRY(s->ctx, cudaEventCreate(&e0));
     CPS_CUDA_TRY(s->ctx, cudaEventCreate(&e1));
-    // candidates: 0 streaming, 1 one-cluster launch, 2 streaming with the
-    // matrix in persisting L2, 3 one persistent grid-synchronised launch,
-    // 4 streaming with the vectors r, p, q in persisting L2
-    double per_iter[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    double per_iter[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    double best_t = 0.0;
+    Cand best{0, 0, 0, 0};
     int rc = CPS_OK;
     cudaGraphExec_t ge = nullptr;
     int64_t per_chunk = 0, dummy = 0;
-    for (int path = 0; path < 5 && rc == CPS_OK; ++path) {
-        if (path == 1 && !try_cluster) continue;
-        if (path == 2 && !(big && l2_window_fits(s, 1))) continue;
-        if (path == 4 && !(big && l2_window_fits(s, 2))) continue;
-        t.l2win = path == 2 ? 1 : (path == 4 ? 2 : 0);
-        rc = l2_set_aside(s, t.l2win, stream);
-        if (rc == CPS_OK) rc = get_chunk_graph<double>(s, CPS_FP64, v, &ge, &per_chunk);
+    for (int ci = 0; ci < nc && rc == CPS_OK; ++ci) {
+        const Cand c = cands[ci];
+        t.l2win = c.win;
+        rc = l2_set_aside(s, c.win, stream);
+        if (rc == CPS_OK && c.path == 0)
+            rc = get_chunk_graph<double>(s, CPS_FP64, v, &ge, &per_chunk);
+        double us = 0.0;
         for (int rep = 0; rep < 2 && rc == CPS_OK; ++rep) {   // first one warms up
             CPS_CUDA_TRY(s->ctx, cudaMemsetAsync(s->wx, 0, sizeof(double) * s->nt, stream));
             CgState h{};
             CPS_CUDA_TRY(s->ctx, cudaEventRecord(e0, stream));
-            if (path == 3) {
+            if (c.path == 2) {
                 k_init64<<<s->grid, kBlock, 0, stream>>>(b, s->wx, v.s, v.a, v.col, s->nt, v.y, v.r,
                                                          v.p0, 0.0, probe, 1, s->partials, s->st);
                 rc = persistent_solve(s, 0, v.a, v.col, v.s, v.y, v.r, v.p0, v.q, nullptr, s->nt,
-                                      0, stream);
+                                      0, c.win ? l2_window_base(s, c.win) : nullptr,
+                                      c.win ? l2_window_bytes(s, c.win) : 0, c.grid, stream);
                 if (rc == CPS_OK) rc = read_state(s, stream, &h);
                 if (rc == CPS_OK && h.status != CPS_OK) rc = CPS_ERR_ARG;   // not usable here
-            } else if (path != 1) {
+            } else if (c.path == 0) {
                 k_init64<<<s->grid, kBlock, 0, stream>>>(b, s->wx, v.s, v.a, v.col, s->nt, v.y, v.r,
                                                          v.p0, 0.0, probe, 1, s->partials, s->st);
                 rc = run_chunks<double>(s, CPS_FP64, v, stream, &h, &dummy);
@@ -552,7 +580,18 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
             CPS_CUDA_TRY(s->ctx, cudaEventSynchronize(e1));
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
-            per_iter[path] = rc == CPS_OK ? ms / (double)(h.iter > 0 ? h.iter : 1) : 0.0;
+            us = rc == CPS_OK ? 1e3 * ms / (double)(h.iter > 0 ? h.iter : 1) : 0.0;
+        }
+        if (rc == CPS_ERR_ARG) {            // a candidate that cannot run here: skip it
+            rc = CPS_OK;
+            cudaGetLastError();
+            continue;
+        }
+        if (rc != CPS_OK || us <= 0.0) continue;
+        if (per_iter[c.slot] == 0.0 || us < per_iter[c.slot]) per_iter[c.slot] = us;
+        if (best_t == 0.0 || us < best_t) {
+            best_t = us;
+            best = c;
         }
     }
     cudaEventDestroy(e0);
@@ -562,21 +601,19 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
         if (rc == CPS_OK) rc = rc2;
     }
     t.l2win = 0;
-    if (rc == CPS_ERR_ARG) rc = CPS_OK;      // a candidate that cannot run here: skip it
     if (rc == CPS_OK) {
-        int best = 0;
-        for (int c = 1; c < 5; ++c)
-            if (per_iter[c] > 0.0 && per_iter[c] < per_iter[best]) best = c;
-        t.path = best == 1 ? 1 : (best == 3 ? 2 : 0);
-        t.l2win = best == 2 ? 1 : (best == 4 ? 2 : 0);
+        t.path = best.path;
+        t.l2win = best.win;
+        t.pgrid = best.grid;
     }
-    for (int c = 0; c < 5; ++c) t.probe_us[c] = 1e3 * per_iter[c];
+    for (int k = 0; k < 6; ++k) t.probe_us[k] = per_iter[k];
     if (rc == CPS_OK) {
         Tuning* c = cached_tuning(s, CPS_FP64);
         c->path_done = true;
         c->path = t.path;
         c->l2win = t.l2win;
-        for (int k = 0; k < 5; ++k) c->probe_us[k] = t.probe_us[k];
+        c->pgrid = t.pgrid;
+        for (int k = 0; k < 6; ++k) c->probe_us[k] = t.probe_us[k];
     }
     return rc;
 }
@@ -600,7 +637,7 @@ static int solve_fp64(cps_sys s, const double* b, double* x, double rtol, int64_
     }
     const bool cluster = !ic0 && s->tune[CPS_FP64].path == 1;
     const bool persistent = !ic0 && s->tune[CPS_FP64].path == 2;
-    const int window = (!ic0 && !cluster && !persistent) ? s->tune[CPS_FP64].l2win : 0;
+    const int window = (!ic0 && !cluster) ? s->tune[CPS_FP64].l2win : 0;
     if (window) {
         int rc = l2_set_aside(s, window, stream);
         if (rc) return rc;
@@ -640,7 +677,9 @@ static int solve_fp64(cps_sys s, const double* b, double* x, double rtol, int64_
         if (persistent) {
             // one launch runs to the stop (it returns at once if init stopped)
             int rc = persistent_solve(s, 0, v.a, v.col, v.s, v.y, v.r, v.p0, v.q, nullptr, n, 0,
-                                      stream);
+                                      window ? l2_window_base(s, window) : nullptr,
+                                      window ? l2_window_bytes(s, window) : 0,
+                                      s->tune[CPS_FP64].pgrid, stream);
             if (rc) return rc;
             ++launches;
             rc = read_state(s, stream, &h);
@@ -726,8 +765,17 @@ static int solve_reduced(cps_sys s, const double* b, double* x, double rtol, int
     vb.n = nB;
     KCfg cb{2, grid_for(s->ctx, nB)};
     cudaGraphExec_t& ge = s->graph[CPS_FP64][2];
-    if (!ge) {
+    // The chunk graph of the reduced iteration, captured with persisting-L2
+    // window `win` (0 none, 2 the vectors r, p, q) on its kernel nodes.
+    auto build_graph = [&](int win) -> int {
+        if (ge && s->graph_l2win[CPS_FP64][2] == win) return CPS_OK;
+        if (ge) {
+            cudaGraphExecDestroy(ge);
+            ge = nullptr;
+        }
         int rc = ensure_capture_stream(s);
+        if (rc) return rc;
+        rc = set_l2_window(s, s->cap_stream, win);
         if (rc) return rc;
         cudaGraph_t graph = nullptr;
         int64_t nl = 0;
@@ -742,6 +790,7 @@ static int solve_reduced(cps_sys s, const double* b, double* x, double rtol, int
         }
         cudaError_t le = cudaGetLastError();
         cudaError_t ce = cudaStreamEndCapture(s->cap_stream, &graph);
+        if (win) set_l2_window(s, s->cap_stream, 0);
         if (le != cudaSuccess || ce != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
             s->ctx->last_error = std::string("graph capture: ") +
@@ -756,17 +805,24 @@ static int solve_reduced(cps_sys s, const double* b, double* x, double rtol, int
             return CPS_ERR_CUDA;
         }
         s->graph_nodes[CPS_FP64][2] = nl;
-    }
+        s->graph_l2win[CPS_FP64][2] = win;
+        return CPS_OK;
+    };
     // Runs CG from the state k_black_init left, on the graph-replayed kernels
-    // or (pers) in one persistent grid-synchronised launch; state into *hh.
-    auto run_cg = [&](bool pers, CgState* hh) -> int {
+    // or (pers) in one persistent grid-synchronised launch of pgrid blocks,
+    // with window win (the caller holds its set-aside); state into *hh.
+    auto run_cg = [&](bool pers, int win, int pgrid, CgState* hh) -> int {
         if (pers) {
-            int rc = persistent_solve(s, 1, A, col, S, y, r, p, q, t, n, nR, stream);
+            int rc = persistent_solve(s, 1, A, col, S, y, r, p, q, t, n, nR,
+                                      win ? l2_window_base(s, win) : nullptr,
+                                      win ? l2_window_bytes(s, win) : 0, pgrid, stream);
             if (rc) return rc;
             ++launches;
             return read_state(s, stream, hh);
         }
-        int rc = read_state(s, stream, hh);
+        int rc = build_graph(win);
+        if (rc) return rc;
+        rc = read_state(s, stream, hh);
         if (rc || hh->done) return rc;
         for (long long k = 0;; ++k) {
             const int slot = (int)(k & 1);
@@ -784,44 +840,97 @@ static int solve_reduced(cps_sys s, const double* b, double* x, double rtol, int
     };
     Tuning& tu = s->tune[CPS_FP64];
     if (!tu.red_done) {
-        // time a short run of each from x = 0 and keep the faster
+        // time a short run of each way from x = 0 and keep the fastest:
+        // slot 0 graph, 1 persistent, 2 graph + window, 3 persistent + window
+        // (persistent at a few grid sizes)
         const long long probe = nB >= kTuneMinRows ? 256 : 64;
+        const bool try_win = nB >= kTuneMinRows && l2_window_fits(s, 2);
+        struct Cand {
+            int slot, win, grid;
+        };
+        Cand cands[10];
+        int nc = 0;
+        cands[nc++] = {0, 0, 0};
+        if (try_win) cands[nc++] = {2, 2, 0};
+        {
+            const int gmax = persistent_max_grid(s, 1);
+            int grids[3] = {gmax, (int)((nB + 8191) / 8192), (int)((nB + 2047) / 2048)};
+            for (int i = 0; i < 3; ++i) {
+                const int gi = grids[i] < 1 ? 1 : (grids[i] > gmax ? gmax : grids[i]);
+                bool dup = gmax <= 0;
+                for (int j = 0; j < i; ++j) dup = dup || grids[j] == gi;
+                grids[i] = gi;
+                if (dup) continue;
+                cands[nc++] = {1, 0, gi};
+                if (try_win) cands[nc++] = {3, 2, gi};
+            }
+        }
         cudaEvent_t e0, e1;
         CPS_CUDA_TRY(s->ctx, cudaEventCreate(&e0));
         CPS_CUDA_TRY(s->ctx, cudaEventCreate(&e1));
-        double per_iter[2] = {0.0, 0.0};
+        double per_iter[4] = {0.0, 0.0, 0.0, 0.0};
+        double best_t = 0.0;
+        Cand best{0, 0, 0};
         int rc = CPS_OK;
-        for (int c = 0; c < 2 && rc == CPS_OK; ++c) {
+        for (int ci = 0; ci < nc && rc == CPS_OK; ++ci) {
+            const Cand c = cands[ci];
+            const bool pers = (c.slot & 1) != 0;
+            rc = l2_set_aside(s, c.win, stream);
+            double us = 0.0;
             for (int rep = 0; rep < 2 && rc == CPS_OK; ++rep) {
                 CPS_CUDA_TRY(s->ctx, cudaMemsetAsync(xx, 0, sizeof(double) * n, stream));
+                if (!pers) rc = build_graph(c.win);        // outside the timed region
+                if (rc) break;
                 CPS_CUDA_TRY(s->ctx, cudaEventRecord(e0, stream));
                 k_red_recover<<<g, kBlock, 0, stream>>>(bb, xx, S, A, col, n, nR, 1, y);
                 k_black_init<<<g, kBlock, 0, stream>>>(bb, xx, S, A, col, n, nR, y, r, p, 0.0,
                                                        probe, s->partials, s->st);
                 CgState hp{};
-                rc = run_cg(c == 1, &hp);
+                rc = run_cg(pers, c.win, c.grid, &hp);
                 if (rc == CPS_OK && hp.status != CPS_OK) rc = CPS_ERR_ARG;
                 CPS_CUDA_TRY(s->ctx, cudaEventRecord(e1, stream));
                 CPS_CUDA_TRY(s->ctx, cudaEventSynchronize(e1));
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, e0, e1);
-                per_iter[c] = rc == CPS_OK ? ms / (double)(hp.iter > 0 ? hp.iter : 1) : 0.0;
+                us = rc == CPS_OK ? 1e3 * ms / (double)(hp.iter > 0 ? hp.iter : 1) : 0.0;
+            }
+            if (rc == CPS_ERR_ARG) {
+                rc = CPS_OK;
+                cudaGetLastError();
+                continue;
+            }
+            if (rc != CPS_OK || us <= 0.0) continue;
+            if (per_iter[c.slot] == 0.0 || us < per_iter[c.slot]) per_iter[c.slot] = us;
+            if (best_t == 0.0 || us < best_t) {
+                best_t = us;
+                best = c;
             }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        if (rc != CPS_OK && rc != CPS_ERR_ARG) return rc;
+        {
+            const int rc2 = l2_set_aside(s, 0, stream);
+            if (rc == CPS_OK) rc = rc2;
+        }
+        if (rc != CPS_OK) return rc;
         tu.red_done = true;
-        tu.red_path = (per_iter[1] > 0.0 && per_iter[1] < per_iter[0]) ? 1 : 0;
-        tu.red_probe_us[0] = 1e3 * per_iter[0];
-        tu.red_probe_us[1] = 1e3 * per_iter[1];
+        tu.red_path = best.slot & 1;
+        tu.red_win = best.win;
+        tu.red_pgrid = best.grid;
+        for (int c = 0; c < 4; ++c) tu.red_probe_us[c] = per_iter[c];
         Tuning* c = cached_tuning(s, CPS_FP64);
         c->red_done = true;
         c->red_path = tu.red_path;
-        c->red_probe_us[0] = tu.red_probe_us[0];
-        c->red_probe_us[1] = tu.red_probe_us[1];
+        c->red_win = tu.red_win;
+        c->red_pgrid = tu.red_pgrid;
+        for (int k = 0; k < 4; ++k) c->red_probe_us[k] = tu.red_probe_us[k];
     }
     const bool pers = tu.red_path == 1;
+    const int win = tu.red_win;
+    if (win) {
+        int rc = l2_set_aside(s, win, stream);
+        if (rc) return rc;
+    }
     CgState h{};
     int status = CPS_OK;
     for (int restart = 0; restart < 8; ++restart) {
@@ -831,7 +940,7 @@ static int solve_reduced(cps_sys s, const double* b, double* x, double rtol, int
                                                s->partials, s->st);
         launches += 2;
         CPS_CUDA_TRY(s->ctx, cudaGetLastError());
-        int rc = run_cg(pers, &h);
+        int rc = run_cg(pers, win, tu.red_pgrid, &h);
         if (rc) return rc;
         total += h.iter;
         status = h.status;
@@ -847,6 +956,10 @@ static int solve_reduced(cps_sys s, const double* b, double* x, double rtol, int
     ++launches;
     CPS_CUDA_TRY(s->ctx, cudaGetLastError());
     CPS_CUDA_TRY(s->ctx, cudaStreamSynchronize(stream));
+    if (win) {
+        int rc = l2_set_aside(s, 0, stream);
+        if (rc) return rc;
+    }
     const double rel = h.bnorm2 > 0 ? std::sqrt(h.rnorm2 / h.bnorm2) : 0.0;
     if (status == CPS_OK && h.bnorm2 > 0 && !(rel <= rtol)) status = CPS_ERR_NOT_CONVERGED;
     fill_stats(stats, total, rel, status, 1, launches);

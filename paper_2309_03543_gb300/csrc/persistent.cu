@@ -508,11 +508,28 @@ __global__ void __launch_bounds__(kPBlock, 2) k_persistent_reduced(PersistArgs P
 
 }  // namespace
 
+// Largest grid of a persistent launch on this device (blocks that stay
+// resident together), 0 if the kernel does not fit.
+int persistent_max_grid(cps_sys s, int reduced) {
+    auto kern = reduced ? k_persistent_reduced : k_persistent_cg;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPBlock, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int G = s->ctx->num_sms * (per_sm < 4 ? per_sm : 4);
+    return G > kMaxGrid ? kMaxGrid : G;
+}
+
 // Launches the persistent solve (reduced = 0: Jacobi on all rows; 1: the
-// reduced system) after the caller's init kernel; state in s->st.
+// reduced system) after the caller's init kernel; state in s->st.  With
+// win_bytes > 0 the launch carries a persisting L2 access-policy window over
+// [win_base, win_base + win_bytes) (the caller holds the set-aside).  grid:
+// blocks of the launch, at most what stays resident (0: that maximum).
 int persistent_solve(cps_sys s, int reduced, const double* a, const int32_t* col,
                      const double* sc, double* y, double* r, double* p, double* q, double* t,
-                     int64_t n, int64_t nR, cudaStream_t stream) {
+                     int64_t n, int64_t nR, const void* win_base, size_t win_bytes, int grid,
+                     cudaStream_t stream) {
     if (!s->gsync) {
         cudaError_t e = cudaMalloc((void**)&s->gsync, sizeof(GridSync));
         if (e != cudaSuccess) {
@@ -531,6 +548,7 @@ int persistent_solve(cps_sys s, int reduced, const double* a, const int32_t* col
     }
     int G = s->ctx->num_sms * (per_sm < 4 ? per_sm : 4);
     if (G > kMaxGrid) G = kMaxGrid;
+    if (grid > 0 && grid < G) G = grid;
     // counter, timeout and the G flags in use start at zero
     CPS_CUDA_TRY(s->ctx, cudaMemsetAsync(s->gsync, 0,
                                          offsetof(GridSync, flag) +
@@ -538,9 +556,23 @@ int persistent_solve(cps_sys s, int reduced, const double* a, const int32_t* col
                                          stream));
     PersistArgs P{a, col, sc, y, r, p, q, t, n, nR, s->partials,
                   reinterpret_cast<GridSync*>(s->gsync), s->st};
-    void* args[] = {&P};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(kPBlock), args,
-                                                0, stream);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(G, 1, 1);
+    cfg.blockDim = dim3(kPBlock, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    at[1].id = cudaLaunchAttributeAccessPolicyWindow;
+    at[1].val.accessPolicyWindow.base_ptr = const_cast<void*>(win_base);
+    at[1].val.accessPolicyWindow.num_bytes = win_bytes;
+    at[1].val.accessPolicyWindow.hitRatio = 1.0f;
+    at[1].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    at[1].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    cfg.attrs = at;
+    cfg.numAttrs = win_bytes > 0 ? 2 : 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, P);
     if (e != cudaSuccess) {
         cudaGetLastError();
         s->ctx->last_error = std::string("persistent launch: ") + cudaGetErrorString(e);

@@ -451,15 +451,20 @@ def test_path_autotuner_reports_every_candidate(ctx):
     tu = s.tuning()
     pr = tu["probe_us_per_iter"]
     assert pr["stream"] > 0 and pr["persistent"] > 0 and pr["cluster"] == 0
-    chosen = [k for k in ("stream", "stream_l2_matrix", "stream_l2_vectors", "persistent")
-              if pr[k] > 0]
+    chosen = [k for k in ("stream", "stream_l2_matrix", "stream_l2_vectors", "persistent",
+                          "persistent_l2_vectors") if pr[k] > 0]
     best = min(chosen, key=lambda k: pr[k])
-    assert tu["persistent"] == (best == "persistent")
-    assert tu["l2_window"] == {"stream_l2_matrix": "matrix",
-                               "stream_l2_vectors": "vectors"}.get(best, "none")
+    assert tu["persistent"] == best.startswith("persistent")
+    assert tu["l2_window"] == {"stream_l2_matrix": "matrix", "stream_l2_vectors": "vectors",
+                               "persistent_l2_vectors": "vectors"}.get(best, "none")
     s.set_precond(cps.PC_REDUCED)
     _, st = s.solve(b, rtol=1e-10)
-    pr = s.tuning()["probe_us_per_iter"]
+    tu = s.tuning()
+    pr = tu["probe_us_per_iter"]
     assert pr["reduced_stream"] > 0 and pr["reduced_persistent"] > 0
-    assert s.tuning()["reduced_persistent"] == (pr["reduced_persistent"] < pr["reduced_stream"])
+    red = [k for k in ("reduced_stream", "reduced_persistent", "reduced_stream_l2_vectors",
+                       "reduced_persistent_l2_vectors") if pr[k] > 0]
+    best = min(red, key=lambda k: pr[k])
+    assert tu["reduced_persistent"] == best.startswith("reduced_persistent")
+    assert tu["reduced_l2_window"] == ("vectors" if best.endswith("l2_vectors") else "none")
     s.free()
