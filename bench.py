@@ -45,8 +45,11 @@ BYTES_PER_CELL_ITER_FP64 = 52 + 24 + 40 + 1
 BYTES_PER_CELL_ITER_MIXED = 48 + 12 + 0.5
 # DRAM bytes (read + write) of one FP64 Jacobi iteration (k_spmv_dot + k_cg_b
 # + k_cg_c) on the 1024 x 1024 channel lattice, from one ncu capture of the
-# current kernels (profiles/pcg_iteration_traffic_channel1024.md).
-TRAFFIC_PER_ITER_N1024 = (96.9 + 33.5 + 50.2) * 1e6
+# configuration below (profiles/pcg_iteration_traffic_channel1024.md); the
+# line reports it only when the autotuner chose that configuration.
+TRAFFIC_PER_ITER_N1024 = (121.8 + 21.9 + 40.9) * 1e6
+TRAFFIC_CONFIG = {"unroll": [4, 1, 2], "grid": [608, 152, 152], "block": [256, 1024, 1024],
+                  "l2_window": "vectors", "persistent": False, "cluster": False}
 
 
 def parse():
@@ -68,6 +71,11 @@ def parse():
                          "--n lattice with checkpointed adjoint backward (own line)")
     ap.add_argument("--chain-rtol", type=float, default=1e-8,
                     help="relative residual of the chained forward and adjoint solves")
+    ap.add_argument("--pin", default="",
+                    help="profiling run only: pin the FP64 Jacobi configuration instead of "
+                         "tuning it (a profiler's replay skews the tuner), as "
+                         "'U0,U1,U2/G0,G1,G2/B0,B1,B2/PATH' with PATH stream, stream_l2 or "
+                         "persistent")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiling run: assemble, then FP64 and mixed solves bounded to this "
                          "many iterations (Jacobi and IC(0)); no timing output")
@@ -375,6 +383,11 @@ def main():
         # profiler should select: ncu --nvtx --nvtx-include "cps_profile/")
         s = ctx.assemble(d["xy"], d["tri"], d["dir"], d["eps"], d["kinv"], cps.PER_VERTEX,
                          cps.KIND_CP2, p.nu, p.dt)
+        if args.pin:
+            u, g, b, path = args.pin.split("/")
+            s.set_kernel_shapes(cps.FP64, *[[int(v) for v in f.split(",")] for f in (u, g, b)])
+            s.set_solver_path({"stream": cps.PATH_STREAM, "stream_l2": cps.PATH_STREAM_L2,
+                               "persistent": cps.PATH_PERSISTENT}[path])
         for pc in (cps.PC_JACOBI, cps.PC_IC0):
             s.set_precond(pc)
             for prec in (cps.FP64, cps.MIXED):
@@ -516,11 +529,11 @@ def main():
     if tf["l2_window"] != "none":
         kname += {"matrix": "; matrix in persisting L2",
                   "vectors": "; r, p, q in persisting L2"}[tf["l2_window"]]
-    streaming = not (tf["persistent"] or tf["cluster"] or tf["l2_window"] != "none")
+    profiled = all(tf[k] == v for k, v in TRAFFIC_CONFIG.items())
     roof = {"bound": "hbm", "kernel": kname,
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "peak_kind": peak_kind, "bytes_per_cell_iter": BYTES_PER_CELL_ITER_FP64,
-            "traffic": TRAFFIC_PER_ITER_N1024 if (args.n == 1024 and streaming) else None,
+            "traffic": TRAFFIC_PER_ITER_N1024 if (args.n == 1024 and profiled) else None,
             "traffic_unit": "bytes per iteration (DRAM read + write, ncu)",
             "algorithmic_bytes_per_iter": BYTES_PER_CELL_ITER_FP64 * nt}
     jm = variants["jacobi_mixed"]

@@ -216,13 +216,27 @@ int cps_adjoint(cps_sys sys, const double* x, const double* g, double* lambda, d
  *   CPS_PATH_PERSISTENT: the whole solve in one cooperative launch of one
  *     resident grid, iterations separated by software grid barriers (every
  *     wait bounded: a wait that runs out ends the solve with
- *     CPS_ERR_TIMEOUT).
+ *     CPS_ERR_TIMEOUT);
+ *   CPS_PATH_STREAM_L2: streaming kernels with the vectors r, p, q held in
+ *     persisting L2 during the solve; CPS_ERR_ARG if the GPU's persisting
+ *     set-aside cannot hold them.
  * IC(0) and mixed precision always stream. */
 #define CPS_PATH_AUTO 0
 #define CPS_PATH_STREAM 1
 #define CPS_PATH_CLUSTER 2
 #define CPS_PATH_PERSISTENT 3
+#define CPS_PATH_STREAM_L2 4
 int cps_set_solver_path(cps_sys sys, int path);
+
+/* Pin the launch shapes of the iteration kernels of one precision instead of
+ * letting the autotuner time them (for reproducible measurements, e.g. under
+ * a profiler whose replay would skew the tuner's timings).  unroll, grid and
+ * block are host arrays of 3 entries (SpMV, residual update, direction
+ * update; the third is ignored for CPS_MIXED): unroll 1, 2 or 4 rows per
+ * thread per trip, grid 1..4096 blocks, block 256 (or, CPS_FP64 only, 1024)
+ * threads.  CPS_ERR_ARG for anything else. */
+int cps_set_kernel_shapes(cps_sys sys, int precision, const int32_t* unroll, const int32_t* grid,
+                          const int32_t* block);
 
 /* Launch configuration the autotuner chose for the iteration kernels of one
  * precision (host outputs of 3 entries each; zeros before the first solve in

@@ -27,7 +27,7 @@ KIND_CP2, KIND_CP1_X, KIND_CP1_Y = 0, 1, 2
 PER_VERTEX, PER_CELL, PER_CELL_LOGK = 0, 1, 2
 PC_JACOBI, PC_IC0, PC_REDUCED = 1, 2, 3
 FP64, MIXED = 0, 1
-PATH_AUTO, PATH_STREAM, PATH_CLUSTER, PATH_PERSISTENT = 0, 1, 2, 3
+PATH_AUTO, PATH_STREAM, PATH_CLUSTER, PATH_PERSISTENT, PATH_STREAM_L2 = 0, 1, 2, 3, 4
 
 ERROR_NAMES = {
     ERR_ARG: "CPS_ERR_ARG", ERR_NONMANIFOLD: "CPS_ERR_NONMANIFOLD",
@@ -67,6 +67,7 @@ SIGNATURES = {
     "cps_matvec": (_I, [_P, _P, _P, _P]),
     "cps_get_tuning": (_I, [_P, _I, _P, _P, _P, _P, _P]),
     "cps_set_solver_path": (_I, [_P, _I]),
+    "cps_set_kernel_shapes": (_I, [_P, _I, _P, _P, _P]),
     "cps_solve_ell_noalloc": (_I, [_I64, _P, _P, _P, _P, _P, _D, _I64, ctypes.POINTER(Stats),
                                    _P]),
 }

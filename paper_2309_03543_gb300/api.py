@@ -154,9 +154,17 @@ class System:
                     "reduced_stream_l2_vectors": pr[8], "reduced_persistent_l2_vectors": pr[9]}}
 
     def set_solver_path(self, path: int):
-        """PATH_AUTO, PATH_STREAM, PATH_CLUSTER or PATH_PERSISTENT for FP64
-        Jacobi and reduced-system solves."""
+        """PATH_AUTO, PATH_STREAM, PATH_CLUSTER, PATH_PERSISTENT or
+        PATH_STREAM_L2 for FP64 Jacobi and reduced-system solves."""
         self.ctx.check(self.ctx.lib.cps_set_solver_path(self.handle, path), "cps_set_solver_path")
+
+    def set_kernel_shapes(self, precision: int, unroll, grid, block):
+        """Pin (unroll, grid, block) of the iteration kernels of a precision
+        (3 entries each) instead of autotuning them."""
+        arr = lambda v: (ctypes.c_int32 * 3)(*[int(t) for t in v])
+        self.ctx.check(self.ctx.lib.cps_set_kernel_shapes(self.handle, precision, arr(unroll),
+                                                          arr(grid), arr(block)),
+                       "cps_set_kernel_shapes")
 
     def set_precond(self, precond: int):
         self.ctx.check(self.ctx.lib.cps_set_precond(self.handle, precond,

@@ -168,6 +168,17 @@ int cps_set_solver_path(cps_sys sys, int path) {
         t.red_win = 0;
         t.pgrid = 0;
         t.red_pgrid = 0;
+    } else if (path == CPS_PATH_STREAM_L2) {
+        if (!cps::l2_vectors_fit(sys)) {
+            sys->ctx->last_error = "set_solver_path: the persisting L2 set-aside cannot hold r, p, q";
+            return CPS_ERR_ARG;
+        }
+        t.path_done = true;
+        t.path = 0;
+        t.l2win = 2;
+        t.red_done = true;
+        t.red_path = 0;
+        t.red_win = 2;
     } else if (path == CPS_PATH_CLUSTER) {
         if (sys->nt > cps::cluster_max_rows(sys->ctx)) {
             sys->ctx->last_error = "set_solver_path: system too large for one cluster";
@@ -179,6 +190,32 @@ int cps_set_solver_path(cps_sys sys, int path) {
     } else {
         return CPS_ERR_ARG;
     }
+    return CPS_OK;
+}
+
+int cps_set_kernel_shapes(cps_sys sys, int precision, const int32_t* unroll, const int32_t* grid,
+                          const int32_t* block) {
+    if (!sys || !unroll || !grid || !block || (precision != CPS_FP64 && precision != CPS_MIXED))
+        return CPS_ERR_ARG;
+    const int nk = precision == CPS_FP64 ? 3 : 2;
+    for (int k = 0; k < nk; ++k) {
+        const bool ok_u = unroll[k] == 1 || unroll[k] == 2 || unroll[k] == 4;
+        const bool ok_g = grid[k] >= 1 && grid[k] <= cps::kMaxGrid;
+        const bool ok_b = block[k] == cps::kBlock || (precision == CPS_FP64 && block[k] == 1024);
+        if (!ok_u || !ok_g || !ok_b) {
+            sys->ctx->last_error = "set_kernel_shapes: unroll 1/2/4, grid 1..4096, block 256 "
+                                   "(or 1024 for FP64)";
+            return CPS_ERR_ARG;
+        }
+    }
+    cps::Tuning& t = sys->tune[precision];
+    for (int k = 0; k < nk; ++k) {
+        t.k[k].unroll = unroll[k];
+        t.k[k].grid = grid[k];
+        t.k[k].block = block[k];
+    }
+    t.done = true;
+    cps::drop_graphs(sys, precision);       // captured with the old shapes
     return CPS_OK;
 }
 

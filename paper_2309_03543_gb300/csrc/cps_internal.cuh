@@ -268,6 +268,8 @@ int persistent_solve(cps_sys s, int reduced, const double* a, const int32_t* col
                      int64_t n, int64_t nR, const void* win_base, size_t win_bytes, int grid,
                      cudaStream_t stream);
 int persistent_max_grid(cps_sys s, int reduced);
+bool l2_vectors_fit(cps_sys s);
+void drop_graphs(cps_sys s, int prec);
 int export_impl(cps_sys sys, double* diag, int32_t* col, double* val, cudaStream_t stream);
 void free_sys(cps_sys sys);
 

@@ -368,6 +368,18 @@ static bool l2_window_fits(cps_sys s, int mode) {
     return s->ctx->l2_persist_max > 0 && l2_window_bytes(s, mode) <= s->ctx->l2_persist_max;
 }
 
+bool l2_vectors_fit(cps_sys s) { return l2_window_fits(s, 2); }
+
+// Forgets the chunk graphs of one precision (captured with launch shapes
+// that have changed).
+void drop_graphs(cps_sys s, int prec) {
+    for (int pc = 0; pc < 3; ++pc)
+        if (s->graph[prec][pc]) {
+            cudaGraphExecDestroy(s->graph[prec][pc]);
+            s->graph[prec][pc] = nullptr;
+        }
+}
+
 // The persisting set-aside is a context-wide reservation that shrinks the L2
 // every other kernel sees, so it is held only for the duration of a solve
 // that uses the window and given back (set to 0) right after.

@@ -468,3 +468,37 @@ def test_path_autotuner_reports_every_candidate(ctx):
     assert tu["reduced_persistent"] == best.startswith("reduced_persistent")
     assert tu["reduced_l2_window"] == ("vectors" if best.endswith("l2_vectors") else "none")
     s.free()
+
+
+def test_pinned_shapes_and_stream_l2_path(ctx):
+    """Launch shapes pinned instead of tuned, and the streaming path with
+    r, p, q in persisting L2, on a system above the tuning threshold: the
+    solve still matches the oracle's matrix, and the tuning report echoes
+    the pin.  Out-of-range shapes are rejected."""
+    p = synth.channel_block_problem(300, seed=8)
+    s = assemble(ctx, p)
+    A = oracle.assemble_problem(p)
+    b = synth.rhs(p.mesh, 5)
+    bt = torch.as_tensor(b, device="cuda")
+    s.set_kernel_shapes(cps.FP64, [4, 1, 2], [608, 152, 152], [256, 1024, 1024])
+    try:
+        s.set_solver_path(cps.PATH_STREAM_L2)
+        window = True
+    except cps.CpsError:
+        s.set_solver_path(cps.PATH_STREAM)      # no persisting set-aside on this GPU
+        window = False
+    x, st = s.solve(bt, rtol=1e-10)
+    r = b - A.matvec(x.cpu().numpy())
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-10 * 1.01
+    tu = s.tuning()
+    assert tu["unroll"] == [4, 1, 2] and tu["grid"] == [608, 152, 152]
+    assert tu["block"] == [256, 1024, 1024]
+    assert tu["l2_window"] == ("vectors" if window else "none")
+    for bad in (([3, 1, 2], [608, 152, 152], [256, 256, 256]),
+                ([4, 1, 2], [0, 152, 152], [256, 256, 256]),
+                ([4, 1, 2], [608, 152, 152], [512, 256, 256])):
+        with pytest.raises(cps.CpsError):
+            s.set_kernel_shapes(cps.FP64, *bad)
+    with pytest.raises(cps.CpsError):
+        s.set_kernel_shapes(cps.MIXED, [2, 2, 2], [608, 608, 608], [1024, 256, 256])
+    s.free()
