@@ -46,9 +46,11 @@ BYTES_PER_CELL_ITER_MIXED = 48 + 12 + 0.5
 # DRAM bytes (read + write) of one FP64 Jacobi iteration (k_spmv_dot + k_cg_b
 # + k_cg_c) on the 1024 x 1024 channel lattice, from one ncu capture of the
 # configuration below (profiles/pcg_iteration_traffic_channel1024.md); the
-# line reports it only when the autotuner chose that configuration.
+# line reports it only when the autotuner chose the same launch grids, block
+# sizes and L2 window (the rows per thread per trip, which the tuner may set
+# differently from box to box, do not change the bytes a kernel moves).
 TRAFFIC_PER_ITER_N1024 = (121.8 + 21.9 + 40.9) * 1e6
-TRAFFIC_CONFIG = {"unroll": [4, 1, 2], "grid": [608, 152, 152], "block": [256, 1024, 1024],
+TRAFFIC_CONFIG = {"grid": [608, 152, 152], "block": [256, 1024, 1024],
                   "l2_window": "vectors", "persistent": False, "cluster": False}
 
 

@@ -238,6 +238,16 @@ int cps_set_solver_path(cps_sys sys, int path);
 int cps_set_kernel_shapes(cps_sys sys, int precision, const int32_t* unroll, const int32_t* grid,
                           const int32_t* block);
 
+/* Test hook for failure detection (no counterpart in the paper).  With
+ * CPS_TEST_STALL_BARRIER, the next persistent launch on this system (see
+ * CPS_PATH_PERSISTENT) waits at its first grid barrier for one arrival that
+ * never comes: every block's bounded wait runs out after about a second, the
+ * kernel ends, and the solve returns CPS_ERR_TIMEOUT.  The context stays
+ * usable.  One-shot; 0 clears a pending fault.  CPS_ERR_ARG for an unknown
+ * fault. */
+#define CPS_TEST_STALL_BARRIER 1
+int cps_test_inject(cps_sys sys, int fault);
+
 /* Launch configuration the autotuner chose for the iteration kernels of one
  * precision (host outputs of 3 entries each; zeros before the first solve in
  * that precision): rows per thread per trip of the grid-stride loop, the

@@ -68,6 +68,7 @@ SIGNATURES = {
     "cps_get_tuning": (_I, [_P, _I, _P, _P, _P, _P, _P]),
     "cps_set_solver_path": (_I, [_P, _I]),
     "cps_set_kernel_shapes": (_I, [_P, _I, _P, _P, _P]),
+    "cps_test_inject": (_I, [_P, _I]),
     "cps_solve_ell_noalloc": (_I, [_I64, _P, _P, _P, _P, _P, _D, _I64, ctypes.POINTER(Stats),
                                    _P]),
 }

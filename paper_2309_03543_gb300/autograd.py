@@ -95,7 +95,7 @@ def chained_solve(model: LogPermeabilityCorrector, theta: torch.Tensor, rhs,
         if not normalized:
             return b + coupling * xp
         nx = torch.linalg.vector_norm(xp)
-        if float(nx) == 0.0:
+        if float(nx.detach()) == 0.0:
             return b.clone()
         return b + coupling * (torch.linalg.vector_norm(b) / nx) * xp
 

@@ -193,6 +193,12 @@ int cps_set_solver_path(cps_sys sys, int path) {
     return CPS_OK;
 }
 
+int cps_test_inject(cps_sys sys, int fault) {
+    if (!sys || (fault != 0 && fault != CPS_TEST_STALL_BARRIER)) return CPS_ERR_ARG;
+    sys->inject = fault;
+    return CPS_OK;
+}
+
 int cps_set_kernel_shapes(cps_sys sys, int precision, const int32_t* unroll, const int32_t* grid,
                           const int32_t* block) {
     if (!sys || !unroll || !grid || !block || (precision != CPS_FP64 && precision != CPS_MIXED))

@@ -223,6 +223,7 @@ struct cps_sys_s {
     cps::Tuning tune[2];        // per precision (CPS_FP64, CPS_MIXED)
     int cluster_size = 0;       // CTAs of the last one-cluster solve
     void* gsync = nullptr;      // grid-barrier state of the persistent solves
+    int inject = 0;             // one-shot test fault (cps_test_inject)
 };
 
 #define CPS_CUDA_TRY(ctx, call)                                                        \

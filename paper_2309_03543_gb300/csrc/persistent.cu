@@ -89,6 +89,7 @@ __device__ bool wait_geq(const unsigned long long* p, unsigned long long target,
 // Barriers passed by this block (reductions and grid barriers).
 struct Epoch {
     unsigned long long k = 0;
+    unsigned long long extra = 0;   // test hook: arrivals a barrier waits for beyond the grid
 };
 
 // Grid-wide sum of v[0..NV) (NV <= 2).  Lane 0 of warp 0 then derives the
@@ -127,7 +128,7 @@ __device__ bool grid_allreduce(double (&v)[NV], double (&out)[NS], int& flag, do
 #pragma unroll
             for (int k = 0; k < NV; ++k) pb[k * kMaxGrid + blockIdx.x] = t[k];
             red_release_add(&gs->count, 1ull);
-            ok = wait_geq(&gs->count, ep.k * (unsigned long long)G, gs) ? 1 : 0;
+            ok = wait_geq(&gs->count, ep.k * (unsigned long long)G + ep.extra, gs) ? 1 : 0;
         }
         __syncwarp();
         ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -158,7 +159,7 @@ __device__ bool grid_barrier(GridSync* gs, Epoch& ep) {
     ++ep.k;
     if (threadIdx.x == 0) {
         red_release_add(&gs->count, 1ull);
-        s_ok = wait_geq(&gs->count, ep.k * (unsigned long long)gridDim.x, gs) ? 1 : 0;
+        s_ok = wait_geq(&gs->count, ep.k * (unsigned long long)gridDim.x + ep.extra, gs) ? 1 : 0;
     }
     __syncthreads();
     return s_ok != 0;
@@ -197,6 +198,7 @@ struct PersistArgs {
     double* partials;
     GridSync* gs;
     CgState* st;
+    int stall;          // test hook: 1 makes every barrier wait for one arrival too many
 };
 
 // Rows per block for m rows over the grid: a multiple of 32.
@@ -250,6 +252,7 @@ __global__ void __launch_bounds__(kPBlock, 2) k_persistent_cg(PersistArgs P) {
     const int64_t lo = blockIdx.x * R < n ? blockIdx.x * R : n;
     const int64_t hi = lo + R < n ? lo + R : n;
     Epoch ep;
+    ep.extra = P.stall ? 1ull : 0ull;
     // the blocks whose rows this block's SpMV reads
     int dlo = blockIdx.x, dhi = blockIdx.x;
     {
@@ -410,6 +413,7 @@ __global__ void __launch_bounds__(kPBlock, 2) k_persistent_reduced(PersistArgs P
     double rnorm2 = st->rnorm2;
     bool ok = true;
     Epoch ep;
+    ep.extra = P.stall ? 1ull : 0ull;
     for (;;) {
         {
             double a0[kU], a1[kU], a2[kU];
@@ -554,8 +558,10 @@ int persistent_solve(cps_sys s, int reduced, const double* a, const int32_t* col
                                          offsetof(GridSync, flag) +
                                              sizeof(unsigned long long) * kFlagStride * G,
                                          stream));
+    const int stall = s->inject == CPS_TEST_STALL_BARRIER ? 1 : 0;
+    s->inject = 0;
     PersistArgs P{a, col, sc, y, r, p, q, t, n, nR, s->partials,
-                  reinterpret_cast<GridSync*>(s->gsync), s->st};
+                  reinterpret_cast<GridSync*>(s->gsync), s->st, stall};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(G, 1, 1);
     cfg.blockDim = dim3(kPBlock, 1, 1);
