@@ -440,8 +440,9 @@ def main():
 
     if args.profile_iters:
         # every variant once (autotuning, path probes), then the FP64 Jacobi
-        # solve again inside the NVTX range "cps_profile" (the launches a
-        # profiler should select: ncu --nvtx --nvtx-include "cps_profile/")
+        # solve again inside the NVTX range "cps_profile" and the mixed Jacobi
+        # solve inside "cps_profile_mixed" (the launches a profiler should
+        # select: ncu --nvtx --nvtx-include "cps_profile/")
         s = ctx.assemble(d["xy"], d["tri"], d["dir"], d["eps"], d["kinv"], cps.PER_VERTEX,
                          cps.KIND_CP2, p.nu, p.dt)
         if args.pin:
@@ -460,6 +461,12 @@ def main():
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("cps_profile")
         s.solve(d["b"], x=x, rtol=args.rtol, max_iter=args.profile_iters, check=False)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        x.zero_()
+        torch.cuda.nvtx.range_push("cps_profile_mixed")
+        s.solve(d["b"], x=x, rtol=args.rtol, max_iter=args.profile_iters, precision=cps.MIXED,
+                check=False)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         tuned = s.tuning(cps.FP64)
