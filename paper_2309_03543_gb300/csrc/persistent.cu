@@ -232,7 +232,8 @@ __device__ __forceinline__ int64_t rows_per_block(int64_t m) {
         }                                                                              \
     }
 
-constexpr int kU = 2;
+constexpr int kU = 4;    // rows per trip in the SpMV phases (7 loads per row)
+constexpr int kUV = 4;   // rows per trip in the vector phases (2 or 3 loads per row)
 
 // FP64 Jacobi CG on the scaled matrix from the state k_init64 left:
 //   [wait for the halo] q = Ahat p, gamma | alpha; r -= alpha q; rho',
@@ -334,8 +335,8 @@ __global__ void __launch_bounds__(kPBlock, 2) k_persistent_cg(PersistArgs P) {
         const bool check = ((it + 1) % 8) == 0;
         double rr[2] = {0.0, 0.0};
         {
-            double qe[kU], re0[kU];
-            CPS_B_LOOP(lo, hi, kU, (qe[u] = q[e], re0[u] = r[e]), {
+            double qe[kUV], re0[kUV];
+            CPS_B_LOOP(lo, hi, kUV, (qe[u] = q[e], re0[u] = r[e]), {
                 const double re = fma(-alpha, qe[u], re0[u]);
                 r[e] = re;
                 rr[0] = fma(re, re, rr[0]);
@@ -362,8 +363,8 @@ __global__ void __launch_bounds__(kPBlock, 2) k_persistent_cg(PersistArgs P) {
         const double beta = sb[0];
         rho = sb[1];
         {
-            double pe[kU], ye[kU], re[kU];
-            CPS_B_LOOP(lo, hi, kU, (pe[u] = p[e], ye[u] = y[e], re[u] = stop ? 0.0 : r[e]), {
+            double pe[kUV], ye[kUV], re[kUV];
+            CPS_B_LOOP(lo, hi, kUV, (pe[u] = p[e], ye[u] = y[e], re[u] = stop ? 0.0 : r[e]), {
                 y[e] = fma(alpha, pe[u], ye[u]);
                 if (!stop) p[e] = fma(beta, pe[u], re[u]);
             })
@@ -463,8 +464,8 @@ __global__ void __launch_bounds__(kPBlock, 2) k_persistent_reduced(PersistArgs P
         const bool check = ((it + 1) % 8) == 0;
         double rr[2] = {0.0, 0.0};
         {
-            double qe[kU], re0[kU];
-            CPS_B_LOOP(blo, bhi, kU, (qe[u] = q[e], re0[u] = r[e]), {
+            double qe[kUV], re0[kUV];
+            CPS_B_LOOP(blo, bhi, kUV, (qe[u] = q[e], re0[u] = r[e]), {
                 const double re = fma(-alpha, qe[u], re0[u]);
                 r[e] = re;
                 rr[0] = fma(re, re, rr[0]);
@@ -491,8 +492,8 @@ __global__ void __launch_bounds__(kPBlock, 2) k_persistent_reduced(PersistArgs P
         const double beta = sb[0];
         rho = sb[1];
         {
-            double pe[kU], ye[kU], re[kU];
-            CPS_B_LOOP(blo, bhi, kU, (pe[u] = p[e], ye[u] = y[e], re[u] = stop ? 0.0 : r[e]), {
+            double pe[kUV], ye[kUV], re[kUV];
+            CPS_B_LOOP(blo, bhi, kUV, (pe[u] = p[e], ye[u] = y[e], re[u] = stop ? 0.0 : r[e]), {
                 y[e] = fma(alpha, pe[u], ye[u]);
                 if (!stop) p[e] = fma(beta, pe[u], re[u]);
             })
