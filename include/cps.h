@@ -233,8 +233,9 @@ int cps_set_solver_path(cps_sys sys, int path);
  * a profiler whose replay would skew the tuner's timings).  unroll, grid and
  * block are host arrays of 3 entries (SpMV, residual update, direction
  * update; the third is ignored for CPS_MIXED): unroll 1, 2 or 4 rows per
- * thread per trip, grid 1..4096 blocks, block 256 (or, CPS_FP64 only, 1024)
- * threads.  CPS_ERR_ARG for anything else. */
+ * thread per trip (also 8 for the two FP64 update kernels), grid 1..4096
+ * blocks, block 256 (or, CPS_FP64 only, 1024) threads.  CPS_ERR_ARG for
+ * anything else. */
 int cps_set_kernel_shapes(cps_sys sys, int precision, const int32_t* unroll, const int32_t* grid,
                           const int32_t* block);
 

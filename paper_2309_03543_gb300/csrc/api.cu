@@ -205,12 +205,13 @@ int cps_set_kernel_shapes(cps_sys sys, int precision, const int32_t* unroll, con
         return CPS_ERR_ARG;
     const int nk = precision == CPS_FP64 ? 3 : 2;
     for (int k = 0; k < nk; ++k) {
-        const bool ok_u = unroll[k] == 1 || unroll[k] == 2 || unroll[k] == 4;
+        const bool ok_u = unroll[k] == 1 || unroll[k] == 2 || unroll[k] == 4 ||
+                          (unroll[k] == 8 && precision == CPS_FP64 && k > 0);
         const bool ok_g = grid[k] >= 1 && grid[k] <= cps::kMaxGrid;
         const bool ok_b = block[k] == cps::kBlock || (precision == CPS_FP64 && block[k] == 1024);
         if (!ok_u || !ok_g || !ok_b) {
-            sys->ctx->last_error = "set_kernel_shapes: unroll 1/2/4, grid 1..4096, block 256 "
-                                   "(or 1024 for FP64)";
+            sys->ctx->last_error = "set_kernel_shapes: unroll 1/2/4 (8 for the FP64 vector "
+                                   "kernels), grid 1..4096, block 256 (or 1024 for FP64)";
             return CPS_ERR_ARG;
         }
     }

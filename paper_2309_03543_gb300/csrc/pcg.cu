@@ -148,6 +148,16 @@ static void launch_a(const KCfg& c, const Run<V>& v, cps_sys s, cudaStream_t st)
             break;                                                                        \
     }
 
+// The vector kernels (residual and direction updates) also take 8 rows per
+// trip: with two or three loads per row they need more rows in flight.
+#define CPS_FP64_SHAPES_V(KERNEL_U_B, ...)                                                \
+    if (c.unroll == 8 && c.block == 1024)                                                 \
+        launch_kb(KERNEL_U_B(8, 1024), c.grid, 1024, __VA_ARGS__);                        \
+    else if (c.unroll == 8)                                                               \
+        launch_kb(KERNEL_U_B(8, kBlock), c.grid, kBlock, __VA_ARGS__);                    \
+    else                                                                                  \
+        CPS_FP64_SHAPES(KERNEL_U_B, __VA_ARGS__)
+
 #define CPS_SPMV64(U, B) k_spmv_dot<double, U, B>
 template <>
 void launch_a<double>(const KCfg& c, const Run<double>& v, cps_sys s, cudaStream_t st) {
@@ -167,7 +177,7 @@ template <typename V, bool NORM, bool JACOBI>
 static void launch_b_u(const KCfg& c, const Run<V>& v, cps_sys s, cudaStream_t st) {
     if constexpr (sizeof(V) == 8) {
 #define CPS_CGB64(U, B) k_cg_b<double, NORM, JACOBI, U, B>
-        CPS_FP64_SHAPES(CPS_CGB64, st, v.r, v.q, v.s, v.n, s->partials, s->st)
+        CPS_FP64_SHAPES_V(CPS_CGB64, st, v.r, v.q, v.s, v.n, s->partials, s->st)
 #undef CPS_CGB64
     } else {
         switch (c.unroll) {
@@ -189,7 +199,7 @@ static void launch_b(const KCfg& c, const Run<V>& v, bool norm, cps_sys s, cudaS
 
 #define CPS_CGC64(U, B) k_cg_c<double, U, B>
 static void launch_c(const KCfg& c, const Run<double>& v, cps_sys s, cudaStream_t st) {
-    CPS_FP64_SHAPES(CPS_CGC64, st, v.y, v.p0, v.z, v.n, s->st)
+    CPS_FP64_SHAPES_V(CPS_CGC64, st, v.y, v.p0, v.z, v.n, s->st)
 }
 
 static Tuning default_tuning(cps_sys s) {
@@ -277,7 +287,7 @@ static int autotune(cps_sys s, int prec, const Run<V>& v, cudaStream_t stream) {
         return best;
     };
     // candidates: rows per thread per trip x (block size, blocks per SM)
-    const int unrolls[3] = {1, 2, 4};
+    const int unrolls[4] = {1, 2, 4, 8};       // 8: FP64 vector kernels only
     struct Shape {
         int block, per_sm;
     };
@@ -287,7 +297,8 @@ static int autotune(cps_sys s, int prec, const Run<V>& v, cudaStream_t stream) {
     for (int kind = 0; kind < nk && rc == CPS_OK; ++kind) {
         KCfg keep = t.k[kind];
         float best = time_loop();
-        for (int ui = 0; ui < 3 && rc == CPS_OK; ++ui)
+        const int nu = (sizeof(V) == 8 && kind > 0) ? 4 : 3;
+        for (int ui = 0; ui < nu && rc == CPS_OK; ++ui)
             for (int gi = 0; gi < nshapes && rc == CPS_OK; ++gi) {
                 const Shape sh = shapes64[gi];
                 KCfg c;
