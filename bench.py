@@ -254,9 +254,12 @@ def run_batch(args):
 
     loop(cps.FP64)
     batch(cps.FP64)   # warm-up (autotuning, graph capture)
+    loop(cps.MIXED)
+    batch(cps.MIXED)
     res = {}
     for name, fn in (("loop_fp64", lambda: loop(cps.FP64)), ("batch_fp64", lambda: batch(cps.FP64)),
-                     ("loop_mixed", lambda: loop(cps.MIXED))):
+                     ("loop_mixed", lambda: loop(cps.MIXED)),
+                     ("batch_mixed", lambda: batch(cps.MIXED))):
         best = None
         for _ in range(max(1, args.steps)):
             t, ci = timed(fn, stream)
@@ -268,7 +271,11 @@ def run_batch(args):
             "config": {"workload": f"{args.batch} systems, log-uniform 2k-500k cells",
                        "cells": cells, "rtol": args.rtol, "host_setup_s": setup},
             "variants": res,
-            "batch_speedup_vs_loop": res["loop_fp64"]["seconds"] / res["batch_fp64"]["seconds"]}
+            "batch_speedup_vs_loop": res["loop_fp64"]["seconds"] / res["batch_fp64"]["seconds"],
+            "batch_mixed_speedup_vs_loop_mixed":
+                res["loop_mixed"]["seconds"] / res["batch_mixed"]["seconds"],
+            "batch_mixed_vs_batch_fp64_seconds":
+                res["batch_mixed"]["seconds"] / res["batch_fp64"]["seconds"]}
     print(json.dumps(line), flush=True)
 
 

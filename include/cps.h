@@ -182,9 +182,13 @@ int cps_solve(cps_sys sys, const double* b, double* x, double rtol, int64_t max_
  * CPS_FP64: one launch per phase for all systems (Jacobi, whatever each
  * system's preconditioner setting), a per-system convergence mask, and
  * iteration chunks replayed from a CUDA graph; a system of more than
- * 33,554,432 cells is rejected (CPS_ERR_ARG) -- solve it alone.  CPS_MIXED
- * solves the systems one after the other.  The return value is the first
- * non-OK per-system status, or CPS_OK. */
+ * 33,554,432 cells is rejected (CPS_ERR_ARG) -- solve it alone.  CPS_MIXED:
+ * each system's solve (whose residual replacements are decided on the host)
+ * runs whole on one of up to 8 internal streams, fed by as many host threads,
+ * so that the systems' launches overlap on the GPU; the call returns after
+ * ordering `stream` behind all of them (it blocks the calling thread until
+ * every system has finished).  The return value is the first non-OK
+ * per-system status, or CPS_OK. */
 int cps_solve_batch(const cps_sys* systems, int nsys, const double* const* b,
                     double* const* x, double rtol, int64_t max_iter, int precision,
                     cps_stats* stats, void* stream);

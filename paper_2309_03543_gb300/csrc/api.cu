@@ -9,7 +9,7 @@ namespace {
 int set_device(cps_ctx ctx) {
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) {
-        ctx->last_error = std::string("cudaSetDevice: ") + cudaGetErrorString(e);
+        cps::set_error(ctx, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
         return CPS_ERR_CUDA;
     }
     return CPS_OK;
@@ -68,11 +68,12 @@ int cps_assemble(cps_ctx ctx, const double* xy, int64_t nv, const int32_t* tri, 
     *out = nullptr;
     int rc = set_device(ctx);
     if (rc) return rc;
-    ctx->last_error.clear();
+    cps::set_error(ctx, "");
     rc = cps::assemble_impl(ctx, xy, nv, tri, nt, dirichlet, nb, eps, kinv, field_loc, kind, nu,
                             dt, out, as_stream(stream));
     if (rc == CPS_OK) {
         ctx->systems.insert(*out);
+        std::lock_guard<std::mutex> lock(ctx->mu);
         auto it = ctx->tune_cache.find({(*out)->nt, (*out)->nv});
         if (it != ctx->tune_cache.end())
             for (int p = 0; p < 2; ++p) (*out)->tune[p] = it->second[p];
@@ -170,7 +171,7 @@ int cps_set_solver_path(cps_sys sys, int path) {
         t.red_pgrid = 0;
     } else if (path == CPS_PATH_STREAM_L2) {
         if (!cps::l2_vectors_fit(sys)) {
-            sys->ctx->last_error = "set_solver_path: the persisting L2 set-aside cannot hold r, p, q";
+            cps::set_error(sys->ctx, "set_solver_path: the persisting L2 set-aside cannot hold r, p, q");
             return CPS_ERR_ARG;
         }
         t.path_done = true;
@@ -181,7 +182,7 @@ int cps_set_solver_path(cps_sys sys, int path) {
         t.red_win = 2;
     } else if (path == CPS_PATH_CLUSTER) {
         if (sys->nt > cps::cluster_max_rows(sys->ctx)) {
-            sys->ctx->last_error = "set_solver_path: system too large for one cluster";
+            cps::set_error(sys->ctx, "set_solver_path: system too large for one cluster");
             return CPS_ERR_ARG;
         }
         t.path_done = true;
@@ -210,8 +211,8 @@ int cps_set_kernel_shapes(cps_sys sys, int precision, const int32_t* unroll, con
         const bool ok_g = grid[k] >= 1 && grid[k] <= cps::kMaxGrid;
         const bool ok_b = block[k] == cps::kBlock || (precision == CPS_FP64 && block[k] == 1024);
         if (!ok_u || !ok_g || !ok_b) {
-            sys->ctx->last_error = "set_kernel_shapes: unroll 1/2/4 (8 for the FP64 vector "
-                                   "kernels), grid 1..4096, block 256 (or 1024 for FP64)";
+            cps::set_error(sys->ctx, "set_kernel_shapes: unroll 1/2/4 (8 for the FP64 vector "
+                                   "kernels), grid 1..4096, block 256 (or 1024 for FP64)");
             return CPS_ERR_ARG;
         }
     }

@@ -340,7 +340,7 @@ template <typename T>
 static int dev_alloc(cps_ctx ctx, T** p, size_t n) {
     cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (n > 0 ? n : 1));
     if (e != cudaSuccess) {
-        ctx->last_error = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+        cps::set_error(ctx, std::string("cudaMalloc: ") + cudaGetErrorString(e));
         *p = nullptr;
         return CPS_ERR_NOMEM;
     }
@@ -367,7 +367,7 @@ void free_sys(cps_sys s) {
 }
 
 static int fail(cps_ctx ctx, int code, const std::string& msg) {
-    ctx->last_error = msg;
+    cps::set_error(ctx, msg);
     return code;
 }
 

@@ -13,7 +13,10 @@
 // of pcg_kernels.cuh (three kernels); a chunk of iterations is one CUDA graph.
 #include "cps_internal.cuh"
 
+#include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <thread>
 #include <vector>
 
 namespace cps {
@@ -345,31 +348,84 @@ __global__ void kb_count_running(const BatchDesc* __restrict__ d, int nsys, int*
 
 }  // namespace
 
+// Mixed-precision ensemble.  Each system's binary32 solve takes its own
+// residual-replacement decisions on the host between its graph chunks, so
+// the systems cannot share one launch per phase as the FP64 batch does.
+// Instead kMixedWorkers host threads take systems from a shared counter and
+// run each system's whole solve on the thread's own stream: the graph chunks
+// of different systems overlap on the GPU (most systems of an ensemble are
+// small, and a small system's solve is bound by launch latency, not by
+// bandwidth).  The caller's stream is ordered before and after all of it.
+constexpr int kMixedWorkers = 8;
+
+static int solve_batch_mixed(const cps_sys* systems, int nsys, const double* const* b,
+                             double* const* x, double rtol, int64_t max_iter, int precision,
+                             cps_stats* stats, cudaStream_t stream) {
+    cps_ctx ctx = systems[0]->ctx;
+    const int nw = std::min(nsys, kMixedWorkers);
+    std::vector<cudaStream_t> streams(nw, nullptr);
+    std::vector<cudaEvent_t> done(nw, nullptr);
+    cudaEvent_t ready = nullptr;
+    int rc = CPS_OK;
+    auto cleanup = [&]() {
+        for (auto& st : streams)
+            if (st) cudaStreamDestroy(st);
+        for (auto& ev : done)
+            if (ev) cudaEventDestroy(ev);
+        if (ready) cudaEventDestroy(ready);
+    };
+    if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess) rc = CPS_ERR_CUDA;
+    for (int w = 0; w < nw && rc == CPS_OK; ++w)
+        if (cudaStreamCreateWithFlags(&streams[w], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&done[w], cudaEventDisableTiming) != cudaSuccess)
+            rc = CPS_ERR_CUDA;
+    if (rc == CPS_OK && cudaEventRecord(ready, stream) != cudaSuccess) rc = CPS_ERR_CUDA;
+    if (rc != CPS_OK) {
+        cudaGetLastError();
+        cleanup();
+        cps::set_error(ctx, "solve_batch: could not create worker streams");
+        return rc;
+    }
+    std::vector<int> rcs(nsys, CPS_OK);
+    std::atomic<int> next{0};
+    auto work = [&](int w) {
+        cudaSetDevice(ctx->device);
+        cudaStreamWaitEvent(streams[w], ready, 0);
+        for (;;) {
+            const int i = next.fetch_add(1);
+            if (i >= nsys) break;
+            rcs[i] = solve_impl(systems[i], b[i], x[i], rtol, max_iter, precision,
+                                stats ? &stats[i] : nullptr, streams[w]);
+        }
+        cudaEventRecord(done[w], streams[w]);
+    };
+    std::vector<std::thread> threads;
+    threads.reserve(nw);
+    for (int w = 0; w < nw; ++w) threads.emplace_back(work, w);
+    for (auto& th : threads) th.join();
+    for (int w = 0; w < nw; ++w) cudaStreamWaitEvent(stream, done[w], 0);
+    cleanup();
+    for (int i = 0; i < nsys; ++i)
+        if (rcs[i] != CPS_OK) return rcs[i];
+    return CPS_OK;
+}
+
 int solve_batch_impl(const cps_sys* systems, int nsys, const double* const* b,
                      double* const* x, double rtol, int64_t max_iter, int precision,
                      cps_stats* stats, cudaStream_t stream) {
     cps_ctx ctx = systems[0]->ctx;
     for (int i = 0; i < nsys; ++i) {
         if (!b[i] || !x[i]) {
-            ctx->last_error = "solve_batch: null vector";
+            cps::set_error(ctx, "solve_batch: null vector");
             return CPS_ERR_ARG;
         }
     }
     if (!(rtol >= 0.0) || max_iter < 0) {
-        ctx->last_error = "solve_batch: bad argument";
+        cps::set_error(ctx, "solve_batch: bad argument");
         return CPS_ERR_ARG;
     }
-    if (precision != CPS_FP64) {
-        // The binary32 refinement needs per-system residual replacement on
-        // the host side: run the systems one after the other.
-        int first = CPS_OK;
-        for (int i = 0; i < nsys; ++i) {
-            int rc = solve_impl(systems[i], b[i], x[i], rtol, max_iter, precision,
-                                stats ? &stats[i] : nullptr, stream);
-            if (rc != CPS_OK && first == CPS_OK) first = rc;
-        }
-        return first;
-    }
+    if (precision != CPS_FP64) return solve_batch_mixed(systems, nsys, b, x, rtol, max_iter,
+                                                        precision, stats, stream);
     std::vector<BatchDesc> hd(nsys);
     int64_t total_tiles = 0;
     for (int i = 0; i < nsys; ++i) {
@@ -390,7 +446,7 @@ int solve_batch_impl(const cps_sys* systems, int nsys, const double* const* b,
         d.ntiles = (int32_t)((s->nt + kTileRows - 1) / kTileRows);
         d.pad = 0;
         if (d.ntiles > 4 * kMaxGrid) {
-            ctx->last_error = "solve_batch: a system is too large for the batched path";
+            cps::set_error(ctx, "solve_batch: a system is too large for the batched path");
             return CPS_ERR_ARG;
         }
         total_tiles += d.ntiles;
@@ -501,14 +557,14 @@ int solve_batch_impl(const cps_sys* systems, int nsys, const double* const* b,
     cudaStreamSynchronize(stream);
     cudaFreeHost(hcount);
     if (rc != CPS_OK) {
-        ctx->last_error = "solve_batch: CUDA failure";
+        cps::set_error(ctx, "solve_batch: CUDA failure");
         return rc;
     }
     int first = CPS_OK;
     for (int i = 0; i < nsys; ++i)
         if (status[i] != CPS_OK && first == CPS_OK) first = status[i];
-    if (first == CPS_ERR_NOT_CONVERGED) ctx->last_error = "solve_batch: max_iter reached";
-    if (first == CPS_ERR_NOT_SPD) ctx->last_error = "solve_batch: p.Ap <= 0";
+    if (first == CPS_ERR_NOT_CONVERGED) cps::set_error(ctx, "solve_batch: max_iter reached");
+    if (first == CPS_ERR_NOT_SPD) cps::set_error(ctx, "solve_batch: p.Ap <= 0");
     return first;
 }
 

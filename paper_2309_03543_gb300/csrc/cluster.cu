@@ -287,7 +287,7 @@ int cluster_solve(cps_sys s, const double* b, const double* x, double* y, double
             e = cudaFuncSetAttribute(k_cluster_cg, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) {
             cudaGetLastError();
-            s->ctx->last_error = std::string("cluster path: ") + cudaGetErrorString(e);
+            cps::set_error(s->ctx, std::string("cluster path: ") + cudaGetErrorString(e));
             return CPS_ERR_ARG;
         }
         configured[dev & 63] = true;
@@ -332,13 +332,13 @@ int cluster_solve(cps_sys s, const double* b, const double* x, double* y, double
         e = cudaLaunchKernelEx(&cfg, k_cluster_cg, A);
         if (e != cudaSuccess) {
             cudaGetLastError();
-            s->ctx->last_error = std::string("cluster launch: ") + cudaGetErrorString(e);
+            cps::set_error(s->ctx, std::string("cluster launch: ") + cudaGetErrorString(e));
             return CPS_ERR_CUDA;
         }
         s->cluster_size = csize;
         return CPS_OK;
     }
-    s->ctx->last_error = "cluster path: no cluster shape fits this system";
+    cps::set_error(s->ctx, "cluster path: no cluster shape fits this system");
     return CPS_ERR_ARG;
 }
 

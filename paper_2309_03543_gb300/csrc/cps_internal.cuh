@@ -9,6 +9,7 @@
 #include <array>
 #include <cstdio>
 #include <map>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <unordered_set>
@@ -146,11 +147,20 @@ struct cps_ctx_s {
     size_t l2_persist_max = 0;   // cudaDevAttrMaxPersistingL2CacheSize
     size_t l2_persist_set = 0;   // persisting L2 limit this process has set
     std::string last_error;
+    std::mutex mu;               // guards last_error and tune_cache (solves may run on threads)
     std::unordered_set<cps_sys_s*> systems;   // live systems, freed with the context
     // Tuned launch choices by mesh size (cells, vertices): a system assembled
     // later on a mesh of the same size starts from them instead of re-timing.
     std::map<std::pair<int64_t, int64_t>, std::array<cps::Tuning, 2>> tune_cache;
 };
+
+namespace cps {
+// Records the context's last error message (thread-safe).
+inline void set_error(cps_ctx_s* ctx, const std::string& msg) {
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    ctx->last_error = msg;
+}
+}  // namespace cps
 
 struct cps_sys_s {
     cps_ctx ctx = nullptr;
@@ -231,7 +241,7 @@ struct cps_sys_s {
         cudaError_t e_ = (call);                                                       \
         if (e_ != cudaSuccess) {                                                       \
             if (ctx) {                                                                 \
-                (ctx)->last_error = std::string(#call) + ": " + cudaGetErrorString(e_); \
+                cps::set_error((ctx), std::string(#call) + ": " + cudaGetErrorString(e_)); \
             }                                                                          \
             return e_ == cudaErrorMemoryAllocation ? CPS_ERR_NOMEM : CPS_ERR_CUDA;     \
         }                                                                              \

@@ -37,7 +37,7 @@ static int ensure_capture_stream(cps_sys s) {
     if (!s->cap_stream) {
         cudaError_t e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) {
-            s->ctx->last_error = std::string("cudaStreamCreate: ") + cudaGetErrorString(e);
+            cps::set_error(s->ctx, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
             return CPS_ERR_CUDA;
         }
     }
@@ -212,8 +212,12 @@ static Tuning default_tuning(cps_sys s) {
 }
 
 // The context's remembered choices for systems of this mesh size.
-static Tuning* cached_tuning(cps_sys s, int prec) {
-    return &s->ctx->tune_cache[{s->nt, s->nv}][prec];
+// f(entry) runs under the context's lock (solves of different systems may
+// run on different host threads).
+template <typename F>
+static void update_cached_tuning(cps_sys s, int prec, F f) {
+    std::lock_guard<std::mutex> lock(s->ctx->mu);
+    f(s->ctx->tune_cache[{s->nt, s->nv}][prec]);
 }
 
 template <typename V>
@@ -320,12 +324,13 @@ static int autotune(cps_sys s, int prec, const Run<V>& v, cudaStream_t stream) {
     cudaEventDestroy(e1);
     if (cudaGetLastError() != cudaSuccess) rc = CPS_ERR_CUDA;
     if (rc) {
-        s->ctx->last_error = "autotune: kernel launch failed";
+        cps::set_error(s->ctx, "autotune: kernel launch failed");
         return rc;
     }
-    Tuning* c = cached_tuning(s, prec);
-    for (int k = 0; k < 3; ++k) c->k[k] = t.k[k];
-    c->done = true;
+    update_cached_tuning(s, prec, [&](Tuning& c) {
+        for (int k = 0; k < 3; ++k) c.k[k] = t.k[k];
+        c.done = true;
+    });
     return CPS_OK;
 }
 
@@ -446,15 +451,15 @@ static int get_chunk_graph(cps_sys s, int prec, const Run<V>& v, cudaGraphExec_t
         cudaError_t ce = cudaStreamEndCapture(s->cap_stream, &graph);
         if (le != cudaSuccess || ce != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
-            s->ctx->last_error = std::string("graph capture: ") +
-                                 cudaGetErrorString(le != cudaSuccess ? le : ce);
+            cps::set_error(s->ctx, std::string("graph capture: ") +
+                                 cudaGetErrorString(le != cudaSuccess ? le : ce));
             return CPS_ERR_CUDA;
         }
         cudaError_t ie = cudaGraphInstantiate(&ge, graph, 0);
         cudaGraphDestroy(graph);
         if (ie != cudaSuccess) {
             ge = nullptr;
-            s->ctx->last_error = std::string("graph instantiate: ") + cudaGetErrorString(ie);
+            cps::set_error(s->ctx, std::string("graph instantiate: ") + cudaGetErrorString(ie));
             return CPS_ERR_CUDA;
         }
         s->graph_nodes[prec][pc] = nl;
@@ -631,12 +636,13 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
     }
     for (int k = 0; k < 6; ++k) t.probe_us[k] = per_iter[k];
     if (rc == CPS_OK) {
-        Tuning* c = cached_tuning(s, CPS_FP64);
-        c->path_done = true;
-        c->path = t.path;
-        c->l2win = t.l2win;
-        c->pgrid = t.pgrid;
-        for (int k = 0; k < 6; ++k) c->probe_us[k] = t.probe_us[k];
+        update_cached_tuning(s, CPS_FP64, [&](Tuning& c) {
+            c.path_done = true;
+            c.path = t.path;
+            c.l2win = t.l2win;
+            c.pgrid = t.pgrid;
+            for (int k = 0; k < 6; ++k) c.probe_us[k] = t.probe_us[k];
+        });
     }
     return rc;
 }
@@ -753,9 +759,9 @@ static int solve_fp64(cps_sys s, const double* b, double* x, double rtol, int64_
     const double rel = h.bnorm2 > 0 ? std::sqrt(h.rnorm2 / h.bnorm2) : 0.0;
     if (status == CPS_OK && h.bnorm2 > 0 && !(rel <= rtol)) status = CPS_ERR_NOT_CONVERGED;
     fill_stats(stats, total, rel, status, 1, launches);
-    if (status == CPS_ERR_NOT_SPD) s->ctx->last_error = "solve: p.Ap <= 0 (matrix not SPD or NaN input)";
-    if (status == CPS_ERR_TIMEOUT) s->ctx->last_error = "solve: a grid barrier wait ran out";
-    if (status == CPS_ERR_NOT_CONVERGED) s->ctx->last_error = "solve: max_iter reached";
+    if (status == CPS_ERR_NOT_SPD) cps::set_error(s->ctx, "solve: p.Ap <= 0 (matrix not SPD or NaN input)");
+    if (status == CPS_ERR_TIMEOUT) cps::set_error(s->ctx, "solve: a grid barrier wait ran out");
+    if (status == CPS_ERR_NOT_CONVERGED) cps::set_error(s->ctx, "solve: max_iter reached");
     return status;
 }
 
@@ -816,15 +822,15 @@ static int solve_reduced(cps_sys s, const double* b, double* x, double rtol, int
         if (win) set_l2_window(s, s->cap_stream, 0);
         if (le != cudaSuccess || ce != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
-            s->ctx->last_error = std::string("graph capture: ") +
-                                 cudaGetErrorString(le != cudaSuccess ? le : ce);
+            cps::set_error(s->ctx, std::string("graph capture: ") +
+                                 cudaGetErrorString(le != cudaSuccess ? le : ce));
             return CPS_ERR_CUDA;
         }
         cudaError_t ie = cudaGraphInstantiate(&ge, graph, 0);
         cudaGraphDestroy(graph);
         if (ie != cudaSuccess) {
             ge = nullptr;
-            s->ctx->last_error = std::string("graph instantiate: ") + cudaGetErrorString(ie);
+            cps::set_error(s->ctx, std::string("graph instantiate: ") + cudaGetErrorString(ie));
             return CPS_ERR_CUDA;
         }
         s->graph_nodes[CPS_FP64][2] = nl;
@@ -941,12 +947,13 @@ static int solve_reduced(cps_sys s, const double* b, double* x, double rtol, int
         tu.red_win = best.win;
         tu.red_pgrid = best.grid;
         for (int c = 0; c < 4; ++c) tu.red_probe_us[c] = per_iter[c];
-        Tuning* c = cached_tuning(s, CPS_FP64);
-        c->red_done = true;
-        c->red_path = tu.red_path;
-        c->red_win = tu.red_win;
-        c->red_pgrid = tu.red_pgrid;
-        for (int k = 0; k < 4; ++k) c->red_probe_us[k] = tu.red_probe_us[k];
+        update_cached_tuning(s, CPS_FP64, [&](Tuning& c) {
+            c.red_done = true;
+            c.red_path = tu.red_path;
+            c.red_win = tu.red_win;
+            c.red_pgrid = tu.red_pgrid;
+            for (int k = 0; k < 4; ++k) c.red_probe_us[k] = tu.red_probe_us[k];
+        });
     }
     const bool pers = tu.red_path == 1;
     const int win = tu.red_win;
@@ -986,9 +993,9 @@ static int solve_reduced(cps_sys s, const double* b, double* x, double rtol, int
     const double rel = h.bnorm2 > 0 ? std::sqrt(h.rnorm2 / h.bnorm2) : 0.0;
     if (status == CPS_OK && h.bnorm2 > 0 && !(rel <= rtol)) status = CPS_ERR_NOT_CONVERGED;
     fill_stats(stats, total, rel, status, 1, launches);
-    if (status == CPS_ERR_NOT_SPD) s->ctx->last_error = "solve: p.Sp <= 0 (reduced system)";
-    if (status == CPS_ERR_TIMEOUT) s->ctx->last_error = "solve: a grid barrier wait ran out";
-    if (status == CPS_ERR_NOT_CONVERGED) s->ctx->last_error = "solve: max_iter reached";
+    if (status == CPS_ERR_NOT_SPD) cps::set_error(s->ctx, "solve: p.Sp <= 0 (reduced system)");
+    if (status == CPS_ERR_TIMEOUT) cps::set_error(s->ctx, "solve: a grid barrier wait ran out");
+    if (status == CPS_ERR_NOT_CONVERGED) cps::set_error(s->ctx, "solve: max_iter reached");
     return status;
 }
 
@@ -1076,20 +1083,20 @@ static int solve_mixed(cps_sys s, const double* b, double* x, double rtol, int64
     CPS_CUDA_TRY(s->ctx, cudaStreamSynchronize(stream));
     const double rel = h.bnorm2 > 0 ? std::sqrt(h.rnorm2 / h.bnorm2) : 0.0;
     fill_stats(stats, base + h.iter, rel, status, updates, launches);
-    if (status == CPS_ERR_NOT_CONVERGED) s->ctx->last_error = "solve: mixed precision did not reach rtol";
-    if (status == CPS_ERR_NOT_SPD) s->ctx->last_error = "solve: p.Ap <= 0 in the binary32 iteration";
+    if (status == CPS_ERR_NOT_CONVERGED) cps::set_error(s->ctx, "solve: mixed precision did not reach rtol");
+    if (status == CPS_ERR_NOT_SPD) cps::set_error(s->ctx, "solve: p.Ap <= 0 in the binary32 iteration");
     return status;
 }
 
 int solve_impl(cps_sys s, const double* b, double* x, double rtol, int64_t max_iter,
                int precision, cps_stats* stats, cudaStream_t stream) {
     if (!b || !x || !(rtol >= 0.0) || max_iter < 0) {
-        s->ctx->last_error = "solve: bad argument";
+        cps::set_error(s->ctx, "solve: bad argument");
         return CPS_ERR_ARG;
     }
     if (s->precond == CPS_PC_REDUCED) {
         if (precision != CPS_FP64) {
-            s->ctx->last_error = "solve: the reduced-system solve is FP64 only";
+            cps::set_error(s->ctx, "solve: the reduced-system solve is FP64 only");
             return CPS_ERR_ARG;
         }
         return solve_reduced(s, b, x, rtol, max_iter, stats, stream);
@@ -1100,13 +1107,13 @@ int solve_impl(cps_sys s, const double* b, double* x, double rtol, int64_t max_i
         return rc;
     }
     if (precision == CPS_MIXED) return solve_mixed(s, b, x, rtol, max_iter, stats, stream);
-    s->ctx->last_error = "solve: bad precision";
+    cps::set_error(s->ctx, "solve: bad precision");
     return CPS_ERR_ARG;
 }
 
 int matvec_impl(cps_sys s, const double* x, double* y, cudaStream_t stream) {
     if (!x || !y) {
-        s->ctx->last_error = "matvec: null pointer";
+        cps::set_error(s->ctx, "matvec: null pointer");
         return CPS_ERR_ARG;
     }
     k_matvec64<<<s->grid, kBlock, 0, stream>>>(x, s->s, s->a, s->col, s->nt, y);
@@ -1116,7 +1123,7 @@ int matvec_impl(cps_sys s, const double* x, double* y, cudaStream_t stream) {
 
 int export_impl(cps_sys s, double* diag, int32_t* col, double* val, cudaStream_t stream) {
     if (!diag || !col || !val) {
-        s->ctx->last_error = "export: null pointer";
+        cps::set_error(s->ctx, "export: null pointer");
         return CPS_ERR_ARG;
     }
     CPS_CUDA_TRY(s->ctx, cudaMemcpyAsync(diag, s->diag, sizeof(double) * s->nt,
@@ -1133,11 +1140,11 @@ int adjoint_impl(cps_sys s, const double* x, const double* g, double* lambda, do
                  double* dtheta, double rtol, int64_t max_iter, cps_stats* stats,
                  cudaStream_t stream) {
     if (!x || !g || !lambda) {
-        s->ctx->last_error = "adjoint: null pointer";
+        cps::set_error(s->ctx, "adjoint: null pointer");
         return CPS_ERR_ARG;
     }
     if (dtheta && !s->iso_cell) {
-        s->ctx->last_error = "adjoint: dtheta needs a CP2 system with an isotropic per-cell field";
+        cps::set_error(s->ctx, "adjoint: dtheta needs a CP2 system with an isotropic per-cell field");
         return CPS_ERR_ARG;
     }
     int rc = solve_fp64(s, g, lambda, rtol, max_iter, stats, stream);

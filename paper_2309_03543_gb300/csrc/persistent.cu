@@ -539,7 +539,7 @@ int persistent_solve(cps_sys s, int reduced, const double* a, const int32_t* col
         cudaError_t e = cudaMalloc((void**)&s->gsync, sizeof(GridSync));
         if (e != cudaSuccess) {
             cudaGetLastError();
-            s->ctx->last_error = "persistent: cudaMalloc failed";
+            cps::set_error(s->ctx, "persistent: cudaMalloc failed");
             return CPS_ERR_NOMEM;
         }
     }
@@ -548,7 +548,7 @@ int persistent_solve(cps_sys s, int reduced, const double* a, const int32_t* col
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPBlock, 0) != cudaSuccess ||
         per_sm < 1) {
         cudaGetLastError();
-        s->ctx->last_error = "persistent: kernel does not fit an SM";
+        cps::set_error(s->ctx, "persistent: kernel does not fit an SM");
         return CPS_ERR_ARG;
     }
     int G = s->ctx->num_sms * (per_sm < 4 ? per_sm : 4);
@@ -582,7 +582,7 @@ int persistent_solve(cps_sys s, int reduced, const double* a, const int32_t* col
     cudaError_t e = cudaLaunchKernelEx(&cfg, kern, P);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        s->ctx->last_error = std::string("persistent launch: ") + cudaGetErrorString(e);
+        cps::set_error(s->ctx, std::string("persistent launch: ") + cudaGetErrorString(e));
         return CPS_ERR_CUDA;
     }
     return CPS_OK;

@@ -341,7 +341,7 @@ static int alloc_ic0(cps_sys s) {
     for (auto& r : req) {
         cudaError_t e = cudaMalloc(r.p, r.bytes);
         if (e != cudaSuccess) {
-            s->ctx->last_error = std::string("set_precond: cudaMalloc: ") + cudaGetErrorString(e);
+            cps::set_error(s->ctx, std::string("set_precond: cudaMalloc: ") + cudaGetErrorString(e));
             return CPS_ERR_NOMEM;
         }
     }
@@ -390,7 +390,7 @@ static int colour_cells(cps_sys s, int32_t* colour, cudaStream_t stream, int* nc
     }
     cudaFreeAsync(w, stream);
     cudaFreeAsync(flags, stream);
-    if (rc != CPS_OK) s->ctx->last_error = "set_precond: colouring failed";
+    if (rc != CPS_OK) cps::set_error(s->ctx, "set_precond: colouring failed");
     return rc;
 }
 
@@ -400,12 +400,12 @@ int precond_impl(cps_sys s, int precond, cudaStream_t stream) {
         return CPS_OK;
     }
     if (precond != CPS_PC_IC0 && precond != CPS_PC_REDUCED) {
-        s->ctx->last_error = "set_precond: unknown preconditioner";
+        cps::set_error(s->ctx, "set_precond: unknown preconditioner");
         return CPS_ERR_ARG;
     }
     if (s->ncolours > 0) {   // ordered and factored already (the matrix is fixed)
         if (precond == CPS_PC_REDUCED && s->ncolours != 2) {
-            s->ctx->last_error = "set_precond: the cell graph is not two-colourable";
+            cps::set_error(s->ctx, "set_precond: the cell graph is not two-colourable");
             return CPS_ERR_ARG;
         }
         s->precond = precond;
@@ -425,7 +425,7 @@ int precond_impl(cps_sys s, int precond, cudaStream_t stream) {
     int ncol = 0;
     rc = colour_cells(s, colour, stream, &ncol);
     if (rc == CPS_OK && (ncol < 1 || ncol > kMaxColours)) {
-        s->ctx->last_error = "set_precond: too many colours";
+        cps::set_error(s->ctx, "set_precond: too many colours");
         rc = CPS_ERR_ARG;
     }
     if (rc == CPS_OK) {
@@ -463,7 +463,7 @@ int precond_impl(cps_sys s, int precond, cudaStream_t stream) {
                 if (cudaStreamSynchronize(stream) != cudaSuccess || cudaGetLastError() != cudaSuccess)
                     rc = CPS_ERR_CUDA;
                 else if (herr) {
-                    s->ctx->last_error = "set_precond: IC(0) pivot <= 0";
+                    cps::set_error(s->ctx, "set_precond: IC(0) pivot <= 0");
                     rc = herr;
                 }
             }
@@ -475,13 +475,13 @@ int precond_impl(cps_sys s, int precond, cudaStream_t stream) {
     cudaFreeAsync(err, stream);
     cudaStreamSynchronize(stream);
     if (rc != CPS_OK) {
-        if (s->ctx->last_error.empty()) s->ctx->last_error = "set_precond: IC(0) set-up failed";
+        if (s->ctx->last_error.empty()) cps::set_error(s->ctx, "set_precond: IC(0) set-up failed");
         return rc;
     }
     s->ncolours = ncol;
     if (precond == CPS_PC_REDUCED && ncol != 2) {
         s->precond = CPS_PC_JACOBI;
-        s->ctx->last_error = "set_precond: the cell graph is not two-colourable";
+        cps::set_error(s->ctx, "set_precond: the cell graph is not two-colourable");
         return CPS_ERR_ARG;
     }
     s->precond = precond;
