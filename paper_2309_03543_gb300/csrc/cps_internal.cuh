@@ -148,6 +148,7 @@ struct cps_ctx_s {
     size_t l2_persist_set = 0;   // persisting L2 limit this process has set
     std::string last_error;
     std::mutex mu;               // guards last_error and tune_cache (solves may run on threads)
+    std::mutex l2_mu;            // guards the persisting-L2 set-aside
     std::unordered_set<cps_sys_s*> systems;   // live systems, freed with the context
     // Tuned launch choices by mesh size (cells, vertices): a system assembled
     // later on a mesh of the same size starts from them instead of re-timing.

@@ -399,12 +399,21 @@ void drop_graphs(cps_sys s, int prec) {
 // The persisting set-aside is a context-wide reservation that shrinks the L2
 // every other kernel sees, so it is held only for the duration of a solve
 // that uses the window and given back (set to 0) right after.
+// Solves running at the same time on one context (host threads) share the
+// set-aside: one may give it back while another's window is in use, which
+// costs speed, not correctness (persistence is a cache hint).
 static int l2_set_aside(cps_sys s, int mode, cudaStream_t st) {
     const size_t want = mode ? l2_window_bytes(s, mode) : 0;
+    std::unique_lock<std::mutex> lock(s->ctx->l2_mu);
     if (s->ctx->l2_persist_set == want) return CPS_OK;
-    CPS_CUDA_TRY(s->ctx, cudaStreamSynchronize(st));
-    if (s->ctx->l2_persist_set) CPS_CUDA_TRY(s->ctx, cudaCtxResetPersistingL2Cache());
-    CPS_CUDA_TRY(s->ctx, cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want));
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && s->ctx->l2_persist_set) e = cudaCtxResetPersistingL2Cache();
+    if (e == cudaSuccess) e = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want);
+    if (e != cudaSuccess) {
+        lock.unlock();
+        cps::set_error(s->ctx, std::string("persisting L2 set-aside: ") + cudaGetErrorString(e));
+        return CPS_ERR_CUDA;
+    }
     s->ctx->l2_persist_set = want;
     return CPS_OK;
 }
@@ -1103,7 +1112,7 @@ int solve_impl(cps_sys s, const double* b, double* x, double rtol, int64_t max_i
     }
     if (precision == CPS_FP64) {
         const int rc = solve_fp64(s, b, x, rtol, max_iter, stats, stream);
-        if (s->ctx->l2_persist_set != 0) l2_set_aside(s, 0, stream);   // error paths
+        l2_set_aside(s, 0, stream);   // error paths: give back a set-aside still held
         return rc;
     }
     if (precision == CPS_MIXED) return solve_mixed(s, b, x, rtol, max_iter, stats, stream);
