@@ -1108,7 +1108,9 @@ int solve_impl(cps_sys s, const double* b, double* x, double rtol, int64_t max_i
             cps::set_error(s->ctx, "solve: the reduced-system solve is FP64 only");
             return CPS_ERR_ARG;
         }
-        return solve_reduced(s, b, x, rtol, max_iter, stats, stream);
+        const int rc = solve_reduced(s, b, x, rtol, max_iter, stats, stream);
+        l2_set_aside(s, 0, stream);   // error paths: give back a set-aside still held
+        return rc;
     }
     if (precision == CPS_FP64) {
         const int rc = solve_fp64(s, b, x, rtol, max_iter, stats, stream);
