@@ -38,7 +38,8 @@ struct CgState {
     int done;          // 1: stop (converged, breakdown or max_iter)
     int status;        // CPS_OK or an error code set on the device
     unsigned int arrive[4];   // arrival counters of the grid reductions
-    int pad[4];
+    double rho_rep;    // mixed precision: r.r of the last residual replacement
+    int pad[2];
 };
 
 // Launch configuration of one iteration kernel: rows per thread per trip of

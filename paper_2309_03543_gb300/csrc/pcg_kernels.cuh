@@ -197,6 +197,11 @@ __global__ void __launch_bounds__(BS) k_cg_b(V* __restrict__ r, const V* __restr
         if (JACOBI) {
             const double rho_new = t[0];
             if (!(rho_new > 0.0)) done = 1;      // exact solution reached
+            // binary32: a recursive residual 1e-13 below the replaced one is
+            // at the format's rounding floor (a system of a few cells gets
+            // there in a few iterations); replace it before rounding noise
+            // builds up in the update
+            if (sizeof(V) == 4 && rho_new <= 1e-13 * st->rho_rep) done = 1;
             st->beta = rho_new / st->rho;
             st->rho = rho_new;
         }
@@ -371,6 +376,7 @@ __global__ void __launch_bounds__(kBlock) k_res64(const double* __restrict__ b,
             st->rho = st->beta > 0.0 ? st->rho / st->beta : INFINITY;
         }
         st->max_iter = st->iter + budget;
+        st->rho_rep = t[0];
         st->done = (t[1] == 0.0 || t[2] <= outer2 || budget <= 0 || !(t[0] > 0.0)) ? 2 : 0;
     }
 }
