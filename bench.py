@@ -81,8 +81,8 @@ def parse():
     ap.add_argument("--pin", default="",
                     help="profiling run only: pin the FP64 Jacobi configuration instead of "
                          "tuning it (a profiler's replay skews the tuner), as "
-                         "'U0,U1,U2/G0,G1,G2/B0,B1,B2/PATH' with PATH stream, stream_l2 or "
-                         "persistent")
+                         "'U0,U1,U2/G0,G1,G2/B0,B1,B2/PATH' with PATH stream, stream_l2, "
+                         "persistent or persistent_l2 (for the reduced system too)")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiling run: assemble, then FP64 and mixed solves bounded to this "
                          "many iterations (Jacobi and IC(0)); no timing output")
@@ -447,16 +447,18 @@ def main():
 
     if args.profile_iters:
         # every variant once (autotuning, path probes), then the FP64 Jacobi
-        # solve again inside the NVTX range "cps_profile" and the mixed Jacobi
-        # solve inside "cps_profile_mixed" (the launches a profiler should
-        # select: ncu --nvtx --nvtx-include "cps_profile/")
+        # solve again inside the NVTX range "cps_profile", the mixed Jacobi
+        # solve inside "cps_profile_mixed" and the reduced-system solve inside
+        # "cps_profile_reduced" (the launches a profiler should select: ncu
+        # --nvtx --nvtx-include "cps_profile/")
         s = ctx.assemble(d["xy"], d["tri"], d["dir"], d["eps"], d["kinv"], cps.PER_VERTEX,
                          cps.KIND_CP2, p.nu, p.dt)
         if args.pin:
             u, g, b, path = args.pin.split("/")
             s.set_kernel_shapes(cps.FP64, *[[int(v) for v in f.split(",")] for f in (u, g, b)])
             s.set_solver_path({"stream": cps.PATH_STREAM, "stream_l2": cps.PATH_STREAM_L2,
-                               "persistent": cps.PATH_PERSISTENT}[path])
+                               "persistent": cps.PATH_PERSISTENT,
+                               "persistent_l2": cps.PATH_PERSISTENT_L2}[path])
         for pc in (cps.PC_JACOBI, cps.PC_IC0):
             s.set_precond(pc)
             for prec in (cps.FP64, cps.MIXED):
@@ -476,6 +478,21 @@ def main():
                 check=False)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
+        # the reduced system: first solve tunes its path, the second is marked
+        try:
+            s.set_precond(cps.PC_REDUCED)
+        except cps.CpsError:
+            pass
+        else:
+            for mark in (False, True):
+                x.zero_()
+                torch.cuda.synchronize()
+                if mark:
+                    torch.cuda.nvtx.range_push("cps_profile_reduced")
+                s.solve(d["b"], x=x, rtol=args.rtol, max_iter=args.profile_iters, check=False)
+                torch.cuda.synchronize()
+                if mark:
+                    torch.cuda.nvtx.range_pop()
         tuned = s.tuning(cps.FP64)
         s.free()
         print(json.dumps({"profile_run": True, "n": args.n, "cells": nt,

@@ -223,13 +223,16 @@ int cps_adjoint(cps_sys sys, const double* x, const double* g, double* lambda, d
  *     CPS_ERR_TIMEOUT);
  *   CPS_PATH_STREAM_L2: streaming kernels with the vectors r, p, q held in
  *     persisting L2 during the solve; CPS_ERR_ARG if the GPU's persisting
- *     set-aside cannot hold them.
+ *     set-aside cannot hold them;
+ *   CPS_PATH_PERSISTENT_L2: the persistent launch with r, p, q in persisting
+ *     L2 (CPS_ERR_ARG as above).
  * IC(0) and mixed precision always stream. */
 #define CPS_PATH_AUTO 0
 #define CPS_PATH_STREAM 1
 #define CPS_PATH_CLUSTER 2
 #define CPS_PATH_PERSISTENT 3
 #define CPS_PATH_STREAM_L2 4
+#define CPS_PATH_PERSISTENT_L2 5
 int cps_set_solver_path(cps_sys sys, int path);
 
 /* Pin the launch shapes of the iteration kernels of one precision instead of

@@ -169,6 +169,19 @@ int cps_set_solver_path(cps_sys sys, int path) {
         t.red_win = 0;
         t.pgrid = 0;
         t.red_pgrid = 0;
+    } else if (path == CPS_PATH_PERSISTENT_L2) {
+        if (!cps::l2_vectors_fit(sys)) {
+            cps::set_error(sys->ctx, "set_solver_path: the persisting L2 set-aside cannot hold r, p, q");
+            return CPS_ERR_ARG;
+        }
+        t.path_done = true;
+        t.path = 2;
+        t.l2win = 2;
+        t.red_done = true;
+        t.red_path = 1;
+        t.red_win = 2;
+        t.pgrid = 0;
+        t.red_pgrid = 0;
     } else if (path == CPS_PATH_STREAM_L2) {
         if (!cps::l2_vectors_fit(sys)) {
             cps::set_error(sys->ctx, "set_solver_path: the persisting L2 set-aside cannot hold r, p, q");

@@ -165,23 +165,57 @@ __device__ bool grid_barrier(GridSync* gs, Epoch& ep) {
     return s_ok != 0;
 }
 
-// This block has finished the direction update of iteration `it` (1-based).
-__device__ __forceinline__ void halo_post(GridSync* gs, unsigned long long it) {
+// This block has finished phase `slot` (0: direction update, 1: the reduced
+// system's red phase) `it` times.
+__device__ __forceinline__ void halo_post(GridSync* gs, unsigned long long it, int slot = 0) {
     __syncthreads();
-    if (threadIdx.x == 0) st_release(&gs->flag[blockIdx.x * kFlagStride], it);
+    if (threadIdx.x == 0) st_release(&gs->flag[blockIdx.x * kFlagStride + slot], it);
 }
 
-// Wait until the blocks [dlo, dhi] (other than this one) have posted `it`.
-__device__ bool halo_wait(GridSync* gs, int dlo, int dhi, unsigned long long it) {
+// Wait until the blocks [dlo, dhi] (other than this one) have posted `it`
+// in `slot`.
+__device__ bool halo_wait(GridSync* gs, int dlo, int dhi, unsigned long long it, int slot = 0) {
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
         int ok = 1;
         for (int d = dlo; d <= dhi && ok; ++d)
-            if (d != (int)blockIdx.x && !wait_geq(&gs->flag[d * kFlagStride], it, gs)) ok = 0;
+            if (d != (int)blockIdx.x && !wait_geq(&gs->flag[d * kFlagStride + slot], it, gs))
+                ok = 0;
         s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+// Range [*lo, *hi] of blocks owning the columns that rows [r0, r1) read
+// (the self column of an empty slot excluded), where block k owns rows
+// base + [k R, (k+1) R) of the columns' range; this block if there is none.
+__device__ void column_blocks(const int32_t* __restrict__ C, int64_t n, int64_t r0, int64_t r1,
+                              int64_t base, int64_t R, int* lo, int* hi) {
+    __shared__ int s_lo, s_hi;
+    if (threadIdx.x == 0) {
+        s_lo = INT32_MAX;
+        s_hi = -1;
+    }
+    __syncthreads();
+    int cmin = INT32_MAX, cmax = -1;
+    for (int64_t e = r0 + threadIdx.x; e < r1; e += kPBlock)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int c = C[j * n + e];
+            if (c == (int)e) continue;
+            const int k = (int)(((int64_t)c - base) / R);
+            cmin = k < cmin ? k : cmin;
+            cmax = k > cmax ? k : cmax;
+        }
+    if (cmax >= 0) {
+        atomicMin(&s_lo, cmin);
+        atomicMax(&s_hi, cmax);
+    }
+    __syncthreads();
+    *lo = s_hi >= 0 ? s_lo : (int)blockIdx.x;
+    *hi = s_hi >= 0 ? s_hi : (int)blockIdx.x;
+    __syncthreads();
 }
 
 struct PersistArgs {
@@ -415,7 +449,31 @@ __global__ void __launch_bounds__(kPBlock, 2) k_persistent_reduced(PersistArgs P
     bool ok = true;
     Epoch ep;
     ep.extra = P.stall ? 1ull : 0ull;
-    for (;;) {
+    // The red phase reads p at black rows, the black phase t at red rows:
+    // on banded numberings both lie in a few neighbouring blocks, and the
+    // two grid barriers become waits on those blocks' flags (slot 0: p
+    // updated, slot 1: t computed), as in k_persistent_cg.
+    int dplo, dphi, dtlo, dthi;
+    column_blocks(C, n, rlo, rhi, nR, Rb, &dplo, &dphi);
+    column_blocks(C, n, blo, bhi, 0, Rr, &dtlo, &dthi);
+    bool halo;
+    {
+        const bool wide = dphi - dplo + 1 > kMaxDeps || dthi - dtlo + 1 > kMaxDeps;
+        double w[1] = {wide ? 1.0 : 0.0};
+        double none[1];
+        int any = 0;
+        ok = grid_allreduce<1, 1>(w, none, any, P.partials, gs, ep,
+                                  [](const double (&tt)[1], double* o, int& f) {
+                                      o[0] = 0.0;
+                                      f = tt[0] > 0.0 ? 1 : 0;
+                                  });
+        halo = any == 0;
+    }
+    while (ok) {
+        if (halo && it > 0) {
+            ok = halo_wait(gs, dplo, dphi, (unsigned long long)it, 0);
+            if (!ok) break;
+        }
         {
             double a0[kU], a1[kU], a2[kU];
             int32_t c0[kU], c1[kU], c2[kU];
@@ -430,7 +488,12 @@ __global__ void __launch_bounds__(kPBlock, 2) k_persistent_reduced(PersistArgs P
                     t[e] = acc;
                 })
         }
-        ok = grid_barrier(gs, ep);
+        if (halo) {
+            halo_post(gs, (unsigned long long)(it + 1), 1);
+            ok = halo_wait(gs, dtlo, dthi, (unsigned long long)(it + 1), 1);
+        } else {
+            ok = grid_barrier(gs, ep);
+        }
         if (!ok) break;
         double g[1] = {0.0};
         {
@@ -499,8 +562,12 @@ __global__ void __launch_bounds__(kPBlock, 2) k_persistent_reduced(PersistArgs P
             })
         }
         if (stop) break;
-        ok = grid_barrier(gs, ep);
-        if (!ok) break;
+        if (halo) {
+            halo_post(gs, (unsigned long long)it, 0);
+        } else {
+            ok = grid_barrier(gs, ep);
+            if (!ok) break;
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->iter = it;

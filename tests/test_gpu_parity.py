@@ -481,6 +481,16 @@ def test_pinned_shapes_and_stream_l2_path(ctx):
     b = synth.rhs(p.mesh, 5)
     bt = torch.as_tensor(b, device="cuda")
     s.set_kernel_shapes(cps.FP64, [4, 1, 2], [608, 152, 152], [256, 1024, 1024])
+    try:                                        # persistent with r, p, q in L2, pinned
+        s.set_solver_path(cps.PATH_PERSISTENT_L2)
+        pinned = True
+    except cps.CpsError:
+        pinned = False                          # no persisting set-aside on this GPU
+    if pinned:
+        xp, _ = s.solve(bt, rtol=1e-10)
+        rp_ = b - A.matvec(xp.cpu().numpy())
+        assert np.linalg.norm(rp_) / np.linalg.norm(b) <= 1e-10 * 1.01
+        assert s.tuning()["persistent"] and s.tuning()["l2_window"] == "vectors"
     try:
         s.set_solver_path(cps.PATH_STREAM_L2)
         window = True
