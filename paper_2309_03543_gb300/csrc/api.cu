@@ -4,6 +4,8 @@
 
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace {
 
 int set_device(cps_ctx ctx) {
@@ -17,6 +19,15 @@ int set_device(cps_ctx ctx) {
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+}  // namespace
+
+// NVTX range over one library call (the calls show up by name in Nsight
+// Systems and select launches in Nsight Compute; free without a tool).
+namespace {
+struct CallRange {
+    explicit CallRange(const char* name) { nvtxRangePushA(name); }
+    ~CallRange() { nvtxRangePop(); }
+};
 }  // namespace
 
 extern "C" {
@@ -64,6 +75,7 @@ const char* cps_last_error(cps_ctx ctx) {
 int cps_assemble(cps_ctx ctx, const double* xy, int64_t nv, const int32_t* tri, int64_t nt,
                  const int32_t* dirichlet, int64_t nb, const double* eps, const double* kinv,
                  int field_loc, int kind, double nu, double dt, cps_sys* out, void* stream) {
+    CallRange range_("cps_assemble");
     if (!ctx || !out) return CPS_ERR_ARG;
     *out = nullptr;
     int rc = set_device(ctx);
@@ -82,6 +94,7 @@ int cps_assemble(cps_ctx ctx, const double* xy, int64_t nv, const int32_t* tri, 
 }
 
 int cps_set_precond(cps_sys sys, int precond, void* stream) {
+    CallRange range_("cps_set_precond");
     if (!sys) return CPS_ERR_ARG;
     int rc = set_device(sys->ctx);
     if (rc) return rc;
@@ -109,6 +122,7 @@ int cps_sys_info(cps_sys sys, int64_t* nt, int64_t* n_interior_sides, double* di
 }
 
 int cps_export_matrix(cps_sys sys, double* diag, int32_t* col, double* val, void* stream) {
+    CallRange range_("cps_export_matrix");
     if (!sys) return CPS_ERR_ARG;
     int rc = set_device(sys->ctx);
     if (rc) return rc;
@@ -117,6 +131,7 @@ int cps_export_matrix(cps_sys sys, double* diag, int32_t* col, double* val, void
 
 int cps_solve(cps_sys sys, const double* b, double* x, double rtol, int64_t max_iter,
               int precision, cps_stats* stats, void* stream) {
+    CallRange range_("cps_solve");
     if (!sys) return CPS_ERR_ARG;
     int rc = set_device(sys->ctx);
     if (rc) return rc;
@@ -126,6 +141,7 @@ int cps_solve(cps_sys sys, const double* b, double* x, double rtol, int64_t max_
 int cps_solve_batch(const cps_sys* systems, int nsys, const double* const* b, double* const* x,
                     double rtol, int64_t max_iter, int precision, cps_stats* stats,
                     void* stream) {
+    CallRange range_("cps_solve_batch");
     if (nsys < 0 || (nsys > 0 && (!systems || !b || !x))) return CPS_ERR_ARG;
     if (nsys == 0) return CPS_OK;
     for (int i = 0; i < nsys; ++i)
@@ -138,6 +154,7 @@ int cps_solve_batch(const cps_sys* systems, int nsys, const double* const* b, do
 
 int cps_adjoint(cps_sys sys, const double* x, const double* g, double* lambda, double* dT,
                 double* dtheta, double rtol, int64_t max_iter, cps_stats* stats, void* stream) {
+    CallRange range_("cps_adjoint");
     if (!sys) return CPS_ERR_ARG;
     int rc = set_device(sys->ctx);
     if (rc) return rc;
@@ -265,6 +282,7 @@ int cps_get_tuning(cps_sys sys, int precision, int32_t* unroll, int32_t* grid, i
 }
 
 int cps_matvec(cps_sys sys, const double* x, double* y, void* stream) {
+    CallRange range_("cps_matvec");
     if (!sys) return CPS_ERR_ARG;
     int rc = set_device(sys->ctx);
     if (rc) return rc;

@@ -21,6 +21,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 
 namespace cg = cooperative_groups;
@@ -275,13 +276,13 @@ int64_t cluster_max_rows(cps_ctx ctx) {
 // scaled iterate in y and the final scalars in s->st (done = 2).
 int cluster_solve(cps_sys s, const double* b, const double* x, double* y, double rtol,
                   long long max_iter, cudaStream_t stream) {
-    static bool configured[64] = {false};
+    static std::atomic<bool> configured[64];   // zero-initialised (static storage)
     const int64_t n = s->nt;
     int csize = 16;
     cudaError_t e = cudaSuccess;
     const int dev = s->ctx->device;
     const size_t lim = cluster_dyn_smem_limit(dev);
-    if (!configured[dev & 63]) {
+    if (!configured[dev & 63].load()) {
         e = cudaFuncSetAttribute(k_cluster_cg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_cluster_cg, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -290,7 +291,7 @@ int cluster_solve(cps_sys s, const double* b, const double* x, double* y, double
             cps::set_error(s->ctx, std::string("cluster path: ") + cudaGetErrorString(e));
             return CPS_ERR_ARG;
         }
-        configured[dev & 63] = true;
+        configured[dev & 63].store(true);
     }
     ClusterArgs A;
     A.a = s->a;
