@@ -5,18 +5,21 @@
 // off-diagonal slots, slot-major (entry j*n + e), and a unit diagonal.  Every
 // reduction is deterministic (fixed grid, fixed summation order).
 //
-// One iteration k of (P)CG is two fused streaming kernels:
-//   k_cg_a: y += alpha_{k-1} p_{k-1}           (x update, one iteration late)
-//           p_k = z_k + beta_{k-1} p_{k-1}      (own row and, recomputed
-//                                                bit-identically, the three
-//                                                neighbours' rows)
-//           q = Ahat p_k, gamma = p_k . q;      last block: alpha_k = rho/gamma
-//   k_cg_b: r -= alpha_k q; Jacobi: rho' = r.r, beta_k = rho'/rho; every
-//           few iterations also ||S r||^2 and the stop test.
-// The search direction alternates between two buffers chosen by the parity
-// of the device iteration counter, so the same captured graph serves any
-// starting iteration.  With IC(0) the preconditioner kernels (ic0 sweeps)
-// run between k_cg_b and the next k_cg_a and produce z, rho and beta.
+// FP64 iteration (GB300 issues FP64 at 1/64 of the FP32 rate, so nothing is
+// recomputed): three streaming kernels,
+//   k_spmv_dot: q = Ahat p, gamma = p.q;           last block: alpha = rho/gamma
+//   k_cg_b:     r -= alpha q; Jacobi: rho' = r.r;  last block: beta, stop test
+//   k_cg_c:     y += alpha p; p = z + beta p
+// (with IC(0) the preconditioner sweeps run between k_cg_b and k_cg_c).
+// Binary32 iteration of the mixed solve: two fused kernels,
+//   k_cg_a: y += alpha_{k-1} p_{k-1} (x update one iteration late);
+//           p_k = z_k + beta_{k-1} p_{k-1} for the own row and, recomputed
+//           bit-identically, the three neighbours' rows; q = Ahat p_k,
+//           gamma = p_k . q
+//   k_cg_b: as above,
+// with the search direction alternating between two buffers by the parity of
+// the device iteration counter, so the same captured graph serves any
+// starting iteration.
 #pragma once
 
 #include "cps_internal.cuh"
