@@ -37,7 +37,7 @@
 namespace cps {
 namespace {
 
-constexpr int kPBlock = 512;
+constexpr int kPBlock = 1024;
 constexpr long long kSpinCap = 1LL << 26;           // polls; each one an L2 round trip
 constexpr unsigned long long kWaitNs = 1000000000ull;
 constexpr int kFlagStride = 16;                      // one 128-byte line per block flag
@@ -272,7 +272,7 @@ constexpr int kUV = 4;   // rows per trip in the vector phases (2 or 3 loads per
 // FP64 Jacobi CG on the scaled matrix from the state k_init64 left:
 //   [wait for the halo] q = Ahat p, gamma | alpha; r -= alpha q; rho',
 //   ||S r||^2 | beta, stop; y += alpha p; p = r + beta p; post
-__global__ void __launch_bounds__(kPBlock, 2) k_persistent_cg(PersistArgs P) {
+__global__ void __launch_bounds__(kPBlock, 1) k_persistent_cg(PersistArgs P) {
     CgState* st = P.st;
     if (st->done) return;                      // uniform: set before the launch
     const int64_t n = P.n;
@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(kPBlock, 2) k_persistent_cg(PersistArgs P) {
 // black rows [nR, n) from the state k_black_init left.  Block b owns red rows
 // [b Rr, (b+1) Rr) and black rows nR + [b Rb, (b+1) Rb).
 //   t_R = E p_B | q_B = p_B - E^T t_R, gamma | r -= alpha q, rho' | y, p |
-__global__ void __launch_bounds__(kPBlock, 2) k_persistent_reduced(PersistArgs P) {
+__global__ void __launch_bounds__(kPBlock, 1) k_persistent_reduced(PersistArgs P) {
     CgState* st = P.st;
     if (st->done) return;
     const int64_t n = P.n, nR = P.nR, nB = n - nR;
