@@ -205,6 +205,35 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def library_spmv(s, x, stream, reps: int = 20) -> dict:
+    """Library comparison point: y = A x in FP64 through cps_matvec (the
+    library's own FP64 SpMV) and through torch's CSR product (cuSPARSE) on
+    the same matrix, exported from the system.  Mean time over `reps`."""
+    import torch
+    diag, col, val = s.export_matrix()
+    nt = diag.shape[0]
+    rows = torch.arange(nt, device=diag.device, dtype=torch.int64)
+    live = col.to(torch.int64) != rows.unsqueeze(0)
+    r_all = torch.cat([rows, rows.unsqueeze(0).expand(3, nt)[live]])
+    c_all = torch.cat([rows, col.to(torch.int64)[live]])
+    v_all = torch.cat([diag, val[live]])
+    order = torch.argsort(r_all * nt + c_all)
+    crow = torch.zeros(nt + 1, dtype=torch.int64, device=diag.device)
+    crow[1:] = torch.cumsum(torch.bincount(r_all, minlength=nt), 0)
+    A = torch.sparse_csr_tensor(crow, c_all[order], v_all[order], size=(nt, nt))
+    xv = torch.randn(nt, dtype=torch.float64, device=diag.device)
+    out = {}
+    for name, fn in (("cps_matvec", lambda: s.matvec(xv)),
+                     ("torch_csr_cusparse", lambda: A @ xv)):
+        fn()
+        t, _ = timed(lambda: [fn() for _ in range(reps)], stream)
+        out[name + "_us"] = 1e6 * t / reps
+    y1, y2 = s.matvec(xv), A @ xv
+    out["max_rel_diff"] = float((y1 - y2).abs().max() / y2.abs().max())
+    out["nnz"] = int(v_all.numel())
+    return out
+
+
 def timed(fn, stream):
     import torch
     torch.cuda.synchronize()
@@ -608,6 +637,7 @@ def main():
             variants[f"{pc_name}_fp64_{path_name}_path"] = {
                 "time_to_rtol_s": t, "iters": st.iters, "us_per_iter": 1e6 * t / max(st.iters, 1)}
         s.set_solver_path(cps.PATH_AUTO)
+    library = library_spmv(s, x, stream)
     s.free()
     jf = variants["jacobi_fp64"]
     achieved = BYTES_PER_CELL_ITER_FP64 * nt * jf["iters"] / jf["time_to_rtol_s"] / 1e9
@@ -644,6 +674,7 @@ def main():
         "roofline": roof,
         "solve_variants": variants,
         "autotuned": tuning,
+        "library_spmv": library,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d_bytes,
                 "d2h_bytes_per_step": d2h_bytes},
         "gpu_launches": launches,
