@@ -19,6 +19,11 @@ Each function names the passage of the paper it follows:
 * ``side_gradient`` / ``theta_gradient`` -- adjoint of one solve with respect
   to the side coefficients and the log-permeability (derived from
   Eq. CS2_sys_coeff).
+* ``cp2_mean_flux`` / ``cp2_tangential_flux`` / ``cp2_update`` /
+  ``cp2_step`` -- the CP2 step around the two solves: the area-weighted mean
+  side flux (Eq. flux_k_+_2/3), the co-normal tangential flux of Xi grad eta
+  (Eq. Cs2_6, Eq. eta_flux, App. C), the two systems of Eq. Cs2_7, the RT0
+  cell velocity (Eq. RT0) and the eps grad Psi update (Eq. grad_PSI).
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py``.
 """
@@ -93,6 +98,10 @@ def _load():
             lib.or_side_gradient.argtypes = [I64, P, P, P, P, P]
             lib.or_side_gradient.restype = None
             lib.or_theta_gradient.argtypes = [I64, P, I64, P, P, P, P, P, D, D, P, P]
+            lib.or_cp2_mean_flux.argtypes = [I64, P, I64, P, P, P, P, P]
+            lib.or_cp2_tangential_flux.argtypes = [I64, P, I64, P, P, P, P, P, I, D, D, P, P]
+            lib.or_cp2_update.argtypes = [I64, P, I64, P, P, P, P, P, I, D, D, P, P, P, P,
+                                          P, P, P, P, P]
             _lib = lib
     return _lib
 
@@ -317,3 +326,106 @@ def solve_problem(problem, b, rtol: float = 1e-13, precond: int = PC_JACOBI, x0=
     if st.status not in (OK, ERR_NOT_CONVERGED):
         raise OracleError(st.status, "pcg")
     return x, st, A
+
+
+# ------------------------------------------------------------------ CP2 step
+
+def _mesh_args(xy, tri, nbr, is_dirichlet):
+    return _f64(xy), _i32(tri), _i32(nbr), _i32(is_dirichlet)
+
+
+def cp2_mean_flux(xy, tri, nbr, is_dirichlet, u) -> np.ndarray:
+    """Fbar [nt, 3]: outward area-weighted mean flux per local side
+    (Eq. flux_k_+_2/3).  u is [2, nt] (x row, y row)."""
+    xy, tri, nbr, isd = _mesh_args(xy, tri, nbr, is_dirichlet)
+    u = _f64(u).reshape(2, -1)
+    nt = tri.shape[0]
+    out = np.empty((nt, 3))
+    _check(_load().or_cp2_mean_flux(xy.shape[0], _p(xy), nt, _p(tri), _p(nbr), _p(isd),
+                                    _p(u), _p(out)), "cp2_mean_flux")
+    return out
+
+
+def cp2_tangential_flux(xy, tri, nbr, is_dirichlet, eps, kinv, field_loc, nu, dt,
+                        eta) -> np.ndarray:
+    """tau [nt, 3]: tangential (co-normal) part of the outward flux of
+    Xi grad(eta) per local side (Eq. Cs2_6, Eq. eta_flux, App. C)."""
+    xy, tri, nbr, isd = _mesh_args(xy, tri, nbr, is_dirichlet)
+    eps = _f64(eps)
+    kinv = _f64(kinv).reshape(-1, 3)
+    eta = _f64(eta)
+    nt = tri.shape[0]
+    out = np.empty((nt, 3))
+    _check(_load().or_cp2_tangential_flux(xy.shape[0], _p(xy), nt, _p(tri), _p(nbr), _p(isd),
+                                          _p(eps), _p(kinv), field_loc, nu, dt, _p(eta),
+                                          _p(out)), "cp2_tangential_flux")
+    return out
+
+
+def cp2_update(xy, tri, nbr, is_dirichlet, eps, kinv, field_loc, nu, dt, fbar, T, tau, eta,
+               u23, g_k):
+    """(Q [nt,3], u_next [2,nt], g_next [2,nt]): outward side fluxes of the
+    new velocity, its RT0 cell value at the centroid (Eq. RT0) and the
+    eps grad Psi update (Eq. grad_PSI)."""
+    xy, tri, nbr, isd = _mesh_args(xy, tri, nbr, is_dirichlet)
+    eps = _f64(eps)
+    kinv = _f64(kinv).reshape(-1, 3)
+    fbar, T, tau, eta = _f64(fbar), _f64(T), _f64(tau), _f64(eta)
+    u23 = _f64(u23).reshape(2, -1)
+    g_k = _f64(g_k).reshape(2, -1)
+    nt = tri.shape[0]
+    Q = np.empty((nt, 3))
+    u_next = np.empty((2, nt))
+    g_next = np.empty((2, nt))
+    _check(_load().or_cp2_update(xy.shape[0], _p(xy), nt, _p(tri), _p(nbr), _p(isd), _p(eps),
+                                 _p(kinv), field_loc, nu, dt, _p(fbar), _p(T), _p(tau),
+                                 _p(eta), _p(u23), _p(g_k), _p(Q), _p(u_next), _p(g_next)),
+           "cp2_update")
+    return Q, u_next, g_next
+
+
+@dataclass
+class CP2Step:
+    fbar: np.ndarray     # [nt, 3]
+    eta_tilde: np.ndarray
+    tau: np.ndarray      # [nt, 3], from eta_tilde
+    eta: np.ndarray
+    Q: np.ndarray        # [nt, 3]
+    u_next: np.ndarray   # [2, nt]
+    g_next: np.ndarray   # [2, nt]
+    A: CSR
+
+
+def cp2_step(problem, u23, g_k, rtol: float = 1e-13, dense: bool | None = None) -> CP2Step:
+    """One CP2 step (Sec. 3.2.3): Fbar -> solve A eta~ = sum Fbar
+    (Eq. Cs2_7_1) -> tau(eta~) -> solve A eta = sum Fbar + sum tau
+    (Eq. Cs2_7_2, warm start eta~) -> fluxes, RT0 velocity, eps grad Psi.
+    Solves by dense Cholesky for nt <= 2000 (or ``dense=True``), else PCG
+    (Jacobi) to ``rtol``."""
+    m = problem.mesh
+    if problem.field_loc not in (PER_VERTEX, PER_CELL):
+        raise ValueError("cp2_step takes vertex or cell fields (Xi from eps, Kinv)")
+    A = assemble_problem(problem, CP2)
+    T, _, isd, nbr = side_coefficients(m.xy, m.tri, m.dirichlet, problem.eps, problem.kinv,
+                                       problem.field_loc, CP2, problem.nu, problem.dt)
+    nt = m.tri.shape[0]
+    if dense is None:
+        dense = nt <= 2000
+    D = A.dense() if dense else None
+
+    def solve(b, x0):
+        if dense:
+            return dense_cholesky_solve(D, b)
+        x, st = pcg(A, b, x0=x0, rtol=rtol, raise_on_error=False)
+        if st.status not in (OK, ERR_NOT_CONVERGED):
+            raise OracleError(st.status, "pcg")
+        return x
+
+    args = (m.xy, m.tri, nbr, isd)
+    fields = (problem.eps, problem.kinv, problem.field_loc, problem.nu, problem.dt)
+    fbar = cp2_mean_flux(*args, u23)
+    eta_t = solve(fbar.sum(axis=1), None)
+    tau = cp2_tangential_flux(*args, *fields, eta_t)
+    eta = solve(fbar.sum(axis=1) + tau.sum(axis=1), eta_t)
+    Q, u_next, g_next = cp2_update(*args, *fields, fbar, T, tau, eta, u23, g_k)
+    return CP2Step(fbar, eta_t, tau, eta, Q, u_next, g_next, A)

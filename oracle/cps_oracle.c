@@ -605,3 +605,226 @@ done:
     free(area); free(cc); free(len); free(nrm); free(dist);
     return rc;
 }
+
+/* ------------------------------------------------------------------ */
+/* 8. The CP2 step around the two solves (Sec. 3.2.3, App. A, App. C).  */
+/*                                                                      */
+/* Sign convention: every flux below is the PHYSICAL flux leaving cell  */
+/* e through its local side j (n_j outward from e).  The velocity at    */
+/* the end of the step has outward side fluxes Q_j = Fbar_j + Phi_j,    */
+/* Phi_j the flux of Xi_j grad eta (Eq. Cs2_3, Eq. Cs2_5), and the     */
+/* mass balance sum_j Q_j = 0 gives the two systems of Eq. Cs2_7:       */
+/*   A eta~ = sum_j Fbar_j,  A eta = sum_j Fbar_j + sum_j tau_j(eta~),  */
+/* with (A eta)_e = sum_j T_j (eta_e - eta_ep) (TPFA part of -Phi) and  */
+/* tau_j the tangential part of Phi_j evaluated with eta~.              */
+/* Readings (the paper is ambiguous or inconsistent here):              */
+/*  - the m-terms carry the sign of Eq. Cs2_6 / Eq. A3.2, the only one   */
+/*    with which the side fluxes of e and ep cancel (as the text after  */
+/*    Eq. eta_flux states); Eq. eta_flux and the second right-hand      */
+/*    side print the opposite sign;                                     */
+/*  - d_{tau,n_l} alpha_l is the component of d_{j,tau} along n_l in    */
+/*    the co-normal decomposition d_{j,tau} = c_1 n_1 + c_2 n_2 of      */
+/*    Eq. A3.1 (oblique components); with it the flux is exact for      */
+/*    linear eta under a uniform tensor;                                */
+/*  - the two one-sided estimates (from e and from ep) are averaged;    */
+/*    an estimate that needs the normal derivative across a no-flux     */
+/*    side does not exist and the other is used alone (none: tau = 0);  */
+/*    across a Dirichlet side eta = 0 at its midpoint;                  */
+/*  - the extra 1/2 of Eq. A3.3 is not applied (Eq. Cs2_6 is followed). */
+/* ------------------------------------------------------------------ */
+
+/* Eq. flux_k_+_2/3: Fbar_j = ((u_e.n_j) A_ep - (u_ep.n_jp) A_e)/(A_e + A_ep)
+ * l_j, with n_jp the outward normal of ep on the shared side.  Reading for
+ * the boundary: a no-flux side carries no flux; a Dirichlet side carries
+ * e's own normal flux (u_e.n_j) l_j.  u is [2*nt]: x components, then y. */
+int or_cp2_mean_flux(int64_t nv, const double* xy, int64_t nt, const int32_t* tri,
+                     const int32_t* nbr, const int32_t* is_dirichlet, const double* u,
+                     double* fbar) {
+    double* area = (double*)malloc(sizeof(double) * nt);
+    double* cc = (double*)malloc(sizeof(double) * 2 * nt);
+    double* len = (double*)malloc(sizeof(double) * 3 * nt);
+    double* nrm = (double*)malloc(sizeof(double) * 6 * nt);
+    double* dist = (double*)malloc(sizeof(double) * 3 * nt);
+    int rc = OR_OK;
+    if (!area || !cc || !len || !nrm || !dist) { rc = OR_ERR_NOMEM; goto done; }
+    rc = or_geometry(nv, xy, nt, tri, nbr, area, cc, len, nrm, dist);
+    if (rc) goto done;
+    for (int64_t e = 0; e < nt; ++e)
+        for (int j = 0; j < 3; ++j) {
+            int64_t s = e * 3 + j;
+            int32_t ep = nbr[s];
+            double une = u[e] * nrm[2 * s] + u[nt + e] * nrm[2 * s + 1];
+            if (ep >= 0) {
+                int jp = 0;
+                while (jp < 3 && nbr[(int64_t)ep * 3 + jp] != (int32_t)e) ++jp;
+                if (jp == 3) { rc = OR_ERR_NONMANIFOLD; goto done; }
+                int64_t sp = (int64_t)ep * 3 + jp;
+                double unp = u[ep] * nrm[2 * sp] + u[nt + ep] * nrm[2 * sp + 1];
+                fbar[s] = (une * area[ep] - unp * area[e]) / (area[e] + area[ep]) * len[s];
+            } else if (is_dirichlet[s]) {
+                fbar[s] = une * len[s];
+            } else {
+                fbar[s] = 0.0;
+            }
+        }
+done:
+    free(area); free(cc); free(len); free(nrm); free(dist);
+    return rc;
+}
+
+/* Side tensor Xi_j (xx, xy, yy) of local side s of cell e, the same
+ * average as the matrix uses (Sec. 3.2). */
+static void side_tensor(const double* xi, const int32_t* tri, const int32_t* nbr,
+                        int field_loc, int64_t e, int j, double* xs) {
+    int64_t s = e * 3 + j;
+    if (field_loc == OR_PER_VERTEX) {
+        const double* xa = &xi[3 * (int64_t)tri[e * 3 + (j + 1) % 3]];
+        const double* xb = &xi[3 * (int64_t)tri[e * 3 + (j + 2) % 3]];
+        for (int c = 0; c < 3; ++c) xs[c] = 0.5 * (xa[c] + xb[c]);
+    } else if (nbr[s] >= 0) {
+        for (int c = 0; c < 3; ++c) xs[c] = 0.5 * (xi[3 * e + c] + xi[3 * (int64_t)nbr[s] + c]);
+    } else {
+        for (int c = 0; c < 3; ++c) xs[c] = xi[3 * e + c];
+    }
+}
+
+/* One-sided estimate of d_tau . grad(eta) from cell c, using the normal
+ * derivatives across c's two sides other than local side jc: d_tau =
+ * c1 n1 + c2 n2 (Cramer's rule on the 2x2 system), n_k . grad(eta) ~
+ * (eta_across - eta_c)/d (Eq. A3.2).  Returns 0 and leaves *est alone if a
+ * needed side is a no-flux side. */
+static int one_sided(int64_t c, int jc, const double* dtau, const int32_t* nbr,
+                     const int32_t* is_dirichlet, const double* nrm, const double* dist,
+                     const double* eta, double* est) {
+    int64_t s1 = c * 3 + (jc + 1) % 3, s2 = c * 3 + (jc + 2) % 3;
+    if ((nbr[s1] < 0 && !is_dirichlet[s1]) || (nbr[s2] < 0 && !is_dirichlet[s2])) return 0;
+    double n1x = nrm[2 * s1], n1y = nrm[2 * s1 + 1];
+    double n2x = nrm[2 * s2], n2y = nrm[2 * s2 + 1];
+    double det = n1x * n2y - n1y * n2x;
+    double c1 = (dtau[0] * n2y - dtau[1] * n2x) / det;
+    double c2 = (n1x * dtau[1] - n1y * dtau[0]) / det;
+    double e1 = nbr[s1] >= 0 ? eta[nbr[s1]] : 0.0;
+    double e2 = nbr[s2] >= 0 ? eta[nbr[s2]] : 0.0;
+    *est = c1 * (e1 - eta[c]) / dist[s1] + c2 * (e2 - eta[c]) / dist[s2];
+    return 1;
+}
+
+/* tau_j: tangential part of the outward flux of Xi_j grad(eta) through
+ * local side j of e (Eq. Cs2_6, Eq. eta_flux, App. C): d_j = Xi_j n_j,
+ * d_{j,tau} = d_j - (d_j.n_j) n_j, tau_j = l_j * mean of the one-sided
+ * estimates of d_{j,tau} . grad(eta) from e and from ep.  Zero on a
+ * no-flux side.  kinv/eps as for or_side_coefficients (CP2 tensor). */
+int or_cp2_tangential_flux(int64_t nv, const double* xy, int64_t nt, const int32_t* tri,
+                           const int32_t* nbr, const int32_t* is_dirichlet, const double* eps,
+                           const double* kinv, int field_loc, double nu, double dt,
+                           const double* eta, double* tau) {
+    if (field_loc != OR_PER_VERTEX && field_loc != OR_PER_CELL) return OR_ERR_ARG;
+    int64_t nf = field_loc == OR_PER_VERTEX ? nv : nt;
+    double* area = (double*)malloc(sizeof(double) * nt);
+    double* cc = (double*)malloc(sizeof(double) * 2 * nt);
+    double* len = (double*)malloc(sizeof(double) * 3 * nt);
+    double* nrm = (double*)malloc(sizeof(double) * 6 * nt);
+    double* dist = (double*)malloc(sizeof(double) * 3 * nt);
+    double* xi = (double*)malloc(sizeof(double) * 3 * nf);
+    int rc = OR_OK;
+    if (!area || !cc || !len || !nrm || !dist || !xi) { rc = OR_ERR_NOMEM; goto done; }
+    rc = or_geometry(nv, xy, nt, tri, nbr, area, cc, len, nrm, dist);
+    if (rc) goto done;
+    or_xi(nf, eps, kinv, nu, dt, xi);
+    for (int64_t e = 0; e < nt; ++e)
+        for (int j = 0; j < 3; ++j) {
+            int64_t s = e * 3 + j;
+            int32_t ep = nbr[s];
+            tau[s] = 0.0;
+            if (ep < 0 && !is_dirichlet[s]) continue;
+            double xs[3];
+            side_tensor(xi, tri, nbr, field_loc, e, j, xs);
+            double nx = nrm[2 * s], ny = nrm[2 * s + 1];
+            double dx = xs[0] * nx + xs[1] * ny, dy = xs[1] * nx + xs[2] * ny;
+            double dn = dx * nx + dy * ny;
+            double dtau[2] = {dx - dn * nx, dy - dn * ny};
+            double sum = 0.0, est;
+            int count = 0;
+            if (one_sided(e, j, dtau, nbr, is_dirichlet, nrm, dist, eta, &est)) {
+                sum += est;
+                ++count;
+            }
+            if (ep >= 0) {
+                int jp = 0;
+                while (jp < 3 && nbr[(int64_t)ep * 3 + jp] != (int32_t)e) ++jp;
+                if (jp == 3) { rc = OR_ERR_NONMANIFOLD; goto done; }
+                if (one_sided(ep, jp, dtau, nbr, is_dirichlet, nrm, dist, eta, &est)) {
+                    sum += est;
+                    ++count;
+                }
+            }
+            if (count > 0) tau[s] = len[s] * sum / count;
+        }
+done:
+    free(area); free(cc); free(len); free(nrm); free(dist); free(xi);
+    return rc;
+}
+
+/* End of the step.  Outward side fluxes Q_j = Fbar_j + Phi_j with
+ * Phi_j = -T_j (eta_e - eta_ep) + tau_j (Dirichlet side: eta_ep = 0;
+ * no-flux side: Q_j = 0).  Cell velocity (Eq. RT0): the RT0 field
+ * sum_j Q_j (x - x_j)/(2 A_e), x_j the node opposite side j, taken at the
+ * centroid (its mean over the cell; the field is constant in e when
+ * sum_j Q_j = 0).  Eq. grad_PSI: g_next = g_k + Mbar_e (u_next - u23), g the
+ * cell field eps grad(Psi), Mbar_e the mean over the cell's nodes of
+ * M = (I + nu eps Kinv dt)/dt (the cell's own M for cell fields).
+ * Q [nt*3] (e*3+j); u23, g_k, u_next, g_next [2*nt] (x, then y). */
+int or_cp2_update(int64_t nv, const double* xy, int64_t nt, const int32_t* tri,
+                  const int32_t* nbr, const int32_t* is_dirichlet, const double* eps,
+                  const double* kinv, int field_loc, double nu, double dt, const double* fbar,
+                  const double* T, const double* tau, const double* eta, const double* u23,
+                  const double* g_k, double* Q, double* u_next, double* g_next) {
+    if (field_loc != OR_PER_VERTEX && field_loc != OR_PER_CELL) return OR_ERR_ARG;
+    for (int64_t e = 0; e < nt; ++e) {
+        for (int k = 0; k < 3; ++k)
+            if (tri[e * 3 + k] < 0 || tri[e * 3 + k] >= nv) return OR_ERR_ARG;
+        const double* p[3];
+        for (int k = 0; k < 3; ++k) p[k] = &xy[2 * (int64_t)tri[e * 3 + k]];
+        double a2 = (p[1][0] - p[0][0]) * (p[2][1] - p[0][1]) -
+                    (p[1][1] - p[0][1]) * (p[2][0] - p[0][0]); /* 2 A_e */
+        double gx = (p[0][0] + p[1][0] + p[2][0]) / 3.0;
+        double gy = (p[0][1] + p[1][1] + p[2][1]) / 3.0;
+        double ux = 0.0, uy = 0.0;
+        for (int j = 0; j < 3; ++j) {
+            int64_t s = e * 3 + j;
+            int32_t ep = nbr[s];
+            double q;
+            if (ep >= 0) q = fbar[s] - T[s] * (eta[e] - eta[ep]) + tau[s];
+            else if (is_dirichlet[s]) q = fbar[s] - T[s] * eta[e] + tau[s];
+            else q = 0.0;
+            Q[s] = q;
+            ux += q * (gx - p[j][0]) / a2;
+            uy += q * (gy - p[j][1]) / a2;
+        }
+        u_next[e] = ux;
+        u_next[nt + e] = uy;
+        double m00, m01, m11;
+        if (field_loc == OR_PER_VERTEX) {
+            m00 = m01 = m11 = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                int64_t v = tri[e * 3 + k];
+                double c = nu * eps[v] * dt;
+                m00 += (1.0 + c * kinv[3 * v + 0]) / dt;
+                m01 += c * kinv[3 * v + 1] / dt;
+                m11 += (1.0 + c * kinv[3 * v + 2]) / dt;
+            }
+            m00 /= 3.0;
+            m01 /= 3.0;
+            m11 /= 3.0;
+        } else {
+            double c = nu * eps[e] * dt;
+            m00 = (1.0 + c * kinv[3 * e + 0]) / dt;
+            m01 = c * kinv[3 * e + 1] / dt;
+            m11 = (1.0 + c * kinv[3 * e + 2]) / dt;
+        }
+        double du = ux - u23[e], dv = uy - u23[nt + e];
+        g_next[e] = g_k[e] + m00 * du + m01 * dv;
+        g_next[nt + e] = g_k[nt + e] + m01 * du + m11 * dv;
+    }
+    return OR_OK;
+}
