@@ -210,6 +210,44 @@ int cps_adjoint(cps_sys sys, const double* x, const double* g, double* lambda, d
                 double* dtheta, double rtol, int64_t max_iter, cps_stats* stats,
                 void* stream);
 
+/* ------------------------------------------- CP2 step around the solves */
+
+/* Prepare the CP2 step (Sec. 3.2.3) on an assembled CP2 system: pass the same
+ * xy, tri, eps and kinv (device pointers, same sizes and field_loc) that built
+ * it; nothing of them is kept.  Stores per side slot the mean-flux geometry
+ * l_j n_j, T_j, four co-normal weights and cell indices of the tangential flux
+ * (App. C), per cell the RT0 weights and Mbar_e (about 360 bytes per cell).
+ * A second call replaces the data.  Errors: CPS_ERR_ARG (not CP2, null
+ * pointer), _NONDELAUNAY, _NONMANIFOLD, _ORIENTATION (inputs that do not
+ * match the system), _NOMEM, _CUDA. */
+int cps_cp2_setup(cps_sys sys, const double* xy, const int32_t* tri, const double* eps,
+                  const double* kinv, void* stream);
+
+/* One CP2 step: from the cell velocity u^{k+2/3} of the first corrector to the
+ * divergence-free u^{k+1} and the updated eps grad(Psi).
+ *   u23[2*nt]     u^{k+2/3} per cell: x components, then y components
+ *   g_k[2*nt]     eps grad(Psi^k) per cell, same layout
+ *   eta_tilde[nt] out: first solution eta~ (may be NULL)
+ *   eta[nt]       out: second solution eta
+ *   u_next[2*nt]  out: u^{k+1}, the RT0 field at the centroid (Eq. RT0)
+ *   g_next[2*nt]  out: eps grad(Psi^{k+1}) = g_k + Mbar_e (u_next - u23) (Eq. grad_PSI)
+ *   flux[3*nt]    out (may be NULL): outward flux Q of u^{k+1} through local
+ *                 side j of cell e at j*nt + e; sum_j Q = 0 per cell to the
+ *                 solve tolerance and Q is antisymmetric across a side
+ *   rtol, max_iter, precision as cps_solve, for both solves
+ *   stats         host array of 2 (first and second solve), may be NULL
+ * Steps: Fbar_j = ((u_e.n_j) A_ep + (u_ep.n_j) A_e)/(A_e + A_ep) l_j
+ * (Eq. flux_k_+_2/3; a Dirichlet side carries (u_e.n_j) l_j, a no-flux side
+ * nothing); A eta~ = sum_j Fbar_j (Eq. Cs2_7_1); tau_j(eta~), the tangential
+ * flux of Xi_j grad(eta) from the co-normal decomposition (Eq. Cs2_6, App. C);
+ * A eta = sum_j (Fbar_j + tau_j) from eta~ (Eq. Cs2_7_2); Q_j = Fbar_j -
+ * T_j (eta_e - eta_ep) + tau_j.  Fluxes are physical and outward.  Needs
+ * cps_cp2_setup.  The outputs must not overlap the inputs.  Errors: as
+ * cps_solve (CPS_ERR_NOT_CONVERGED still completes the step), CPS_ERR_ARG. */
+int cps_cp2_step(cps_sys sys, const double* u23, const double* g_k, double* eta_tilde,
+                 double* eta, double* u_next, double* g_next, double* flux, double rtol,
+                 int64_t max_iter, int precision, cps_stats* stats, void* stream);
+
 /* Choose how FP64 Jacobi and reduced-system solves run:
  *   CPS_PATH_AUTO (default): the autotuner times the applicable paths on the
  *     system's first solve of that kind and keeps the fastest;

@@ -210,6 +210,40 @@ class System:
         out = xd.cpu() if host else xd
         return out, _stats(st)
 
+    def cp2_setup(self, xy, tri, eps, kinv):
+        """Prepare the CP2 step on this (CP2) system from the mesh and fields it
+        was assembled from (kinv holds theta for log-permeability systems)."""
+        d = self.ctx.dev
+        xy_d, tri_d = d(xy, torch.float64), d(tri, torch.int32)
+        eps_d, kinv_d = d(eps, torch.float64), d(kinv, torch.float64)
+        rc = self.ctx.lib.cps_cp2_setup(self.handle, P(xy_d.data_ptr()), P(tri_d.data_ptr()),
+                                        P(eps_d.data_ptr()), P(kinv_d.data_ptr()),
+                                        _stream(self.ctx.device))
+        self.ctx.check(rc, "cps_cp2_setup")
+
+    def cp2_step(self, u23, g_k, rtol: float = 1e-10, max_iter: int = 1_000_000,
+                 precision: int = _cps.FP64, check: bool = True) -> dict:
+        """One CP2 step (Sec. 3.2.3) from the cell velocity u23 [2, nt] and the
+        cell field g_k = eps grad(Psi^k) [2, nt].  Returns device tensors
+        eta_tilde, eta [nt], u_next, g_next [2, nt], flux [3, nt] (outward
+        side fluxes of u_next) and the stats of the two solves."""
+        u = self.ctx.dev(u23, torch.float64).reshape(2, self.nt)
+        g = self.ctx.dev(g_k, torch.float64).reshape(2, self.nt)
+        z = lambda *shape: torch.empty(*shape, dtype=torch.float64, device=self.ctx.device)
+        out = {"eta_tilde": z(self.nt), "eta": z(self.nt), "u_next": z(2, self.nt),
+               "g_next": z(2, self.nt), "flux": z(3, self.nt)}
+        st = (_cps.Stats * 2)()
+        rc = self.ctx.lib.cps_cp2_step(self.handle, P(u.data_ptr()), P(g.data_ptr()),
+                                       P(out["eta_tilde"].data_ptr()), P(out["eta"].data_ptr()),
+                                       P(out["u_next"].data_ptr()), P(out["g_next"].data_ptr()),
+                                       P(out["flux"].data_ptr()), rtol, max_iter, precision, st,
+                                       _stream(self.ctx.device))
+        if check:
+            self.ctx.check(rc, "cps_cp2_step")
+        out["stats"] = (_stats(st[0]), _stats(st[1]))
+        out["status"] = rc
+        return out
+
     def adjoint(self, x, g, lam=None, dT=None, dtheta=None, rtol: float = 1e-12,
                 max_iter: int = 1_000_000):
         """lambda = A^-1 g; accumulates dL/dT into dT [3, nt] and dL/dtheta

@@ -152,6 +152,26 @@ int cps_solve_batch(const cps_sys* systems, int nsys, const double* const* b, do
                                  as_stream(stream));
 }
 
+int cps_cp2_setup(cps_sys sys, const double* xy, const int32_t* tri, const double* eps,
+                  const double* kinv, void* stream) {
+    CallRange range_("cps_cp2_setup");
+    if (!sys) return CPS_ERR_ARG;
+    int rc = set_device(sys->ctx);
+    if (rc) return rc;
+    return cps::cp2_setup_impl(sys, xy, tri, eps, kinv, as_stream(stream));
+}
+
+int cps_cp2_step(cps_sys sys, const double* u23, const double* g_k, double* eta_tilde,
+                 double* eta, double* u_next, double* g_next, double* flux, double rtol,
+                 int64_t max_iter, int precision, cps_stats* stats, void* stream) {
+    CallRange range_("cps_cp2_step");
+    if (!sys) return CPS_ERR_ARG;
+    int rc = set_device(sys->ctx);
+    if (rc) return rc;
+    return cps::cp2_step_impl(sys, u23, g_k, eta_tilde, eta, u_next, g_next, flux, rtol,
+                              max_iter, precision, stats, as_stream(stream));
+}
+
 int cps_adjoint(cps_sys sys, const double* x, const double* g, double* lambda, double* dT,
                 double* dtheta, double rtol, int64_t max_iter, cps_stats* stats, void* stream) {
     CallRange range_("cps_adjoint");

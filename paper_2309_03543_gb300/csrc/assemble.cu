@@ -98,6 +98,8 @@ __global__ void k_side_lookup(const int32_t* __restrict__ tri, int64_t nt, int64
     }
 }
 
+}  // namespace
+
 __global__ void k_cell_geometry(const double* __restrict__ xy, const int32_t* __restrict__ tri,
                                 int64_t nt, int64_t nv, double* __restrict__ area,
                                 double* __restrict__ ccx, double* __restrict__ ccy, int* err) {
@@ -124,14 +126,6 @@ __global__ void k_cell_geometry(const double* __restrict__ xy, const int32_t* __
     }
 }
 
-// Component comp (0 xx, 1 xy, 2 yy) of K^-1 at field point i: stored, or
-// exp(-theta_i) I for a log-permeability field.
-__device__ __forceinline__ double kinv_at(const double* __restrict__ kinv, int64_t i, int comp,
-                                          bool logk) {
-    if (logk) return comp == 1 ? 0.0 : exp(-kinv[i]);
-    return kinv[3 * i + comp];
-}
-
 // Xi = eps dt (I + c Kinv)^-1, c = nu eps dt, explicit 2x2 inverse.
 __global__ void k_xi(const double* __restrict__ eps, const double* __restrict__ kinv, int64_t nf,
                      double nu, double dt, bool logk, double* __restrict__ xi, int* err) {
@@ -150,6 +144,8 @@ __global__ void k_xi(const double* __restrict__ eps, const double* __restrict__ 
         xi[3 * i + 2] = sc * m00;
     }
 }
+
+namespace {
 
 __global__ void k_mark_dirichlet(const int32_t* __restrict__ dirichlet, int64_t nb, int64_t nt,
                                  const int32_t* __restrict__ nbr, int32_t* __restrict__ kind,
@@ -349,6 +345,7 @@ static int dev_alloc(cps_ctx ctx, T** p, size_t n) {
 
 void free_sys(cps_sys s) {
     if (!s) return;
+    free_cp2(s);
     // s->col lives inside s->a's allocation (one range for the L2 window)
     void* bufs[] = {s->s,     s->diag,  s->a,     s->a32,     s->s32,      s->gfac,
                     s->dxi,   s->slot_kind, s->perm, s->iperm, s->pa,  s->pcol,     s->pl,
@@ -396,6 +393,7 @@ int assemble_impl(cps_ctx ctx, const double* xy, int64_t nv, const int32_t* tri,
     s->nv = nv;
     s->kind = kind;
     s->field_loc = field_loc;
+    s->logk = logk;
     s->nu = nu;
     s->dt = dt;
     const int64_t nf = field_loc == CPS_PER_VERTEX ? nv : nt;

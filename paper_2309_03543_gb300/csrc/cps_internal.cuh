@@ -78,6 +78,41 @@ __device__ __forceinline__ void set_error(int* err, int code) {
     atomicCAS(err, 0, code);
 }
 
+// Component comp (0 xx, 1 xy, 2 yy) of K^-1 at field point i: stored, or
+// exp(-theta_i) I for a log-permeability field.
+__device__ __forceinline__ double kinv_at(const double* __restrict__ kinv, int64_t i, int comp,
+                                          bool logk) {
+    if (logk) return comp == 1 ? 0.0 : exp(-kinv[i]);
+    return kinv[3 * i + comp];
+}
+
+// Per cell area and circumcentre (Sec. 3.1); CPS_ERR_ARG / _ORIENTATION in err.
+__global__ void k_cell_geometry(const double* __restrict__ xy, const int32_t* __restrict__ tri,
+                                int64_t nt, int64_t nv, double* __restrict__ area,
+                                double* __restrict__ ccx, double* __restrict__ ccy, int* err);
+// Xi = eps dt (I + nu eps dt Kinv)^-1 at nf field points (Eq. Cs2_4), [nf][3].
+__global__ void k_xi(const double* __restrict__ eps, const double* __restrict__ kinv, int64_t nf,
+                     double nu, double dt, bool logk, double* __restrict__ xi, int* err);
+
+// Data of the CP2 step around the two solves (Sec. 3.2.3), set up once per
+// system by cps_cp2_setup; every array is a slice of buf.  Slot-major [k][nt]
+// like the matrix: slot j*nt + e is local side j of cell e.
+struct Cp2Data {
+    void* buf = nullptr;
+    double* area = nullptr;   // [nt]
+    double* lnx = nullptr;    // [3nt] l_j n_j, x
+    double* lny = nullptr;    // [3nt] l_j n_j, y
+    double* T = nullptr;      // [3nt] side coefficient (interior, Dirichlet), 0 no-flux
+    double* tw = nullptr;     // [4][3nt] co-normal weights of the tangential flux
+    double* rt0 = nullptr;    // [6][nt] (centroid - x_j)/(2 A_e), j = 0..2, x then y
+    double* mbar = nullptr;   // [3][nt] Mbar_e (xx, xy, yy)
+    double* fbar = nullptr;   // [3nt] mean side flux of the current step
+    double* tau = nullptr;    // [3nt] tangential flux of the current step
+    double* rhs = nullptr;    // [nt] right-hand side of the current solve
+    double* eta_t = nullptr;  // [nt] first solution when the caller keeps none
+    int32_t* tidx = nullptr;  // [4][3nt] cell whose eta enters each weight (-1: eta = 0)
+};
+
 // Block-wide sum of v[0..NV) over BS threads (BS = blockDim.x); on return
 // every thread holds the totals.  GB300 issues FP64 adds at 1/64 of the FP32
 // rate, so the adds are kept few: every thread stores its values to shared
@@ -175,6 +210,8 @@ struct cps_sys_s {
     double diag_min = 0;
     int is_mmatrix = 0;
     bool iso_cell = false;      // CPS_PER_CELL with isotropic Kinv (adjoint theta chain)
+    bool logk = false;          // assembled from CPS_PER_CELL_LOGK (kinv holds theta)
+    cps::Cp2Data* cp2 = nullptr;  // CP2 step data (cps_cp2_setup)
     int64_t assembly_launches = 0;
 
     // Matrix in symmetrically scaled padded-ELL form: A = S (I + Aoff) S with
@@ -285,5 +322,11 @@ bool l2_vectors_fit(cps_sys s);
 void drop_graphs(cps_sys s, int prec);
 int export_impl(cps_sys sys, double* diag, int32_t* col, double* val, cudaStream_t stream);
 void free_sys(cps_sys sys);
+void free_cp2(cps_sys sys);
+int cp2_setup_impl(cps_sys sys, const double* xy, const int32_t* tri, const double* eps,
+                   const double* kinv, cudaStream_t stream);
+int cp2_step_impl(cps_sys sys, const double* u23, const double* g_k, double* eta_tilde,
+                  double* eta, double* u_next, double* g_next, double* flux, double rtol,
+                  int64_t max_iter, int precision, cps_stats* stats, cudaStream_t stream);
 
 }  // namespace cps

@@ -339,6 +339,17 @@ def log_permeability_problem(n: int, seed: int = 0, eps0: float = 0.4,
                    meta={"workload": f"log-permeability n={n}", "seed": seed}), theta
 
 
+def cell_vector_field(mesh: Mesh, seed: int, mean=(0.0, 0.0), scale: float = 1.0) -> np.ndarray:
+    """[2, nt]: two independent random-Fourier fields at the cell centroids
+    (standardised, times scale) plus a uniform mean -- the stand-in for the
+    first corrector's cell velocity u^{k+2/3} (not divergence free) and for the
+    cell field eps grad(Psi^k) entering the second corrector."""
+    rng = np.random.default_rng(seed + 104729)
+    c = cell_centroids(mesh)
+    f = np.stack([random_fourier_field(c, rng, mesh.width, mesh.height) for _ in range(2)])
+    return np.asarray(mean, dtype=np.float64)[:, None] + scale * f
+
+
 def rhs(mesh: Mesh, seed: int) -> np.ndarray:
     """b_e = A_e * N(0, 1)."""
     rng = np.random.default_rng(seed)
