@@ -49,6 +49,19 @@ BYTES_PER_CELL_ITER_MIXED = 48 + 12 + 0.5
 # line reports it only when the autotuner chose the same launch grids, block
 # sizes and L2 window (the rows per thread per trip, which the tuner may set
 # differently from box to box, do not change the bytes a kernel moves).
+# Algorithmic bytes per cell of the CP2 step kernels (each array counted once):
+# mean flux: u 16, per side col 4 + area weight 8 + l n 16, Fbar out 24, B1 out 8;
+# tangential: eta 8, per side col 4 + 4 weights 32 + 4 indices 16, tau out 24,
+# B2 read and write 16; update: eta 8, per side col 4 + Fbar 8 + T 8 + tau 8,
+# RT0 48, Mbar 24, u 16, g 16, flux out 24, u out 16, g out 16.
+BYTES_PER_CELL_CP2 = {"mean_flux": 132, "tangential": 204, "update": 252}
+# FP64 arithmetic instructions per cell of the same kernels, counted from the
+# source (per side: mean flux 3 mul + 3 fma/add + 2 for the sum; tangential
+# 4 x (sub + fma) + 1; update sub, fma, add and 2 fma; plus the cell terms).
+# GB300 issues about 2 FP64 FMAs per SM per clock, which bounds these kernels
+# before HBM does.
+FP64_INSTR_PER_CELL_CP2 = {"mean_flux": 24, "tangential": 28, "update": 21}
+FP64_INSTR_PER_SM_CLK = 2
 TRAFFIC_PER_ITER_N1024 = (121.8 + 21.9 + 40.9) * 1e6
 TRAFFIC_CONFIG = {"grid": [608, 152, 152], "block": [256, 1024, 1024],
                   "l2_window": "vectors", "persistent": False, "cluster": False}
@@ -78,6 +91,12 @@ def parse():
                          "of the --n lattice (4096: 33.5M cells), right-hand side redrawn each "
                          "step, FP64 and mixed, each solve capped at --seq-iters (own line)")
     ap.add_argument("--seq-iters", type=int, default=500)
+    ap.add_argument("--cp2-step", type=int, default=0,
+                    help="CP2-step mode: this many timed CP2 steps (mean flux, two PCG solves, "
+                         "tangential flux, RT0 velocity, eps grad Psi) on the --n lattice, "
+                         "after --warmup untimed ones (own line)")
+    ap.add_argument("--cp2-precond", default="jacobi", choices=["jacobi", "ic0", "reduced"],
+                    help="preconditioner of the CP2-step mode's solves")
     ap.add_argument("--pin", default="",
                     help="profiling run only: pin the FP64 Jacobi configuration instead of "
                          "tuning it (a profiler's replay skews the tuner), as "
@@ -422,6 +441,72 @@ def run_sequence(args):
     print(json.dumps(line), flush=True)
 
 
+def run_cp2_step(args):
+    """Whole CP2 steps on the channel-block workload: each step takes a new
+    cell velocity u^{k+2/3} (seeded random-Fourier field plus a mean flow) and
+    the previous step's eps grad(Psi); the line reports steps per second, the
+    iterations of the two solves (the second warm-started from the first), the
+    device time of each step kernel against the measured copy bandwidth, and
+    the largest net cell flux left after the step."""
+    import torch
+    import paper_2309_03543_gb300 as cps
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    ctx = cps.Context(0)
+    p = synth.channel_block_problem(args.n, seed=0)
+    m = p.mesh
+    nt = m.nt
+    s = ctx.assemble(m.xy, m.tri, m.dirichlet, p.eps, p.kinv, p.field_loc, cps.KIND_CP2,
+                     p.nu, p.dt)
+    s.cp2_setup(m.xy, m.tri, p.eps, p.kinv)
+    pc = {"jacobi": cps.PC_JACOBI, "ic0": cps.PC_IC0, "reduced": cps.PC_REDUCED}[args.cp2_precond]
+    if pc != cps.PC_JACOBI:
+        s.set_precond(pc)
+    total = args.warmup + args.cp2_step
+    us = [torch.as_tensor(synth.cell_vector_field(m, 100 + t, mean=(0.05, 0.01), scale=0.02),
+                          device=dev) for t in range(total)]
+    g = torch.as_tensor(synth.cell_vector_field(m, 12, scale=1e-3), device=dev)
+    peak, peak_kind = measured_peaks()
+    secs, iters, kms, imbalance = [], [], [], 0.0
+    for t in range(total):
+        dt_, out = timed(lambda: s.cp2_step(us[t], g, rtol=args.rtol), stream)
+        g = out["g_next"]
+        if t >= args.warmup:
+            secs.append(dt_)
+            iters.append([out["stats"][0].iters, out["stats"][1].iters])
+            kms.append(s.cp2_kernel_times())
+            q = out["flux"]
+            imbalance = max(imbalance, float(q.sum(dim=0).abs().max() / q.abs().max()))
+    kernels = {}
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = sms * FP64_INSTR_PER_SM_CLK * 2070e6     # FP64 instructions/s at the max clock
+    for k, name in enumerate(("mean_flux", "tangential", "update")):
+        ms = sum(x[k] for x in kms) / len(kms)
+        gbs = BYTES_PER_CELL_CP2[name] * nt / (ms * 1e-3) / 1e9
+        ips = FP64_INSTR_PER_CELL_CP2[name] * nt / (ms * 1e-3)
+        kernels[name] = {"ms": ms, "bytes_per_cell": BYTES_PER_CELL_CP2[name],
+                         "achieved_gbs": gbs, "frac": gbs / peak,
+                         "fp64_instr_per_cell": FP64_INSTR_PER_CELL_CP2[name],
+                         "fp64_frac_of_issue_peak": ips / alu_peak}
+    kernel_s = sum(v["ms"] for v in kernels.values()) * 1e-3
+    t_step = sum(secs) / len(secs)
+    s.free()
+    line = {"metric": "CP2 steps per second (mean flux, two PCG solves to rtol, tangential "
+                      "flux, RT0 velocity, eps grad Psi)",
+            "value": 1.0 / t_step, "unit": "steps/s", "higher_is_better": True,
+            "ms_per_step": 1e3 * t_step, "steps": args.cp2_step, "warmup": args.warmup,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"channel-block-aniso lattice n={args.n}", "cells": nt,
+                       "rtol": args.rtol, "precond": args.cp2_precond,
+                       "u23": "random-Fourier field + mean flow, seed 100+t",
+                       "l2": "step working set ~1.2 GB, larger than L2"},
+            "solve_iters": iters, "step_kernels": kernels,
+            "step_kernels_share_of_step": kernel_s / t_step,
+            "peak": peak, "peak_kind": peak_kind,
+            "fp64_issue_peak_instr_per_s": alu_peak, "max_net_cell_flux_rel": imbalance}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -435,6 +520,9 @@ def main():
         return
     if args.sequence:
         run_sequence(args)
+        return
+    if args.cp2_step:
+        run_cp2_step(args)
         return
     import torch
     import paper_2309_03543_gb300 as cps

@@ -248,6 +248,12 @@ int cps_cp2_step(cps_sys sys, const double* u23, const double* g_k, double* eta_
                  double* eta, double* u_next, double* g_next, double* flux, double rtol,
                  int64_t max_iter, int precision, cps_stats* stats, void* stream);
 
+/* Device durations in milliseconds (host ms[3]) of the last cps_cp2_step's
+ * three step kernels -- mean flux, tangential flux, update -- from CUDA events
+ * recorded around each on the step's stream (-1 if unavailable).
+ * Errors: CPS_ERR_ARG (no CP2 step data). */
+int cps_cp2_kernel_times(cps_sys sys, float* ms);
+
 /* Choose how FP64 Jacobi and reduced-system solves run:
  *   CPS_PATH_AUTO (default): the autotuner times the applicable paths on the
  *     system's first solve of that kind and keeps the fastest;

@@ -67,6 +67,7 @@ SIGNATURES = {
     "cps_adjoint": (_I, [_P, _P, _P, _P, _P, _P, _D, _I64, ctypes.POINTER(Stats), _P]),
     "cps_matvec": (_I, [_P, _P, _P, _P]),
     "cps_cp2_setup": (_I, [_P, _P, _P, _P, _P, _P]),
+    "cps_cp2_kernel_times": (_I, [_P, _P]),
     "cps_cp2_step": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _D, _I64, _I, ctypes.POINTER(Stats),
                           _P]),
     "cps_get_tuning": (_I, [_P, _I, _P, _P, _P, _P, _P]),

@@ -244,6 +244,13 @@ class System:
         out["status"] = rc
         return out
 
+    def cp2_kernel_times(self) -> list:
+        """Device milliseconds of the last CP2 step's kernels: mean flux,
+        tangential flux, update."""
+        ms = (ctypes.c_float * 3)()
+        self.ctx.check(self.ctx.lib.cps_cp2_kernel_times(self.handle, ms), "cps_cp2_kernel_times")
+        return list(ms)
+
     def adjoint(self, x, g, lam=None, dT=None, dtheta=None, rtol: float = 1e-12,
                 max_iter: int = 1_000_000):
         """lambda = A^-1 g; accumulates dL/dT into dT [3, nt] and dL/dtheta

@@ -172,6 +172,11 @@ int cps_cp2_step(cps_sys sys, const double* u23, const double* g_k, double* eta_
                               max_iter, precision, stats, as_stream(stream));
 }
 
+int cps_cp2_kernel_times(cps_sys sys, float* ms) {
+    if (!sys) return CPS_ERR_ARG;
+    return cps::cp2_kernel_times(sys, ms);
+}
+
 int cps_adjoint(cps_sys sys, const double* x, const double* g, double* lambda, double* dT,
                 double* dtheta, double rtol, int64_t max_iter, cps_stats* stats, void* stream) {
     CallRange range_("cps_adjoint");

@@ -24,8 +24,11 @@
 // across a Dirichlet side eta = 0 at the midpoint.
 //
 // Set-up folds the geometry, the side tensor and the co-normal components into
-// four weights and four cell indices per side slot, so the step itself is
-// three streaming kernels (1, 3, 5) around the two solves.
+// per-slot weights (the area weight of the mean flux, l_j n_j zeroed on no-flux
+// sides, four co-normal weights and cell indices), so the step itself is three
+// branch-free streaming kernels (1, 3, 5) around the two solves, one thread per
+// cell.  A boundary slot is recognised by its column (col = e); no-flux slots
+// carry zero coefficients and need no test.
 #include "cps_internal.cuh"
 
 #include <string>
@@ -94,6 +97,7 @@ struct SideArgs {
     const int32_t* slot_kind;
     const double* ccx;
     const double* ccy;
+    const double* area;
     const double* xi;
     int64_t nt, nv;
     bool per_vertex;
@@ -106,6 +110,7 @@ struct SideArgs {
     double* lnx;    // [3nt] outputs
     double* lny;
     double* T;
+    double* wgt;
     int* err;
 };
 
@@ -121,6 +126,7 @@ __global__ void k_cp2_side(SideArgs A) {
                 const int64_t slot = (int64_t)j * nt + e;
                 A.nx[slot] = A.ny[slot] = A.len[slot] = A.dist[slot] = 0.0;
                 A.dtx[slot] = A.dty[slot] = A.lnx[slot] = A.lny[slot] = A.T[slot] = 0.0;
+                A.wgt[slot] = 1.0;
             }
             continue;
         }
@@ -162,9 +168,10 @@ __global__ void k_cp2_side(SideArgs A) {
             A.dist[slot] = d;
             A.dtx[slot] = dx - dn * nx;
             A.dty[slot] = dy - dn * ny;
-            A.lnx[slot] = l * nx;
-            A.lny[slot] = l * ny;
+            A.lnx[slot] = sk != 0 ? l * nx : 0.0;
+            A.lny[slot] = sk != 0 ? l * ny : 0.0;
             A.T[slot] = sk != 0 ? l * dn / d : 0.0;
+            A.wgt[slot] = sk == 1 ? A.area[ep] / (A.area[e] + A.area[ep]) : 1.0;
         }
     }
 }
@@ -252,28 +259,27 @@ __global__ void k_cp2_weights(WeightArgs A) {
     }
 }
 
-// Step 1: Fbar per slot and B1_e = sum_j Fbar_j.
-__global__ void k_cp2_mean_flux(const double* __restrict__ u, const int32_t* __restrict__ col,
-                                const int32_t* __restrict__ slot_kind,
-                                const double* __restrict__ area, const double* __restrict__ lnx,
-                                const double* __restrict__ lny, int64_t nt,
-                                double* __restrict__ fbar, double* __restrict__ rhs) {
+// Step 1: Fbar per slot and B1_e = sum_j Fbar_j, as
+// l_j n_j . (w u_e + (1 - w) u_ep) with w = A_ep/(A_e + A_ep) (Eq. flux_k_+_2/3
+// with n_jp = -n_j).  A Dirichlet slot has col = e and w = 1 (e's own flux); a
+// no-flux slot has l_j n_j = 0.
+__global__ void __launch_bounds__(kBlock)
+k_cp2_mean_flux(const double* __restrict__ u, const int32_t* __restrict__ col,
+                const double* __restrict__ wgt, const double* __restrict__ lnx,
+                const double* __restrict__ lny, int64_t nt, double* __restrict__ fbar,
+                double* __restrict__ rhs) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nt;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const double ue = u[e], ve = u[nt + e], ae = area[e];
+        const double ue = u[e], ve = u[nt + e];
         double sum = 0.0;
+#pragma unroll
         for (int j = 0; j < 3; ++j) {
             const int64_t slot = (int64_t)j * nt + e;
-            const int sk = slot_kind[slot];
-            const double lx = lnx[slot], ly = lny[slot];
-            double f = 0.0;
-            if (sk == 1) {
-                const int32_t ep = col[slot];
-                const double ap = area[ep];
-                f = ((ue * lx + ve * ly) * ap + (u[ep] * lx + u[nt + ep] * ly) * ae) / (ae + ap);
-            } else if (sk == 2) {
-                f = ue * lx + ve * ly;
-            }
+            const int32_t c = col[slot];
+            const double w = wgt[slot];
+            const double ux = w * ue + (1.0 - w) * u[c];
+            const double uy = w * ve + (1.0 - w) * u[nt + c];
+            const double f = lnx[slot] * ux + lny[slot] * uy;
             fbar[slot] = f;
             sum += f;
         }
@@ -282,7 +288,8 @@ __global__ void k_cp2_mean_flux(const double* __restrict__ u, const int32_t* __r
 }
 
 // Step 3: tau per slot from eta~ and B2_e = B1_e + sum_j tau_j.
-__global__ void k_cp2_tangential(const double* __restrict__ eta, const int32_t* __restrict__ col,
+__global__ void __launch_bounds__(kBlock)
+k_cp2_tangential(const double* __restrict__ eta, const int32_t* __restrict__ col,
                                  const double* __restrict__ tw, const int32_t* __restrict__ tidx,
                                  int64_t nt, double* __restrict__ tau, double* __restrict__ rhs) {
     const int64_t ns = 3 * nt;
@@ -290,10 +297,12 @@ __global__ void k_cp2_tangential(const double* __restrict__ eta, const int32_t* 
          e += (int64_t)gridDim.x * blockDim.x) {
         const double ee = eta[e];
         double sum = 0.0;
+#pragma unroll
         for (int j = 0; j < 3; ++j) {
             const int64_t slot = (int64_t)j * nt + e;
             const double ep = eta[col[slot]];
             double t = 0.0;
+#pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const int32_t i = tidx[k * ns + slot];
                 const double ek = i >= 0 ? eta[i] : 0.0;
@@ -306,27 +315,27 @@ __global__ void k_cp2_tangential(const double* __restrict__ eta, const int32_t* 
     }
 }
 
-// Step 5: side fluxes, RT0 cell velocity, eps grad(Psi) update.
-__global__ void k_cp2_update(const double* __restrict__ eta, const int32_t* __restrict__ col,
-                             const int32_t* __restrict__ slot_kind,
-                             const double* __restrict__ fbar, const double* __restrict__ T,
-                             const double* __restrict__ tau, const double* __restrict__ rt0,
-                             const double* __restrict__ mbar, const double* __restrict__ u23,
-                             const double* __restrict__ g_k, int64_t nt,
-                             double* __restrict__ flux, double* __restrict__ u_next,
-                             double* __restrict__ g_next) {
+// Step 5: side fluxes, RT0 cell velocity, eps grad(Psi) update.  On a
+// boundary slot (col = e) eta across is 0 (Dirichlet); a no-flux slot has
+// Fbar = T = tau = 0 and so Q = 0.
+__global__ void __launch_bounds__(kBlock, 4)
+k_cp2_update(const double* __restrict__ eta, const int32_t* __restrict__ col,
+             const double* __restrict__ fbar, const double* __restrict__ T,
+             const double* __restrict__ tau, const double* __restrict__ rt0,
+             const double* __restrict__ mbar, const double* __restrict__ u23,
+             const double* __restrict__ g_k, int64_t nt, double* __restrict__ flux,
+             double* __restrict__ u_next, double* __restrict__ g_next) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nt;
          e += (int64_t)gridDim.x * blockDim.x) {
         const double ee = eta[e];
         double ux = 0.0, uy = 0.0;
+#pragma unroll
         for (int j = 0; j < 3; ++j) {
             const int64_t slot = (int64_t)j * nt + e;
-            const int sk = slot_kind[slot];
-            double q = 0.0;
-            if (sk != 0) {
-                const double ep = sk == 1 ? eta[col[slot]] : 0.0;
-                q = fbar[slot] - T[slot] * (ee - ep) + tau[slot];
-            }
+            const int32_t c = col[slot];
+            const double ec = eta[c];
+            const double eb = c != (int32_t)e ? ec : 0.0;
+            const double q = fbar[slot] - T[slot] * (ee - eb) + tau[slot];
             if (flux) flux[slot] = q;
             ux += q * rt0[(2 * j) * nt + e];
             uy += q * rt0[(2 * j + 1) * nt + e];
@@ -349,6 +358,8 @@ int fail(cps_sys s, int code, const std::string& msg) {
 
 void free_cp2(cps_sys s) {
     if (!s || !s->cp2) return;
+    for (cudaEvent_t ev : s->cp2->ev)
+        if (ev) cudaEventDestroy(ev);
     if (s->cp2->buf) cudaFree(s->cp2->buf);
     delete s->cp2;
     s->cp2 = nullptr;
@@ -363,10 +374,10 @@ int cp2_setup_impl(cps_sys s, const double* xy, const int32_t* tri, const double
     const int64_t nf = per_vertex ? nv : nt;
     free_cp2(s);
     Cp2Data* c = new Cp2Data();
-    // doubles: area 1, lnx 3, lny 3, T 3, tw 12, rt0 6, mbar 3, fbar 3, tau 3, rhs 1,
+    // doubles: wgt 3, lnx 3, lny 3, T 3, tw 12, rt0 6, mbar 3, fbar 3, tau 3, rhs 1,
     // eta_t 1 (x nt, each slice 256-byte aligned); then tidx 12 nt int32
     const int64_t st = (nt + 31) / 32 * 32;
-    const int64_t nd = 39 * st;
+    const int64_t nd = 41 * st;
     const size_t bytes = sizeof(double) * (size_t)nd + sizeof(int32_t) * (size_t)(12 * st);
     cudaError_t ce = cudaMalloc(&c->buf, bytes);
     if (ce != cudaSuccess) {
@@ -375,7 +386,7 @@ int cp2_setup_impl(cps_sys s, const double* xy, const int32_t* tri, const double
     }
     double* d = static_cast<double*>(c->buf);
     auto take = [&](int64_t k) { double* p = d; d += k * st; return p; };
-    c->area = take(1);
+    c->wgt = take(3);
     c->lnx = take(3);
     c->lny = take(3);
     c->T = take(3);
@@ -388,27 +399,36 @@ int cp2_setup_impl(cps_sys s, const double* xy, const int32_t* tri, const double
     c->eta_t = take(1);
     c->tidx = reinterpret_cast<int32_t*>(d);
     s->cp2 = c;
+    for (cudaEvent_t& ev : c->ev) {
+        ce = cudaEventCreate(&ev);
+        if (ce != cudaSuccess) {
+            free_cp2(s);
+            return fail(s, CPS_ERR_CUDA, std::string("cp2_setup: cudaEventCreate: ") +
+                                             cudaGetErrorString(ce));
+        }
+    }
     // A slice of k st doubles holds the k rows [k][nt] at stride nt (k nt <= k st).
 
-    double *ccx = nullptr, *ccy = nullptr, *xi = nullptr, *scratch = nullptr;
+    double *ccx = nullptr, *ccy = nullptr, *area = nullptr, *xi = nullptr, *scratch = nullptr;
     int* err = nullptr;
     int h_err = 0;
     auto A = [&](void** p, size_t b) { return cudaMallocAsync(p, b, stream); };
     ce = A((void**)&ccx, sizeof(double) * nt);
     if (ce == cudaSuccess) ce = A((void**)&ccy, sizeof(double) * nt);
+    if (ce == cudaSuccess) ce = A((void**)&area, sizeof(double) * nt);
     if (ce == cudaSuccess) ce = A((void**)&xi, sizeof(double) * 3 * nf);
     if (ce == cudaSuccess) ce = A((void**)&scratch, sizeof(double) * 6 * ns);
     if (ce == cudaSuccess) ce = A((void**)&err, sizeof(int));
     if (ce == cudaSuccess) ce = cudaMemsetAsync(err, 0, sizeof(int), stream);
     if (ce == cudaSuccess) {
         const int g = s->grid;
-        k_cell_geometry<<<g, kBlock, 0, stream>>>(xy, tri, nt, nv, c->area, ccx, ccy, err);
+        k_cell_geometry<<<g, kBlock, 0, stream>>>(xy, tri, nt, nv, area, ccx, ccy, err);
         k_xi<<<g, kBlock, 0, stream>>>(eps, kinv, nf, s->nu, s->dt, s->logk, xi, err);
         k_cp2_cell<<<g, kBlock, 0, stream>>>(xy, tri, nt, nv, eps, kinv, per_vertex, s->logk,
                                              s->nu, s->dt, c->rt0, c->mbar, err);
-        SideArgs sa{xy, tri, s->col, s->slot_kind, ccx, ccy, xi, nt, nv, per_vertex,
+        SideArgs sa{xy, tri, s->col, s->slot_kind, ccx, ccy, area, xi, nt, nv, per_vertex,
                     scratch, scratch + ns, scratch + 2 * ns, scratch + 3 * ns,
-                    scratch + 4 * ns, scratch + 5 * ns, c->lnx, c->lny, c->T, err};
+                    scratch + 4 * ns, scratch + 5 * ns, c->lnx, c->lny, c->T, c->wgt, err};
         k_cp2_side<<<g, kBlock, 0, stream>>>(sa);
         WeightArgs wa{s->col, s->slot_kind, sa.nx, sa.ny, sa.len, sa.dist, sa.dtx, sa.dty, nt,
                       c->tw, c->tidx, err};
@@ -417,7 +437,7 @@ int cp2_setup_impl(cps_sys s, const double* xy, const int32_t* tri, const double
         if (ce == cudaSuccess)
             ce = cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, stream);
     }
-    void* tmp[] = {ccx, ccy, xi, scratch, err};
+    void* tmp[] = {ccx, ccy, area, xi, scratch, err};
     for (void* p : tmp)
         if (p) cudaFreeAsync(p, stream);
     cudaError_t se = cudaStreamSynchronize(stream);
@@ -442,33 +462,51 @@ int cp2_step_impl(cps_sys s, const double* u23, const double* g_k, double* eta_t
     if (!u23 || !g_k || !eta || !u_next || !g_next)
         return fail(s, CPS_ERR_ARG, "cp2_step: null pointer");
     const int64_t nt = s->nt;
-    const int g = s->grid;
+    // one thread per cell: the step kernels are short, gather-heavy streams
+    const int g = (int)((nt + kBlock - 1) / kBlock);
     double* et = eta_tilde ? eta_tilde : c->eta_t;
     cps_stats st[2];
-    k_cp2_mean_flux<<<g, kBlock, 0, stream>>>(u23, s->col, s->slot_kind, c->area, c->lnx, c->lny,
-                                              nt, c->fbar, c->rhs);
+    // Events around each step kernel on the caller's stream; their durations
+    // are read after the final synchronisation (cps_cp2_kernel_times).
+    cudaEventRecord(c->ev[0], stream);
+    k_cp2_mean_flux<<<g, kBlock, 0, stream>>>(u23, s->col, c->wgt, c->lnx, c->lny, nt, c->fbar,
+                                              c->rhs);
+    cudaEventRecord(c->ev[1], stream);
     cudaError_t ce = cudaGetLastError();
     if (ce == cudaSuccess) ce = cudaMemsetAsync(et, 0, sizeof(double) * nt, stream);
     if (ce != cudaSuccess) return fail(s, CPS_ERR_CUDA, std::string("cp2_step: ") + cudaGetErrorString(ce));
     int rc1 = solve_impl(s, c->rhs, et, rtol, max_iter, precision, &st[0], stream);
     if (rc1 != CPS_OK && rc1 != CPS_ERR_NOT_CONVERGED) return rc1;
+    cudaEventRecord(c->ev[2], stream);
     k_cp2_tangential<<<g, kBlock, 0, stream>>>(et, s->col, c->tw, c->tidx, nt, c->tau, c->rhs);
+    cudaEventRecord(c->ev[3], stream);
     ce = cudaGetLastError();
     if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(eta, et, sizeof(double) * nt, cudaMemcpyDeviceToDevice, stream);
     if (ce != cudaSuccess) return fail(s, CPS_ERR_CUDA, std::string("cp2_step: ") + cudaGetErrorString(ce));
     int rc2 = solve_impl(s, c->rhs, eta, rtol, max_iter, precision, &st[1], stream);
     if (rc2 != CPS_OK && rc2 != CPS_ERR_NOT_CONVERGED) return rc2;
-    k_cp2_update<<<g, kBlock, 0, stream>>>(eta, s->col, s->slot_kind, c->fbar, c->T, c->tau,
-                                           c->rt0, c->mbar, u23, g_k, nt, flux, u_next, g_next);
+    cudaEventRecord(c->ev[4], stream);
+    k_cp2_update<<<g, kBlock, 0, stream>>>(eta, s->col, c->fbar, c->T, c->tau, c->rt0, c->mbar,
+                                           u23, g_k, nt, flux, u_next, g_next);
+    cudaEventRecord(c->ev[5], stream);
     ce = cudaGetLastError();
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
     if (ce != cudaSuccess) return fail(s, CPS_ERR_CUDA, std::string("cp2_step: ") + cudaGetErrorString(ce));
+    for (int k = 0; k < 3; ++k)
+        if (cudaEventElapsedTime(&c->kernel_ms[k], c->ev[2 * k], c->ev[2 * k + 1]) != cudaSuccess)
+            c->kernel_ms[k] = -1.f;
     if (stats) {
         stats[0] = st[0];
         stats[1] = st[1];
     }
     return rc1 != CPS_OK ? rc1 : rc2;
+}
+
+int cp2_kernel_times(cps_sys s, float* ms) {
+    if (!s->cp2 || !ms) return fail(s, CPS_ERR_ARG, "cp2_kernel_times: no CP2 step data");
+    for (int k = 0; k < 3; ++k) ms[k] = s->cp2->kernel_ms[k];
+    return CPS_OK;
 }
 
 }  // namespace cps

@@ -99,9 +99,9 @@ __global__ void k_xi(const double* __restrict__ eps, const double* __restrict__ 
 // like the matrix: slot j*nt + e is local side j of cell e.
 struct Cp2Data {
     void* buf = nullptr;
-    double* area = nullptr;   // [nt]
-    double* lnx = nullptr;    // [3nt] l_j n_j, x
-    double* lny = nullptr;    // [3nt] l_j n_j, y
+    double* wgt = nullptr;    // [3nt] A_ep/(A_e + A_ep) (1 on a boundary side)
+    double* lnx = nullptr;    // [3nt] l_j n_j, x (0 on a no-flux side)
+    double* lny = nullptr;    // [3nt] l_j n_j, y (0 on a no-flux side)
     double* T = nullptr;      // [3nt] side coefficient (interior, Dirichlet), 0 no-flux
     double* tw = nullptr;     // [4][3nt] co-normal weights of the tangential flux
     double* rt0 = nullptr;    // [6][nt] (centroid - x_j)/(2 A_e), j = 0..2, x then y
@@ -111,6 +111,8 @@ struct Cp2Data {
     double* rhs = nullptr;    // [nt] right-hand side of the current solve
     double* eta_t = nullptr;  // [nt] first solution when the caller keeps none
     int32_t* tidx = nullptr;  // [4][3nt] cell whose eta enters each weight (-1: eta = 0)
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    float kernel_ms[3] = {0.f, 0.f, 0.f};   // last step: mean flux, tangential, update
 };
 
 // Block-wide sum of v[0..NV) over BS threads (BS = blockDim.x); on return
@@ -328,5 +330,6 @@ int cp2_setup_impl(cps_sys sys, const double* xy, const int32_t* tri, const doub
 int cp2_step_impl(cps_sys sys, const double* u23, const double* g_k, double* eta_tilde,
                   double* eta, double* u_next, double* g_next, double* flux, double rtol,
                   int64_t max_iter, int precision, cps_stats* stats, cudaStream_t stream);
+int cp2_kernel_times(cps_sys sys, float* ms);
 
 }  // namespace cps
