@@ -24,6 +24,9 @@ Each function names the passage of the paper it follows:
   side flux (Eq. flux_k_+_2/3), the co-normal tangential flux of Xi grad eta
   (Eq. Cs2_6, Eq. eta_flux, App. C), the two systems of Eq. Cs2_7, the RT0
   cell velocity (Eq. RT0) and the eps grad Psi update (Eq. grad_PSI).
+* ``cp1_mass`` / ``cp1_laplacian`` / ``cp1_step`` -- the two CP1 systems
+  (Eq. cs1_sys2, Eq. CS1_sys_coeff) coupled through Mbar_12 and solved by the
+  outer iteration of App. B (Eq. A1).
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py``.
 """
@@ -99,6 +102,7 @@ def _load():
             lib.or_side_gradient.restype = None
             lib.or_theta_gradient.argtypes = [I64, P, I64, P, P, P, P, P, D, D, P, P]
             lib.or_cp2_mean_flux.argtypes = [I64, P, I64, P, P, P, P, P]
+            lib.or_cp1_mass.argtypes = [I64, P, I64, P, P, P, I, D, D, P]
             lib.or_cp2_tangential_flux.argtypes = [I64, P, I64, P, P, P, P, P, I, D, D, P, P]
             lib.or_cp2_update.argtypes = [I64, P, I64, P, P, P, P, P, I, D, D, P, P, P, P,
                                           P, P, P, P, P]
@@ -429,3 +433,98 @@ def cp2_step(problem, u23, g_k, rtol: float = 1e-13, dense: bool | None = None) 
     eta = solve(fbar.sum(axis=1) + tau.sum(axis=1), eta_t)
     Q, u_next, g_next = cp2_update(*args, *fields, fbar, T, tau, eta, u23, g_k)
     return CP2Step(fbar, eta_t, tau, eta, Q, u_next, g_next, A)
+
+
+# ------------------------------------------------------------------ CP1 step
+
+def cp1_mass(xy, tri, eps, kinv, field_loc, nu, dt) -> np.ndarray:
+    """[nt, 3]: (Mbar_11 A_e, Mbar_12 A_e, Mbar_22 A_e) per cell."""
+    xy, tri = _f64(xy), _i32(tri)
+    eps = _f64(eps)
+    kinv = _f64(kinv).reshape(-1, 3)
+    nt = tri.shape[0]
+    out = np.empty((nt, 3))
+    _check(_load().or_cp1_mass(xy.shape[0], _p(xy), nt, _p(tri), _p(eps), _p(kinv), field_loc,
+                               nu, dt, _p(out)), "cp1_mass")
+    return out
+
+
+def cp1_laplacian(T, nbr, is_dirichlet, u) -> np.ndarray:
+    """(nu L u)_e = sum_j T_j (u_e - u_ep), T_j = nu l_j / d_{e,ep}; a Dirichlet
+    side (zero increment at its midpoint) adds T_j u_e, a no-flux side
+    nothing -- the off-diagonal part of Eq. CS1_sys_coeff as an operator."""
+    u = _f64(u)
+    across = np.where(nbr >= 0, u[np.maximum(nbr, 0)], 0.0)
+    open_side = (nbr >= 0) | (is_dirichlet != 0)
+    return np.where(open_side, T * (u[:, None] - across), 0.0).sum(axis=1)
+
+
+@dataclass
+class CP1Step:
+    du: np.ndarray          # [2, nt] the converged increments (x row, y row)
+    outer: int              # outer iterations after the uncoupled start
+    err: float              # last err = min(err_x, err_y)
+    history: list           # err per outer iteration
+
+
+def cp1_step(problem, du_breve, toll: float = 1e-4, max_outer: int = 1000, rtol: float = 1e-13,
+             dense: bool | None = None, criterion: str = "min") -> CP1Step:
+    """The CP1 solves of one time step (Sec. 3.2.2, App. B).
+
+    Per component k (x, y) the system (Eq. cs1_sys2 with the coefficients of
+    Eq. CS1_sys_coeff) is
+        (Mbar_kk A_e + nu L) du_k = -nu L du_breve_k - Mbar_12 A_e du_other,
+    the right-hand side with the sign of Eq. CS1_new / CS1_2 written with the
+    outward normal derivative (a backward-Euler viscous update of the
+    predictor increment).  Eq. A1: i = 0 solves both with the coupling left
+    out; then both are solved again, each with the other's previous iterate,
+    until err = min(err_x, err_y) <= toll, err_k = ||du_k^{i+1} - du_k^i|| /
+    ||du_k^i|| (2-norms; 0/0 = 0).  ``criterion="max"`` stops on the larger
+    of the two instead (used by the pins to reach the coupled solution)."""
+    m = problem.mesh
+    if problem.field_loc not in (PER_VERTEX, PER_CELL):
+        raise ValueError("cp1_step takes vertex or cell fields")
+    f = (problem.eps, problem.kinv, problem.field_loc, problem.nu, problem.dt)
+    Ax = assemble(m.xy, m.tri, m.dirichlet, problem.eps, problem.kinv, problem.field_loc, CP1_X,
+                  problem.nu, problem.dt)
+    Ay = assemble(m.xy, m.tri, m.dirichlet, problem.eps, problem.kinv, problem.field_loc, CP1_Y,
+                  problem.nu, problem.dt)
+    T, _, isd, nbr = side_coefficients(m.xy, m.tri, m.dirichlet, *f[:3], CP1_X, f[3], f[4])
+    mass = cp1_mass(m.xy, m.tri, *f)
+    nt = m.tri.shape[0]
+    if dense is None:
+        dense = nt <= 2000
+    Dx, Dy = (Ax.dense(), Ay.dense()) if dense else (None, None)
+
+    def solve(A, D, b, x0):
+        if dense:
+            return dense_cholesky_solve(D, b)
+        x, st = pcg(A, b, x0=x0, rtol=rtol, raise_on_error=False)
+        if st.status not in (OK, ERR_NOT_CONVERGED):
+            raise OracleError(st.status, "pcg")
+        return x
+
+    du_breve = _f64(du_breve).reshape(2, nt)
+    lap = np.stack([-cp1_laplacian(T, nbr, isd, du_breve[0]),
+                    -cp1_laplacian(T, nbr, isd, du_breve[1])])
+    u = solve(Ax, Dx, lap[0], None)
+    v = solve(Ay, Dy, lap[1], None)
+
+    def rel(new, old):
+        d, o = np.linalg.norm(new - old), np.linalg.norm(old)
+        return 0.0 if d == 0.0 else (d / o if o > 0.0 else np.inf)
+
+    hist = []
+    it = 0
+    err = np.inf
+    while it < max_outer:
+        un = solve(Ax, Dx, lap[0] - mass[:, 1] * v, u)
+        vn = solve(Ay, Dy, lap[1] - mass[:, 1] * u, v)
+        ex, ey = rel(un, u), rel(vn, v)
+        err = min(ex, ey) if criterion == "min" else max(ex, ey)
+        u, v = un, vn
+        it += 1
+        hist.append(err)
+        if err <= toll:
+            break
+    return CP1Step(np.stack([u, v]), it, err, hist)

@@ -828,3 +828,47 @@ int or_cp2_update(int64_t nv, const double* xy, int64_t nt, const int32_t* tri,
     }
     return OR_OK;
 }
+
+/* ------------------------------------------------------------------ */
+/* 9. CP1 mass coupling (Sec. 3.2.2, Eq. cs1_sys2, App. B).             */
+/* ------------------------------------------------------------------ */
+
+/* Per cell the mass terms of the two CP1 systems and their coupling:
+ * out[3e+0] = Mbar_11 A_e, out[3e+1] = Mbar_12 A_e, out[3e+2] = Mbar_22 A_e,
+ * Mbar_e the mean over the cell's nodes of M = (I + nu eps Kinv dt)/dt (the
+ * cell's own M for cell fields). */
+int or_cp1_mass(int64_t nv, const double* xy, int64_t nt, const int32_t* tri,
+                const double* eps, const double* kinv, int field_loc, double nu, double dt,
+                double* out) {
+    if (field_loc != OR_PER_VERTEX && field_loc != OR_PER_CELL) return OR_ERR_ARG;
+    for (int64_t e = 0; e < nt; ++e) {
+        for (int k = 0; k < 3; ++k)
+            if (tri[e * 3 + k] < 0 || tri[e * 3 + k] >= nv) return OR_ERR_ARG;
+        const double* a = &xy[2 * (int64_t)tri[e * 3 + 0]];
+        const double* b = &xy[2 * (int64_t)tri[e * 3 + 1]];
+        const double* c = &xy[2 * (int64_t)tri[e * 3 + 2]];
+        double area = 0.5 * ((b[0] - a[0]) * (c[1] - a[1]) - (b[1] - a[1]) * (c[0] - a[0]));
+        double m00 = 0.0, m01 = 0.0, m11 = 0.0;
+        if (field_loc == OR_PER_VERTEX) {
+            for (int k = 0; k < 3; ++k) {
+                int64_t v = tri[e * 3 + k];
+                double cf = nu * eps[v] * dt;
+                m00 += (1.0 + cf * kinv[3 * v + 0]) / dt;
+                m01 += cf * kinv[3 * v + 1] / dt;
+                m11 += (1.0 + cf * kinv[3 * v + 2]) / dt;
+            }
+            m00 /= 3.0;
+            m01 /= 3.0;
+            m11 /= 3.0;
+        } else {
+            double cf = nu * eps[e] * dt;
+            m00 = (1.0 + cf * kinv[3 * e + 0]) / dt;
+            m01 = cf * kinv[3 * e + 1] / dt;
+            m11 = (1.0 + cf * kinv[3 * e + 2]) / dt;
+        }
+        out[3 * e + 0] = m00 * area;
+        out[3 * e + 1] = m01 * area;
+        out[3 * e + 2] = m11 * area;
+    }
+    return OR_OK;
+}
