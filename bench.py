@@ -97,6 +97,11 @@ def parse():
                          "after --warmup untimed ones (own line)")
     ap.add_argument("--cp2-precond", default="jacobi", choices=["jacobi", "ic0", "reduced"],
                     help="preconditioner of the CP2-step mode's solves")
+    ap.add_argument("--cp1-step", type=int, default=0,
+                    help="CP1-step mode: this many timed CP1 steps (x and y systems coupled "
+                         "through Mbar_12, outer iteration to --cp1-toll) on the --n lattice "
+                         "with no-slip walls, after --warmup untimed ones (own line)")
+    ap.add_argument("--cp1-toll", type=float, default=1e-4)
     ap.add_argument("--pin", default="",
                     help="profiling run only: pin the FP64 Jacobi configuration instead of "
                          "tuning it (a profiler's replay skews the tuner), as "
@@ -507,6 +512,73 @@ def run_cp2_step(args):
     print(json.dumps(line), flush=True)
 
 
+def run_cp1_step(args):
+    """Whole CP1 steps on the channel-block workload with no-slip walls: each
+    step takes a new predictor increment (seeded random-Fourier field) and
+    runs the outer iteration of App. B to --cp1-toll; the line reports steps
+    per second, outer sweeps and PCG iterations per step."""
+    import dataclasses
+    import torch
+    import paper_2309_03543_gb300 as cps
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    ctx = cps.Context(0)
+    p = synth.channel_block_problem(args.n, seed=0)
+    m = p.mesh
+    nbr = side_neighbours(m.tri)
+    e, j = np.nonzero(nbr < 0)
+    m = dataclasses.replace(m, dirichlet=(e * 3 + j).astype(np.int32))
+    nt = m.nt
+    sx = ctx.assemble(m.xy, m.tri, m.dirichlet, p.eps, p.kinv, p.field_loc, cps.KIND_CP1_X,
+                      p.nu, p.dt)
+    sy = ctx.assemble(m.xy, m.tri, m.dirichlet, p.eps, p.kinv, p.field_loc, cps.KIND_CP1_Y,
+                      p.nu, p.dt)
+    cps.cp1_setup(sx, sy, m.xy, m.tri, p.eps, p.kinv)
+    total = args.warmup + args.cp1_step
+    dus = [torch.as_tensor(synth.cell_vector_field(m, 200 + t, mean=(0.01, -0.02), scale=0.05),
+                           device=dev) for t in range(total)]
+    secs, outer, iters = [], [], []
+    for t in range(total):
+        dt_, (du, st) = timed(lambda: cps.cp1_step(sx, sy, dus[t], toll=args.cp1_toll,
+                                                   rtol=args.rtol, check=False), stream)
+        if t >= args.warmup:
+            secs.append(dt_)
+            outer.append(st["outer"])
+            iters.append(st["solve_iters"])
+    t_step = sum(secs) / len(secs)
+    sx.free()
+    sy.free()
+    line = {"metric": "CP1 steps per second (x and y solves coupled through Mbar_12, outer "
+                      "iteration of App. B)",
+            "value": 1.0 / t_step, "unit": "steps/s", "higher_is_better": True,
+            "ms_per_step": 1e3 * t_step, "steps": args.cp1_step, "warmup": args.warmup,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"channel-block-aniso lattice n={args.n}, no-slip walls",
+                       "cells": nt, "toll": args.cp1_toll, "rtol": args.rtol,
+                       "du_breve": "random-Fourier field + mean, seed 200+t"},
+            "outer_sweeps": outer, "solve_iters": iters,
+            "us_per_solve_iter": 1e6 * sum(secs) / max(sum(iters), 1)}
+    print(json.dumps(line), flush=True)
+
+
+def side_neighbours(tri):
+    """Neighbour across each local side (-1 on the boundary), by sorting the
+    sides' vertex pairs; host-side set-up of the no-slip wall list."""
+    nt = tri.shape[0]
+    a = tri[:, [1, 2, 0]].astype(np.int64)
+    b = tri[:, [2, 0, 1]].astype(np.int64)
+    key = np.minimum(a, b) * (int(tri.max()) + 1) + np.maximum(a, b)
+    flat = key.ravel()
+    order = np.argsort(flat, kind="stable")
+    sk = flat[order]
+    nbr = np.full(3 * nt, -1, dtype=np.int64)
+    same = np.flatnonzero(sk[1:] == sk[:-1])
+    s0, s1 = order[same], order[same + 1]
+    nbr[s0] = s1 // 3
+    nbr[s1] = s0 // 3
+    return nbr.reshape(nt, 3)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -523,6 +595,9 @@ def main():
         return
     if args.cp2_step:
         run_cp2_step(args)
+        return
+    if args.cp1_step:
+        run_cp1_step(args)
         return
     import torch
     import paper_2309_03543_gb300 as cps

@@ -248,6 +248,47 @@ int cps_cp2_step(cps_sys sys, const double* u23, const double* g_k, double* eta_
                  double* eta, double* u_next, double* g_next, double* flux, double rtol,
                  int64_t max_iter, int precision, cps_stats* stats, void* stream);
 
+/* ------------------------------------------------ CP1 step (two systems) */
+
+typedef struct {
+    int64_t outer;        /* outer sweeps after the uncoupled first one */
+    int64_t solve_iters;  /* PCG iterations of all solves */
+    double err;           /* last min(err_x, err_y) (App. B) */
+    double rel_res_max;   /* largest final relative residual of the solves */
+} cps_cp1_stats;
+
+/* Prepare the CP1 step (Sec. 3.2.2) on a pair of systems assembled with
+ * CPS_KIND_CP1_X (sys_x) and CPS_KIND_CP1_Y (sys_y) from the same mesh, fields
+ * and Dirichlet sides; pass the same xy, tri, eps and kinv (device pointers).
+ * Stores on sys_x the side coefficients nu l_j/d (nu l_j/delta on Dirichlet
+ * sides) and per cell Mbar_11 A_e, Mbar_12 A_e, Mbar_22 A_e (Mbar the mean over
+ * the cell's nodes of (I + nu eps Kinv dt)/dt).  Errors: CPS_ERR_ARG (kinds,
+ * sizes, contexts, null pointers), _NONDELAUNAY, _NOMEM, _CUDA. */
+int cps_cp1_setup(cps_sys sys_x, cps_sys sys_y, const double* xy, const int32_t* tri,
+                  const double* eps, const double* kinv, void* stream);
+
+/* The CP1 solves of one time step with the outer iteration of App. B (Eq. A1):
+ *   du_breve[2*nt]  predictor increment u^{k+1/3} - u^{k-1/3} per cell (x
+ *                   components, then y)
+ *   du[2*nt]        in: initial guess of the first solves (zeros for a cold
+ *                   start); out: the increment u^{k+2/3} - u^{k+1/3}
+ *   toll            outer tolerance (the paper uses 1e-4 .. 1e-3)
+ *   max_outer       bound on the outer sweeps after the first (0: the
+ *                   uncoupled first sweep only)
+ *   rtol, max_iter, precision   as cps_solve, for every solve
+ *   stats           host, may be NULL
+ * Each component solves (Mbar_kk A_e + nu L) du_k = -nu L du_breve_k -
+ * Mbar_12 A_e du_other, nu L the off-diagonal operator of the CP1 matrix
+ * (Eq. cs1_sys2, Eq. CS1_sys_coeff with the sign of Eq. CS1_2).  Sweep 0 drops
+ * the coupling; each later sweep solves both components with the other's
+ * previous iterate, warm-started, until min(err_x, err_y) <= toll, err_k =
+ * ||du_k^{i+1} - du_k^i||_2 / ||du_k^i||_2.  Needs cps_cp1_setup.  Errors: as
+ * cps_solve; CPS_ERR_NOT_CONVERGED also when max_outer sweeps end above toll
+ * (du holds the last iterate). */
+int cps_cp1_step(cps_sys sys_x, cps_sys sys_y, const double* du_breve, double* du, double toll,
+                 int64_t max_outer, double rtol, int64_t max_iter, int precision,
+                 cps_cp1_stats* stats, void* stream);
+
 /* Device durations in milliseconds (host ms[3]) of the last cps_cp2_step's
  * three step kernels -- mean flux, tangential flux, update -- from CUDA events
  * recorded around each on the step's stream (-1 if unavailable).

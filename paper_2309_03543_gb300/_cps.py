@@ -51,6 +51,11 @@ class Stats(ctypes.Structure):
                 ("launches", ctypes.c_int64)]
 
 
+class Cp1Stats(ctypes.Structure):
+    _fields_ = [("outer", ctypes.c_int64), ("solve_iters", ctypes.c_int64),
+                ("err", ctypes.c_double), ("rel_res_max", ctypes.c_double)]
+
+
 SIGNATURES = {
     "cps_create": (_I, [ctypes.POINTER(_P), _I]),
     "cps_destroy": (_I, [_P]),
@@ -68,6 +73,9 @@ SIGNATURES = {
     "cps_matvec": (_I, [_P, _P, _P, _P]),
     "cps_cp2_setup": (_I, [_P, _P, _P, _P, _P, _P]),
     "cps_cp2_kernel_times": (_I, [_P, _P]),
+    "cps_cp1_setup": (_I, [_P, _P, _P, _P, _P, _P, _P]),
+    "cps_cp1_step": (_I, [_P, _P, _P, _P, _D, _I64, _D, _I64, _I, ctypes.POINTER(Cp1Stats),
+                          _P]),
     "cps_cp2_step": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _D, _I64, _I, ctypes.POINTER(Stats),
                           _P]),
     "cps_get_tuning": (_I, [_P, _I, _P, _P, _P, _P, _P]),

@@ -268,6 +268,40 @@ class System:
         return lam, _stats(st)
 
 
+def cp1_setup(sys_x: System, sys_y: System, xy, tri, eps, kinv):
+    """Prepare the CP1 step on a CP1_X / CP1_Y pair assembled from the same
+    mesh, fields and Dirichlet sides (the data lives on sys_x)."""
+    d = sys_x.ctx.dev
+    xy_d, tri_d = d(xy, torch.float64), d(tri, torch.int32)
+    eps_d, kinv_d = d(eps, torch.float64), d(kinv, torch.float64)
+    rc = sys_x.ctx.lib.cps_cp1_setup(sys_x.handle, sys_y.handle, P(xy_d.data_ptr()),
+                                     P(tri_d.data_ptr()), P(eps_d.data_ptr()),
+                                     P(kinv_d.data_ptr()), _stream(sys_x.ctx.device))
+    sys_x.ctx.check(rc, "cps_cp1_setup")
+
+
+def cp1_step(sys_x: System, sys_y: System, du_breve, du=None, toll: float = 1e-4,
+             max_outer: int = 1000, rtol: float = 1e-10, max_iter: int = 1_000_000,
+             precision: int = _cps.FP64, check: bool = True):
+    """The CP1 solves of one step (Sec. 3.2.2) with the outer iteration of
+    App. B.  du_breve [2, nt] is the predictor increment; du (device [2, nt],
+    optional) is the initial guess and is overwritten.  Returns (du, stats
+    dict with outer, solve_iters, err, rel_res_max, status)."""
+    ctx = sys_x.ctx
+    nt = sys_x.nt
+    b = ctx.dev(du_breve, torch.float64).reshape(2, nt)
+    if du is None:
+        du = torch.zeros(2, nt, dtype=torch.float64, device=ctx.device)
+    st = _cps.Cp1Stats()
+    rc = ctx.lib.cps_cp1_step(sys_x.handle, sys_y.handle, P(b.data_ptr()), P(du.data_ptr()),
+                              toll, max_outer, rtol, max_iter, precision, ctypes.byref(st),
+                              _stream(ctx.device))
+    if check:
+        ctx.check(rc, "cps_cp1_step")
+    return du, {"outer": int(st.outer), "solve_iters": int(st.solve_iters), "err": float(st.err),
+                "rel_res_max": float(st.rel_res_max), "status": rc}
+
+
 def solve_batch(systems, bs, xs, rtol: float = 1e-10, max_iter: int = 1_000_000,
                 precision: int = _cps.FP64, check: bool = True):
     """Solve several systems (device tensors b, x per system) in one call."""

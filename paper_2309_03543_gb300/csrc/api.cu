@@ -172,6 +172,26 @@ int cps_cp2_step(cps_sys sys, const double* u23, const double* g_k, double* eta_
                               max_iter, precision, stats, as_stream(stream));
 }
 
+int cps_cp1_setup(cps_sys sys_x, cps_sys sys_y, const double* xy, const int32_t* tri,
+                  const double* eps, const double* kinv, void* stream) {
+    CallRange range_("cps_cp1_setup");
+    if (!sys_x) return CPS_ERR_ARG;
+    int rc = set_device(sys_x->ctx);
+    if (rc) return rc;
+    return cps::cp1_setup_impl(sys_x, sys_y, xy, tri, eps, kinv, as_stream(stream));
+}
+
+int cps_cp1_step(cps_sys sys_x, cps_sys sys_y, const double* du_breve, double* du, double toll,
+                 int64_t max_outer, double rtol, int64_t max_iter, int precision,
+                 cps_cp1_stats* stats, void* stream) {
+    CallRange range_("cps_cp1_step");
+    if (!sys_x) return CPS_ERR_ARG;
+    int rc = set_device(sys_x->ctx);
+    if (rc) return rc;
+    return cps::cp1_step_impl(sys_x, sys_y, du_breve, du, toll, max_outer, rtol, max_iter,
+                              precision, stats, as_stream(stream));
+}
+
 int cps_cp2_kernel_times(cps_sys sys, float* ms) {
     if (!sys) return CPS_ERR_ARG;
     return cps::cp2_kernel_times(sys, ms);

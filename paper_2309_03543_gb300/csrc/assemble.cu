@@ -346,6 +346,7 @@ static int dev_alloc(cps_ctx ctx, T** p, size_t n) {
 void free_sys(cps_sys s) {
     if (!s) return;
     free_cp2(s);
+    free_cp1(s);
     // s->col lives inside s->a's allocation (one range for the L2 window)
     void* bufs[] = {s->s,     s->diag,  s->a,     s->a32,     s->s32,      s->gfac,
                     s->dxi,   s->slot_kind, s->perm, s->iperm, s->pa,  s->pcol,     s->pl,

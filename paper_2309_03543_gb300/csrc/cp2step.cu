@@ -67,26 +67,11 @@ __global__ void k_cp2_cell(const double* __restrict__ xy, const int32_t* __restr
             rt0[(2 * j) * nt + e] = (gx - px[j]) / a2;
             rt0[(2 * j + 1) * nt + e] = (gy - py[j]) / a2;
         }
-        double m00 = 0.0, m01 = 0.0, m11 = 0.0;
-        if (per_vertex) {
-            for (int k = 0; k < 3; ++k) {
-                const double c = nu * eps[v[k]] * dt;
-                m00 += (1.0 + c * kinv_at(kinv, v[k], 0, false)) / dt;
-                m01 += c * kinv_at(kinv, v[k], 1, false) / dt;
-                m11 += (1.0 + c * kinv_at(kinv, v[k], 2, false)) / dt;
-            }
-            m00 /= 3.0;
-            m01 /= 3.0;
-            m11 /= 3.0;
-        } else {
-            const double c = nu * eps[e] * dt;
-            m00 = (1.0 + c * kinv_at(kinv, e, 0, logk)) / dt;
-            m01 = c * kinv_at(kinv, e, 1, logk) / dt;
-            m11 = (1.0 + c * kinv_at(kinv, e, 2, logk)) / dt;
-        }
-        mbar[e] = m00;
-        mbar[nt + e] = m01;
-        mbar[2 * nt + e] = m11;
+        double mb[3];
+        cell_mbar(eps, kinv, v, e, per_vertex, logk, nu, dt, mb);
+        mbar[e] = mb[0];
+        mbar[nt + e] = mb[1];
+        mbar[2 * nt + e] = mb[2];
     }
 }
 

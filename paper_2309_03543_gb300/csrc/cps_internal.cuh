@@ -86,6 +86,35 @@ __device__ __forceinline__ double kinv_at(const double* __restrict__ kinv, int64
     return kinv[3 * i + comp];
 }
 
+// Mbar_e (xx, xy, yy): the mean over the cell's nodes v[0..3) of
+// M = (I + nu eps Kinv dt)/dt, or the cell's own M for cell fields (Sec. 3.1,
+// Sec. 3.2 cell averages).
+__device__ __forceinline__ void cell_mbar(const double* __restrict__ eps,
+                                          const double* __restrict__ kinv, const int64_t* v,
+                                          int64_t e, bool per_vertex, bool logk, double nu,
+                                          double dt, double* m) {
+    double m00 = 0.0, m01 = 0.0, m11 = 0.0;
+    if (per_vertex) {
+        for (int k = 0; k < 3; ++k) {
+            const double c = nu * eps[v[k]] * dt;
+            m00 += (1.0 + c * kinv_at(kinv, v[k], 0, false)) / dt;
+            m01 += c * kinv_at(kinv, v[k], 1, false) / dt;
+            m11 += (1.0 + c * kinv_at(kinv, v[k], 2, false)) / dt;
+        }
+        m00 /= 3.0;
+        m01 /= 3.0;
+        m11 /= 3.0;
+    } else {
+        const double c = nu * eps[e] * dt;
+        m00 = (1.0 + c * kinv_at(kinv, e, 0, logk)) / dt;
+        m01 = c * kinv_at(kinv, e, 1, logk) / dt;
+        m11 = (1.0 + c * kinv_at(kinv, e, 2, logk)) / dt;
+    }
+    m[0] = m00;
+    m[1] = m01;
+    m[2] = m11;
+}
+
 // Per cell area and circumcentre (Sec. 3.1); CPS_ERR_ARG / _ORIENTATION in err.
 __global__ void k_cell_geometry(const double* __restrict__ xy, const int32_t* __restrict__ tri,
                                 int64_t nt, int64_t nv, double* __restrict__ area,
@@ -93,6 +122,19 @@ __global__ void k_cell_geometry(const double* __restrict__ xy, const int32_t* __
 // Xi = eps dt (I + nu eps dt Kinv)^-1 at nf field points (Eq. Cs2_4), [nf][3].
 __global__ void k_xi(const double* __restrict__ eps, const double* __restrict__ kinv, int64_t nf,
                      double nu, double dt, bool logk, double* __restrict__ xi, int* err);
+
+// Data of the CP1 step (Sec. 3.2.2, App. B), set up once per pair of CP1
+// systems (kept on the x system).  Slot-major like the matrix.
+struct Cp1Data {
+    void* buf = nullptr;
+    double* T = nullptr;      // [3nt] nu l_j / d (interior), nu l_j / delta (Dirichlet), 0
+    double* mass = nullptr;   // [3][nt] Mbar_11 A_e, Mbar_12 A_e, Mbar_22 A_e
+    double* lap = nullptr;    // [2][nt] -nu L du_breve (x, y)
+    double* rhs = nullptr;    // [2][nt]
+    double* prev = nullptr;   // [2][nt] previous iterate
+    double* partials = nullptr;  // [kMaxGrid][4] + [4] error sums
+    int64_t nt = 0;
+};
 
 // Data of the CP2 step around the two solves (Sec. 3.2.3), set up once per
 // system by cps_cp2_setup; every array is a slice of buf.  Slot-major [k][nt]
@@ -214,6 +256,7 @@ struct cps_sys_s {
     bool iso_cell = false;      // CPS_PER_CELL with isotropic Kinv (adjoint theta chain)
     bool logk = false;          // assembled from CPS_PER_CELL_LOGK (kinv holds theta)
     cps::Cp2Data* cp2 = nullptr;  // CP2 step data (cps_cp2_setup)
+    cps::Cp1Data* cp1 = nullptr;  // CP1 step data (cps_cp1_setup, on the x system)
     int64_t assembly_launches = 0;
 
     // Matrix in symmetrically scaled padded-ELL form: A = S (I + Aoff) S with
@@ -331,5 +374,11 @@ int cp2_step_impl(cps_sys sys, const double* u23, const double* g_k, double* eta
                   double* eta, double* u_next, double* g_next, double* flux, double rtol,
                   int64_t max_iter, int precision, cps_stats* stats, cudaStream_t stream);
 int cp2_kernel_times(cps_sys sys, float* ms);
+void free_cp1(cps_sys sys);
+int cp1_setup_impl(cps_sys sx, cps_sys sy, const double* xy, const int32_t* tri,
+                   const double* eps, const double* kinv, cudaStream_t stream);
+int cp1_step_impl(cps_sys sx, cps_sys sy, const double* du_breve, double* du, double toll,
+                  int64_t max_outer, double rtol, int64_t max_iter, int precision,
+                  cps_cp1_stats* stats, cudaStream_t stream);
 
 }  // namespace cps
