@@ -310,7 +310,12 @@ int cps_cp2_kernel_times(cps_sys sys, float* ms);
  *     persisting L2 during the solve; CPS_ERR_ARG if the GPU's persisting
  *     set-aside cannot hold them;
  *   CPS_PATH_PERSISTENT_L2: the persistent launch with r, p, q in persisting
- *     L2 (CPS_ERR_ARG as above).
+ *     L2 (CPS_ERR_ARG as above);
+ *   CPS_PATH_CLUSTER_1RED (FP64 Jacobi only): the one-cluster launch with the
+ *     single-reduction (Chronopoulos-Gear) recurrences -- s = A p and w = A r
+ *     are carried so that both inner products of an iteration come from one
+ *     SpMV (two cluster barriers per iteration instead of three; one more
+ *     vector in shared memory, so a somewhat smaller size limit).
  * IC(0) and mixed precision always stream. */
 #define CPS_PATH_AUTO 0
 #define CPS_PATH_STREAM 1
@@ -318,6 +323,7 @@ int cps_cp2_kernel_times(cps_sys sys, float* ms);
 #define CPS_PATH_PERSISTENT 3
 #define CPS_PATH_STREAM_L2 4
 #define CPS_PATH_PERSISTENT_L2 5
+#define CPS_PATH_CLUSTER_1RED 6
 int cps_set_solver_path(cps_sys sys, int path);
 
 /* Pin the launch shapes of the iteration kernels of one precision instead of
@@ -350,7 +356,8 @@ int cps_test_inject(cps_sys sys, int fault);
  * the system's own data at its first solve; systems below 131072 cells keep
  * the defaults (unroll 2, 8 blocks per SM).  For CPS_FP64 Jacobi solves it
  * also times the ways of running the loop: flags (may be NULL, 5 entries)
- * receives {one-cluster launch chosen, persisting-L2 window (0 none, 1 the
+ * receives {one-cluster launch chosen (0 no, 1 textbook recurrences, 2 the
+ * single-reduction recurrences), persisting-L2 window (0 none, 1 the
  * matrix, 2 the vectors r, p, q), persistent launch chosen, reduced system:
  * persistent launch chosen, reduced system: window (0 or 2)}, probe_us (may
  * be NULL, 10 entries) the microseconds per iteration measured for
@@ -358,7 +365,7 @@ int cps_test_inject(cps_sys sys, int fault);
  * vectors in L2, persistent + vectors in L2, reduced system: streaming,
  * persistent, streaming + vectors in L2, persistent + vectors in L2} (0
  * where not tried; the persistent figures are the best over the grid sizes
- * tried).
+ * tried, the one-cluster figure the better of its two recurrences).
  * The context remembers what the tuner chose per mesh size (cells,
  * vertices): a system assembled later on the same context with the same
  * sizes starts from those choices and is not timed again.  A path forced by

@@ -144,7 +144,8 @@ class System:
         self.ctx.check(self.ctx.lib.cps_get_tuning(self.handle, precision, u, g, bl, f, pr),
                        "cps_get_tuning")
         return {"unroll": list(u), "grid": list(g), "block": list(bl),
-                "cluster": bool(f[0]), "l2_window": ("none", "matrix", "vectors")[f[1]],
+                "cluster": bool(f[0]),
+                "cluster_recurrence": (None, "textbook", "single_reduction")[f[0]], "l2_window": ("none", "matrix", "vectors")[f[1]],
                 "persistent": bool(f[2]), "reduced_persistent": bool(f[3]),
                 "reduced_l2_window": ("none", "matrix", "vectors")[f[4]],
                 "probe_us_per_iter": {

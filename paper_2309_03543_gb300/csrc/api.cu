@@ -255,14 +255,16 @@ int cps_set_solver_path(cps_sys sys, int path) {
         t.red_done = true;
         t.red_path = 0;
         t.red_win = 2;
-    } else if (path == CPS_PATH_CLUSTER) {
-        if (sys->nt > cps::cluster_max_rows(sys->ctx)) {
+    } else if (path == CPS_PATH_CLUSTER || path == CPS_PATH_CLUSTER_1RED) {
+        const int var = path == CPS_PATH_CLUSTER_1RED ? 1 : 0;
+        if (sys->nt > cps::cluster_max_rows(sys->ctx, var)) {
             cps::set_error(sys->ctx, "set_solver_path: system too large for one cluster");
             return CPS_ERR_ARG;
         }
         t.path_done = true;
         t.path = 1;
         t.l2win = 0;
+        t.cluster_variant = var;
     } else {
         return CPS_ERR_ARG;
     }
@@ -313,7 +315,7 @@ int cps_get_tuning(cps_sys sys, int precision, int32_t* unroll, int32_t* grid, i
         if (block) block[k] = t.done ? t.k[k].block : 0;
     }
     if (flags) {
-        flags[0] = t.path_done && t.path == 1;
+        flags[0] = (t.path_done && t.path == 1) ? 1 + t.cluster_variant : 0;
         flags[1] = t.path_done ? t.l2win : 0;
         flags[2] = t.path_done && t.path == 2;
         flags[3] = t.red_done && t.red_path == 1;

@@ -16,6 +16,15 @@
 // Iteration (3 cluster barriers):
 //   q = Ahat p, gamma = p.q | alpha = rho/gamma; r -= alpha q; y += alpha p;
 //   rho' = r.r (and ||S r||^2) | beta = rho'/rho; stop test; p = r + beta p |
+//
+// Single-reduction variant (Chronopoulos-Gear recurrences; 2 cluster barriers):
+// the CTA also keeps s = Ahat p and w = Ahat r, so that both inner products of
+// an iteration come out of the one SpMV:
+//   p = r + beta p; s = w + beta s; y += alpha p; r -= alpha s |
+//   w = Ahat r, gamma = r.r, delta = w.r (and ||S r||^2) |
+//   beta = gamma/gamma_old, alpha = gamma/(delta - beta gamma/alpha_old).
+// Same iterates as the textbook recurrence in exact arithmetic; one barrier
+// fewer per iteration for the latency-bound small systems this path serves.
 #include "cps_internal.cuh"
 
 #include <cooperative_groups.h>
@@ -244,11 +253,183 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_cluster_cg(ClusterArgs A
     cluster.sync();         // no CTA leaves while others may still read its memory
 }
 
+// Single-reduction layout: a [3][R], p, r, y, w, q (= Ahat p), s [R] doubles,
+// col [3][R] int32, then the reduction buffer.
+constexpr size_t kRowBytes1 = 3 * sizeof(double) + 3 * sizeof(int32_t) + 6 * sizeof(double);
+__host__ __device__ inline size_t cluster1_red_offset(int R) {
+    return ((size_t)R * kRowBytes1 + 15) / 16 * 16;
+}
+__host__ __device__ inline size_t cluster1_smem_bytes(int R) {
+    return cluster1_red_offset(R) + kRedBufBytes;
+}
+
+__global__ void __launch_bounds__(kClusterThreads, 1) k_cluster_cg1(ClusterArgs A) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int C = (int)cluster.num_blocks();
+    const int rank = (int)cluster.block_rank();
+    const int R = A.rows;
+    const int64_t n = A.n;
+    const int64_t r0 = (int64_t)rank * R;
+    const int nloc = (int)((r0 + R <= n) ? R : (n > r0 ? n - r0 : 0));
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    double* a_s = reinterpret_cast<double*>(smem);          // [3][R]
+    double* p_s = a_s + 3 * R;
+    double* r_s = p_s + R;
+    double* y_s = r_s + R;
+    double* w_s = y_s + R;
+    double* q_s = w_s + R;
+    double* s_s = q_s + R;
+    int32_t* c_s = reinterpret_cast<int32_t*>(s_s + R);      // [3][R] packed (rank << 16) | local
+    double* rbuf = reinterpret_cast<double*>(smem + cluster1_red_offset(R));
+    __shared__ double red[4][16];   // red[k][c]: partial k of CTA c
+    __shared__ double tot[4];
+    __shared__ double sc[2];        // alpha, beta, derived once per CTA by thread 0
+    __shared__ int s_stop;
+
+    const int tid = threadIdx.x;
+    for (int i = tid; i < nloc; i += blockDim.x) {
+        const int64_t e = r0 + i;
+        for (int j = 0; j < 3; ++j) {
+            a_s[j * R + i] = A.a[j * n + e];
+            const int32_t c = A.col[j * n + e];
+            const int cr = c / R;
+            c_s[j * R + i] = (cr << 16) | (c - cr * R);
+        }
+        const double se = A.s[e];
+        s_s[i] = se;
+        y_s[i] = se * A.x[e];
+        p_s[i] = 0.0;
+        q_s[i] = 0.0;
+    }
+    cluster.sync();
+    auto gather = [&](double* base, int32_t packed) -> double {
+        const int cr = packed >> 16, li = packed & 0xFFFF;
+        if (cr == rank) return base[li];
+        return cluster.map_shared_rank(base, cr)[li];
+    };
+    auto push = [&](int k, double v) {
+        if (tid < C) cluster.map_shared_rank(&red[k][0], tid)[rank] = v;
+    };
+    auto cluster_sum = [&](int k) -> double {
+        double t = 0.0;
+        for (int c = 0; c < C; ++c) t += red[k][c];
+        return t;
+    };
+
+    // r = S^-1 b - Ahat y; ||b||^2, ||S r||^2
+    {
+        double v1[1] = {0.0};
+        for (int i = tid; i < nloc; i += blockDim.x) {
+            double ay = y_s[i];
+            for (int j = 0; j < 3; ++j) ay = fma(a_s[j * R + i], gather(y_s, c_s[j * R + i]), ay);
+            const double be = A.b[r0 + i];
+            r_s[i] = be / s_s[i] - ay;
+            v1[0] = fma(be, be, v1[0]);
+        }
+        block_sum_buf<1>(v1, rbuf, tot);
+        push(3, v1[0]);
+    }
+    cluster.sync();         // r complete everywhere
+    // w = Ahat r, gamma = r.r, delta = w.r, ||S r||^2
+    auto spmv_dots = [&](bool norm) {
+        double v3[3] = {0.0, 0.0, 0.0};
+        for (int i = tid; i < nloc; i += blockDim.x) {
+            const double re = r_s[i];
+            double v = re;
+            for (int j = 0; j < 3; ++j) v = fma(a_s[j * R + i], gather(r_s, c_s[j * R + i]), v);
+            w_s[i] = v;
+            v3[0] = fma(re, re, v3[0]);
+            v3[1] = fma(v, re, v3[1]);
+            if (norm) {
+                const double t = s_s[i] * re;
+                v3[2] = fma(t, t, v3[2]);
+            }
+        }
+        block_sum_buf<3>(v3, rbuf, tot);
+        push(0, v3[0]);
+        push(1, v3[1]);
+        push(2, v3[2]);
+    };
+    spmv_dots(true);
+    cluster.sync();
+    double gamma = 0.0, alpha = 0.0, bnorm2 = 0.0, rnorm2 = 0.0, thresh2 = 0.0;
+    int status = CPS_OK;
+    if (tid == 0) {
+        gamma = cluster_sum(0);
+        const double delta = cluster_sum(1);
+        rnorm2 = cluster_sum(2);
+        bnorm2 = cluster_sum(3);
+        thresh2 = A.rtol * A.rtol * bnorm2;
+        int stop = (bnorm2 == 0.0 || rnorm2 <= thresh2 || A.max_iter <= 0) ? 1 : 0;
+        if (!stop && (!(delta > 0.0) || !isfinite(delta))) stop = 2;
+        alpha = stop ? 0.0 : gamma / delta;
+        sc[0] = alpha;
+        sc[1] = 0.0;
+        s_stop = stop;
+    }
+    __syncthreads();
+    long long it = 0;
+    int stop = s_stop;
+    if (stop == 2) status = CPS_ERR_NOT_SPD;
+    while (!stop) {
+        const double al = sc[0], be = sc[1];
+        for (int i = tid; i < nloc; i += blockDim.x) {
+            const double pe = fma(be, p_s[i], r_s[i]);
+            const double qe = fma(be, q_s[i], w_s[i]);
+            p_s[i] = pe;
+            q_s[i] = qe;
+            y_s[i] = fma(al, pe, y_s[i]);
+            r_s[i] = fma(-al, qe, r_s[i]);
+        }
+        cluster.sync();     // new r everywhere; last step's partials read
+        ++it;
+        const bool check = (it % kCheck) == 0;
+        spmv_dots(check);
+        cluster.sync();
+        if (tid == 0) {
+            const double g = cluster_sum(0);
+            const double delta = cluster_sum(1);
+            int halt = (!(g > 0.0) || it >= A.max_iter) ? 1 : 0;
+            if (check) {
+                rnorm2 = cluster_sum(2);
+                if (rnorm2 <= thresh2) halt = 1;
+            }
+            const double beta = g / gamma;
+            const double den = delta - beta * g / alpha;
+            if (!halt && (!(den > 0.0) || !isfinite(den))) halt = 2;
+            alpha = halt ? alpha : g / den;
+            gamma = g;
+            sc[0] = alpha;
+            sc[1] = beta;
+            s_stop = halt;
+        }
+        __syncthreads();
+        stop = s_stop;
+        if (stop == 2) status = CPS_ERR_NOT_SPD;
+    }
+    for (int i = tid; i < nloc; i += blockDim.x) A.y_out[r0 + i] = y_s[i];
+    if (rank == 0 && tid == 0) {
+        CgState* st = A.st;
+        st->rho = gamma;
+        st->bnorm2 = bnorm2;
+        st->thresh2 = thresh2;
+        st->rnorm2 = rnorm2;
+        st->iter = it;
+        st->max_iter = A.max_iter;
+        st->status = status;
+        st->done = 2;
+        st->alpha = 0.0;
+        st->beta = 0.0;
+    }
+    cluster.sync();         // no CTA leaves while others may still read its memory
+}
+
 }  // namespace
 
-// Dynamic shared memory a CTA of k_cluster_cg may use on this device: the
-// opt-in limit minus the kernel's static shared memory.
-static size_t cluster_dyn_smem_limit(int dev) {
+// Dynamic shared memory a CTA of the cluster kernel may use on this device:
+// the opt-in limit minus the kernel's static shared memory.
+static size_t cluster_dyn_smem_limit(int dev, int variant) {
     int smem_optin = 0;
     if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
         cudaSuccess) {
@@ -256,42 +437,45 @@ static size_t cluster_dyn_smem_limit(int dev) {
         return 0;
     }
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, k_cluster_cg) != cudaSuccess) {
+    if (cudaFuncGetAttributes(&fa, variant ? k_cluster_cg1 : k_cluster_cg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     return (size_t)smem_optin > fa.sharedSizeBytes ? (size_t)smem_optin - fa.sharedSizeBytes : 0;
 }
 
-// Largest system the cluster path takes on this GPU (0: not available).
-int64_t cluster_max_rows(cps_ctx ctx) {
-    const size_t lim = cluster_dyn_smem_limit(ctx->device);
+// Largest system the cluster path (variant 0 textbook, 1 single reduction)
+// takes on this GPU (0: not available).
+int64_t cluster_max_rows(cps_ctx ctx, int variant) {
+    const size_t lim = cluster_dyn_smem_limit(ctx->device, variant);
     const size_t fixed = kRedBufBytes + 16;
     if (lim <= fixed) return 0;
-    const int64_t R = (int64_t)((lim - fixed) / kRowBytes);
+    const int64_t R = (int64_t)((lim - fixed) / (variant ? kRowBytes1 : kRowBytes));
     return std::min<int64_t>(R, 0xFFFF) * 16;
 }
 
 // Runs a whole FP64 Jacobi solve (from x) in one cluster launch; leaves the
 // scaled iterate in y and the final scalars in s->st (done = 2).
 int cluster_solve(cps_sys s, const double* b, const double* x, double* y, double rtol,
-                  long long max_iter, cudaStream_t stream) {
-    static std::atomic<bool> configured[64];   // zero-initialised (static storage)
+                  long long max_iter, cudaStream_t stream, int variant) {
+    static std::atomic<bool> configured[2][64];   // zero-initialised (static storage)
+    variant = variant ? 1 : 0;
+    void (*kern)(ClusterArgs) = variant ? k_cluster_cg1 : k_cluster_cg;
     const int64_t n = s->nt;
     int csize = 16;
     cudaError_t e = cudaSuccess;
     const int dev = s->ctx->device;
-    const size_t lim = cluster_dyn_smem_limit(dev);
-    if (!configured[dev & 63].load()) {
-        e = cudaFuncSetAttribute(k_cluster_cg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
+    const size_t lim = cluster_dyn_smem_limit(dev, variant);
+    if (!configured[variant][dev & 63].load()) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_cluster_cg, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) {
             cudaGetLastError();
             cps::set_error(s->ctx, std::string("cluster path: ") + cudaGetErrorString(e));
             return CPS_ERR_ARG;
         }
-        configured[dev & 63].store(true);
+        configured[variant][dev & 63].store(true);
     }
     ClusterArgs A;
     A.a = s->a;
@@ -306,7 +490,8 @@ int cluster_solve(cps_sys s, const double* b, const double* x, double* y, double
     A.max_iter = max_iter;
     for (; csize >= 2; csize /= 2) {
         const int R = (int)((n + csize - 1) / csize);
-        if (R > 0xFFFF || cluster_smem_bytes(R) > lim) continue;
+        const size_t smem = variant ? cluster1_smem_bytes(R) : cluster_smem_bytes(R);
+        if (R > 0xFFFF || smem > lim) continue;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(csize, 1, 1);
         // one row per thread where the rows allow (fewer threads: cheaper
@@ -314,7 +499,7 @@ int cluster_solve(cps_sys s, const double* b, const double* x, double* y, double
         const int threads =
             R >= kClusterThreads ? kClusterThreads : (R < 128 ? 128 : (R + 31) / 32 * 32);
         cfg.blockDim = dim3(threads, 1, 1);
-        cfg.dynamicSmemBytes = cluster_smem_bytes(R);
+        cfg.dynamicSmemBytes = smem;
         cfg.stream = stream;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -324,13 +509,13 @@ int cluster_solve(cps_sys s, const double* b, const double* x, double* y, double
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int nclusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&nclusters, k_cluster_cg, &cfg) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess ||
             nclusters < 1) {
             cudaGetLastError();
             continue;
         }
         A.rows = R;
-        e = cudaLaunchKernelEx(&cfg, k_cluster_cg, A);
+        e = cudaLaunchKernelEx(&cfg, kern, A);
         if (e != cudaSuccess) {
             cudaGetLastError();
             cps::set_error(s->ctx, std::string("cluster launch: ") + cudaGetErrorString(e));

@@ -71,6 +71,7 @@ struct Tuning {
     int red_win = 0;         // reduced system: persisting L2 window (0 none, 2 r, p, q)
     int pgrid = 0;           // blocks of the persistent launch (0: all that stay resident)
     int red_pgrid = 0;       // the same for the reduced system
+    int cluster_variant = 0; // one-cluster launch: 0 textbook CG, 1 single reduction
 };
 
 // Device error flag written by the assembly kernels (first error wins).
@@ -355,9 +356,10 @@ int adjoint_impl(cps_sys sys, const double* x, const double* g, double* lambda, 
                  double* dtheta, double rtol, int64_t max_iter, cps_stats* stats,
                  cudaStream_t stream);
 int matvec_impl(cps_sys sys, const double* x, double* y, cudaStream_t stream);
-int64_t cluster_max_rows(cps_ctx ctx);
+int64_t cluster_max_rows(cps_ctx ctx, int variant = 0);
 int cluster_solve(cps_sys s, const double* b, const double* x, double* y, double rtol,
-                  long long max_iter, cudaStream_t stream);
+                  long long max_iter, cudaStream_t stream,
+                  int variant = 0);
 int persistent_solve(cps_sys s, int reduced, const double* a, const int32_t* col,
                      const double* sc, double* y, double* r, double* p, double* q, double* t,
                      int64_t n, int64_t nR, const void* win_base, size_t win_bytes, int grid,

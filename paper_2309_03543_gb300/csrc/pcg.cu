@@ -556,14 +556,16 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
     // persistent launch is timed at a few grid sizes (fewer blocks
     // synchronise faster; more blocks move more bytes).
     struct Cand {
-        int slot, path, win, grid;
+        int slot, path, win, grid, var;
     };
     Cand cands[16];
     int nc = 0;
-    cands[nc++] = {0, 0, 0, 0};
-    if (try_cluster) cands[nc++] = {1, 1, 0, 0};
-    if (big && l2_window_fits(s, 1)) cands[nc++] = {2, 0, 1, 0};
-    if (big && l2_window_fits(s, 2)) cands[nc++] = {4, 0, 2, 0};
+    cands[nc++] = {0, 0, 0, 0, 0};
+    if (try_cluster) cands[nc++] = {1, 1, 0, 0, 0};
+    // the single-reduction cluster solve (one barrier fewer per iteration)
+    if (s->nt <= cluster_max_rows(s->ctx, 1)) cands[nc++] = {1, 1, 0, 0, 1};
+    if (big && l2_window_fits(s, 1)) cands[nc++] = {2, 0, 1, 0, 0};
+    if (big && l2_window_fits(s, 2)) cands[nc++] = {4, 0, 2, 0, 0};
     {
         const int gmax = persistent_max_grid(s, 0);
         int grids[3] = {gmax, (int)((s->nt + 8191) / 8192), (int)((s->nt + 2047) / 2048)};
@@ -573,8 +575,8 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
             for (int j = 0; j < i; ++j) dup = dup || grids[j] == gi;
             grids[i] = gi;
             if (dup) continue;
-            cands[nc++] = {3, 2, 0, gi};
-            if (big && l2_window_fits(s, 2)) cands[nc++] = {5, 2, 2, gi};
+            cands[nc++] = {3, 2, 0, gi, 0};
+            if (big && l2_window_fits(s, 2)) cands[nc++] = {5, 2, 2, gi, 0};
         }
     }
     cudaEvent_t e0, e1;
@@ -582,7 +584,7 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
     CPS_CUDA_TRY(s->ctx, cudaEventCreate(&e1));
     double per_iter[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     double best_t = 0.0;
-    Cand best{0, 0, 0, 0};
+    Cand best{0, 0, 0, 0, 0};
     int rc = CPS_OK;
     cudaGraphExec_t ge = nullptr;
     int64_t per_chunk = 0, dummy = 0;
@@ -610,7 +612,7 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
                                                          v.p0, 0.0, probe, 1, s->partials, s->st);
                 rc = run_chunks<double>(s, CPS_FP64, v, stream, &h, &dummy);
             } else {
-                rc = cluster_solve(s, b, s->wx, v.y, 0.0, probe, stream);
+                rc = cluster_solve(s, b, s->wx, v.y, 0.0, probe, stream, c.var);
                 if (rc == CPS_OK) rc = read_state(s, stream, &h);
             }
             CPS_CUDA_TRY(s->ctx, cudaEventRecord(e1, stream));
@@ -642,6 +644,7 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
         t.path = best.path;
         t.l2win = best.win;
         t.pgrid = best.grid;
+        t.cluster_variant = best.var;
     }
     for (int k = 0; k < 6; ++k) t.probe_us[k] = per_iter[k];
     if (rc == CPS_OK) {
@@ -650,6 +653,7 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
             c.path = t.path;
             c.l2win = t.l2win;
             c.pgrid = t.pgrid;
+            c.cluster_variant = t.cluster_variant;
             for (int k = 0; k < 6; ++k) c.probe_us[k] = t.probe_us[k];
         });
     }
@@ -693,7 +697,8 @@ static int solve_fp64(cps_sys s, const double* b, double* x, double rtol, int64_
     for (int restart = 0; restart < 8; ++restart) {
         const long long budget = (long long)(max_iter - total);
         if (cluster) {
-            int rc = cluster_solve(s, bb, xx, v.y, rtol, budget, stream);
+            int rc = cluster_solve(s, bb, xx, v.y, rtol, budget, stream,
+                                   s->tune[CPS_FP64].cluster_variant);
             if (rc) return rc;
             ++launches;
             CgState hc{};

@@ -303,16 +303,20 @@ def test_batched_solve_matches_oracle_per_system(ctx):
         s.free()
 
 
+@pytest.mark.parametrize("path", ["textbook", "single_reduction"])
 @pytest.mark.parametrize("name", ["block37", "channel64", "defect20"])
-def test_cluster_path_matches_oracle(ctx, name):
+def test_cluster_path_matches_oracle(ctx, name, path):
     """The one-launch cluster solve (system held in the cluster's shared
-    memory, neighbours read through distributed shared memory) against the
-    oracle, and against the streaming path on the same system."""
+    memory, neighbours read through distributed shared memory), with the
+    textbook and with the single-reduction recurrences, against the oracle,
+    and against the streaming path on the same system (same iterates in
+    exact arithmetic, so nearly the same iteration count)."""
+    cluster = cps.PATH_CLUSTER if path == "textbook" else cps.PATH_CLUSTER_1RED
     p = PROBLEMS[name]
     s = assemble(ctx, p)
     b = synth.rhs(p.mesh, 23)
     bt = torch.as_tensor(b, device="cuda")
-    s.set_solver_path(cps.PATH_CLUSTER)
+    s.set_solver_path(cluster)
     x, st = s.solve(bt, rtol=1e-12, check=False)
     assert st.status in (0, cps._cps.ERR_NOT_CONVERGED) and st.rel_res < 1e-10
     xo, _, _ = oracle.solve_problem(p, b, rtol=1e-13)
@@ -322,7 +326,7 @@ def test_cluster_path_matches_oracle(ctx, name):
     x2, st2 = s.solve(bt, rtol=1e-12, check=False)
     assert abs(st2.iters - st.iters) <= max(8, 0.02 * st.iters)
     # warm start and zero right-hand side on the cluster path
-    s.set_solver_path(cps.PATH_CLUSTER)
+    s.set_solver_path(cluster)
     x3 = x.clone()
     _, st3 = s.solve(bt, x=x3, rtol=1e-8)
     assert st3.iters == 0
@@ -338,8 +342,9 @@ def test_cluster_path_matches_oracle(ctx, name):
 def test_cluster_path_rejects_oversized_systems(ctx):
     p = synth.channel_block_problem(300, seed=1)
     s = assemble(ctx, p)
-    with pytest.raises(cps.CpsError):
-        s.set_solver_path(cps.PATH_CLUSTER)
+    for path in (cps.PATH_CLUSTER, cps.PATH_CLUSTER_1RED):
+        with pytest.raises(cps.CpsError):
+            s.set_solver_path(path)
     s.free()
 
 
