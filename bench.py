@@ -102,6 +102,10 @@ def parse():
                          "through Mbar_12, outer iteration to --cp1-toll) on the --n lattice "
                          "with no-slip walls, after --warmup untimed ones (own line)")
     ap.add_argument("--cp1-toll", type=float, default=1e-4)
+    ap.add_argument("--graded", type=int, default=0,
+                    help="graded-mesh mode: FP64 Jacobi and IC(0) solves on the unstructured "
+                         "graded Delaunay mesh of this lattice size (900: ~2.0M cells), Morton "
+                         "and triangulation numbering (own line)")
     ap.add_argument("--pin", default="",
                     help="profiling run only: pin the FP64 Jacobi configuration instead of "
                          "tuning it (a profiler's replay skews the tuner), as "
@@ -561,6 +565,53 @@ def run_cp1_step(args):
     print(json.dumps(line), flush=True)
 
 
+def run_graded(args):
+    """Solves on an unstructured Delaunay mesh graded toward the porous
+    block's interface (two levels of refinement, up to four colours): FP64
+    Jacobi on its tuned path and multicolour IC(0) to --rtol, with the cells
+    numbered along a Morton curve and as the triangulation left them."""
+    import torch
+    import paper_2309_03543_gb300 as cps
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    ctx = cps.Context(0)
+    peak, peak_kind = measured_peaks()
+    res = {}
+    cells = 0
+    for order in ("morton", "none"):
+        p = synth.graded_problem(args.graded, seed=0, order=order)
+        m = p.mesh
+        cells = m.nt
+        s = ctx.assemble(m.xy, m.tri, m.dirichlet, p.eps, p.kinv, p.field_loc, cps.KIND_CP2,
+                         p.nu, p.dt)
+        b = torch.as_tensor(synth.rhs(m, seed=1), device=dev)
+        for name, pc in (("jacobi", cps.PC_JACOBI), ("ic0", cps.PC_IC0)):
+            s.set_precond(pc)
+            x = torch.zeros_like(b)
+            s.solve(b, x=x, rtol=args.rtol, check=False)   # tuning, path probes
+            ts = []
+            for _ in range(max(args.steps, 1)):
+                x.zero_()
+                dt_, st = timed(lambda: s.solve(b, x=x, rtol=args.rtol, check=False)[1], stream)
+                ts.append(dt_)
+            t = sorted(ts)[len(ts) // 2]
+            entry = {"seconds": t, "iters": st.iters, "us_per_iter": 1e6 * t / st.iters,
+                     "rel_res": st.rel_res, "status": st.status}
+            if name == "jacobi":
+                gbs = BYTES_PER_CELL_ITER_FP64 * cells / (t / st.iters) / 1e9
+                entry.update({"algorithmic_gbs": gbs, "frac": gbs / peak,
+                              "path": s.tuning(cps.FP64)})
+            res[f"{order}_{name}"] = entry
+        s.free()
+    line = {"metric": "time to rtol on a graded unstructured Delaunay mesh",
+            "value": res["morton_jacobi"]["seconds"], "unit": "s", "higher_is_better": False,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"graded-delaunay n={args.graded} levels=2 (channel-block "
+                                   f"fields, anisotropic K)", "cells": cells, "rtol": args.rtol},
+            "peak": peak, "peak_kind": peak_kind, **res}
+    print(json.dumps(line), flush=True)
+
+
 def side_neighbours(tri):
     """Neighbour across each local side (-1 on the boundary), by sorting the
     sides' vertex pairs; host-side set-up of the no-slip wall list."""
@@ -598,6 +649,9 @@ def main():
         return
     if args.cp1_step:
         run_cp1_step(args)
+        return
+    if args.graded:
+        run_graded(args)
         return
     import torch
     import paper_2309_03543_gb300 as cps

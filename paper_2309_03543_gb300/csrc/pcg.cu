@@ -775,7 +775,11 @@ static int solve_fp64(cps_sys s, const double* b, double* x, double rtol, int64_
     fill_stats(stats, total, rel, status, 1, launches);
     if (status == CPS_ERR_NOT_SPD) cps::set_error(s->ctx, "solve: p.Ap <= 0 (matrix not SPD or NaN input)");
     if (status == CPS_ERR_TIMEOUT) cps::set_error(s->ctx, "solve: a grid barrier wait ran out");
-    if (status == CPS_ERR_NOT_CONVERGED) cps::set_error(s->ctx, "solve: max_iter reached");
+    if (status == CPS_ERR_NOT_CONVERGED)
+        cps::set_error(s->ctx, total >= max_iter
+                                   ? "solve: max_iter reached"
+                                   : "solve: the true residual stays above rtol (FP64 rounding "
+                                     "floor of this system and right-hand side)");
     return status;
 }
 
@@ -1009,7 +1013,11 @@ static int solve_reduced(cps_sys s, const double* b, double* x, double rtol, int
     fill_stats(stats, total, rel, status, 1, launches);
     if (status == CPS_ERR_NOT_SPD) cps::set_error(s->ctx, "solve: p.Sp <= 0 (reduced system)");
     if (status == CPS_ERR_TIMEOUT) cps::set_error(s->ctx, "solve: a grid barrier wait ran out");
-    if (status == CPS_ERR_NOT_CONVERGED) cps::set_error(s->ctx, "solve: max_iter reached");
+    if (status == CPS_ERR_NOT_CONVERGED)
+        cps::set_error(s->ctx, total >= max_iter
+                                   ? "solve: max_iter reached"
+                                   : "solve: the true residual stays above rtol (FP64 rounding "
+                                     "floor of this system and right-hand side)");
     return status;
 }
 

@@ -197,6 +197,139 @@ def defect_problem(n: int, seed: int = 0) -> Problem:
                    meta={"workload": f"defect-lattice n={n}", "seed": seed})
 
 
+def _tri_lattice(h: float, W: float, H: float) -> np.ndarray:
+    """Triangular-lattice points of spacing h covering [0, W] x [0, H]."""
+    dy = h * math.sqrt(3.0) / 2.0
+    rows = np.arange(0.0, H + dy, dy)
+    pts = []
+    for j, y in enumerate(rows):
+        xs = np.arange(0.5 * h * (j % 2), W + h, h)
+        pts.append(np.stack([xs, np.full_like(xs, y)], axis=1))
+    return np.concatenate(pts)
+
+
+def _morton(c: np.ndarray, bits: int = 16) -> np.ndarray:
+    """Morton (Z-order) key of points c [n, 2] scaled to the unit square."""
+    lo, hi = c.min(axis=0), c.max(axis=0)
+    q = ((c - lo) / np.maximum(hi - lo, 1e-300) * ((1 << bits) - 1)).astype(np.uint64)
+    key = np.zeros(c.shape[0], dtype=np.uint64)
+    for b in range(bits):
+        for d in range(2):
+            key |= ((q[:, d] >> np.uint64(b)) & np.uint64(1)) << np.uint64(2 * b + d)
+    return key
+
+
+def graded_mesh(n: int, seed: int = 0, levels: int = 2, band: float = 6.0,
+                jitter: float = 0.05, order: str = "morton") -> Mesh:
+    """Unstructured Delaunay mesh graded toward the porous block's interface
+    (the transition layer the paper refines, Sec. 4): a triangular lattice of
+    spacing 1 on [0, n-1] x [0, (n-1) sqrt3/2], replaced within distance
+    band / 2^(k-1) of the block boundary (x in [W/3, 2W/3], y < 0.8 H) by a
+    lattice of spacing 2^-k, k = 1..levels; interior points jittered by
+    jitter x spacing; the boundary points lie on a rectangle bulged outward by
+    1e-3 (strictly convex, so the Delaunay triangulation keeps every boundary
+    point).  Cells are numbered along a Morton curve of their centroids
+    (order="morton") or as triangulated ("none").  Dirichlet sides on the
+    right edge.  Needs scipy (the triangulation is an input-generation step).
+    """
+    from scipy.spatial import Delaunay
+    W, H = float(n - 1), (n - 1) * math.sqrt(3.0) / 2.0
+    rng = np.random.default_rng(seed)
+    lo, hi = (W / 3, -H), (2 * W / 3, 0.8 * H)
+
+    def dist(p):
+        return np.abs(box_signed_distance(p, lo, hi))
+
+    pts, spacing = [], []
+    for k in range(levels + 1):
+        h = 2.0 ** (-k)
+        q = _tri_lattice(h, W, H)
+        d = dist(q)
+        keep = np.ones(q.shape[0], dtype=bool)
+        if k > 0:
+            keep &= d < band / 2.0 ** (k - 1)
+        if k < levels:
+            keep &= d >= band / 2.0 ** k
+        q = q[keep]
+        # interior only, off the boundary by a third of the spacing
+        inner = ((q[:, 0] > h / 3) & (q[:, 0] < W - h / 3) & (q[:, 1] > h / 3) &
+                 (q[:, 1] < H - h / 3))
+        q = q[inner]
+        pts.append(q)
+        spacing.append(np.full(q.shape[0], h))
+    pts = np.concatenate(pts)
+    spacing = np.concatenate(spacing)
+    r = jitter * spacing * np.sqrt(rng.random(pts.shape[0]))
+    phi = 2.0 * math.pi * rng.random(pts.shape[0])
+    pts = pts + np.stack([r * np.cos(phi), r * np.sin(phi)], axis=1)
+    # boundary: the local interior spacing along each edge, then bulged outward
+    def edge_points(a, b):
+        # vertical edges at the lattice's row height, so that every boundary
+        # point sits on a row and the cell opposite a boundary side is acute
+        rowf = math.sqrt(3.0) / 2.0 if a[0] == b[0] else 1.0
+        length = math.hypot(b[0] - a[0], b[1] - a[1])
+        t = np.linspace(0.0, 1.0, 8 * int(math.ceil(length)) * 2 ** levels + 1)
+        probe = np.asarray(a)[None, :] + t[:, None] * (np.asarray(b) - np.asarray(a))[None, :]
+        dd = dist(probe)
+        hloc = np.ones_like(dd)
+        for k in range(1, levels + 1):
+            hloc = np.where(dd < band / 2.0 ** (k - 1), 2.0 ** (-k), hloc)
+        out, s_ = [np.asarray(a, dtype=float)], 0.0
+        while True:
+            i = min(int(s_ / length * (t.size - 1)), t.size - 1)
+            s_ += rowf * hloc[i]
+            if s_ >= length - 0.5 * rowf * hloc[i]:
+                break
+            out.append(np.asarray(a) + (s_ / length) * (np.asarray(b) - np.asarray(a)))
+        return np.array(out)
+
+    corners = [(0.0, 0.0), (W, 0.0), (W, H), (0.0, H)]
+    bnd = np.concatenate([edge_points(corners[i], corners[(i + 1) % 4]) for i in range(4)])
+    # bulge: push each boundary point outward by 1e-3 x (distance-to-corner profile)
+    bx, by = bnd[:, 0], bnd[:, 1]
+    eps_b = 1e-3
+    on_bottom, on_top = by == 0.0, by == H
+    on_left, on_right = (bx == 0.0) & ~on_bottom & ~on_top, (bx == W) & ~on_bottom & ~on_top
+    u = bx / W
+    v = by / H
+    bnd = bnd.copy()
+    bnd[on_bottom, 1] -= eps_b * 4 * u[on_bottom] * (1 - u[on_bottom])
+    bnd[on_top, 1] += eps_b * 4 * u[on_top] * (1 - u[on_top])
+    bnd[on_left, 0] -= eps_b * 4 * v[on_left] * (1 - v[on_left])
+    bnd[on_right, 0] += eps_b * 4 * v[on_right] * (1 - v[on_right])
+    right = np.zeros(bnd.shape[0] + pts.shape[0], dtype=bool)
+    right[: bnd.shape[0]] = (bx == W)
+    xy = np.concatenate([bnd, pts])
+    tri = Delaunay(xy).simplices.astype(np.int64)
+    a, b, c = xy[tri[:, 0]], xy[tri[:, 1]], xy[tri[:, 2]]
+    cross = (b[:, 0] - a[:, 0]) * (c[:, 1] - a[:, 1]) - (b[:, 1] - a[:, 1]) * (c[:, 0] - a[:, 0])
+    flip = cross < 0
+    tri[flip] = tri[flip][:, [0, 2, 1]]
+    if order == "morton":
+        cen = xy[tri].mean(axis=1)
+        tri = tri[np.argsort(_morton(cen), kind="stable")]
+    tri = np.ascontiguousarray(tri.astype(np.int32))
+    dirichlet = sides_on_vertex_set(tri, right)
+    return Mesh(n=n, xy=xy, tri=tri, dirichlet=dirichlet)
+
+
+def graded_problem(n: int, seed: int = 0, levels: int = 2, beta: float = 100.0,
+                   alpha_deg: float = 30.0, order: str = "morton") -> Problem:
+    """The channel-block fields (random-Fourier porosity in the block, clear
+    fluid outside, anisotropic Kozeny-Carman) on the graded mesh."""
+    mesh = graded_mesh(n, seed, levels=levels, order=order)
+    W, H = mesh.width, mesh.height
+    rng = np.random.default_rng(seed + 7919)
+    f = random_fourier_field(mesh.xy, rng, W, H)
+    eps_blk = np.clip(0.45 + 0.1 * f, 0.3, 0.6)
+    sd = box_signed_distance(mesh.xy, (W / 3, -H), (2 * W / 3, 0.8 * H))
+    w = transition_weight(sd, 2.0 / 1.5 * 2 ** levels)
+    eps = 1.0 + (eps_blk - 1.0) * w
+    kinv = aniso_kinv(kozeny_carman_kinv(eps), beta, math.radians(alpha_deg))
+    return Problem(mesh, eps, kinv, PER_VERTEX,
+                   meta={"workload": f"graded-delaunay n={n} levels={levels}", "seed": seed})
+
+
 def triangle_areas(mesh: Mesh) -> np.ndarray:
     """Shoelace area of each triangle (used to scale the random RHS)."""
     p = mesh.xy[mesh.tri]
