@@ -291,8 +291,11 @@ def test_batched_solve_matches_oracle_per_system(ctx):
         xo, _, _ = oracle.solve_problem(p, b.cpu().numpy(), rtol=1e-13)
         err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
         assert err < 1e-9, (i, err)
+        # a single solve may take another recurrence (the tuner's single-
+        # reduction cluster path): the same iterates in exact arithmetic, but
+        # at rtol 1e-12, near the FP64 floor, the counts drift a few percent
         x1, st1 = systems[i].solve(b, rtol=1e-12, check=False)
-        assert abs(st1.iters - st.iters) <= max(4, 0.02 * st1.iters)
+        assert abs(st1.iters - st.iters) <= max(8, 0.05 * st1.iters)
     # a second batched call on the same handles (state reuse) and mixed mode
     xs2 = [torch.zeros_like(b) for b in bs]
     stats2 = cps.solve_batch(systems, bs, xs2, rtol=1e-10, precision=cps.MIXED, check=False)
