@@ -43,6 +43,10 @@ UNIT = "cell-iters/s"
 #     writes p_new, q, y (4+4+4+12+12 + 4+4+4 = 48); k_cg_b 12; +0.5 for s.
 BYTES_PER_CELL_ITER_FP64 = 52 + 24 + 40 + 1
 BYTES_PER_CELL_ITER_MIXED = 48 + 12 + 0.5
+#   FP64 single-reduction loop, two kernels: k_gear_update reads p, s, w, r, y
+#     and writes p, s, y, r (72); k_gear_spmv reads r, 3 values, 3 columns and
+#     writes w (8 + 24 + 12 + 8 = 52); every 8th SpMV also reads S (+1).
+BYTES_PER_CELL_ITER_FP64_1RED = 72 + 52 + 1
 # DRAM bytes (read + write) of one FP64 Jacobi iteration (k_spmv_dot + k_cg_b
 # + k_cg_c) on the 1024 x 1024 channel lattice, from one ncu capture of the
 # configuration below (profiles/pcg_iteration_traffic_channel1024.md); the
@@ -64,7 +68,26 @@ FP64_INSTR_PER_CELL_CP2 = {"mean_flux": 24, "tangential": 28, "update": 21}
 FP64_INSTR_PER_SM_CLK = 2
 TRAFFIC_PER_ITER_N1024 = (121.8 + 21.9 + 40.9) * 1e6
 TRAFFIC_CONFIG = {"grid": [608, 152, 152], "block": [256, 1024, 1024],
-                  "l2_window": "vectors", "persistent": False, "cluster": False}
+                  "l2_window": "vectors", "persistent": False, "cluster": False,
+                  "stream_single_reduction": False}
+# The same for the single-reduction loop (k_gear_update + k_gear_spmv; its
+# update kernel takes the residual update's tuned shape, the SpMV the SpMV's).
+TRAFFIC_PER_ITER_N1024_1RED = None
+TRAFFIC_CONFIG_1RED = {"grid": [608, 152, 152], "block": [256, 1024, 1024],
+                       "l2_window": "vectors5", "persistent": False, "cluster": False,
+                       "stream_single_reduction": True}
+
+
+def traffic_for(tf: dict, n: int):
+    """ncu DRAM bytes per iteration of the loop the tuner chose, when a
+    capture of that loop, grids, blocks and window exists (n = 1024)."""
+    if n != 1024:
+        return None
+    for cfg, traffic in ((TRAFFIC_CONFIG, TRAFFIC_PER_ITER_N1024),
+                         (TRAFFIC_CONFIG_1RED, TRAFFIC_PER_ITER_N1024_1RED)):
+        if traffic is not None and all(tf[k] == v for k, v in cfg.items()):
+            return traffic
+    return None
 
 
 def parse():
@@ -110,7 +133,8 @@ def parse():
                     help="profiling run only: pin the FP64 Jacobi configuration instead of "
                          "tuning it (a profiler's replay skews the tuner), as "
                          "'U0,U1,U2/G0,G1,G2/B0,B1,B2/PATH' with PATH stream, stream_l2, "
-                         "persistent or persistent_l2 (for the reduced system too)")
+                         "persistent, persistent_l2, stream_1red or stream_1red_l2 (for the "
+                         "reduced system too)")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiling run: assemble, then FP64 and mixed solves bounded to this "
                          "many iterations (Jacobi and IC(0)); no timing output")
@@ -704,7 +728,9 @@ def main():
             s.set_kernel_shapes(cps.FP64, *[[int(v) for v in f.split(",")] for f in (u, g, b)])
             s.set_solver_path({"stream": cps.PATH_STREAM, "stream_l2": cps.PATH_STREAM_L2,
                                "persistent": cps.PATH_PERSISTENT,
-                               "persistent_l2": cps.PATH_PERSISTENT_L2}[path])
+                               "persistent_l2": cps.PATH_PERSISTENT_L2,
+                               "stream_1red": cps.PATH_STREAM_1RED,
+                               "stream_1red_l2": cps.PATH_STREAM_1RED_L2}[path])
         for pc in (cps.PC_JACOBI, cps.PC_IC0):
             s.set_precond(pc)
             for prec in (cps.FP64, cps.MIXED):
@@ -839,8 +865,9 @@ def main():
         except cps.CpsError:
             continue
         for path_name, path in (("stream", cps.PATH_STREAM), ("cluster", cps.PATH_CLUSTER),
-                                ("persistent", cps.PATH_PERSISTENT)):
-            if pc == cps.PC_REDUCED and path == cps.PATH_CLUSTER:
+                                ("persistent", cps.PATH_PERSISTENT),
+                                ("stream_1red", cps.PATH_STREAM_1RED)):
+            if pc == cps.PC_REDUCED and path in (cps.PATH_CLUSTER, cps.PATH_STREAM_1RED):
                 continue
             try:
                 s.set_solver_path(path)
@@ -857,24 +884,29 @@ def main():
     library = library_spmv(s, x, stream)
     s.free()
     jf = variants["jacobi_fp64"]
-    achieved = BYTES_PER_CELL_ITER_FP64 * nt * jf["iters"] / jf["time_to_rtol_s"] / 1e9
     tf = tuning["fp64"]
+    bpc = BYTES_PER_CELL_ITER_FP64_1RED if tf["stream_single_reduction"] else \
+        BYTES_PER_CELL_ITER_FP64
+    achieved = bpc * nt * jf["iters"] / jf["time_to_rtol_s"] / 1e9
     if tf["persistent"]:
         kname = "k_persistent_cg (whole Jacobi-PCG solve in one cooperative launch)"
     elif tf["cluster"]:
         kname = "k_cluster_cg (whole Jacobi-PCG solve in one thread-block cluster)"
+    elif tf["stream_single_reduction"]:
+        kname = ("pcg_iteration_fp64_single_reduction (k_gear_update + k_gear_spmv, Jacobi, "
+                 "Chronopoulos-Gear recurrences)")
     else:
         kname = "pcg_iteration_fp64 (k_spmv_dot + k_cg_b + k_cg_c, Jacobi)"
     if tf["l2_window"] != "none":
         kname += {"matrix": "; matrix in persisting L2",
-                  "vectors": "; r, p, q in persisting L2"}[tf["l2_window"]]
-    profiled = all(tf[k] == v for k, v in TRAFFIC_CONFIG.items())
+                  "vectors": "; r, p, q in persisting L2",
+                  "vectors5": "; r, p, s, y, w in persisting L2"}[tf["l2_window"]]
     roof = {"bound": "hbm", "kernel": kname,
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "peak_kind": peak_kind, "bytes_per_cell_iter": BYTES_PER_CELL_ITER_FP64,
-            "traffic": TRAFFIC_PER_ITER_N1024 if (args.n == 1024 and profiled) else None,
+            "peak_kind": peak_kind, "bytes_per_cell_iter": bpc,
+            "traffic": traffic_for(tf, args.n),
             "traffic_unit": "bytes per iteration (DRAM read + write, ncu)",
-            "algorithmic_bytes_per_iter": BYTES_PER_CELL_ITER_FP64 * nt}
+            "algorithmic_bytes_per_iter": bpc * nt}
     jm = variants["jacobi_mixed"]
     jm["inner_gbs"] = BYTES_PER_CELL_ITER_MIXED * nt * jm["iters"] / jm["time_to_rtol_s"] / 1e9
 

@@ -311,6 +311,12 @@ int cps_cp2_kernel_times(cps_sys sys, float* ms);
  *     set-aside cannot hold them;
  *   CPS_PATH_PERSISTENT_L2: the persistent launch with r, p, q in persisting
  *     L2 (CPS_ERR_ARG as above);
+ *   CPS_PATH_STREAM_1RED, CPS_PATH_STREAM_1RED_L2 (FP64 Jacobi only):
+ *     graph-replayed streaming kernels with the single-reduction
+ *     (Chronopoulos-Gear) recurrences -- two kernels and one grid reduction
+ *     per iteration instead of three and two -- without / with its vectors
+ *     in persisting L2 (all five where the set-aside holds them, else r, p,
+ *     q; CPS_ERR_ARG as above when it cannot hold r, p, q);
  *   CPS_PATH_CLUSTER_1RED (FP64 Jacobi only): the one-cluster launch with the
  *     single-reduction (Chronopoulos-Gear) recurrences -- s = A p and w = A r
  *     are carried so that both inner products of an iteration come from one
@@ -324,6 +330,8 @@ int cps_cp2_kernel_times(cps_sys sys, float* ms);
 #define CPS_PATH_STREAM_L2 4
 #define CPS_PATH_PERSISTENT_L2 5
 #define CPS_PATH_CLUSTER_1RED 6
+#define CPS_PATH_STREAM_1RED 7
+#define CPS_PATH_STREAM_1RED_L2 8
 int cps_set_solver_path(cps_sys sys, int path);
 
 /* Pin the launch shapes of the iteration kernels of one precision instead of
@@ -355,17 +363,20 @@ int cps_test_inject(cps_sys sys, int fault);
  * (CPS_FP64 only) the direction update.  The tuner times every candidate on
  * the system's own data at its first solve; systems below 131072 cells keep
  * the defaults (unroll 2, 8 blocks per SM).  For CPS_FP64 Jacobi solves it
- * also times the ways of running the loop: flags (may be NULL, 5 entries)
+ * also times the ways of running the loop: flags (may be NULL, 6 entries)
  * receives {one-cluster launch chosen (0 no, 1 textbook recurrences, 2 the
  * single-reduction recurrences), persisting-L2 window (0 none, 1 the
- * matrix, 2 the vectors r, p, q), persistent launch chosen, reduced system:
- * persistent launch chosen, reduced system: window (0 or 2)}, probe_us (may
- * be NULL, 10 entries) the microseconds per iteration measured for
- * {streaming, one cluster, streaming + matrix in L2, persistent, streaming +
- * vectors in L2, persistent + vectors in L2, reduced system: streaming,
- * persistent, streaming + vectors in L2, persistent + vectors in L2} (0
- * where not tried; the persistent figures are the best over the grid sizes
- * tried, the one-cluster figure the better of its two recurrences).
+ * matrix, 2 the vectors r, p, q, 3 the five vectors of the single-reduction
+ * loop), persistent launch chosen, reduced system:
+ * persistent launch chosen, reduced system: window (0 or 2), single-reduction
+ * streaming chosen}, probe_us (may be NULL, 12 entries) the microseconds per
+ * iteration measured for {streaming, one cluster, streaming + matrix in L2,
+ * persistent, streaming + vectors in L2, persistent + vectors in L2, reduced
+ * system: streaming, persistent, streaming + vectors in L2, persistent +
+ * vectors in L2, single-reduction streaming, single-reduction streaming +
+ * vectors in L2} (0 where not tried; the persistent figures are the best over
+ * the grid sizes tried, the one-cluster figure the better of its two
+ * recurrences).
  * The context remembers what the tuner chose per mesh size (cells,
  * vertices): a system assembled later on the same context with the same
  * sizes starts from those choices and is not timed again.  A path forced by

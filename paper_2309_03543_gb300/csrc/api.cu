@@ -222,6 +222,19 @@ int cps_set_solver_path(cps_sys sys, int path) {
         t.red_done = true;
         t.red_path = 0;
         t.red_win = 0;
+    } else if (path == CPS_PATH_STREAM_1RED || path == CPS_PATH_STREAM_1RED_L2) {
+        // with L2: all five vectors of the loop where the set-aside holds them, else r, p, q
+        int win = 0;
+        if (path == CPS_PATH_STREAM_1RED_L2) {
+            win = cps::l2_window_fits_mode(sys, 3) ? 3 : 2;
+            if (!cps::l2_vectors_fit(sys)) {
+                cps::set_error(sys->ctx, "set_solver_path: the persisting L2 set-aside cannot hold r, p, q");
+                return CPS_ERR_ARG;
+            }
+        }
+        t.path_done = true;
+        t.path = 3;
+        t.l2win = win;
     } else if (path == CPS_PATH_PERSISTENT) {
         t.path_done = true;
         t.path = 2;
@@ -320,10 +333,13 @@ int cps_get_tuning(cps_sys sys, int precision, int32_t* unroll, int32_t* grid, i
         flags[2] = t.path_done && t.path == 2;
         flags[3] = t.red_done && t.red_path == 1;
         flags[4] = t.red_done ? t.red_win : 0;
+        flags[5] = t.path_done && t.path == 3;
     }
     if (probe_us) {
         for (int k = 0; k < 6; ++k) probe_us[k] = t.probe_us[k];
         for (int k = 0; k < 4; ++k) probe_us[6 + k] = t.red_probe_us[k];
+        probe_us[10] = t.probe_us[6];
+        probe_us[11] = t.probe_us[7];
     }
     return CPS_OK;
 }

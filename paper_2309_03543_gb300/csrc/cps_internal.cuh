@@ -57,15 +57,17 @@ struct Tuning {
     KCfg k[3];
     bool done = false;
     int path = 0;            // FP64 Jacobi: 0 graph-replayed kernels, 1 one-cluster launch,
-                             // 2 one persistent grid-synchronised launch
+                             // 2 one persistent grid-synchronised launch, 3 graph-replayed
+                             // single-reduction kernels
     int red_path = 0;        // reduced system: 0 graph-replayed kernels, 1 persistent launch
     bool red_done = false;
     bool path_done = false;
     int l2win = 0;           // FP64 Jacobi stream path, persisting L2 window: 0 none,
-                             // 1 the matrix, 2 the vectors r, p, q
-    double probe_us[6] = {0, 0, 0, 0, 0, 0};   // us/iteration: stream, cluster, stream +
-                                               // matrix in L2, persistent, stream + vectors
-                                               // in L2, persistent + vectors in L2
+                             // 1 the matrix, 2 the vectors r, p, q, 3 r, p, q, y, p1
+    double probe_us[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // us/iteration: stream, cluster,
+                                               // stream + matrix in L2, persistent, stream +
+                                               // vectors in L2, persistent + vectors in L2,
+                                               // single-reduction stream (+ vectors in L2)
     double red_probe_us[4] = {0, 0, 0, 0};   // reduced system: stream, persistent, and the
                                              // same with r, p, q in persisting L2
     int red_win = 0;         // reduced system: persisting L2 window (0 none, 2 r, p, q)
@@ -311,10 +313,11 @@ struct cps_sys_s {
 
     // CUDA graphs of a chunk of iterations, per (precision, preconditioner).
     cudaStream_t cap_stream = nullptr;
-    // [precision][0 Jacobi, 1 IC(0), 2 reduced system]
-    cudaGraphExec_t graph[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
-    int64_t graph_nodes[2][3] = {{0, 0, 0}, {0, 0, 0}};
-    int graph_l2win[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    // [precision][0 Jacobi, 1 IC(0), 2 reduced system, 3 single-reduction Jacobi]
+    cudaGraphExec_t graph[2][4] = {{nullptr, nullptr, nullptr, nullptr},
+                                   {nullptr, nullptr, nullptr, nullptr}};
+    int64_t graph_nodes[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+    int graph_l2win[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
     cps::Tuning tune[2];        // per precision (CPS_FP64, CPS_MIXED)
     int cluster_size = 0;       // CTAs of the last one-cluster solve
     void* gsync = nullptr;      // grid-barrier state of the persistent solves
@@ -366,6 +369,7 @@ int persistent_solve(cps_sys s, int reduced, const double* a, const int32_t* col
                      cudaStream_t stream);
 int persistent_max_grid(cps_sys s, int reduced);
 bool l2_vectors_fit(cps_sys s);
+bool l2_window_fits_mode(cps_sys s, int mode);
 void drop_graphs(cps_sys s, int prec);
 int export_impl(cps_sys sys, double* diag, int32_t* col, double* val, cudaStream_t stream);
 void free_sys(cps_sys sys);

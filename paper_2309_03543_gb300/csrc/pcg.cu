@@ -202,6 +202,39 @@ static void launch_c(const KCfg& c, const Run<double>& v, cps_sys s, cudaStream_
     CPS_FP64_SHAPES_V(CPS_CGC64, st, v.y, v.p0, v.z, v.n, s->st)
 }
 
+// The update kernel keeps five loaded vectors per row in registers: with
+// 1024-thread blocks (64 registers a thread) more than two rows per trip spill.
+#define CPS_GEARU64(U, B) k_gear_update<U, B>
+static void launch_gear_update(const KCfg& cfg, const Run<double>& v, cps_sys s,
+                               cudaStream_t st) {
+    KCfg c = cfg;
+    if (c.block == 1024 && c.unroll > 2) c.unroll = 2;
+    CPS_FP64_SHAPES_V(CPS_GEARU64, st, v.y, v.r, v.p0, v.q, v.p1, v.n, s->st)
+}
+
+static void launch_gear_spmv(const KCfg& c, const Run<double>& v, bool norm, cps_sys s,
+                             cudaStream_t st) {
+    if (norm) {
+#define CPS_GEARS64(U, B) k_gear_spmv<true, U, B>
+        CPS_FP64_SHAPES(CPS_GEARS64, st, v.a, v.col, v.r, v.p1, v.s, v.n, s->partials, s->st)
+#undef CPS_GEARS64
+    } else {
+#define CPS_GEARS64(U, B) k_gear_spmv<false, U, B>
+        CPS_FP64_SHAPES(CPS_GEARS64, st, v.a, v.col, v.r, v.p1, v.s, v.n, s->partials, s->st)
+#undef CPS_GEARS64
+    }
+}
+
+// One single-reduction FP64 Jacobi iteration: the update kernel with the
+// residual-update kernel's tuned shape, the SpMV with the SpMV's.
+static int64_t enqueue_iteration_gear(cps_sys s, const Run<double>& v, bool norm,
+                                      cudaStream_t st) {
+    const Tuning& t = s->tune[CPS_FP64];
+    launch_gear_update(t.k[1], v, s, st);
+    launch_gear_spmv(t.k[0], v, norm, s, st);
+    return 2;
+}
+
 static Tuning default_tuning(cps_sys s) {
     Tuning t;
     for (auto& k : t.k) {
@@ -374,22 +407,26 @@ static int64_t enqueue_iteration(cps_sys s, const Run<V>& v, int prec, bool norm
 // mode 2 the vectors r, p and q (one contiguous range; each is read and
 // written every iteration, 64 of the 117 bytes a row moves).  At a few
 // million cells either fits GB300's 129 MB L2 next to the streamed rest.
+// Mode 3, for the single-reduction loop, holds r, p, q (= s), y and p1
+// (= w): every vector that loop reads and writes (five contiguous slices).
 static void* l2_window_base(cps_sys s, int mode) {
     return mode == 1 ? (void*)s->a : (void*)s->wr;
 }
 static size_t l2_window_bytes(cps_sys s, int mode) {
-    return mode == 1 ? s->mat_bytes : (size_t)3 * s->vec_stride * sizeof(double);
+    if (mode == 1) return s->mat_bytes;
+    return (size_t)(mode == 3 ? 5 : 3) * s->vec_stride * sizeof(double);
 }
 static bool l2_window_fits(cps_sys s, int mode) {
     return s->ctx->l2_persist_max > 0 && l2_window_bytes(s, mode) <= s->ctx->l2_persist_max;
 }
 
 bool l2_vectors_fit(cps_sys s) { return l2_window_fits(s, 2); }
+bool l2_window_fits_mode(cps_sys s, int mode) { return l2_window_fits(s, mode); }
 
 // Forgets the chunk graphs of one precision (captured with launch shapes
 // that have changed).
 void drop_graphs(cps_sys s, int prec) {
-    for (int pc = 0; pc < 3; ++pc)
+    for (int pc = 0; pc < 4; ++pc)
         if (s->graph[prec][pc]) {
             cudaGraphExecDestroy(s->graph[prec][pc]);
             s->graph[prec][pc] = nullptr;
@@ -437,9 +474,9 @@ static int set_l2_window(cps_sys s, cudaStream_t st, int mode) {
 
 template <typename V>
 static int get_chunk_graph(cps_sys s, int prec, const Run<V>& v, cudaGraphExec_t* out,
-                           int64_t* per_chunk) {
-    const int pc = v.l ? 1 : 0;
-    const int win = (prec == CPS_FP64 && pc == 0) ? s->tune[CPS_FP64].l2win : 0;
+                           int64_t* per_chunk, bool gear = false) {
+    const int pc = gear ? 3 : (v.l ? 1 : 0);
+    const int win = (prec == CPS_FP64 && (pc == 0 || pc == 3)) ? s->tune[CPS_FP64].l2win : 0;
     if (s->graph[prec][pc] && s->graph_l2win[prec][pc] != win) {
         cudaGraphExecDestroy(s->graph[prec][pc]);
         s->graph[prec][pc] = nullptr;
@@ -454,8 +491,16 @@ static int get_chunk_graph(cps_sys s, int prec, const Run<V>& v, cudaGraphExec_t
         s->graph_l2win[prec][pc] = win;
         cudaGraph_t graph = nullptr;
         CPS_CUDA_TRY(s->ctx, cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
-        for (int k = 0; k < kChunk; ++k)
-            nl += enqueue_iteration<V>(s, v, prec, (k % kCheckEvery) == kCheckEvery - 1, s->cap_stream);
+        for (int k = 0; k < kChunk; ++k) {
+            const bool norm = (k % kCheckEvery) == kCheckEvery - 1;
+            if constexpr (sizeof(V) == 8) {
+                if (gear) {
+                    nl += enqueue_iteration_gear(s, v, norm, s->cap_stream);
+                    continue;
+                }
+            }
+            nl += enqueue_iteration<V>(s, v, prec, norm, s->cap_stream);
+        }
         cudaError_t le = cudaGetLastError();
         cudaError_t ce = cudaStreamEndCapture(s->cap_stream, &graph);
         if (le != cudaSuccess || ce != cudaSuccess) {
@@ -487,10 +532,10 @@ static int get_chunk_graph(cps_sys s, int prec, const Run<V>& v, cudaGraphExec_t
 // chunk enqueued after the stop returns at once in every kernel.
 template <typename V>
 static int run_chunks(cps_sys s, int prec, const Run<V>& v, cudaStream_t stream,
-                      CgState* final_state, int64_t* launches) {
+                      CgState* final_state, int64_t* launches, bool gear = false) {
     cudaGraphExec_t ge = nullptr;
     int64_t per_chunk = 0;
-    int rc = get_chunk_graph<V>(s, prec, v, &ge, &per_chunk);
+    int rc = get_chunk_graph<V>(s, prec, v, &ge, &per_chunk, gear);
     if (rc) return rc;
     for (long long k = 0;; ++k) {
         const int slot = (int)(k & 1);
@@ -566,6 +611,10 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
     if (s->nt <= cluster_max_rows(s->ctx, 1)) cands[nc++] = {1, 1, 0, 0, 1};
     if (big && l2_window_fits(s, 1)) cands[nc++] = {2, 0, 1, 0, 0};
     if (big && l2_window_fits(s, 2)) cands[nc++] = {4, 0, 2, 0, 0};
+    // single-reduction streaming (two kernels per iteration)
+    if (!try_cluster) cands[nc++] = {6, 3, 0, 0, 0};
+    if (big && l2_window_fits(s, 2)) cands[nc++] = {7, 3, 2, 0, 0};
+    if (big && l2_window_fits(s, 3)) cands[nc++] = {7, 3, 3, 0, 0};
     {
         const int gmax = persistent_max_grid(s, 0);
         int grids[3] = {gmax, (int)((s->nt + 8191) / 8192), (int)((s->nt + 2047) / 2048)};
@@ -582,7 +631,7 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
     cudaEvent_t e0, e1;
     CPS_CUDA_TRY(s->ctx, cudaEventCreate(&e0));
     CPS_CUDA_TRY(s->ctx, cudaEventCreate(&e1));
-    double per_iter[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    double per_iter[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     double best_t = 0.0;
     Cand best{0, 0, 0, 0, 0};
     int rc = CPS_OK;
@@ -592,8 +641,8 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
         const Cand c = cands[ci];
         t.l2win = c.win;
         rc = l2_set_aside(s, c.win, stream);
-        if (rc == CPS_OK && c.path == 0)
-            rc = get_chunk_graph<double>(s, CPS_FP64, v, &ge, &per_chunk);
+        if (rc == CPS_OK && (c.path == 0 || c.path == 3))
+            rc = get_chunk_graph<double>(s, CPS_FP64, v, &ge, &per_chunk, c.path == 3);
         double us = 0.0;
         for (int rep = 0; rep < 2 && rc == CPS_OK; ++rep) {   // first one warms up
             CPS_CUDA_TRY(s->ctx, cudaMemsetAsync(s->wx, 0, sizeof(double) * s->nt, stream));
@@ -607,10 +656,13 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
                                       c.win ? l2_window_bytes(s, c.win) : 0, c.grid, stream);
                 if (rc == CPS_OK) rc = read_state(s, stream, &h);
                 if (rc == CPS_OK && h.status != CPS_OK) rc = CPS_ERR_ARG;   // not usable here
-            } else if (c.path == 0) {
+            } else if (c.path == 0 || c.path == 3) {
                 k_init64<<<s->grid, kBlock, 0, stream>>>(b, s->wx, v.s, v.a, v.col, s->nt, v.y, v.r,
                                                          v.p0, 0.0, probe, 1, s->partials, s->st);
-                rc = run_chunks<double>(s, CPS_FP64, v, stream, &h, &dummy);
+                if (c.path == 3)
+                    k_gear_start<<<s->grid, kBlock, 0, stream>>>(v.a, v.col, v.r, v.p1, v.p0, v.q,
+                                                                 s->nt, s->partials, s->st);
+                rc = run_chunks<double>(s, CPS_FP64, v, stream, &h, &dummy, c.path == 3);
             } else {
                 rc = cluster_solve(s, b, s->wx, v.y, 0.0, probe, stream, c.var);
                 if (rc == CPS_OK) rc = read_state(s, stream, &h);
@@ -646,7 +698,7 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
         t.pgrid = best.grid;
         t.cluster_variant = best.var;
     }
-    for (int k = 0; k < 6; ++k) t.probe_us[k] = per_iter[k];
+    for (int k = 0; k < 8; ++k) t.probe_us[k] = per_iter[k];
     if (rc == CPS_OK) {
         update_cached_tuning(s, CPS_FP64, [&](Tuning& c) {
             c.path_done = true;
@@ -654,7 +706,7 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
             c.l2win = t.l2win;
             c.pgrid = t.pgrid;
             c.cluster_variant = t.cluster_variant;
-            for (int k = 0; k < 6; ++k) c.probe_us[k] = t.probe_us[k];
+            for (int k = 0; k < 8; ++k) c.probe_us[k] = t.probe_us[k];
         });
     }
     return rc;
@@ -679,6 +731,7 @@ static int solve_fp64(cps_sys s, const double* b, double* x, double rtol, int64_
     }
     const bool cluster = !ic0 && s->tune[CPS_FP64].path == 1;
     const bool persistent = !ic0 && s->tune[CPS_FP64].path == 2;
+    const bool gear = !ic0 && s->tune[CPS_FP64].path == 3;
     const int window = (!ic0 && !cluster) ? s->tune[CPS_FP64].l2win : 0;
     if (window) {
         int rc = l2_set_aside(s, window, stream);
@@ -743,11 +796,16 @@ static int solve_fp64(cps_sys s, const double* b, double* x, double rtol, int64_
             k_copy<double><<<g, kBlock, 0, stream>>>(v.p0, v.z, n);
             ++launches;
         }
+        if (gear) {
+            k_gear_start<<<g, kBlock, 0, stream>>>(v.a, v.col, v.r, v.p1, v.p0, v.q, n,
+                                                   s->partials, s->st);
+            ++launches;
+        }
         CPS_CUDA_TRY(s->ctx, cudaGetLastError());
         int rc = read_state(s, stream, &h);
         if (rc) return rc;
         if (!h.done && budget > 0) {
-            rc = run_chunks<double>(s, CPS_FP64, v, stream, &h, &launches);
+            rc = run_chunks<double>(s, CPS_FP64, v, stream, &h, &launches, gear);
             if (rc) return rc;
         }
         total += h.iter;

@@ -212,6 +212,129 @@ __global__ void __launch_bounds__(BS) k_cg_b(V* __restrict__ r, const V* __restr
     }
 }
 
+// ---- FP64 single-reduction iteration (Jacobi; Chronopoulos-Gear recurrences):
+// two streaming kernels and one grid reduction per iteration,
+//   k_gear_update: p = r + beta p; s = w + beta s; y += alpha p; r -= alpha s
+//   k_gear_spmv:   w = Ahat r; gamma = r.r, delta = w.r (and ||S r||^2);
+//                  last block: stop test, beta = gamma/gamma_old,
+//                  alpha = gamma/(delta - beta gamma/alpha_old)
+// with s = Ahat p carried by recurrence.  The same iterates as the textbook
+// loop in exact arithmetic; 125 algorithmic bytes and 9 FP64 FMAs per row
+// (117 and 8), for one kernel boundary and one grid reduction fewer.  The stop
+// is decided where the iteration ends (after the SpMV of the new residual), so
+// k_gear_spmv sets done = 2 directly.  s lives in q, w in p1.
+
+// After k_init64: w = Ahat r, delta = w.r, p = s = 0; alpha = rho/delta, beta = 0.
+__global__ void __launch_bounds__(kBlock) k_gear_start(const double* __restrict__ a,
+                                                       const int32_t* __restrict__ col,
+                                                       const double* __restrict__ r,
+                                                       double* __restrict__ w,
+                                                       double* __restrict__ p,
+                                                       double* __restrict__ q, int64_t n,
+                                                       double* partials, CgState* st) {
+    if (st->done) return;
+    double dd = 0.0;
+    CPS_GRID_STRIDE(e, n) {
+        const double re = r[e];
+        double v = re;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) v = fma(a[j * n + e], r[col[j * n + e]], v);
+        w[e] = v;
+        p[e] = 0.0;
+        q[e] = 0.0;
+        dd = fma(v, re, dd);
+    }
+    double t[1] = {dd};
+    if (grid_sum<1>(t, partials, &st->arrive[1]) && threadIdx.x == 0) {
+        const double delta = t[0];
+        st->gamma = delta;
+        st->beta = 0.0;
+        if (!(delta > 0.0) || !isfinite(delta)) {
+            st->status = CPS_ERR_NOT_SPD;
+            st->done = 2;
+        } else {
+            st->alpha = st->rho / delta;
+        }
+    }
+}
+
+template <int U, int BS = kBlock>
+__global__ void __launch_bounds__(BS) k_gear_update(double* __restrict__ y,
+                                                    double* __restrict__ r,
+                                                    double* __restrict__ p,
+                                                    double* __restrict__ s,
+                                                    const double* __restrict__ w, int64_t n,
+                                                    const CgState* st) {
+    if (st->done) return;
+    const double al = st->alpha;
+    const double be = st->beta;
+    double pe[U], se[U], we[U], re[U], ye[U];
+    CPS_UNROLLED_LOOP(n, U, (pe[u] = p[e], se[u] = s[e], we[u] = w[e], re[u] = r[e], ye[u] = y[e]),
+        {
+            const double pn = fma(be, pe[u], re[u]);
+            const double sn = fma(be, se[u], we[u]);
+            p[e] = pn;
+            s[e] = sn;
+            y[e] = fma(al, pn, ye[u]);
+            r[e] = fma(-al, sn, re[u]);
+        })
+}
+
+template <bool NORM, int U, int BS = kBlock>
+__global__ void __launch_bounds__(BS) k_gear_spmv(const double* __restrict__ a,
+                                                  const int32_t* __restrict__ col,
+                                                  const double* __restrict__ r,
+                                                  double* __restrict__ w,
+                                                  const double* __restrict__ sc, int64_t n,
+                                                  double* partials, CgState* st) {
+    if (st->done) return;
+    double gg = 0.0, dd = 0.0, nn = 0.0;
+    double re[U], a0[U], a1[U], a2[U], se[U];
+    int32_t c0[U], c1[U], c2[U];
+    CPS_UNROLLED_LOOP(n, U,
+        (re[u] = r[e], a0[u] = a[e], a1[u] = a[n + e], a2[u] = a[2 * n + e],
+         c0[u] = col[e], c1[u] = col[n + e], c2[u] = col[2 * n + e], se[u] = NORM ? sc[e] : 0.0),
+        {
+            double v = fma(a0[u], r[c0[u]], re[u]);
+            v = fma(a1[u], r[c1[u]], v);
+            v = fma(a2[u], r[c2[u]], v);
+            w[e] = v;
+            gg = fma(re[u], re[u], gg);
+            dd = fma(v, re[u], dd);
+            if (NORM) {
+                const double t = se[u] * re[u];
+                nn = fma(t, t, nn);
+            }
+        })
+    double t[3] = {gg, dd, nn};
+    if (grid_sum<3, BS>(t, partials, &st->arrive[0]) && threadIdx.x == 0) {
+        const long long it = st->iter + 1;
+        st->iter = it;
+        int done = 0;
+        if (NORM) {
+            st->rnorm2 = t[2];
+            if (t[2] <= st->thresh2) done = 1;
+        }
+        if (it >= st->max_iter) done = 1;
+        const double g = t[0], d = t[1];
+        if (!(g > 0.0)) done = 1;                // exact solution reached
+        if (!done) {
+            const double be = g / st->rho;
+            const double den = d - be * g / st->alpha;
+            if (!(den > 0.0) || !isfinite(den)) {
+                st->status = CPS_ERR_NOT_SPD;
+                done = 1;
+            } else {
+                st->beta = be;
+                st->alpha = g / den;
+            }
+        }
+        st->rho = g;
+        st->gamma = d;
+        if (done) st->done = 2;
+    }
+}
+
 // Autotuning: keep the iteration kernels running whatever the data does.
 __global__ void k_tune_prime(CgState* st) {
     st->done = 0;

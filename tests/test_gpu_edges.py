@@ -59,8 +59,8 @@ def test_tiny_systems_every_path(ctx, name):
     xo = oracle.dense_cholesky_solve(A.dense(), b)
     s = _assemble(ctx, p)
     bt = torch.as_tensor(b, device="cuda")
-    paths = [cps.PATH_AUTO, cps.PATH_STREAM, cps.PATH_CLUSTER, cps.PATH_CLUSTER_1RED,
-             cps.PATH_PERSISTENT]
+    paths = [cps.PATH_AUTO, cps.PATH_STREAM, cps.PATH_STREAM_1RED, cps.PATH_CLUSTER,
+             cps.PATH_CLUSTER_1RED, cps.PATH_PERSISTENT]
     for path in paths:
         s.set_solver_path(path)
         x, st = s.solve(bt, rtol=1e-12)

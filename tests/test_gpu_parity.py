@@ -459,12 +459,17 @@ def test_path_autotuner_reports_every_candidate(ctx):
     tu = s.tuning()
     pr = tu["probe_us_per_iter"]
     assert pr["stream"] > 0 and pr["persistent"] > 0 and pr["cluster"] == 0
+    assert pr["stream_1red"] > 0
     chosen = [k for k in ("stream", "stream_l2_matrix", "stream_l2_vectors", "persistent",
-                          "persistent_l2_vectors") if pr[k] > 0]
+                          "persistent_l2_vectors", "stream_1red", "stream_1red_l2_vectors")
+              if pr[k] > 0]
     best = min(chosen, key=lambda k: pr[k])
     assert tu["persistent"] == best.startswith("persistent")
-    assert tu["l2_window"] == {"stream_l2_matrix": "matrix", "stream_l2_vectors": "vectors",
-                               "persistent_l2_vectors": "vectors"}.get(best, "none")
+    assert tu["stream_single_reduction"] == best.startswith("stream_1red")
+    want = {"stream_l2_matrix": ("matrix",), "stream_l2_vectors": ("vectors",),
+            "persistent_l2_vectors": ("vectors",),
+            "stream_1red_l2_vectors": ("vectors", "vectors5")}.get(best, ("none",))
+    assert tu["l2_window"] in want
     s.set_precond(cps.PC_REDUCED)
     _, st = s.solve(b, rtol=1e-10)
     tu = s.tuning()
@@ -475,6 +480,41 @@ def test_path_autotuner_reports_every_candidate(ctx):
     best = min(red, key=lambda k: pr[k])
     assert tu["reduced_persistent"] == best.startswith("reduced_persistent")
     assert tu["reduced_l2_window"] == ("vectors" if best.endswith("l2_vectors") else "none")
+    s.free()
+
+
+@pytest.mark.parametrize("name", ["channel64", "defect20", "ensemble", "channel300"])
+def test_stream_single_reduction_matches_oracle(ctx, name):
+    """The streaming single-reduction (Chronopoulos-Gear) FP64 Jacobi loop,
+    without and with r, p, q in persisting L2, against the oracle; the same
+    iterates as the textbook loop in exact arithmetic, so nearly the same
+    iteration count.  channel300 (178k cells) runs with tuned launch shapes."""
+    p = PROBLEMS[name] if name in PROBLEMS else synth.channel_block_problem(300, seed=8)
+    s = assemble(ctx, p)
+    b = synth.rhs(p.mesh, 31)
+    bt = torch.as_tensor(b, device="cuda")
+    xo, _, A = oracle.solve_problem(p, b, rtol=1e-13)
+    s.set_solver_path(cps.PATH_STREAM)
+    _, st0 = s.solve(bt, rtol=1e-12, check=False)
+    for path in (cps.PATH_STREAM_1RED, cps.PATH_STREAM_1RED_L2):
+        try:
+            s.set_solver_path(path)
+        except cps.CpsError:
+            assert path == cps.PATH_STREAM_1RED_L2      # no persisting set-aside here
+            continue
+        x, st = s.solve(bt, rtol=1e-12, check=False)
+        assert st.status in (0, cps._cps.ERR_NOT_CONVERGED) and st.rel_res < 1e-10
+        err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
+        assert err < 1e-9, (path, err)
+        assert abs(st.iters - st0.iters) <= max(8, 0.05 * st0.iters)
+        assert s.tuning()["stream_single_reduction"]
+        # warm start from the solution, and a zero right-hand side
+        x2 = x.clone()
+        _, st2 = s.solve(bt, x=x2, rtol=1e-8)
+        assert st2.iters == 0
+        z = torch.ones_like(bt)
+        s.solve(torch.zeros_like(bt), x=z)
+        assert torch.all(z == 0)
     s.free()
 
 
