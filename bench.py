@@ -70,9 +70,10 @@ TRAFFIC_PER_ITER_N1024 = (121.8 + 21.9 + 40.9) * 1e6
 TRAFFIC_CONFIG = {"grid": [608, 152, 152], "block": [256, 1024, 1024],
                   "l2_window": "vectors", "persistent": False, "cluster": False,
                   "stream_single_reduction": False}
-# The same for the single-reduction loop (k_gear_update + k_gear_spmv; its
-# update kernel takes the residual update's tuned shape, the SpMV the SpMV's).
-TRAFFIC_PER_ITER_N1024_1RED = None
+# The same for the single-reduction loop (k_gear_update + k_gear_spmv, the
+# five vectors in persisting L2; its update kernel takes the residual update's
+# tuned shape, the SpMV the SpMV's).
+TRAFFIC_PER_ITER_N1024_1RED = (108.3 + 124.5) * 1e6   # profiles/pcg_iteration_single_reduction_channel1024.md
 TRAFFIC_CONFIG_1RED = {"grid": [608, 152, 152], "block": [256, 1024, 1024],
                        "l2_window": "vectors5", "persistent": False, "cluster": False,
                        "stream_single_reduction": True}
