@@ -76,7 +76,7 @@ TRAFFIC_CONFIG = {"grid": [608, 152, 152], "block": [256, 1024, 1024],
 TRAFFIC_PER_ITER_N1024_1RED = (108.3 + 124.5) * 1e6   # profiles/pcg_iteration_single_reduction_channel1024.md
 TRAFFIC_CONFIG_1RED = {"grid": [608, 152, 152], "block": [256, 1024, 1024],
                        "l2_window": "vectors5", "persistent": False, "cluster": False,
-                       "stream_single_reduction": True}
+                       "stream_single_reduction": True, "update_1red_grid_block": [152, 1024]}
 
 
 def traffic_for(tf: dict, n: int):
@@ -84,6 +84,7 @@ def traffic_for(tf: dict, n: int):
     capture of that loop, grids, blocks and window exists (n = 1024)."""
     if n != 1024:
         return None
+    tf = dict(tf, update_1red_grid_block=tf.get("update_1red", [0, 0, 0])[1:])
     for cfg, traffic in ((TRAFFIC_CONFIG, TRAFFIC_PER_ITER_N1024),
                          (TRAFFIC_CONFIG_1RED, TRAFFIC_PER_ITER_N1024_1RED)):
         if traffic is not None and all(tf[k] == v for k, v in cfg.items()):

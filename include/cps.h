@@ -381,6 +381,12 @@ int cps_test_inject(cps_sys sys, int fault);
  * vertices): a system assembled later on the same context with the same
  * sizes starts from those choices and is not timed again.  A path forced by
  * cps_set_solver_path applies to that system only. */
+/* Launch shape (host outputs: rows per thread per trip, blocks, threads per
+ * block) of the single-reduction loop's update kernel, which the FP64 path
+ * probe tunes on its own once it has chosen that loop (the residual update's
+ * shape before; 0s before the first FP64 solve).  Errors: CPS_ERR_ARG. */
+int cps_get_gear_shape(cps_sys sys, int32_t* unroll, int32_t* grid, int32_t* block);
+
 int cps_get_tuning(cps_sys sys, int precision, int32_t* unroll, int32_t* grid, int32_t* block,
                    int32_t* flags, double* probe_us);
 

@@ -81,6 +81,7 @@ SIGNATURES = {
     "cps_cp2_step": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _D, _I64, _I, ctypes.POINTER(Stats),
                           _P]),
     "cps_get_tuning": (_I, [_P, _I, _P, _P, _P, _P, _P]),
+    "cps_get_gear_shape": (_I, [_P, _P, _P, _P]),
     "cps_set_solver_path": (_I, [_P, _I]),
     "cps_set_kernel_shapes": (_I, [_P, _I, _P, _P, _P]),
     "cps_test_inject": (_I, [_P, _I]),

@@ -143,6 +143,10 @@ class System:
         pr = (ctypes.c_double * 12)()
         self.ctx.check(self.ctx.lib.cps_get_tuning(self.handle, precision, u, g, bl, f, pr),
                        "cps_get_tuning")
+        gu, gg, gb = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        self.ctx.check(self.ctx.lib.cps_get_gear_shape(self.handle, ctypes.byref(gu),
+                                                      ctypes.byref(gg), ctypes.byref(gb)),
+                       "cps_get_gear_shape")
         return {"unroll": list(u), "grid": list(g), "block": list(bl),
                 "cluster": bool(f[0]),
                 "cluster_recurrence": (None, "textbook", "single_reduction")[f[0]],
@@ -150,6 +154,7 @@ class System:
                 "persistent": bool(f[2]), "reduced_persistent": bool(f[3]),
                 "reduced_l2_window": ("none", "matrix", "vectors")[f[4]],
                 "stream_single_reduction": bool(f[5]),
+                "update_1red": [gu.value, gg.value, gb.value],
                 "probe_us_per_iter": {
                     "stream": pr[0], "cluster": pr[1], "stream_l2_matrix": pr[2],
                     "persistent": pr[3], "stream_l2_vectors": pr[4], "persistent_l2_vectors": pr[5],

@@ -313,6 +313,7 @@ int cps_set_kernel_shapes(cps_sys sys, int precision, const int32_t* unroll, con
         t.k[k].block = block[k];
     }
     t.done = true;
+    t.kg_set = false;        // the single-reduction update follows the pinned residual update
     cps::drop_graphs(sys, precision);       // captured with the old shapes
     return CPS_OK;
 }
@@ -341,6 +342,16 @@ int cps_get_tuning(cps_sys sys, int precision, int32_t* unroll, int32_t* grid, i
         probe_us[10] = t.probe_us[6];
         probe_us[11] = t.probe_us[7];
     }
+    return CPS_OK;
+}
+
+int cps_get_gear_shape(cps_sys sys, int32_t* unroll, int32_t* grid, int32_t* block) {
+    if (!sys || !unroll || !grid || !block) return CPS_ERR_ARG;
+    const cps::Tuning& t = sys->tune[CPS_FP64];
+    const cps::KCfg c = t.kg_set ? t.kg : t.k[1];
+    *unroll = t.done ? (c.block == 1024 && c.unroll > 2 ? 2 : c.unroll) : 0;
+    *grid = t.done ? c.grid : 0;
+    *block = t.done ? c.block : 0;
     return CPS_OK;
 }
 

@@ -74,6 +74,8 @@ struct Tuning {
     int pgrid = 0;           // blocks of the persistent launch (0: all that stay resident)
     int red_pgrid = 0;       // the same for the reduced system
     int cluster_variant = 0; // one-cluster launch: 0 textbook CG, 1 single reduction
+    KCfg kg;                 // single-reduction update kernel (if kg_set; else k[1])
+    bool kg_set = false;
 };
 
 // Device error flag written by the assembly kernels (first error wins).

@@ -225,12 +225,13 @@ static void launch_gear_spmv(const KCfg& c, const Run<double>& v, bool norm, cps
     }
 }
 
-// One single-reduction FP64 Jacobi iteration: the update kernel with the
-// residual-update kernel's tuned shape, the SpMV with the SpMV's.
+// One single-reduction FP64 Jacobi iteration: the update kernel with its own
+// tuned shape (the residual update's until the path probe has timed it), the
+// SpMV with the SpMV's.
 static int64_t enqueue_iteration_gear(cps_sys s, const Run<double>& v, bool norm,
                                       cudaStream_t st) {
     const Tuning& t = s->tune[CPS_FP64];
-    launch_gear_update(t.k[1], v, s, st);
+    launch_gear_update(t.kg_set ? t.kg : t.k[1], v, s, st);
     launch_gear_spmv(t.k[0], v, norm, s, st);
     return 2;
 }
@@ -637,17 +638,20 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
     int rc = CPS_OK;
     cudaGraphExec_t ge = nullptr;
     int64_t per_chunk = 0, dummy = 0;
-    for (int ci = 0; ci < nc && rc == CPS_OK; ++ci) {
-        const Cand c = cands[ci];
+    // microseconds per iteration of one candidate (0: it cannot run here)
+    auto time_cand = [&](const Cand& c) -> double {
         t.l2win = c.win;
         rc = l2_set_aside(s, c.win, stream);
         if (rc == CPS_OK && (c.path == 0 || c.path == 3))
             rc = get_chunk_graph<double>(s, CPS_FP64, v, &ge, &per_chunk, c.path == 3);
         double us = 0.0;
         for (int rep = 0; rep < 2 && rc == CPS_OK; ++rep) {   // first one warms up
-            CPS_CUDA_TRY(s->ctx, cudaMemsetAsync(s->wx, 0, sizeof(double) * s->nt, stream));
+            if (cudaMemsetAsync(s->wx, 0, sizeof(double) * s->nt, stream) != cudaSuccess ||
+                cudaEventRecord(e0, stream) != cudaSuccess) {
+                rc = CPS_ERR_CUDA;
+                break;
+            }
             CgState h{};
-            CPS_CUDA_TRY(s->ctx, cudaEventRecord(e0, stream));
             if (c.path == 2) {
                 k_init64<<<s->grid, kBlock, 0, stream>>>(b, s->wx, v.s, v.a, v.col, s->nt, v.y, v.r,
                                                          v.p0, 0.0, probe, 1, s->partials, s->st);
@@ -667,8 +671,11 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
                 rc = cluster_solve(s, b, s->wx, v.y, 0.0, probe, stream, c.var);
                 if (rc == CPS_OK) rc = read_state(s, stream, &h);
             }
-            CPS_CUDA_TRY(s->ctx, cudaEventRecord(e1, stream));
-            CPS_CUDA_TRY(s->ctx, cudaEventSynchronize(e1));
+            if (cudaEventRecord(e1, stream) != cudaSuccess ||
+                cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = CPS_ERR_CUDA;
+                break;
+            }
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
             us = rc == CPS_OK ? 1e3 * ms / (double)(h.iter > 0 ? h.iter : 1) : 0.0;
@@ -676,14 +683,56 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
         if (rc == CPS_ERR_ARG) {            // a candidate that cannot run here: skip it
             rc = CPS_OK;
             cudaGetLastError();
-            continue;
+            return 0.0;
         }
+        return rc == CPS_OK ? us : 0.0;
+    };
+    for (int ci = 0; ci < nc && rc == CPS_OK; ++ci) {
+        const Cand c = cands[ci];
+        const double us = time_cand(c);
         if (rc != CPS_OK || us <= 0.0) continue;
         if (per_iter[c.slot] == 0.0 || us < per_iter[c.slot]) per_iter[c.slot] = us;
         if (best_t == 0.0 || us < best_t) {
             best_t = us;
             best = c;
         }
+    }
+    // The single-reduction update kernel moves 72 bytes a row (the residual
+    // update whose tuned shape it starts from moves 24): time a few shapes of
+    // its own on the chosen loop and keep the fastest.
+    if (rc == CPS_OK && best.path == 3 && big) {
+        t.path = 3;
+        const KCfg start = t.kg_set ? t.kg : t.k[1];
+        const KCfg shapes[5] = {start, t.k[2],
+                                {2, grid_for(s->ctx, s->nt, 8), kBlock},
+                                {4, grid_for(s->ctx, s->nt, 4), kBlock},
+                                {2, grid_for(s->ctx, s->nt * kBlock / 1024, 2), 1024}};
+        KCfg keep = start;
+        double keep_t = best_t;
+        for (int k = 0; k < 5 && rc == CPS_OK; ++k) {
+            if (k > 0 && shapes[k].unroll == keep.unroll && shapes[k].grid == keep.grid &&
+                shapes[k].block == keep.block)
+                continue;
+            t.kg = shapes[k];
+            t.kg_set = true;
+            if (s->graph[CPS_FP64][3]) {
+                cudaGraphExecDestroy(s->graph[CPS_FP64][3]);
+                s->graph[CPS_FP64][3] = nullptr;
+            }
+            const double us = time_cand(best);
+            if (rc == CPS_OK && us > 0.0 && us < keep_t) {
+                keep_t = us;
+                keep = shapes[k];
+            }
+        }
+        t.kg = keep;
+        t.kg_set = true;
+        if (s->graph[CPS_FP64][3]) {
+            cudaGraphExecDestroy(s->graph[CPS_FP64][3]);
+            s->graph[CPS_FP64][3] = nullptr;
+        }
+        best_t = keep_t;
+        per_iter[best.slot] = keep_t;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -706,6 +755,8 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
             c.l2win = t.l2win;
             c.pgrid = t.pgrid;
             c.cluster_variant = t.cluster_variant;
+            c.kg = t.kg;
+            c.kg_set = t.kg_set;
             for (int k = 0; k < 8; ++k) c.probe_us[k] = t.probe_us[k];
         });
     }
