@@ -11,6 +11,10 @@
 //   k_cg_b:     r -= alpha q; Jacobi: rho' = r.r;  last block: beta, stop test
 //   k_cg_c:     y += alpha p; p = z + beta p
 // (with IC(0) the preconditioner sweeps run between k_cg_b and k_cg_c).
+// FP64 Jacobi, single-reduction alternative (Chronopoulos-Gear): two kernels,
+//   k_gear_update: p = r + beta p; s = w + beta s; y += alpha p; r -= alpha s
+//   k_gear_spmv:   w = Ahat r, gamma = r.r, delta = w.r; last block: alpha, beta
+// (the autotuner picks between the two loops per system).
 // Binary32 iteration of the mixed solve: two fused kernels,
 //   k_cg_a: y += alpha_{k-1} p_{k-1} (x update one iteration late);
 //           p_k = z_k + beta_{k-1} p_{k-1} for the own row and, recomputed
