@@ -227,7 +227,8 @@ int cps_cp2_setup(cps_sys sys, const double* xy, const int32_t* tri, const doubl
  * divergence-free u^{k+1} and the updated eps grad(Psi).
  *   u23[2*nt]     u^{k+2/3} per cell: x components, then y components
  *   g_k[2*nt]     eps grad(Psi^k) per cell, same layout
- *   eta_tilde[nt] out: first solution eta~ (may be NULL)
+ *   eta_tilde[nt] out: first solution eta~ (may be NULL, or eta itself, in
+ *                 which case eta ends as the second solution)
  *   eta[nt]       out: second solution eta
  *   u_next[2*nt]  out: u^{k+1}, the RT0 field at the centroid (Eq. RT0)
  *   g_next[2*nt]  out: eps grad(Psi^{k+1}) = g_k + Mbar_e (u_next - u23) (Eq. grad_PSI)

@@ -466,7 +466,7 @@ int cp2_step_impl(cps_sys s, const double* u23, const double* g_k, double* eta_t
     k_cp2_tangential<<<g, kBlock, 0, stream>>>(et, s->col, c->tw, c->tidx, nt, c->tau, c->rhs);
     cudaEventRecord(c->ev[3], stream);
     ce = cudaGetLastError();
-    if (ce == cudaSuccess)
+    if (ce == cudaSuccess && eta != et)     // one buffer for both: the warm start is in place
         ce = cudaMemcpyAsync(eta, et, sizeof(double) * nt, cudaMemcpyDeviceToDevice, stream);
     if (ce != cudaSuccess) return fail(s, CPS_ERR_CUDA, std::string("cp2_step: ") + cudaGetErrorString(ce));
     int rc2 = solve_impl(s, c->rhs, eta, rtol, max_iter, precision, &st[1], stream);
