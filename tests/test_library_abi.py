@@ -48,3 +48,60 @@ def test_null_handles_are_rejected_without_a_gpu(lib):
     # no device in this container: create must fail cleanly, not crash
     rc = lib.cps_create(ctypes.byref(out), 0)
     assert rc in (0, -1, -9)
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include "cps.h"
+int main(void) {
+    cps_stats st;
+    cps_cp1_stats st1;
+    (void)st; (void)st1;
+    /* null handles are rejected with CPS_ERR_ARG; nothing touches a GPU */
+    if (cps_sys_free(NULL) != CPS_ERR_ARG) return 1;
+    if (cps_destroy(NULL) != CPS_ERR_ARG) return 2;
+    if (cps_solve(NULL, NULL, NULL, 1e-10, 10, CPS_FP64, NULL, NULL) != CPS_ERR_ARG) return 3;
+    if (cps_cp2_step(NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, 1e-10, 10, CPS_FP64,
+                     NULL, NULL) != CPS_ERR_ARG) return 4;
+    if (cps_cp1_step(NULL, NULL, NULL, NULL, 1e-4, 10, 1e-10, 10, CPS_FP64, NULL,
+                     NULL) != CPS_ERR_ARG) return 5;
+    puts("ok");
+    return 0;
+}
+"""
+
+
+@pytest.mark.parametrize("compiler,std", [("gcc", "-std=c11"), ("g++", "-std=c++17")])
+def test_header_compiles_as_c_and_cpp(tmp_path, compiler, std):
+    """cps.h is a plain C header (usable from C and C++)."""
+    import shutil
+    import subprocess
+    if shutil.which(compiler) is None:
+        pytest.skip(f"{compiler} not installed")
+    src = tmp_path / ("t.c" if compiler == "gcc" else "t.cpp")
+    src.write_text('#include "cps.h"\nint main(void) { return CPS_OK; }\n')
+    r = subprocess.run([compiler, std, "-Wall", "-Wextra", "-Werror", "-pedantic", "-fsyntax-only",
+                        "-I", os.path.join(ROOT, "include"), str(src)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
+def test_c_program_links_and_runs_without_a_gpu(tmp_path, lib):
+    """A C program built against cps.h links libcps.so and gets CPS_ERR_ARG
+    for null handles without touching a GPU."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not installed")
+    from paper_2309_03543_gb300.build import LIB
+    src = tmp_path / "prog.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "prog"
+    libdir = os.path.dirname(LIB)
+    r = subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        str(src), "-o", str(exe), "-L", libdir, "-l:" + os.path.basename(LIB),
+                        "-Wl,-rpath," + libdir], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    run = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert run.returncode == 0 and run.stdout.strip() == "ok", (run.returncode, run.stdout,
+                                                                 run.stderr)
