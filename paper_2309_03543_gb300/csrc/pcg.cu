@@ -203,13 +203,23 @@ static void launch_c(const KCfg& c, const Run<double>& v, cps_sys s, cudaStream_
 }
 
 // The update kernel keeps five loaded vectors per row in registers: with
-// 1024-thread blocks (64 registers a thread) more than two rows per trip spill.
-#define CPS_GEARU64(U, B) k_gear_update<U, B>
-static void launch_gear_update(const KCfg& cfg, const Run<double>& v, cps_sys s,
+// 1024-thread blocks (64 registers a thread) more than two rows per trip
+// spill, so those shapes take two (and are not instantiated).
+static void launch_gear_update(const KCfg& c, const Run<double>& v, cps_sys s,
                                cudaStream_t st) {
-    KCfg c = cfg;
-    if (c.block == 1024 && c.unroll > 2) c.unroll = 2;
-    CPS_FP64_SHAPES_V(CPS_GEARU64, st, v.y, v.r, v.p0, v.q, v.p1, v.n, s->st)
+    if (c.block == 1024) {
+        if (c.unroll == 1)
+            launch_kb(k_gear_update<1, 1024>, c.grid, 1024, st, v.y, v.r, v.p0, v.q, v.p1, v.n, s->st);
+        else
+            launch_kb(k_gear_update<2, 1024>, c.grid, 1024, st, v.y, v.r, v.p0, v.q, v.p1, v.n, s->st);
+        return;
+    }
+    switch (c.unroll) {
+        case 1: launch_kb(k_gear_update<1, kBlock>, c.grid, kBlock, st, v.y, v.r, v.p0, v.q, v.p1, v.n, s->st); break;
+        case 4: launch_kb(k_gear_update<4, kBlock>, c.grid, kBlock, st, v.y, v.r, v.p0, v.q, v.p1, v.n, s->st); break;
+        case 8: launch_kb(k_gear_update<8, kBlock>, c.grid, kBlock, st, v.y, v.r, v.p0, v.q, v.p1, v.n, s->st); break;
+        default: launch_kb(k_gear_update<2, kBlock>, c.grid, kBlock, st, v.y, v.r, v.p0, v.q, v.p1, v.n, s->st); break;
+    }
 }
 
 static void launch_gear_spmv(const KCfg& c, const Run<double>& v, bool norm, cps_sys s,
