@@ -216,7 +216,7 @@ int cps_adjoint(cps_sys sys, const double* x, const double* g, double* lambda, d
  * xy, tri, eps and kinv (device pointers, same sizes and field_loc) that built
  * it; nothing of them is kept.  Stores per side slot the mean-flux geometry
  * l_j n_j, T_j, four co-normal weights and cell indices of the tangential flux
- * (App. C), per cell the RT0 weights and Mbar_e (about 360 bytes per cell).
+ * (App. C), per cell the RT0 weights and Mbar_e (about 376 bytes per cell).
  * A second call replaces the data.  Errors: CPS_ERR_ARG (not CP2, null
  * pointer), _NONDELAUNAY, _NONMANIFOLD, _ORIENTATION (inputs that do not
  * match the system), _NOMEM, _CUDA. */
