@@ -624,9 +624,12 @@ def run_graded(args):
             entry = {"seconds": t, "iters": st.iters, "us_per_iter": 1e6 * t / st.iters,
                      "rel_res": st.rel_res, "status": st.status}
             if name == "jacobi":
-                gbs = BYTES_PER_CELL_ITER_FP64 * cells / (t / st.iters) / 1e9
+                tf = s.tuning(cps.FP64)
+                bpc = BYTES_PER_CELL_ITER_FP64_1RED if tf["stream_single_reduction"] else \
+                    BYTES_PER_CELL_ITER_FP64
+                gbs = bpc * cells / (t / st.iters) / 1e9
                 entry.update({"algorithmic_gbs": gbs, "frac": gbs / peak,
-                              "path": s.tuning(cps.FP64)})
+                              "bytes_per_cell_iter": bpc, "path": tf})
             res[f"{order}_{name}"] = entry
         s.free()
     line = {"metric": "time to rtol on a graded unstructured Delaunay mesh",
