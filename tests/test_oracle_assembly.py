@@ -88,6 +88,24 @@ def test_cp1_matrix_rows_are_strictly_dominant_by_the_mass_term():
         assert np.all(sigma >= g.area / p.dt * (1 - 1e-14))
 
 
+@pytest.mark.parametrize("field_loc", [oracle.PER_VERTEX, oracle.PER_CELL])
+def test_cp1_mass_term_closed_form_for_uniform_fields(field_loc):
+    """Uniform eps and Kinv on the unjittered lattice: every cell's CP1 mass
+    term is Mbar_kk A_e = (1 + nu eps Kinv_kk dt)/dt * sqrt3/4 (the mean of
+    identical nodal values is that value), and T = nu l/d = nu sqrt3."""
+    m = synth.lattice(8, jitter=0.0)
+    nf = m.nv if field_loc == oracle.PER_VERTEX else m.nt
+    eps0, kxx, kxy, kyy = 0.4, 3.0e7, 1.0e6, 5.0e6
+    eps = np.full(nf, eps0)
+    kinv = np.tile([kxx, kxy, kyy], (nf, 1))
+    for kind, kk in ((oracle.CP1_X, kxx), (oracle.CP1_Y, kyy)):
+        T, sigma, isd, nbr = oracle.side_coefficients(m.xy, m.tri, m.dirichlet, eps, kinv,
+                                                      field_loc, kind, NU, DT)
+        want = (1.0 + NU * eps0 * kk * DT) / DT * S3 / 4
+        np.testing.assert_allclose(sigma, want, rtol=1e-13)
+        np.testing.assert_allclose(T[nbr >= 0], NU * S3, rtol=1e-13)
+
+
 def test_uniform_isotropic_lattice_transmissibility_closed_form():
     """Unjittered lattice, clear fluid: Xi = dt I, so every interior side has
     T = l d_n / d = 1 * dt / (1/sqrt3) and a Dirichlet side l dt / (1/(2 sqrt3))."""

@@ -1,4 +1,4 @@
-"""The pins of the corrector-step oracle catch plausible mistakes.
+"""The pins of the oracle catch plausible mistakes.
 
 Each case copies the oracle (and the input generator) to a scratch
 directory, plants one mistake in the copy -- a flipped or dropped term,
@@ -17,8 +17,55 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 CP2 = "test_oracle_cp2.py"
 CP1 = "test_oracle_cp1.py"
+GEO = "test_oracle_geometry.py"
+ASM = "test_oracle_assembly.py"
+SOL = "test_oracle_solve.py"
+ADJ = "test_oracle_adjoint.py"
 
 MISTAKES = [
+    # geometry (Sec. 3.1, Eq. cs1_discr)
+    ("circumcentre_sign", "cps_oracle.c", GEO,
+     "cc[2 * e + 0] = a[0] + (cy * b2 - by * c2) / (2.0 * cross);",
+     "cc[2 * e + 0] = a[0] + (by * c2 - cy * b2) / (2.0 * cross);"),
+    ("inward_normals", "cps_oracle.c", GEO,
+     "double nx = ty / l, ny = -tx / l; /* outward for a CCW triangle */",
+     "double nx = -ty / l, ny = tx / l; /* outward for a CCW triangle */"),
+    ("boundary_distance_halved", "cps_oracle.c", GEO,
+     "d = (mx - cc[2 * e]) * nx + (my - cc[2 * e + 1]) * ny;",
+     "d = 0.5 * ((mx - cc[2 * e]) * nx + (my - cc[2 * e + 1]) * ny);"),
+    # Xi (Eq. Cs2_4) and assembly (Eq. CS2_sys_coeff, Eq. CS1_sys_coeff)
+    ("xi_determinant_sign", "cps_oracle.c", ASM,
+     "double det = m00 * m11 - m01 * m01;", "double det = m00 * m11 + m01 * m01;"),
+    ("xi_offdiagonal_sign", "cps_oracle.c", ASM,
+     "xi[1] = -s * m01;", "xi[1] = s * m01;"),
+    ("transmissibility_times_distance", "cps_oracle.c", ASM,
+     "T[s] = len[s] * dn / d;", "T[s] = len[s] * dn * d;"),
+    ("side_tensor_from_one_node", "cps_oracle.c", ASM,
+     "for (int c = 0; c < 3; ++c) xs[c] = 0.5 * (xa[c] + xb[c]);\n                } else if (ep >= 0) {",
+     "for (int c = 0; c < 3; ++c) xs[c] = xa[c];\n                } else if (ep >= 0) {"),
+    ("cp1_mass_mean_over_two_nodes", "cps_oracle.c", ASM,
+     "mkk /= 3.0;", "mkk /= 2.0;"),
+    ("dirichlet_side_ignored", "cps_oracle.c", ASM,
+     "if (ep < 0 && !is_dirichlet[s]) continue; /* no-flux side */",
+     "if (ep < 0) continue; /* no-flux side */"),
+    # solves (Sec. 3.2.2: PCG with incomplete Cholesky)
+    ("cg_beta_inverted", "cps_oracle.c", SOL,
+     "double beta = rho_new / rho;", "double beta = rho / rho_new;"),
+    ("ic0_pivot_not_square_rooted", "cps_oracle.c", SOL,
+     "f->v[dpos] = sqrt(s);", "f->v[dpos] = s;"),
+    ("ic0_offdiagonal_not_scaled", "cps_oracle.c", SOL,
+     "f->v[p] = s / f->v[f->rp[kk + 1] - 1];", "f->v[p] = s;"),
+    ("dense_cholesky_diagonal", "cps_oracle.c", SOL,
+     "double ljj = sqrt(s);", "double ljj = s;"),
+    # adjoint (derived from Eq. CS2_sys_coeff)
+    ("side_gradient_sign", "cps_oracle.c", ADJ,
+     "if (ep >= 0) dT[s] = -(lambda[e] - lambda[ep]) * (x[e] - x[ep]);",
+     "if (ep >= 0) dT[s] = (lambda[e] - lambda[ep]) * (x[e] - x[ep]);"),
+    ("theta_chain_factor", "cps_oracle.c", ADJ,
+     "double dxi = xi * s / (1.0 + s);", "double dxi = xi / (1.0 + s);"),
+    ("interior_side_half_weight_dropped", "cps_oracle.c", ADJ,
+     "if (nbr[k] >= 0) g += dT[k] * len[k] / (2.0 * dist[k]);",
+     "if (nbr[k] >= 0) g += dT[k] * len[k] / dist[k];"),
     # CP2 step (Eq. flux_k_+_2/3, Eq. Cs2_6 / App. C, Eq. RT0, Eq. grad_PSI)
     ("ep_estimate_sign", "cps_oracle.c", CP2,
      "sum += est;\n                    ++count;\n                }\n            }\n            if (count",
@@ -83,14 +130,16 @@ def _copy(work, pins):
     shutil.copy(os.path.join(ROOT, "tests", pins), work / "tests")
 
 
-def _run_pins(work, pins):
-    return subprocess.run([sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider",
-                           os.path.join("tests", pins)], cwd=work, capture_output=True,
+def _run_pins(work, pins, first_failure=False):
+    args = [sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider"]
+    if first_failure:
+        args.append("-x")                     # one failing pin is enough
+    return subprocess.run(args + [os.path.join("tests", pins)], cwd=work, capture_output=True,
                           text=True, timeout=600)
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("pins", [CP2, CP1])
+@pytest.mark.parametrize("pins", [CP2, CP1, GEO, ASM, SOL, ADJ])
 def test_unplanted_copy_passes_its_pins(tmp_path, pins):
     """Control: the copy itself, with nothing planted, passes every pin."""
     if shutil.which("gcc") is None:
@@ -112,5 +161,5 @@ def test_pins_catch_planted_mistake(tmp_path, name, fname, pins, old, new):
     text = target.read_text()
     assert text.count(old) == 1, f"the planted line is not unique or missing in {fname}"
     target.write_text(text.replace(old, new))
-    r = _run_pins(work, pins)
+    r = _run_pins(work, pins, first_failure=True)
     assert r.returncode == 1 and " failed" in r.stdout, (name, r.stdout[-2000:], r.stderr[-2000:])
