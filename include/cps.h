@@ -25,7 +25,8 @@
  *   - Floating point arrays are IEEE binary64, row-major, contiguous.
  *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
  *     enqueued on it; calls that return a result the host needs (assemble,
- *     solve, adjoint) synchronise that stream before they return.
+ *     solve, adjoint, the CP1 and CP2 steps and their set-ups) synchronise that
+ *     stream before they return.
  *   - The return value is a status: CPS_OK (0) or a negative CPS_ERR_* code.
  *     No entry point aborts, traps or throws.  cps_last_error() gives a
  *     human-readable message for the last failing call on a context.
