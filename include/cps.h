@@ -172,7 +172,10 @@ int cps_export_matrix(cps_sys sys, double* diag, int32_t* col, double* val, void
  *               outer residual b - A x and update of x)
  *   stats       host pointer, may be NULL
  * b = 0 gives x = 0.  Errors: CPS_ERR_ARG, _NOT_SPD, _NOT_CONVERGED (x holds
- * the last iterate), _CUDA. */
+ * the last iterate; CPS_MIXED: the iterate with the least true residual, with
+ * that residual in stats -- where kappa(A) times the binary32 unit roundoff
+ * approaches 1 the binary32 corrections stop reducing the FP64 residual, and
+ * the solve ends there instead of letting refinement drive it up), _CUDA. */
 int cps_solve(cps_sys sys, const double* b, double* x, double rtol, int64_t max_iter,
               int precision, cps_stats* stats, void* stream);
 
@@ -323,7 +326,12 @@ int cps_cp2_kernel_times(cps_sys sys, float* ms);
  *     single-reduction (Chronopoulos-Gear) recurrences -- s = A p and w = A r
  *     are carried so that both inner products of an iteration come from one
  *     SpMV (two cluster barriers per iteration instead of three; one more
- *     vector in shared memory, so a somewhat smaller size limit).
+ *     vector in shared memory, so a somewhat smaller size limit);
+ *   CPS_PATH_PERSISTENT_1RED, CPS_PATH_PERSISTENT_1RED_L2 (FP64 Jacobi
+ *     only): the persistent launch with the single-reduction recurrences --
+ *     per iteration one wait on the neighbouring blocks and one grid
+ *     reduction -- without / with its five vectors in persisting L2
+ *     (CPS_ERR_ARG when the set-aside cannot hold them).
  * IC(0) and mixed precision always stream. */
 #define CPS_PATH_AUTO 0
 #define CPS_PATH_STREAM 1
@@ -334,6 +342,8 @@ int cps_cp2_kernel_times(cps_sys sys, float* ms);
 #define CPS_PATH_CLUSTER_1RED 6
 #define CPS_PATH_STREAM_1RED 7
 #define CPS_PATH_STREAM_1RED_L2 8
+#define CPS_PATH_PERSISTENT_1RED 9
+#define CPS_PATH_PERSISTENT_1RED_L2 10
 int cps_set_solver_path(cps_sys sys, int path);
 
 /* Pin the launch shapes of the iteration kernels of one precision instead of
@@ -365,20 +375,21 @@ int cps_test_inject(cps_sys sys, int fault);
  * (CPS_FP64 only) the direction update.  The tuner times every candidate on
  * the system's own data at its first solve; systems below 131072 cells keep
  * the defaults (unroll 2, 8 blocks per SM).  For CPS_FP64 Jacobi solves it
- * also times the ways of running the loop: flags (may be NULL, 6 entries)
+ * also times the ways of running the loop: flags (may be NULL, 7 entries)
  * receives {one-cluster launch chosen (0 no, 1 textbook recurrences, 2 the
  * single-reduction recurrences), persisting-L2 window (0 none, 1 the
  * matrix, 2 the vectors r, p, q, 3 the five vectors of the single-reduction
- * loop), persistent launch chosen, reduced system:
+ * loop), persistent launch chosen (either recurrence), reduced system:
  * persistent launch chosen, reduced system: window (0 or 2), single-reduction
- * streaming chosen}, probe_us (may be NULL, 12 entries) the microseconds per
- * iteration measured for {streaming, one cluster, streaming + matrix in L2,
- * persistent, streaming + vectors in L2, persistent + vectors in L2, reduced
- * system: streaming, persistent, streaming + vectors in L2, persistent +
- * vectors in L2, single-reduction streaming, single-reduction streaming +
- * vectors in L2} (0 where not tried; the persistent figures are the best over
- * the grid sizes tried, the one-cluster figure the better of its two
- * recurrences).
+ * streaming chosen, single-reduction persistent launch chosen}, probe_us (may
+ * be NULL, 14 entries) the microseconds per iteration measured for
+ * {streaming, one cluster, streaming + matrix in L2, persistent, streaming +
+ * vectors in L2, persistent + vectors in L2, reduced system: streaming,
+ * persistent, streaming + vectors in L2, persistent + vectors in L2,
+ * single-reduction streaming, single-reduction streaming + vectors in L2,
+ * single-reduction persistent, single-reduction persistent + vectors in L2}
+ * (0 where not tried; the persistent figures are the best over the grid sizes
+ * tried, the one-cluster figure the better of its two recurrences).
  * The context remembers what the tuner chose per mesh size (cells,
  * vertices): a system assembled later on the same context with the same
  * sizes starts from those choices and is not timed again.  A path forced by
@@ -415,12 +426,24 @@ int cps_get_tuning(cps_sys sys, int precision, int32_t* unroll, int32_t* grid, i
  *   stream            cudaStream_t on the current device
  * The first call on a device looks up the device address of the array
  * (cudaGetSymbolAddress) for that device, which is the current device of the
- * calling thread; make that first call before any stream capture.  Every
- * call on a device shares the same array and resets the parts that must
- * start at zero, so calls whose work overlaps on the GPU (different streams
- * or host threads at the same time) race with each other: serialise them.
+ * calling thread; make that first call before any stream capture.  Under
+ * CUDA's default lazy module loading that first call is also the moment the
+ * library's device code and data, this array included, are loaded onto the
+ * device: it is the one call that commits device memory and may synchronise
+ * the device.  Callers with a spent memory budget or a no-synchronisation
+ * rule should therefore make the first call during their start-up (or run
+ * with CUDA_MODULE_LOADING=EAGER, which loads everything at context
+ * creation).  Every call waits for its stream: it reads the iteration state
+ * back to the host after the set-up and after each chunk of 32 iterations.
+ * Every call on a device shares the same array and resets the parts that
+ * must start at zero, so calls whose work overlaps on the GPU (different
+ * streams or host threads at the same time) race with each other: serialise
+ * them.
  * Errors: CPS_ERR_ARG (size, NULL, column out of range), CPS_ERR_NOT_SPD
- * (diagonal <= 0 or p.Ap <= 0), CPS_ERR_NOT_CONVERGED, CPS_ERR_CUDA. */
+ * (diagonal <= 0 or p.Ap <= 0), CPS_ERR_NOT_CONVERGED, CPS_ERR_CUDA (also
+ * returned, without clearing it, when a CUDA error from the caller's earlier
+ * work is still pending on entry).  stats->status always equals the return
+ * value; rel_res is NaN when the call returned before computing a residual. */
 int cps_solve_ell_noalloc(int64_t n, const double* diag, const int32_t* col, const double* val,
                           const double* b, double* x, double rtol, int64_t max_iter,
                           cps_stats* stats, void* stream);

@@ -110,35 +110,40 @@ int read_state(const Scratch* sc, cudaStream_t stream, CgState* h) {
 extern "C" int cps_solve_ell_noalloc(int64_t n, const double* diag, const int32_t* col,
                                      const double* val, const double* b, double* x, double rtol,
                                      int64_t max_iter, cps_stats* stats, void* stream_ptr) {
-    if (n < 0 || n > kNoAllocMaxRows) return CPS_ERR_ARG;
-    if (n > 0 && (!diag || !col || !val || !b || !x)) return CPS_ERR_ARG;
-    if (!(rtol >= 0.0) || max_iter < 0) return CPS_ERR_ARG;
-    if (stats) *stats = cps_stats{0, 0.0, CPS_OK, 1, 0};
-    if (n == 0) return CPS_OK;
+    // Every return goes through finish(): stats, when given, always carries
+    // the returned status (rel_res NaN where no residual was computed).
+    int64_t total = 0, launches = 0;
+    auto finish = [&](int status, double rel) -> int {
+        if (stats) *stats = cps_stats{total, rel, status, 1, launches};
+        return status;
+    };
+    const double kNoResidual = std::nan("");
+    if (n < 0 || n > kNoAllocMaxRows) return finish(CPS_ERR_ARG, kNoResidual);
+    if (n > 0 && (!diag || !col || !val || !b || !x)) return finish(CPS_ERR_ARG, kNoResidual);
+    if (!(rtol >= 0.0) || max_iter < 0) return finish(CPS_ERR_ARG, kNoResidual);
+    if (n == 0) return finish(CPS_OK, 0.0);
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_ptr);
-    // A failure recorded by earlier, unrelated runtime calls would otherwise be
-    // reported as this call's own.
-    cudaGetLastError();
+    // An error left pending by the caller's earlier work is not this call's:
+    // report it without clearing it, so that the caller still sees it.
+    if (cudaPeekAtLastError() != cudaSuccess) return finish(CPS_ERR_CUDA, kNoResidual);
     Scratch* sc = nullptr;
     int rc = scratch_for_current_device(&sc);
-    if (rc) return rc;
+    if (rc) return finish(rc, kNoResidual);
     namespace K = cps_noalloc::cps;
     const int g = kNoAllocGrid;
-    int64_t launches = 0;
     // The state (including the reductions' arrival counters) and the error
     // flag must start at zero; the previous call's contents are stale.
     if (cudaMemsetAsync(&sc->st, 0, sizeof(CgState), stream) != cudaSuccess ||
         cudaMemsetAsync(&sc->err, 0, sizeof(int), stream) != cudaSuccess)
-        return CPS_ERR_CUDA;
+        return finish(CPS_ERR_CUDA, kNoResidual);
     kn_sqrt_diag<<<g, kBlock, 0, stream>>>(diag, n, sc->s, &sc->err);
     kn_scale<<<g, kBlock, 0, stream>>>(col, val, sc->s, n, sc->a, &sc->err);
     launches += 2;
     int herr = 0;
     if (cudaMemcpyAsync(&herr, &sc->err, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
         cudaStreamSynchronize(stream) != cudaSuccess)
-        return CPS_ERR_CUDA;
-    if (herr) return herr;
-    int64_t total = 0;
+        return finish(CPS_ERR_CUDA, kNoResidual);
+    if (herr) return finish(herr, kNoResidual);
     CgState h{};
     int status = CPS_OK;
     for (int restart = 0; restart < 8; ++restart) {
@@ -147,7 +152,7 @@ extern "C" int cps_solve_ell_noalloc(int64_t n, const double* diag, const int32_
                                               budget, 1, sc->partials, &sc->st);
         ++launches;
         rc = read_state(sc, stream, &h);
-        if (rc) return rc;
+        if (rc) return finish(rc, kNoResidual);
         while (!h.done && budget > 0) {
             for (int k = 0; k < kChunkIters; ++k) {
                 K::k_spmv_dot<double, 2><<<g, kBlock, 0, stream>>>(sc->a, col, sc->p, sc->q, n,
@@ -161,9 +166,9 @@ extern "C" int cps_solve_ell_noalloc(int64_t n, const double* diag, const int32_
                 K::k_cg_c<double, 2><<<g, kBlock, 0, stream>>>(sc->y, sc->p, sc->r, n, &sc->st);
                 launches += 3;
             }
-            if (cudaGetLastError() != cudaSuccess) return CPS_ERR_CUDA;
+            if (cudaGetLastError() != cudaSuccess) return finish(CPS_ERR_CUDA, kNoResidual);
             rc = read_state(sc, stream, &h);
-            if (rc) return rc;
+            if (rc) return finish(rc, kNoResidual);
         }
         total += h.iter;
         status = h.status;
@@ -171,11 +176,10 @@ extern "C" int cps_solve_ell_noalloc(int64_t n, const double* diag, const int32_
                                                &sc->st);
         ++launches;
         rc = read_state(sc, stream, &h);
-        if (rc) return rc;
+        if (rc) return finish(rc, kNoResidual);
         if (status != CPS_OK || h.rnorm2 <= h.thresh2 || total >= max_iter) break;
     }
     const double rel = h.bnorm2 > 0 ? std::sqrt(h.rnorm2 / h.bnorm2) : 0.0;
     if (status == CPS_OK && h.bnorm2 > 0 && !(rel <= rtol)) status = CPS_ERR_NOT_CONVERGED;
-    if (stats) *stats = cps_stats{total, rel, status, 1, launches};
-    return status;
+    return finish(status, rel);
 }
