@@ -15,6 +15,9 @@ Each function names the passage of the paper it follows:
   (CP2 transmissibility l_j d_{j,n}/d_{e,ep}), Eq. CS1_sys_coeff (CP1).
 * ``pcg`` -- PCG with Jacobi or incomplete Cholesky IC(0) in natural or a
   given (colour) order, Sec. 3.2.2 / 3.2.3.
+* ``pcg_jacobi_omp`` -- the same Jacobi-PCG with OpenMP parallel loops on
+  all host cores (``cps_oracle_omp.c``): a timing variant for the CPU
+  baseline, checked against ``pcg`` in the tests; never a parity reference.
 * ``dense_cholesky_solve`` -- textbook Cholesky, for tiny meshes.
 * ``side_gradient`` / ``theta_gradient`` -- adjoint of one solve with respect
   to the side coefficients and the log-permeability (derived from
@@ -43,6 +46,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "cps_oracle.c")
 _LIB = os.path.join(_HERE, "libcps_oracle.so")
+_SRC_OMP = os.path.join(_HERE, "cps_oracle_omp.c")
+_LIB_OMP = os.path.join(_HERE, "libcps_oracle_omp.so")
 
 OK = 0
 ERR_ARG = -1
@@ -68,13 +73,30 @@ class OracleError(RuntimeError):
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle shared library with gcc (plain C11, -O2)."""
+    """Compile the oracle shared library with gcc (plain C11, -O2), and its
+    multi-threaded timing variant (``build_omp``)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"],
                        check=True)
         os.replace(tmp, _LIB)
+    build_omp(force)
     return _LIB
+
+
+def build_omp(force: bool = False) -> str:
+    """Compile cps_oracle_omp.c (the oracle's Jacobi-PCG with OpenMP parallel
+    loops, the benchmark's CPU baseline) with -fopenmp; where the compiler
+    has no OpenMP the same source builds single-threaded."""
+    if force or not os.path.exists(_LIB_OMP) or \
+            os.path.getmtime(_LIB_OMP) < os.path.getmtime(_SRC_OMP):
+        tmp = _LIB_OMP + f".tmp{os.getpid()}"
+        base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC_OMP, "-lm"]
+        r = subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True)
+        if r.returncode != 0:
+            subprocess.run(base, check=True)
+        os.replace(tmp, _LIB_OMP)
+    return _LIB_OMP
 
 
 def _load():
@@ -274,6 +296,43 @@ def pcg(A: CSR, b, x0=None, rtol: float = 1e-10, maxit: int = 100000,
                         precond, None if pp is None else _p(pp), _p(st))
     if raise_on_error and rc not in (OK,):
         raise OracleError(rc, "pcg")
+    return x, SolveStats(int(st[0]), float(st[1]), float(st[2]), rc)
+
+
+_lib_omp = None
+
+
+def _load_omp():
+    global _lib_omp
+    with _lock:
+        if _lib_omp is None:
+            build_omp()
+            lib = ctypes.CDLL(_LIB_OMP)
+            P = ctypes.c_void_p
+            lib.oro_threads.argtypes = []
+            lib.oro_threads.restype = ctypes.c_int
+            lib.oro_pcg_jacobi.argtypes = [ctypes.c_int64, P, P, P, P, P, ctypes.c_double,
+                                           ctypes.c_int64, P]
+            _lib_omp = lib
+    return _lib_omp
+
+
+def omp_threads() -> int:
+    """Threads of the multi-threaded timing variant (OMP_NUM_THREADS, else
+    every core the process may run on)."""
+    return int(_load_omp().oro_threads())
+
+
+def pcg_jacobi_omp(A: CSR, b, x0=None, rtol: float = 1e-10, maxit: int = 100000):
+    """The textbook Jacobi-PCG of ``pcg`` with OpenMP parallel row loops and
+    reductions on all host cores (cps_oracle_omp.c): the benchmark's CPU
+    baseline.  Returns (x, SolveStats); the iterates equal ``pcg``'s up to
+    the summation order of the inner products."""
+    b = _f64(b)
+    x = np.zeros(A.n) if x0 is None else _f64(x0).copy()
+    st = np.zeros(3)
+    rc = _load_omp().oro_pcg_jacobi(A.n, _p(A.rowptr), _p(A.col), _p(A.val), _p(b), _p(x),
+                                    rtol, maxit, _p(st))
     return x, SolveStats(int(st[0]), float(st[1]), float(st[2]), rc)
 
 
