@@ -45,14 +45,34 @@ BYTES_PER_CELL_ITER_FP64 = 52 + 24 + 40 + 1
 BYTES_PER_CELL_ITER_MIXED = 48 + 12 + 0.5
 #   FP64 single-reduction loop, two kernels: k_gear_update reads p, s, w, r, y
 #     and writes p, s, y, r (72); k_gear_spmv reads r, 3 values, 3 columns and
-#     writes w (8 + 24 + 12 + 8 = 52); every 8th SpMV also reads S (+1).
+#     writes w (8 + 24 + 12 + 8 = 52); every 8th SpMV also reads S (+1).  The
+#     persistent single-reduction launch moves the same bytes.
 BYTES_PER_CELL_ITER_FP64_1RED = 72 + 52 + 1
-# DRAM bytes (read + write) of one FP64 Jacobi iteration (k_spmv_dot + k_cg_b
-# + k_cg_c) on the 1024 x 1024 channel lattice, from one ncu capture of the
-# configuration below (profiles/pcg_iteration_traffic_channel1024.md); the
-# line reports it only when the autotuner chose the same launch grids, block
-# sizes and L2 window (the rows per thread per trip, which the tuner may set
+# The method's own unit, whatever loop runs it: one Jacobi-PCG iteration must
+# stream the matrix once (diagonal 8 + three values 24 + three int32 columns
+# 12 = 44 B) and read and write the state vectors x, r, p and q = A p once each
+# (4 x 16 = 64 B): 108 B per cell per iteration.  The headline roofline
+# fraction divides these bytes; the bytes the chosen loop moves (117 or 125,
+# extra vectors of its recurrence included) are reported beside it.
+BYTES_PER_CELL_ITER_METHOD = 44 + 64
+# DRAM bytes (read + write) of one FP64 Jacobi iteration, measured by ncu on
+# the 1024 x 1024 channel lattice for a fixed launch configuration of each
+# loop (grids, block sizes, L2 window).  The line reports a figure only when
+# the autotuner chose that same configuration, and says that it comes from a
+# stored capture (the rows per thread per trip, which the tuner may set
 # differently from box to box, do not change the bytes a kernel moves).
+TRAFFIC_CAPTURES = [
+    # textbook three-kernel loop, r, p, q in persisting L2
+    ({"grid": [608, 152, 152], "block": [256, 1024, 1024], "l2_window": "vectors",
+      "persistent": False, "cluster": False, "stream_single_reduction": False},
+     (121.8 + 21.9 + 40.9) * 1e6),
+    # single-reduction streaming loop (k_gear_update + k_gear_spmv), the five
+    # vectors in persisting L2, update kernel on 152 x 1024 threads
+    ({"grid": [608, 152, 152], "block": [256, 1024, 1024], "l2_window": "vectors5",
+      "persistent": False, "cluster": False, "stream_single_reduction": True,
+      "update_1red_grid_block": [152, 1024]},
+     (108.3 + 124.5) * 1e6),
+]
 # Algorithmic bytes per cell of the CP2 step kernels (each array counted once):
 # mean flux: u 16, per side col 4 + area weight 8 + l n 16, Fbar out 24, B1 out 8;
 # tangential: eta 8, per side col 4 + 4 weights 32 + 4 indices 16, tau out 24,
@@ -66,30 +86,75 @@ BYTES_PER_CELL_CP2 = {"mean_flux": 132, "tangential": 204, "update": 252}
 # before HBM does.
 FP64_INSTR_PER_CELL_CP2 = {"mean_flux": 24, "tangential": 28, "update": 21}
 FP64_INSTR_PER_SM_CLK = 2
-TRAFFIC_PER_ITER_N1024 = (121.8 + 21.9 + 40.9) * 1e6
-TRAFFIC_CONFIG = {"grid": [608, 152, 152], "block": [256, 1024, 1024],
-                  "l2_window": "vectors", "persistent": False, "cluster": False,
-                  "stream_single_reduction": False}
-# The same for the single-reduction loop (k_gear_update + k_gear_spmv, the
-# five vectors in persisting L2; its update kernel takes the residual update's
-# tuned shape, the SpMV the SpMV's).
-TRAFFIC_PER_ITER_N1024_1RED = (108.3 + 124.5) * 1e6   # profiles/pcg_iteration_single_reduction_channel1024.md
-TRAFFIC_CONFIG_1RED = {"grid": [608, 152, 152], "block": [256, 1024, 1024],
-                       "l2_window": "vectors5", "persistent": False, "cluster": False,
-                       "stream_single_reduction": True, "update_1red_grid_block": [152, 1024]}
 
 
 def traffic_for(tf: dict, n: int):
-    """ncu DRAM bytes per iteration of the loop the tuner chose, when a
+    """ncu DRAM bytes per iteration of the loop the tuner chose, when a stored
     capture of that loop, grids, blocks and window exists (n = 1024)."""
     if n != 1024:
         return None
     tf = dict(tf, update_1red_grid_block=tf.get("update_1red", [0, 0, 0])[1:])
-    for cfg, traffic in ((TRAFFIC_CONFIG, TRAFFIC_PER_ITER_N1024),
-                         (TRAFFIC_CONFIG_1RED, TRAFFIC_PER_ITER_N1024_1RED)):
-        if traffic is not None and all(tf[k] == v for k, v in cfg.items()):
+    for cfg, traffic in TRAFFIC_CAPTURES:
+        if all(tf.get(k) == v for k, v in cfg.items()):
             return traffic
     return None
+
+
+def loop_name(tf: dict) -> str:
+    """The FP64 Jacobi loop the tuner chose, with its kernels."""
+    if tf.get("persistent_single_reduction"):
+        kname = ("k_persistent_gear (whole Jacobi-PCG solve in one cooperative launch, "
+                 "Chronopoulos-Gear recurrences)")
+    elif tf["persistent"]:
+        kname = "k_persistent_cg (whole Jacobi-PCG solve in one cooperative launch)"
+    elif tf["cluster"]:
+        kname = "k_cluster_cg (whole Jacobi-PCG solve in one thread-block cluster)"
+    elif tf["stream_single_reduction"]:
+        kname = ("pcg_iteration_fp64_single_reduction (k_gear_update + k_gear_spmv, Jacobi, "
+                 "Chronopoulos-Gear recurrences)")
+    else:
+        kname = "pcg_iteration_fp64 (k_spmv_dot + k_cg_b + k_cg_c, Jacobi)"
+    if tf["l2_window"] != "none":
+        kname += {"matrix": "; matrix in persisting L2",
+                  "vectors": "; r, p, q in persisting L2",
+                  "vectors5": "; r, p, s, y, w in persisting L2"}[tf["l2_window"]]
+    return kname
+
+
+def loop_bytes(tf: dict) -> int:
+    """Bytes per cell per iteration the chosen FP64 Jacobi loop moves."""
+    single = tf["stream_single_reduction"] or tf.get("persistent_single_reduction")
+    return BYTES_PER_CELL_ITER_FP64_1RED if single else BYTES_PER_CELL_ITER_FP64
+
+
+def roofline(tf: dict, nt: int, iters: int, seconds: float, peak: float, peak_kind: str,
+             n: int) -> dict:
+    """Roofline of one FP64 Jacobi-PCG iteration: achieved = the method's
+    108 algorithmic bytes per cell x cells / (solve time / iterations); the
+    solve time is the whole timed solve (start-up, stop tests and the final
+    true residual included), so the per-iteration figure is a lower bound."""
+    per_iter = seconds / max(iters, 1)
+    bpc = loop_bytes(tf)
+    achieved = BYTES_PER_CELL_ITER_METHOD * nt / per_iter / 1e9
+    loop_achieved = bpc * nt / per_iter / 1e9
+    traffic = traffic_for(tf, n)
+    return {"bound": "hbm", "kernel": loop_name(tf),
+            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_kind": peak_kind, "bytes_per_cell_iter": BYTES_PER_CELL_ITER_METHOD,
+            "algorithmic_bytes_per_iter": BYTES_PER_CELL_ITER_METHOD * nt,
+            "us_per_iter": 1e6 * per_iter,
+            "loop_bytes_per_cell_iter": bpc, "loop_achieved": loop_achieved,
+            "loop_frac": loop_achieved / peak,
+            "traffic": traffic,
+            "traffic_unit": "bytes per iteration (DRAM read + write, ncu)",
+            "traffic_source": ("stored ncu capture of this loop and launch configuration on "
+                               "this workload" if traffic is not None else
+                               "no capture of this loop and configuration")}
+
+
+def workload_label(n: int, rtol: float) -> str:
+    """The benchmark's workload, named the same way by both arms."""
+    return f"channel-block-aniso lattice n={n} (CP2, Jacobi-PCG, rtol {rtol:g})"
 
 
 def parse():
@@ -101,8 +166,8 @@ def parse():
     ap.add_argument("--rtol", type=float, default=1e-10)
     ap.add_argument("--impl", default="cps", choices=["cps", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-iters", type=int, default=0,
-                    help="oracle PCG iterations in the CPU sample (0: auto)")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="seconds of multi-threaded oracle PCG in the CPU baseline sample")
     ap.add_argument("--batch", type=int, default=0,
                     help="ensemble mode: this many systems of log-uniform 2k-500k cells, "
                          "batched solve vs a loop of single solves (prints its own line)")
@@ -135,7 +200,8 @@ def parse():
                     help="profiling run only: pin the FP64 Jacobi configuration instead of "
                          "tuning it (a profiler's replay skews the tuner), as "
                          "'U0,U1,U2/G0,G1,G2/B0,B1,B2/PATH' with PATH stream, stream_l2, "
-                         "persistent, persistent_l2, stream_1red or stream_1red_l2 (for the "
+                         "persistent, persistent_l2, stream_1red, stream_1red_l2, persistent_1red "
+                         "or persistent_1red_l2 (for the "
                          "reduced system too)")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiling run: assemble, then FP64 and mixed solves bounded to this "
@@ -217,44 +283,68 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def cpu_baseline(problem, b, iters: int) -> dict:
-    """The oracle as it stands (single thread) on a bounded sample: assembly
-    plus a fixed number of Jacobi-PCG iterations on the same workload."""
+def host_cores() -> int:
+    """Cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(problem, b, seconds: float = 10.0) -> dict:
+    """The CPU baseline on a bounded sample of the same workload: the oracle's
+    assembly, then its Jacobi-PCG with OpenMP parallel loops on all the host's
+    cores (oracle.pcg_jacobi_omp) for as many iterations as fill about
+    `seconds` (sized from a 20-iteration calibration run).  The single-
+    threaded oracle's rate on a shorter sample is reported beside it."""
     import oracle
     t0 = time.perf_counter()
     A = oracle.assemble_problem(problem)
     t1 = time.perf_counter()
-    x, st = oracle.pcg(A, b, rtol=0.0, maxit=iters, precond=oracle.PC_JACOBI,
-                       raise_on_error=False)
-    t2 = time.perf_counter()
     nt = problem.mesh.nt
-    return {"value": nt * st.iters / (t2 - t0), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"oracle assembly ({t1 - t0:.2f} s) + {st.iters} Jacobi-PCG iterations "
-                      f"({t2 - t1:.2f} s) on the same {nt}-cell system, single thread",
-            "pcg_only_cell_iters_per_s": nt * st.iters / (t2 - t1)}
+    _, cal = oracle.pcg_jacobi_omp(A, b, rtol=0.0, maxit=20)
+    t2 = time.perf_counter()
+    per_iter = max((t2 - t1) / max(cal.iters, 1), 1e-6)
+    iters = max(20, int(seconds / per_iter))
+    _, st = oracle.pcg_jacobi_omp(A, b, rtol=0.0, maxit=iters)
+    t3 = time.perf_counter()
+    threads = oracle.omp_threads()
+    one_iters = max(5, iters // (4 * threads))
+    _, st1 = oracle.pcg(A, b, rtol=0.0, maxit=one_iters, precond=oracle.PC_JACOBI,
+                        raise_on_error=False)
+    t4 = time.perf_counter()
+    return {"value": nt * st.iters / ((t3 - t2) + (t1 - t0)), "unit": UNIT, "cores": threads,
+            "host_cores": host_cores(), "kind": "oracle",
+            "sample": f"oracle assembly ({t1 - t0:.2f} s, single thread) + {st.iters} Jacobi-PCG "
+                      f"iterations ({t3 - t2:.2f} s) of the oracle's PCG with OpenMP parallel "
+                      f"loops on {threads} threads, same {nt}-cell system",
+            "pcg_only_cell_iters_per_s": nt * st.iters / (t3 - t2),
+            "single_thread_oracle_pcg_cell_iters_per_s": nt * st1.iters / (t4 - t3)}
 
 
 def run_reference(args):
-    """--impl reference: the CPU oracle timed on the host cores."""
+    """--impl reference: the CPU baseline (the oracle's assembly and its
+    Jacobi-PCG on all host cores) timed on the same workload and metric.
+    Each step is a bounded sample sized so that warm-up plus timed steps take
+    about two minutes."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
     p = synth.channel_block_problem(args.n, seed=0)
     b = synth.rhs(p.mesh, seed=1)
-    iters = args.cpu_iters or max(20, int(1e9 / p.mesh.nt))
+    per_step = min(10.0, max(1.0, 120.0 / max(args.warmup + args.steps, 1)))
     vals = []
     for k in range(args.warmup + args.steps):
-        r = cpu_baseline(p, b, iters)
+        r = cpu_baseline(p, b, seconds=per_step)
         if k >= args.warmup:
             vals.append(r)
     v = float(np.mean([r["value"] for r in vals]))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"channel-block-aniso lattice n={args.n}",
-                       "cells": p.mesh.nt},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": vals[0]["sample"]},
+            "config": {"workload": workload_label(args.n, args.rtol), "cells": p.mesh.nt},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[0]["cores"],
+                             "kind": "oracle", "sample": vals[0]["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -625,11 +715,13 @@ def run_graded(args):
                      "rel_res": st.rel_res, "status": st.status}
             if name == "jacobi":
                 tf = s.tuning(cps.FP64)
-                bpc = BYTES_PER_CELL_ITER_FP64_1RED if tf["stream_single_reduction"] else \
-                    BYTES_PER_CELL_ITER_FP64
-                gbs = bpc * cells / (t / st.iters) / 1e9
+                bpc = loop_bytes(tf)
+                gbs = BYTES_PER_CELL_ITER_METHOD * cells / (t / st.iters) / 1e9
                 entry.update({"algorithmic_gbs": gbs, "frac": gbs / peak,
-                              "bytes_per_cell_iter": bpc, "path": tf})
+                              "bytes_per_cell_iter": BYTES_PER_CELL_ITER_METHOD,
+                              "loop_bytes_per_cell_iter": bpc,
+                              "loop_frac": bpc / BYTES_PER_CELL_ITER_METHOD * gbs / peak,
+                              "path": tf})
             res[f"{order}_{name}"] = entry
         s.free()
     line = {"metric": "time to rtol on a graded unstructured Delaunay mesh",
@@ -735,7 +827,9 @@ def main():
                                "persistent": cps.PATH_PERSISTENT,
                                "persistent_l2": cps.PATH_PERSISTENT_L2,
                                "stream_1red": cps.PATH_STREAM_1RED,
-                               "stream_1red_l2": cps.PATH_STREAM_1RED_L2}[path])
+                               "stream_1red_l2": cps.PATH_STREAM_1RED_L2,
+                               "persistent_1red": cps.PATH_PERSISTENT_1RED,
+                               "persistent_1red_l2": cps.PATH_PERSISTENT_1RED_L2}[path])
         for pc in (cps.PC_JACOBI, cps.PC_IC0):
             s.set_precond(pc)
             for prec in (cps.FP64, cps.MIXED):
@@ -871,8 +965,14 @@ def main():
             continue
         for path_name, path in (("stream", cps.PATH_STREAM), ("cluster", cps.PATH_CLUSTER),
                                 ("persistent", cps.PATH_PERSISTENT),
-                                ("stream_1red", cps.PATH_STREAM_1RED)):
-            if pc == cps.PC_REDUCED and path in (cps.PATH_CLUSTER, cps.PATH_STREAM_1RED):
+                                ("stream_1red", cps.PATH_STREAM_1RED),
+                                ("stream_1red_l2", cps.PATH_STREAM_1RED_L2),
+                                ("persistent_1red", cps.PATH_PERSISTENT_1RED),
+                                ("persistent_1red_l2", cps.PATH_PERSISTENT_1RED_L2)):
+            if pc == cps.PC_REDUCED and path in (cps.PATH_CLUSTER, cps.PATH_STREAM_1RED,
+                                                 cps.PATH_STREAM_1RED_L2,
+                                                 cps.PATH_PERSISTENT_1RED,
+                                                 cps.PATH_PERSISTENT_1RED_L2):
                 continue
             try:
                 s.set_solver_path(path)
@@ -889,29 +989,8 @@ def main():
     library = library_spmv(s, x, stream)
     s.free()
     jf = variants["jacobi_fp64"]
-    tf = tuning["fp64"]
-    bpc = BYTES_PER_CELL_ITER_FP64_1RED if tf["stream_single_reduction"] else \
-        BYTES_PER_CELL_ITER_FP64
-    achieved = bpc * nt * jf["iters"] / jf["time_to_rtol_s"] / 1e9
-    if tf["persistent"]:
-        kname = "k_persistent_cg (whole Jacobi-PCG solve in one cooperative launch)"
-    elif tf["cluster"]:
-        kname = "k_cluster_cg (whole Jacobi-PCG solve in one thread-block cluster)"
-    elif tf["stream_single_reduction"]:
-        kname = ("pcg_iteration_fp64_single_reduction (k_gear_update + k_gear_spmv, Jacobi, "
-                 "Chronopoulos-Gear recurrences)")
-    else:
-        kname = "pcg_iteration_fp64 (k_spmv_dot + k_cg_b + k_cg_c, Jacobi)"
-    if tf["l2_window"] != "none":
-        kname += {"matrix": "; matrix in persisting L2",
-                  "vectors": "; r, p, q in persisting L2",
-                  "vectors5": "; r, p, s, y, w in persisting L2"}[tf["l2_window"]]
-    roof = {"bound": "hbm", "kernel": kname,
-            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "peak_kind": peak_kind, "bytes_per_cell_iter": bpc,
-            "traffic": traffic_for(tf, args.n),
-            "traffic_unit": "bytes per iteration (DRAM read + write, ncu)",
-            "algorithmic_bytes_per_iter": bpc * nt}
+    roof = roofline(tuning["fp64"], nt, jf["iters"], jf["time_to_rtol_s"], peak, peak_kind,
+                    args.n)
     jm = variants["jacobi_mixed"]
     jm["inner_gbs"] = BYTES_PER_CELL_ITER_MIXED * nt * jm["iters"] / jm["time_to_rtol_s"] / 1e9
 
@@ -920,8 +999,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"channel-block-aniso lattice n={args.n} (CP2, Jacobi-PCG, "
-                               f"rtol {args.rtol:g})",
+        "config": {"workload": workload_label(args.n, args.rtol),
                    "cells": nt, "iters_per_step": int(np.mean(iters)),
                    "l2": "256 MB buffer written between steps",
                    "parallelism": f"replicas x{world}"},
@@ -935,8 +1013,7 @@ def main():
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        iters_cpu = args.cpu_iters or max(20, int(1e9 / nt))
-        line["cpu_baseline"] = cpu_baseline(p, b_np, iters_cpu)
+        line["cpu_baseline"] = cpu_baseline(p, b_np, seconds=args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg is not None:

@@ -139,8 +139,8 @@ class System:
         u = (ctypes.c_int32 * 3)()
         g = (ctypes.c_int32 * 3)()
         bl = (ctypes.c_int32 * 3)()
-        f = (ctypes.c_int32 * 6)()
-        pr = (ctypes.c_double * 12)()
+        f = (ctypes.c_int32 * 7)()
+        pr = (ctypes.c_double * 14)()
         self.ctx.check(self.ctx.lib.cps_get_tuning(self.handle, precision, u, g, bl, f, pr),
                        "cps_get_tuning")
         gu, gg, gb = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
@@ -154,18 +154,21 @@ class System:
                 "persistent": bool(f[2]), "reduced_persistent": bool(f[3]),
                 "reduced_l2_window": ("none", "matrix", "vectors")[f[4]],
                 "stream_single_reduction": bool(f[5]),
+                "persistent_single_reduction": bool(f[6]),
                 "update_1red": [gu.value, gg.value, gb.value],
                 "probe_us_per_iter": {
                     "stream": pr[0], "cluster": pr[1], "stream_l2_matrix": pr[2],
                     "persistent": pr[3], "stream_l2_vectors": pr[4], "persistent_l2_vectors": pr[5],
                     "reduced_stream": pr[6], "reduced_persistent": pr[7],
                     "reduced_stream_l2_vectors": pr[8], "reduced_persistent_l2_vectors": pr[9],
-                    "stream_1red": pr[10], "stream_1red_l2_vectors": pr[11]}}
+                    "stream_1red": pr[10], "stream_1red_l2_vectors": pr[11],
+                    "persistent_1red": pr[12], "persistent_1red_l2_vectors": pr[13]}}
 
     def set_solver_path(self, path: int):
         """PATH_AUTO, PATH_STREAM, PATH_CLUSTER, PATH_CLUSTER_1RED,
-        PATH_PERSISTENT, PATH_STREAM_L2, PATH_PERSISTENT_L2, PATH_STREAM_1RED or
-        PATH_STREAM_1RED_L2 for FP64 Jacobi (and reduced-system) solves."""
+        PATH_PERSISTENT, PATH_STREAM_L2, PATH_PERSISTENT_L2, PATH_STREAM_1RED,
+        PATH_STREAM_1RED_L2, PATH_PERSISTENT_1RED or PATH_PERSISTENT_1RED_L2 for
+        FP64 Jacobi (and reduced-system) solves."""
         self.ctx.check(self.ctx.lib.cps_set_solver_path(self.handle, path), "cps_set_solver_path")
 
     def set_kernel_shapes(self, precision: int, unroll, grid, block):

@@ -235,6 +235,16 @@ int cps_set_solver_path(cps_sys sys, int path) {
         t.path_done = true;
         t.path = 3;
         t.l2win = win;
+    } else if (path == CPS_PATH_PERSISTENT_1RED || path == CPS_PATH_PERSISTENT_1RED_L2) {
+        if (path == CPS_PATH_PERSISTENT_1RED_L2 && !cps::l2_window_fits_mode(sys, 3)) {
+            cps::set_error(sys->ctx, "set_solver_path: the persisting L2 set-aside cannot hold "
+                                     "the five vectors of the single-reduction loop");
+            return CPS_ERR_ARG;
+        }
+        t.path_done = true;
+        t.path = 4;
+        t.l2win = path == CPS_PATH_PERSISTENT_1RED_L2 ? 3 : 0;
+        t.pgrid = 0;
     } else if (path == CPS_PATH_PERSISTENT) {
         t.path_done = true;
         t.path = 2;
@@ -331,16 +341,19 @@ int cps_get_tuning(cps_sys sys, int precision, int32_t* unroll, int32_t* grid, i
     if (flags) {
         flags[0] = (t.path_done && t.path == 1) ? 1 + t.cluster_variant : 0;
         flags[1] = t.path_done ? t.l2win : 0;
-        flags[2] = t.path_done && t.path == 2;
+        flags[2] = t.path_done && (t.path == 2 || t.path == 4);
         flags[3] = t.red_done && t.red_path == 1;
         flags[4] = t.red_done ? t.red_win : 0;
         flags[5] = t.path_done && t.path == 3;
+        flags[6] = t.path_done && t.path == 4;
     }
     if (probe_us) {
         for (int k = 0; k < 6; ++k) probe_us[k] = t.probe_us[k];
         for (int k = 0; k < 4; ++k) probe_us[6 + k] = t.red_probe_us[k];
         probe_us[10] = t.probe_us[6];
         probe_us[11] = t.probe_us[7];
+        probe_us[12] = t.probe_us[8];
+        probe_us[13] = t.probe_us[9];
     }
     return CPS_OK;
 }

@@ -421,7 +421,7 @@ int assemble_impl(cps_ctx ctx, const double* xy, int64_t nv, const int32_t* tri,
     TRY_ALLOC(s->slot_kind, 3 * nt);
     {
         const int64_t vs = (nt + 31) / 32 * 32;     // 256-byte aligned slices
-        TRY_ALLOC(s->wvec, 8 * vs);
+        TRY_ALLOC(s->wvec, 9 * vs);
         s->vec_stride = vs;
         double* w = s->wvec;
         s->wr = w;
@@ -432,6 +432,7 @@ int assemble_impl(cps_ctx ctx, const double* xy, int64_t nv, const int32_t* tri,
         s->wz = w + 5 * vs;
         s->wb = w + 6 * vs;
         s->wx = w + 7 * vs;
+        s->wbest = w + 8 * vs;
     }
     TRY_ALLOC(s->partials, (kNumPartials + 16) * kMaxGrid);
     TRY_ALLOC(s->st, 2);

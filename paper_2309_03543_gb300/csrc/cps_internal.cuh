@@ -58,16 +58,19 @@ struct Tuning {
     bool done = false;
     int path = 0;            // FP64 Jacobi: 0 graph-replayed kernels, 1 one-cluster launch,
                              // 2 one persistent grid-synchronised launch, 3 graph-replayed
-                             // single-reduction kernels
+                             // single-reduction kernels, 4 one persistent launch of the
+                             // single-reduction recurrences
     int red_path = 0;        // reduced system: 0 graph-replayed kernels, 1 persistent launch
     bool red_done = false;
     bool path_done = false;
     int l2win = 0;           // FP64 Jacobi stream path, persisting L2 window: 0 none,
                              // 1 the matrix, 2 the vectors r, p, q, 3 r, p, q, y, p1
-    double probe_us[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // us/iteration: stream, cluster,
-                                               // stream + matrix in L2, persistent, stream +
-                                               // vectors in L2, persistent + vectors in L2,
-                                               // single-reduction stream (+ vectors in L2)
+    double probe_us[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};   // us/iteration: stream,
+                                               // cluster, stream + matrix in L2, persistent,
+                                               // stream + vectors in L2, persistent + vectors
+                                               // in L2, single-reduction stream (+ vectors in
+                                               // L2), single-reduction persistent (+ vectors
+                                               // in L2)
     double red_probe_us[4] = {0, 0, 0, 0};   // reduced system: stream, persistent, and the
                                              // same with r, p, q in persisting L2
     int red_win = 0;         // reduced system: persisting L2 window (0 none, 2 r, p, q)
@@ -294,9 +297,9 @@ struct cps_sys_s {
     float* ps32 = nullptr;
 
     // PCG workspace (allocated at assembly so that solves never allocate), one
-    // allocation of 8 vectors of vec_stride doubles in the order r, p0, q, y,
-    // p1, z, b, x: r, p0 and q, the vectors every iteration reads and writes,
-    // are one contiguous range for an L2 access-policy window.
+    // allocation of 9 vectors of vec_stride doubles in the order r, p0, q, y,
+    // p1, z, b, x, best: r, p0 and q, the vectors every iteration reads and
+    // writes, are one contiguous range for an L2 access-policy window.
     double* wvec = nullptr;
     int64_t vec_stride = 0;
     double* wy = nullptr;       // [nt] iterate (scaled)
@@ -307,6 +310,7 @@ struct cps_sys_s {
     double* wz = nullptr;       // [nt] preconditioned residual (IC0)
     double* wb = nullptr;       // [nt] right-hand side in colour order
     double* wx = nullptr;       // [nt] FP64 iterate in colour order
+    double* wbest = nullptr;    // [nt] mixed precision: FP64 iterate with the least residual
     double* partials = nullptr; // [(kNumPartials + 16) * kMaxGrid]
     cps::CgState* st = nullptr; // device state
     cps::CgState* hst = nullptr;  // pinned host mirror (2 slots)

@@ -29,6 +29,7 @@ constexpr int kChunk = 32;          // iterations per graph replay
 constexpr int kCheckEvery = 8;      // stop test period inside a chunk
 constexpr double kDelta = 0.5;      // residual drop between reliable updates
 constexpr int kMaxUpdates = 2000;
+constexpr double kDiverge = 1e4;    // mixed: ||r||^2 this far above the best ends the solve
 constexpr int64_t kTuneMinRows = 1 << 17;   // smaller systems keep the defaults
 constexpr int kTuneIters = 32;               // iterations per timed candidate
 }  // namespace
@@ -608,13 +609,16 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
     // candidates (slot in probe_us): 0 streaming, 1 one-cluster launch,
     // 2 streaming with the matrix in persisting L2, 3 one persistent
     // grid-synchronised launch, 4 streaming with the vectors r, p, q in
-    // persisting L2, 5 persistent with the vectors in persisting L2.  The
-    // persistent launch is timed at a few grid sizes (fewer blocks
-    // synchronise faster; more blocks move more bytes).
+    // persisting L2, 5 persistent with the vectors in persisting L2,
+    // 6 single-reduction streaming, 7 the same with its vectors in
+    // persisting L2, 8 single-reduction persistent, 9 the same with its five
+    // vectors in persisting L2.  The persistent launches are timed at a few
+    // grid sizes (fewer blocks synchronise faster; more blocks move more
+    // bytes).
     struct Cand {
         int slot, path, win, grid, var;
     };
-    Cand cands[16];
+    Cand cands[24];
     int nc = 0;
     cands[nc++] = {0, 0, 0, 0, 0};
     if (try_cluster) cands[nc++] = {1, 1, 0, 0, 0};
@@ -639,10 +643,21 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
             if (big && l2_window_fits(s, 2)) cands[nc++] = {5, 2, 2, gi, 0};
         }
     }
+    if (!try_cluster) {
+        const int gmax = persistent_max_grid(s, 2);
+        int grids[2] = {gmax, (int)((s->nt + 8191) / 8192)};
+        for (int i = 0; i < 2; ++i) {
+            const int gi = grids[i] < 1 ? 1 : (grids[i] > gmax ? gmax : grids[i]);
+            if (gmax <= 0 || (i == 1 && gi == grids[0])) continue;
+            grids[i] = gi;
+            cands[nc++] = {8, 4, 0, gi, 0};
+            if (big && l2_window_fits(s, 3)) cands[nc++] = {9, 4, 3, gi, 0};
+        }
+    }
     cudaEvent_t e0, e1;
     CPS_CUDA_TRY(s->ctx, cudaEventCreate(&e0));
     CPS_CUDA_TRY(s->ctx, cudaEventCreate(&e1));
-    double per_iter[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    double per_iter[10] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     double best_t = 0.0;
     Cand best{0, 0, 0, 0, 0};
     int rc = CPS_OK;
@@ -662,10 +677,14 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
                 break;
             }
             CgState h{};
-            if (c.path == 2) {
+            if (c.path == 2 || c.path == 4) {
                 k_init64<<<s->grid, kBlock, 0, stream>>>(b, s->wx, v.s, v.a, v.col, s->nt, v.y, v.r,
                                                          v.p0, 0.0, probe, 1, s->partials, s->st);
-                rc = persistent_solve(s, 0, v.a, v.col, v.s, v.y, v.r, v.p0, v.q, nullptr, s->nt,
+                if (c.path == 4)
+                    k_gear_start<<<s->grid, kBlock, 0, stream>>>(v.a, v.col, v.r, v.p1, v.p0, v.q,
+                                                                 s->nt, s->partials, s->st);
+                rc = persistent_solve(s, c.path == 4 ? 2 : 0, v.a, v.col, v.s, v.y, v.r, v.p0, v.q,
+                                      c.path == 4 ? v.p1 : nullptr, s->nt,
                                       0, c.win ? l2_window_base(s, c.win) : nullptr,
                                       c.win ? l2_window_bytes(s, c.win) : 0, c.grid, stream);
                 if (rc == CPS_OK) rc = read_state(s, stream, &h);
@@ -757,7 +776,7 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
         t.pgrid = best.grid;
         t.cluster_variant = best.var;
     }
-    for (int k = 0; k < 8; ++k) t.probe_us[k] = per_iter[k];
+    for (int k = 0; k < 10; ++k) t.probe_us[k] = per_iter[k];
     if (rc == CPS_OK) {
         update_cached_tuning(s, CPS_FP64, [&](Tuning& c) {
             c.path_done = true;
@@ -767,7 +786,7 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
             c.cluster_variant = t.cluster_variant;
             c.kg = t.kg;
             c.kg_set = t.kg_set;
-            for (int k = 0; k < 8; ++k) c.probe_us[k] = t.probe_us[k];
+            for (int k = 0; k < 10; ++k) c.probe_us[k] = t.probe_us[k];
         });
     }
     return rc;
@@ -791,7 +810,8 @@ static int solve_fp64(cps_sys s, const double* b, double* x, double rtol, int64_
         if (rc) return rc;
     }
     const bool cluster = !ic0 && s->tune[CPS_FP64].path == 1;
-    const bool persistent = !ic0 && s->tune[CPS_FP64].path == 2;
+    const bool persistent = !ic0 && (s->tune[CPS_FP64].path == 2 || s->tune[CPS_FP64].path == 4);
+    const bool pgear = !ic0 && s->tune[CPS_FP64].path == 4;
     const bool gear = !ic0 && s->tune[CPS_FP64].path == 3;
     const int window = (!ic0 && !cluster) ? s->tune[CPS_FP64].l2win : 0;
     if (window) {
@@ -832,8 +852,14 @@ static int solve_fp64(cps_sys s, const double* b, double* x, double rtol, int64_
                                             budget, ic0 ? 0 : 1, s->partials, s->st);
         ++launches;
         if (persistent) {
+            if (pgear) {
+                k_gear_start<<<g, kBlock, 0, stream>>>(v.a, v.col, v.r, v.p1, v.p0, v.q, n,
+                                                       s->partials, s->st);
+                ++launches;
+            }
             // one launch runs to the stop (it returns at once if init stopped)
-            int rc = persistent_solve(s, 0, v.a, v.col, v.s, v.y, v.r, v.p0, v.q, nullptr, n, 0,
+            int rc = persistent_solve(s, pgear ? 2 : 0, v.a, v.col, v.s, v.y, v.r, v.p0, v.q,
+                                      pgear ? v.p1 : nullptr, n, 0,
                                       window ? l2_window_base(s, window) : nullptr,
                                       window ? l2_window_bytes(s, window) : 0,
                                       s->tune[CPS_FP64].pgrid, stream);
@@ -1165,7 +1191,13 @@ static int solve_mixed(cps_sys s, const double* b, double* x, double rtol, int64
     }
     int64_t base = 0;          // iterations of runs before the last restart
     int updates = 0, stall = 0, restarts = 0;
-    double prev = INFINITY;
+    double prev = INFINITY, last = INFINITY;
+    // The FP64 iterate with the least true residual so far is kept in wbest:
+    // where kappa(A) u_32 approaches 1 the binary32 corrections stop helping
+    // and refinement can drive the residual up; the solve then ends with that
+    // iterate and CPS_ERR_NOT_CONVERGED.
+    double best = INFINITY;
+    bool restore = false;
     int first = 1;
     CgState h{};
     int status = CPS_OK;
@@ -1179,21 +1211,35 @@ static int solve_mixed(cps_sys s, const double* b, double* x, double rtol, int64
         int rc = read_state(s, stream, &h);
         if (rc) return rc;
         if (h.bnorm2 == 0.0 || h.rnorm2 <= rtol * rtol * h.bnorm2) break;   // converged
+        if (h.rnorm2 < best) {
+            best = h.rnorm2;
+            CPS_CUDA_TRY(s->ctx, cudaMemcpyAsync(s->wbest, xx, sizeof(double) * n,
+                                                 cudaMemcpyDeviceToDevice, stream));
+        } else if (!(h.rnorm2 <= kDiverge * best)) {
+            status = CPS_ERR_NOT_CONVERGED;      // refinement diverging
+            restore = true;
+            break;
+        }
         if (base + h.iter >= max_iter || updates >= kMaxUpdates) {
             status = CPS_ERR_NOT_CONVERGED;
+            restore = h.rnorm2 > best;
             break;
         }
         // A replaced residual that stops falling (no 10% gain over 8
-        // replacements): restart the search directions.
+        // replacements) or that rose since the last replacement: restart
+        // the search directions.
         if (h.rnorm2 < 0.81 * prev) {
             prev = h.rnorm2;
             stall = 0;
         } else {
             ++stall;
         }
-        if (stall >= 8 && !first) {
+        const bool rose = h.rnorm2 > last;
+        last = h.rnorm2;
+        if ((stall >= 8 || rose) && !first) {
             if (++restarts > 4) {
                 status = CPS_ERR_NOT_CONVERGED;
+                restore = h.rnorm2 > best;
                 break;
             }
             base += h.iter;
@@ -1215,6 +1261,11 @@ static int solve_mixed(cps_sys s, const double* b, double* x, double rtol, int64
         k_correct<<<g, kBlock, 0, stream>>>(xx, v.y, S64, n);
         launches += 2;
     }
+    if (restore) {
+        CPS_CUDA_TRY(s->ctx, cudaMemcpyAsync(xx, s->wbest, sizeof(double) * n,
+                                             cudaMemcpyDeviceToDevice, stream));
+        h.rnorm2 = best;
+    }
     if (ic0) {
         k_permute_out<<<g, kBlock, 0, stream>>>(s->wx, s->perm, n, x);
         ++launches;
@@ -1224,7 +1275,11 @@ static int solve_mixed(cps_sys s, const double* b, double* x, double rtol, int64
     CPS_CUDA_TRY(s->ctx, cudaStreamSynchronize(stream));
     const double rel = h.bnorm2 > 0 ? std::sqrt(h.rnorm2 / h.bnorm2) : 0.0;
     fill_stats(stats, base + h.iter, rel, status, updates, launches);
-    if (status == CPS_ERR_NOT_CONVERGED) cps::set_error(s->ctx, "solve: mixed precision did not reach rtol");
+    if (status == CPS_ERR_NOT_CONVERGED)
+        cps::set_error(s->ctx, restore ? "solve: mixed precision did not reach rtol (binary32 "
+                                         "refinement stopped reducing the residual; x holds the "
+                                         "iterate with the least residual)"
+                                       : "solve: mixed precision did not reach rtol");
     if (status == CPS_ERR_NOT_SPD) cps::set_error(s->ctx, "solve: p.Ap <= 0 in the binary32 iteration");
     return status;
 }

@@ -42,6 +42,7 @@ constexpr long long kSpinCap = 1LL << 26;           // polls; each one an L2 rou
 constexpr unsigned long long kWaitNs = 1000000000ull;
 constexpr int kFlagStride = 16;                      // one 128-byte line per block flag
 constexpr int kMaxDeps = 8;
+constexpr int kPartialSlots = 4;                     // quantities per reduction buffer
 
 struct GridSync {
     unsigned long long count;   // arrivals since the launch
@@ -62,6 +63,11 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
     unsigned long long v;
     asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
+}
+
+// Hint: fetch the line holding p into this SM's L1 (no register result).
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -86,64 +92,142 @@ __device__ bool wait_geq(const unsigned long long* p, unsigned long long target,
     return *(volatile int*)&gs->timeout == 0;
 }
 
-// Barriers passed by this block (reductions and grid barriers).
+// Barriers passed by this block: reductions (k picks the partial buffer) and
+// the arrival count that completes the latest barrier (every barrier adds its
+// arrivals per block x the grid).
 struct Epoch {
     unsigned long long k = 0;
+    unsigned long long target = 0;
     unsigned long long extra = 0;   // test hook: arrivals a barrier waits for beyond the grid
 };
 
-// Grid-wide sum of v[0..NV) (NV <= 2).  Lane 0 of warp 0 then derives the
-// block's scalars from the totals, post(tot, sc, flag) (once per block: a
-// FP64 divide per thread would cost GB300 more than a vector sweep), and
-// every thread receives sc[0..NS) and the flag.  Returns false if a wait ran
-// out somewhere.
+__device__ __forceinline__ void named_barrier(int id, int threads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+// ---- Exact sums in integer arithmetic.  GB300 issues FP64 at 2 per SM per
+// clock, and a chain of dependent FP64 adds pays the FP64 latency per add: a
+// block sum of 1024 doubles took about 2 us that way.  Here a set of doubles
+// is summed by aligning every value to the set's largest exponent E
+// (rounding to the nearest multiple of 2^(E - 1075 + h), h bits of headroom)
+// and adding the aligned integers exactly, with warp integer reductions on
+// 18-20-bit limbs.  The result depends on the set only, not on the order of
+// the values (deterministic, bit-identical in every block that sums the same
+// set); each value is off by at most half a unit of 2^(E - 1075 + h).
+
+// Biased exponent of v's binade (1 for zero and subnormals).
+__device__ __forceinline__ int align_exp(double v) {
+    const int e = (int)((__double_as_longlong(v) >> 52) & 0x7FF);
+    return e > 0 ? e : 1;
+}
+
+// round(v / 2^(E - 1075 + h)) for |v| < 2^(E - 1022), h >= 1: at most 2^(53 - h)
+// in magnitude.
+__device__ __forceinline__ long long align_fixed(double v, int E, int h) {
+    const long long bits = __double_as_longlong(v);
+    const int e = (int)((bits >> 52) & 0x7FF);
+    long long m = bits & 0xFFFFFFFFFFFFFLL;
+    if (e) m |= 1LL << 52;
+    const int sh = E - (e > 0 ? e : 1) + h;
+    const long long f = sh > 62 ? 0 : ((m + (1LL << (sh - 1))) >> sh);
+    return bits < 0 ? -f : f;
+}
+
+// T 2^(E - 1075 + h) as a double (NaN if the set held an infinity or NaN).
+__device__ __forceinline__ double fixed_to_double(long long T, int E, int h) {
+    if (E >= 2047) return __longlong_as_double(0x7FF8000000000000LL);
+    return ldexp(__ll2double_rn(T), E - 1075 + h);
+}
+
+// Exact sum over the warp of x, |x| <= 2^B (B <= 57): the biased value
+// x + 2^B is split into three limbs whose 32-lane sums fit 32 bits; the
+// recombination runs modulo 2^64, exact because the true sum (at most
+// 2^(B + 5)) fits a signed 64-bit integer.
+template <int B>
+__device__ __forceinline__ long long warp_sum_fixed(long long x) {
+    constexpr int L = (B + 4) / 3;
+    static_assert(B <= 57 && L <= 26 && 3 * L >= B + 2, "limbs of the biased value");
+    const unsigned long long u = (unsigned long long)x + (1ULL << B);
+    const unsigned mask = (1u << L) - 1u;
+    const unsigned long long s0 = __reduce_add_sync(0xffffffffu, (unsigned)(u & mask));
+    const unsigned long long s1 = __reduce_add_sync(0xffffffffu, (unsigned)((u >> L) & mask));
+    const unsigned long long s2 = __reduce_add_sync(0xffffffffu, (unsigned)(u >> (2 * L)));
+    return (long long)(s0 + (s1 << L) + (s2 << (2 * L)) - (32ULL << B));
+}
+
+// Grid-wide sum of v[0..NV) (NV <= 4), every stage in exact integer sums:
+// the block aligns its 1024 values per quantity to their largest exponent
+// and sums them (two warp-reduction rounds through shared memory); warp k
+// stores the block total of quantity k and, after the grid's arrivals, stages
+// the G block totals in buf[k] (G <= kPBlock) and sums them the same way.
+// Lane 0 of warp 0 then derives the block's scalars from the totals,
+// post(tot, sc, flag) (once per block: a FP64 divide per thread would cost
+// more than a vector sweep), and every thread receives sc[0..NS) and the
+// flag.  Returns false if a wait ran out somewhere.
 template <int NV, int NS, typename Post>
-__device__ bool grid_allreduce(double (&v)[NV], double (&out)[NS], int& flag, double* partials,
-                               GridSync* gs, Epoch& ep, Post post) {
-    static_assert(NV >= 1 && NV <= 2, "two partial slots per buffer");
-    __shared__ double buf[NV][kPBlock];
+__device__ __forceinline__ bool grid_allreduce(double (*buf)[kPBlock], double (&v)[NV],
+                                               double (&out)[NS], int& flag, double* partials,
+                                               GridSync* gs, Epoch& ep, Post post) {
+    static_assert(NV >= 1 && NV <= kPartialSlots, "partial slots per buffer");
+    __shared__ int s_e[kPartialSlots][32];
+    __shared__ long long s_w[kPartialSlots][32];
+    __shared__ int s_eb[kPartialSlots];
+    __shared__ double tot[kPartialSlots];
     __shared__ double sc[NS];
     __shared__ int s_flag;
     __shared__ int s_ok;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < NV; ++k) buf[k][threadIdx.x] = v[k];
+    for (int k = 0; k < NV; ++k) {
+        const int em = __reduce_max_sync(0xffffffffu, align_exp(v[k]));
+        if (lane == 0) s_e[k][warp] = em;
+    }
     __syncthreads();            // also orders every thread's phase writes before the arrival
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const int E = __reduce_max_sync(0xffffffffu, s_e[k][lane]);
+        const long long w = warp_sum_fixed<52>(align_fixed(v[k], E, 1));
+        if (lane == 0) {
+            s_w[k][warp] = w;
+            if (warp == 0) s_eb[k] = E;
+        }
+    }
+    __syncthreads();
     const unsigned int G = gridDim.x;
-    double* pb = partials + (size_t)(ep.k & 1) * (2 * kMaxGrid);
+    double* pb = partials + (size_t)(ep.k & 1) * (kPartialSlots * kMaxGrid);
     ++ep.k;
-    if (threadIdx.x < 32) {
+    ep.target += G;
+    if (warp < NV) {
+        const long long T = warp_sum_fixed<57>(s_w[warp][lane]);
+        if (lane == 0) pb[warp * kMaxGrid + blockIdx.x] = fixed_to_double(T, s_eb[warp], 1);
+        // the arrival (one per block) follows the NV partial stores; the
+        // barrier among the NV warps orders them before warp 0's release
+        if (NV > 1) named_barrier(1, NV * 32);
+        if (warp == 0 && lane == 0) {
+            red_release_add(&gs->count, 1ull);
+            s_ok = wait_geq(&gs->count, ep.target + ep.extra, gs) ? 1 : 0;
+        }
+        if (NV > 1) named_barrier(1, NV * 32);
+        else __syncwarp();
+        int em = 1;
+        for (unsigned int i = lane; i < G; i += 32) {
+            const double t = __ldcg(&pb[warp * kMaxGrid + i]);
+            buf[warp][i] = t;
+            em = max(em, align_exp(t));
+        }
+        const int E = __reduce_max_sync(0xffffffffu, em);
+        __syncwarp();
+        long long acc = 0;       // at most G/32 <= 32 values of 2^50 a lane
+        for (unsigned int i = lane; i < G; i += 32) acc += align_fixed(buf[warp][i], E, 3);
+        const long long T2 = warp_sum_fixed<57>(acc);
+        if (lane == 0) tot[warp] = fixed_to_double(T2, E, 3);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
         double t[NV];
 #pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            double a = buf[k][lane];
-#pragma unroll
-            for (int j = lane + 32; j < kPBlock; j += 32) a += buf[k][j];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-            t[k] = a;
-        }
-        int ok = 1;
-        if (lane == 0) {
-#pragma unroll
-            for (int k = 0; k < NV; ++k) pb[k * kMaxGrid + blockIdx.x] = t[k];
-            red_release_add(&gs->count, 1ull);
-            ok = wait_geq(&gs->count, ep.k * (unsigned long long)G + ep.extra, gs) ? 1 : 0;
-        }
-        __syncwarp();
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            double a = 0.0;
-            for (unsigned int i = lane; i < G; i += 32) a += __ldcg(&pb[k * kMaxGrid + i]);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-            t[k] = a;
-        }
-        if (lane == 0) {
-            s_ok = ok;
-            post(t, sc, s_flag);
-        }
+        for (int k = 0; k < NV; ++k) t[k] = tot[k];
+        post(t, sc, s_flag);
     }
     __syncthreads();
 #pragma unroll
@@ -156,10 +240,10 @@ __device__ bool grid_allreduce(double (&v)[NV], double (&out)[NS], int& flag, do
 __device__ bool grid_barrier(GridSync* gs, Epoch& ep) {
     __shared__ int s_ok;
     __syncthreads();
-    ++ep.k;
+    ep.target += gridDim.x;
     if (threadIdx.x == 0) {
         red_release_add(&gs->count, 1ull);
-        s_ok = wait_geq(&gs->count, ep.k * (unsigned long long)gridDim.x + ep.extra, gs) ? 1 : 0;
+        s_ok = wait_geq(&gs->count, ep.target + ep.extra, gs) ? 1 : 0;
     }
     __syncthreads();
     return s_ok != 0;
@@ -233,6 +317,7 @@ struct PersistArgs {
     GridSync* gs;
     CgState* st;
     int stall;          // test hook: 1 makes every barrier wait for one arrival too many
+    double dmin;        // single-reduction Jacobi: smallest diagonal entry (stop-test gate)
 };
 
 // Rows per block for m rows over the grid: a multiple of 32.
@@ -273,6 +358,10 @@ constexpr int kUV = 4;   // rows per trip in the vector phases (2 or 3 loads per
 //   [wait for the halo] q = Ahat p, gamma | alpha; r -= alpha q; rho',
 //   ||S r||^2 | beta, stop; y += alpha p; p = r + beta p; post
 __global__ void __launch_bounds__(kPBlock, 1) k_persistent_cg(PersistArgs P) {
+    __shared__ double rbuf[2][kPBlock];
+    // the run's scalars (the same in every block) in shared memory, so that
+    // the streaming phases keep their registers: rho, ||S r||^2
+    __shared__ double sc[2];
     CgState* st = P.st;
     if (st->done) return;                      // uniform: set before the launch
     const int64_t n = P.n;
@@ -319,7 +408,7 @@ __global__ void __launch_bounds__(kPBlock, 1) k_persistent_cg(PersistArgs P) {
         double wide[1] = {(dhi - dlo + 1 > kMaxDeps) ? 1.0 : 0.0};
         double none[1];
         int any = 0;
-        ok = grid_allreduce<1, 1>(wide, none, any, P.partials, gs, ep,
+        ok = grid_allreduce<1, 1>(rbuf, wide, none, any, P.partials, gs, ep,
                                   [](const double (&t)[1], double* o, int& f) {
                                       o[0] = 0.0;
                                       f = t[0] > 0.0 ? 1 : 0;
@@ -327,12 +416,12 @@ __global__ void __launch_bounds__(kPBlock, 1) k_persistent_cg(PersistArgs P) {
         halo = any == 0;
     }
     // the run's scalars (the same values in every thread of every block)
-    double rho = st->rho;
-    const double thresh2 = st->thresh2;
-    const long long max_iter = st->max_iter;
+    if (threadIdx.x == 0) {
+        sc[0] = st->rho;
+        sc[1] = st->rnorm2;
+    }
     long long it = 0;
     int status = CPS_OK;
-    double rnorm2 = st->rnorm2;
     while (ok) {
         if (halo && it > 0) {
             ok = halo_wait(gs, dlo, dhi, (unsigned long long)it);
@@ -355,10 +444,10 @@ __global__ void __launch_bounds__(kPBlock, 1) k_persistent_cg(PersistArgs P) {
         }
         double sa[1];
         int bad = 0;
-        ok = grid_allreduce<1, 1>(g, sa, bad, P.partials, gs, ep,
+        ok = grid_allreduce<1, 1>(rbuf, g, sa, bad, P.partials, gs, ep,
                                   [&](const double (&t)[1], double* o, int& f) {
                                       f = (t[0] > 0.0 && isfinite(t[0])) ? 0 : 1;
-                                      o[0] = f ? 0.0 : rho / t[0];
+                                      o[0] = f ? 0.0 : sc[0] / t[0];
                                   });
         if (!ok) break;
         if (bad) {
@@ -380,22 +469,23 @@ __global__ void __launch_bounds__(kPBlock, 1) k_persistent_cg(PersistArgs P) {
                 }
             })
         }
-        double sb[3];
+        double sb[1];
         int stop = 0;
-        ok = grid_allreduce<2, 3>(rr, sb, stop, P.partials, gs, ep,
+        const long long it1 = it + 1;
+        ok = grid_allreduce<2, 1>(rbuf, rr, sb, stop, P.partials, gs, ep,
                                   [&](const double (&t)[2], double* o, int& f) {
-                                      bool halt = !(t[0] > 0.0) || it + 1 >= max_iter;
-                                      if (check && t[1] <= thresh2) halt = true;
-                                      o[0] = t[0] / rho;     // beta
-                                      o[1] = t[0];           // rho'
-                                      o[2] = t[1];           // ||S r||^2
+                                      bool halt = !(t[0] > 0.0) || it1 >= st->max_iter;
+                                      if (check) {
+                                          sc[1] = t[1];  // ||S r||^2
+                                          if (t[1] <= st->thresh2) halt = true;
+                                      }
+                                      o[0] = t[0] / sc[0];   // beta
+                                      sc[0] = t[0];          // rho'
                                       f = halt ? 1 : 0;
                                   });
         if (!ok) break;
         ++it;
-        if (check) rnorm2 = sb[2];
         const double beta = sb[0];
-        rho = sb[1];
         {
             double pe[kUV], ye[kUV], re[kUV];
             CPS_B_LOOP(lo, hi, kUV, (pe[u] = p[e], ye[u] = y[e], re[u] = stop ? 0.0 : r[e]), {
@@ -412,9 +502,216 @@ __global__ void __launch_bounds__(kPBlock, 1) k_persistent_cg(PersistArgs P) {
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->iter = it;
-        st->rho = rho;
-        st->rnorm2 = rnorm2;
+        st->rho = sc[0];
+        st->rnorm2 = sc[1];
         st->status = ok ? status : CPS_ERR_TIMEOUT;
+        st->done = 2;
+    }
+}
+
+constexpr int kUG = 2;    // rows per trip in the single-reduction update (5 loads per row)
+constexpr int kUGS = 2;   // rows per trip in its SpMV phase
+constexpr double kNormGate = 64.0;   // margin of the stop-test gate (see k_persistent_gear)
+
+// FP64 Jacobi CG with the single-reduction (Chronopoulos-Gear) recurrences,
+// from the state k_init64 + k_gear_start left (w = Ahat r, p = s = 0,
+// alpha = rho / delta, beta = 0), s = Ahat p and w = Ahat r carried by
+// recurrence so that both inner products of an iteration come from one SpMV:
+//   p = r + beta p; s = w + beta s; y += alpha p; r -= alpha s       | post
+//   [wait for the halo] w = Ahat r; gamma = r.r, delta = w.r (every 8th:
+//   ||S r||^2) | one grid reduction: stop test, beta = gamma / gamma_old,
+//   alpha = gamma / (delta - beta gamma / alpha_old)
+// One neighbour wait and one grid reduction per iteration (the textbook
+// persistent loop has two reductions), at 9 FP64 FMAs per row.  The
+// reduction after the SpMV also orders the next update's writes of r after
+// every block's reads of it.  s lives in P.q, w in P.t.
+__global__ void __launch_bounds__(kPBlock, 1) k_persistent_gear(PersistArgs P) {
+    __shared__ double rbuf[3][kPBlock];
+    // The run's scalars, the same values in every block: kept in shared
+    // memory (thread 0 updates them inside the reduction) so that the
+    // streaming phases keep their registers.
+    // rho, alpha, beta, ||S r||^2, 1/rho, 1/(rho alpha), stop threshold
+    __shared__ double sc[7];
+    __shared__ long long s_max_iter;
+    __shared__ int s_stop;        // 1 stop, 2 breakdown
+    CgState* st = P.st;
+    if (st->done) return;                      // uniform: set before the launch
+    const int64_t n = P.n;
+    const double* __restrict__ A = P.a;
+    const int32_t* __restrict__ C = P.col;
+    double* __restrict__ y = P.y;
+    double* __restrict__ r = P.r;
+    double* __restrict__ p = P.p;
+    double* __restrict__ s = P.q;
+    double* __restrict__ w = P.t;
+    GridSync* gs = P.gs;
+    const int64_t R = rows_per_block(n);
+    const int64_t lo = blockIdx.x * R < n ? blockIdx.x * R : n;
+    const int64_t hi = lo + R < n ? lo + R : n;
+    Epoch ep;
+    ep.extra = P.stall ? 1ull : 0ull;
+    int dlo, dhi;
+    column_blocks(C, n, lo, hi, 0, R, &dlo, &dhi);
+    if (threadIdx.x == 0) {
+        sc[0] = st->rho;
+        sc[1] = st->alpha;
+        sc[2] = st->beta;
+        sc[3] = st->rnorm2;
+        sc[4] = 1.0 / st->rho;
+        sc[5] = 1.0 / (st->rho * st->alpha);
+        sc[6] = st->thresh2;
+        s_max_iter = st->max_iter;
+        s_stop = 0;
+    }
+    bool ok;
+    bool halo;
+    {
+        double wide[1] = {(dhi - dlo + 1 > kMaxDeps) ? 1.0 : 0.0};
+        double none[1];
+        int any = 0;
+        ok = grid_allreduce<1, 1>(rbuf, wide, none, any, P.partials, gs, ep,
+                                  [](const double (&t)[1], double* o, int& f) {
+                                      o[0] = 0.0;
+                                      f = t[0] > 0.0 ? 1 : 0;
+                                  });
+        halo = any == 0;
+    }
+    long long it = 0;
+    while (ok) {
+        {
+            const double alpha = sc[1], beta = sc[2];
+            double pe[kUG], se[kUG], we[kUG], re[kUG], ye[kUG];
+            CPS_B_LOOP(lo, hi, kUG,
+                (pe[u] = p[e], se[u] = s[e], we[u] = w[e], re[u] = r[e], ye[u] = y[e]),
+                {
+                    const double pn = fma(beta, pe[u], re[u]);
+                    const double sn = fma(beta, se[u], we[u]);
+                    p[e] = pn;
+                    s[e] = sn;
+                    y[e] = fma(alpha, pn, ye[u]);
+                    r[e] = fma(-alpha, sn, re[u]);
+                })
+        }
+        if (halo) {
+            halo_post(gs, (unsigned long long)(it + 1));
+            // the SpMV's first trip reads this block's rows only up to the
+            // gathers: fetch them into L1 while waiting on the neighbours
+#pragma unroll
+            for (int u = 0; u < kUGS; ++u) {
+                const int64_t e = lo + threadIdx.x + u * (int64_t)kPBlock;
+                if (e < hi) {
+                    prefetch_l1(r + e);
+                    prefetch_l1(A + e);
+                    prefetch_l1(A + n + e);
+                    prefetch_l1(A + 2 * n + e);
+                    prefetch_l1(C + e);
+                    prefetch_l1(C + n + e);
+                    prefetch_l1(C + 2 * n + e);
+                }
+            }
+            ok = halo_wait(gs, dlo, dhi, (unsigned long long)(it + 1));
+        } else {
+            ok = grid_barrier(gs, ep);
+        }
+        if (!ok) break;
+        // Stop test on ||S r||^2 every 8th iteration, and only once it can
+        // hold: ||S r||^2 >= min(diag) r.r, so while min(diag) gamma stays
+        // above kNormGate times the threshold the test cannot pass (gamma of
+        // the last iteration stands in for this one's, with that margin) and
+        // the sum is skipped (two FP64 operations a row).
+        const bool check = ((it + 1) % 8) == 0 && P.dmin * sc[0] <= kNormGate * sc[6];
+        double sums[3] = {0.0, 0.0, 0.0};
+        {
+            double re[kUGS], a0[kUGS], a1[kUGS], a2[kUGS];
+            int32_t c0[kUGS], c1[kUGS], c2[kUGS];
+            CPS_B_LOOP(lo, hi, kUGS,
+                (re[u] = r[e], a0[u] = A[e], a1[u] = A[n + e], a2[u] = A[2 * n + e],
+                 c0[u] = C[e], c1[u] = C[n + e], c2[u] = C[2 * n + e]),
+                {
+                    double v = fma(a0[u], r[c0[u]], re[u]);
+                    v = fma(a1[u], r[c1[u]], v);
+                    v = fma(a2[u], r[c2[u]], v);
+                    w[e] = v;
+                    sums[0] = fma(re[u], re[u], sums[0]);
+                    sums[1] = fma(v, re[u], sums[1]);
+                    if (check) {
+                        const double tt = P.s[e] * re[u];
+                        sums[2] = fma(tt, tt, sums[2]);
+                    }
+                })
+        }
+        // the next update's first trip reads only this block's own rows,
+        // final now: fetch them into L1 during the reduction
+#pragma unroll
+        for (int u = 0; u < kUG; ++u) {
+            const int64_t e = lo + threadIdx.x + u * (int64_t)kPBlock;
+            if (e < hi) {
+                prefetch_l1(p + e);
+                prefetch_l1(s + e);
+                prefetch_l1(w + e);
+                prefetch_l1(r + e);
+                prefetch_l1(y + e);
+            }
+        }
+        // thread 0, from the totals: the stop test, beta = gamma/gamma_old
+        // and alpha = gamma/den with den = delta - beta gamma/alpha_old =
+        // delta - gamma^2/(gamma_old alpha_old).  1/gamma_old and
+        // 1/(gamma_old alpha_old) are carried, so one divide stays on the
+        // critical path; 1/gamma issues beside it.
+        const long long it1 = it + 1;
+        auto post = [&](const double* t, bool chk, int& f) {
+            const double g = t[0], d = t[1];
+            bool halt = !(g > 0.0) || it1 >= s_max_iter;       // exact solution, budget
+            if (chk) {
+                sc[3] = t[2];
+                if (t[2] <= sc[6]) halt = true;
+            }
+            f = halt ? 1 : 0;
+            if (!halt) {
+                const double den = fma(-(g * g), sc[5], d);
+                if (!(den > 0.0) || !isfinite(den)) {
+                    f = 2;
+                } else {
+                    const double ig = 1.0 / g;
+                    sc[1] = g / den;
+                    sc[2] = g * sc[4];
+                    sc[4] = ig;
+                    sc[5] = den * ig * ig;
+                }
+            }
+            sc[0] = g;
+        };
+        double none[1];
+        int flag = 0;
+        if (check) {
+            double v3[3] = {sums[0], sums[1], sums[2]};
+            ok = grid_allreduce<3, 1>(rbuf, v3, none, flag, P.partials, gs, ep,
+                                      [&](const double (&t)[3], double* o, int& f) {
+                                          o[0] = 0.0;
+                                          post(t, true, f);
+                                      });
+        } else {
+            double v2[2] = {sums[0], sums[1]};
+            ok = grid_allreduce<2, 1>(rbuf, v2, none, flag, P.partials, gs, ep,
+                                      [&](const double (&t)[2], double* o, int& f) {
+                                          o[0] = 0.0;
+                                          post(t, false, f);
+                                      });
+        }
+        if (!ok) break;
+        it = it1;
+        if (flag) {
+            if (threadIdx.x == 0) s_stop = flag;
+            break;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->iter = it;
+        st->rho = sc[0];
+        st->alpha = sc[1];
+        st->beta = sc[2];
+        st->rnorm2 = sc[3];
+        st->status = ok ? (s_stop == 2 ? CPS_ERR_NOT_SPD : CPS_OK) : CPS_ERR_TIMEOUT;
         st->done = 2;
     }
 }
@@ -424,6 +721,10 @@ __global__ void __launch_bounds__(kPBlock, 1) k_persistent_cg(PersistArgs P) {
 // [b Rr, (b+1) Rr) and black rows nR + [b Rb, (b+1) Rb).
 //   t_R = E p_B | q_B = p_B - E^T t_R, gamma | r -= alpha q, rho' | y, p |
 __global__ void __launch_bounds__(kPBlock, 1) k_persistent_reduced(PersistArgs P) {
+    __shared__ double rbuf[2][kPBlock];
+    // the run's scalars (the same in every block) in shared memory, so that
+    // the streaming phases keep their registers: rho, ||S r||^2
+    __shared__ double sc[2];
     CgState* st = P.st;
     if (st->done) return;
     const int64_t n = P.n, nR = P.nR, nB = n - nR;
@@ -440,12 +741,12 @@ __global__ void __launch_bounds__(kPBlock, 1) k_persistent_reduced(PersistArgs P
     const int64_t rhi = rlo + Rr < nR ? rlo + Rr : nR;
     const int64_t blo = nR + (blockIdx.x * Rb < nB ? blockIdx.x * Rb : nB);
     const int64_t bhi = blo + Rb < n ? blo + Rb : n;
-    double rho = st->rho;
-    const double thresh2 = st->thresh2;
-    const long long max_iter = st->max_iter;
+    if (threadIdx.x == 0) {
+        sc[0] = st->rho;
+        sc[1] = st->rnorm2;
+    }
     long long it = 0;
     int status = CPS_OK;
-    double rnorm2 = st->rnorm2;
     bool ok = true;
     Epoch ep;
     ep.extra = P.stall ? 1ull : 0ull;
@@ -462,7 +763,7 @@ __global__ void __launch_bounds__(kPBlock, 1) k_persistent_reduced(PersistArgs P
         double w[1] = {wide ? 1.0 : 0.0};
         double none[1];
         int any = 0;
-        ok = grid_allreduce<1, 1>(w, none, any, P.partials, gs, ep,
+        ok = grid_allreduce<1, 1>(rbuf, w, none, any, P.partials, gs, ep,
                                   [](const double (&tt)[1], double* o, int& f) {
                                       o[0] = 0.0;
                                       f = tt[0] > 0.0 ? 1 : 0;
@@ -513,10 +814,10 @@ __global__ void __launch_bounds__(kPBlock, 1) k_persistent_reduced(PersistArgs P
         }
         double sa[1];
         int bad = 0;
-        ok = grid_allreduce<1, 1>(g, sa, bad, P.partials, gs, ep,
+        ok = grid_allreduce<1, 1>(rbuf, g, sa, bad, P.partials, gs, ep,
                                   [&](const double (&t)[1], double* o, int& f) {
                                       f = (t[0] > 0.0 && isfinite(t[0])) ? 0 : 1;
-                                      o[0] = f ? 0.0 : rho / t[0];
+                                      o[0] = f ? 0.0 : sc[0] / t[0];
                                   });
         if (!ok) break;
         if (bad) {
@@ -538,22 +839,23 @@ __global__ void __launch_bounds__(kPBlock, 1) k_persistent_reduced(PersistArgs P
                 }
             })
         }
-        double sb[3];
+        double sb[1];
         int stop = 0;
-        ok = grid_allreduce<2, 3>(rr, sb, stop, P.partials, gs, ep,
+        const long long it1 = it + 1;
+        ok = grid_allreduce<2, 1>(rbuf, rr, sb, stop, P.partials, gs, ep,
                                   [&](const double (&t)[2], double* o, int& f) {
-                                      bool halt = !(t[0] > 0.0) || it + 1 >= max_iter;
-                                      if (check && t[1] <= thresh2) halt = true;
-                                      o[0] = t[0] / rho;     // beta
-                                      o[1] = t[0];           // rho'
-                                      o[2] = t[1];           // ||S r||^2
+                                      bool halt = !(t[0] > 0.0) || it1 >= st->max_iter;
+                                      if (check) {
+                                          sc[1] = t[1];  // ||S r||^2
+                                          if (t[1] <= st->thresh2) halt = true;
+                                      }
+                                      o[0] = t[0] / sc[0];   // beta
+                                      sc[0] = t[0];          // rho'
                                       f = halt ? 1 : 0;
                                   });
         if (!ok) break;
         ++it;
-        if (check) rnorm2 = sb[2];
         const double beta = sb[0];
-        rho = sb[1];
         {
             double pe[kUV], ye[kUV], re[kUV];
             CPS_B_LOOP(blo, bhi, kUV, (pe[u] = p[e], ye[u] = y[e], re[u] = stop ? 0.0 : r[e]), {
@@ -571,8 +873,8 @@ __global__ void __launch_bounds__(kPBlock, 1) k_persistent_reduced(PersistArgs P
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->iter = it;
-        st->rho = rho;
-        st->rnorm2 = rnorm2;
+        st->rho = sc[0];
+        st->rnorm2 = sc[1];
         st->status = ok ? status : CPS_ERR_TIMEOUT;
         st->done = 2;
     }
@@ -580,21 +882,29 @@ __global__ void __launch_bounds__(kPBlock, 1) k_persistent_reduced(PersistArgs P
 
 }  // namespace
 
+// The persistent kernel of a solve kind: 0 textbook Jacobi, 1 the reduced
+// system, 2 single-reduction Jacobi.
+static void (*persistent_kernel(int kind))(PersistArgs) {
+    return kind == 1 ? k_persistent_reduced : (kind == 2 ? k_persistent_gear : k_persistent_cg);
+}
+
 // Largest grid of a persistent launch on this device (blocks that stay
 // resident together), 0 if the kernel does not fit.
 int persistent_max_grid(cps_sys s, int reduced) {
-    auto kern = reduced ? k_persistent_reduced : k_persistent_cg;
+    auto kern = persistent_kernel(reduced);
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPBlock, 0) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     int G = s->ctx->num_sms * (per_sm < 4 ? per_sm : 4);
-    return G > kMaxGrid ? kMaxGrid : G;
+    return G > kPBlock ? kPBlock : G;
 }
 
 // Launches the persistent solve (reduced = 0: Jacobi on all rows; 1: the
-// reduced system) after the caller's init kernel; state in s->st.  With
+// reduced system; 2: single-reduction Jacobi on all rows, after k_init64 and
+// k_gear_start, with s = A p in q and w = A r in t) after the caller's init
+// kernel; state in s->st.  With
 // win_bytes > 0 the launch carries a persisting L2 access-policy window over
 // [win_base, win_base + win_bytes) (the caller holds the set-aside).  grid:
 // blocks of the launch, at most what stays resident (0: that maximum).
@@ -610,7 +920,7 @@ int persistent_solve(cps_sys s, int reduced, const double* a, const int32_t* col
             return CPS_ERR_NOMEM;
         }
     }
-    auto kern = reduced ? k_persistent_reduced : k_persistent_cg;
+    auto kern = persistent_kernel(reduced);
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPBlock, 0) != cudaSuccess ||
         per_sm < 1) {
@@ -619,7 +929,7 @@ int persistent_solve(cps_sys s, int reduced, const double* a, const int32_t* col
         return CPS_ERR_ARG;
     }
     int G = s->ctx->num_sms * (per_sm < 4 ? per_sm : 4);
-    if (G > kMaxGrid) G = kMaxGrid;
+    if (G > kPBlock) G = kPBlock;          // the reductions stage one value per block in a row
     if (grid > 0 && grid < G) G = grid;
     // counter, timeout and the G flags in use start at zero
     CPS_CUDA_TRY(s->ctx, cudaMemsetAsync(s->gsync, 0,
@@ -629,7 +939,7 @@ int persistent_solve(cps_sys s, int reduced, const double* a, const int32_t* col
     const int stall = s->inject == CPS_TEST_STALL_BARRIER ? 1 : 0;
     s->inject = 0;
     PersistArgs P{a, col, sc, y, r, p, q, t, n, nR, s->partials,
-                  reinterpret_cast<GridSync*>(s->gsync), s->st, stall};
+                  reinterpret_cast<GridSync*>(s->gsync), s->st, stall, s->diag_min};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(G, 1, 1);
     cfg.blockDim = dim3(kPBlock, 1, 1);

@@ -26,22 +26,39 @@ def _tuned(**kw):
 
 
 def test_traffic_is_reported_only_for_captured_configurations():
-    assert bench.traffic_for(_tuned(), 1024) == bench.TRAFFIC_PER_ITER_N1024
-    gear = _tuned(stream_single_reduction=True, l2_window="vectors5")
-    assert bench.traffic_for(gear, 1024) == bench.TRAFFIC_PER_ITER_N1024_1RED
+    textbook, gear = (t for _, t in bench.TRAFFIC_CAPTURES)
+    assert bench.traffic_for(_tuned(), 1024) == textbook
+    g = _tuned(stream_single_reduction=True, l2_window="vectors5")
+    assert bench.traffic_for(g, 1024) == gear
     # rows per trip do not change the bytes a kernel moves
-    assert bench.traffic_for(dict(gear, update_1red=[2, 152, 1024]), 1024) == \
-        bench.TRAFFIC_PER_ITER_N1024_1RED
-    assert bench.traffic_for(dict(gear, update_1red=[2, 608, 256]), 1024) is None
+    assert bench.traffic_for(dict(g, update_1red=[2, 152, 1024]), 1024) == gear
+    assert bench.traffic_for(dict(g, update_1red=[2, 608, 256]), 1024) is None
     assert bench.traffic_for(_tuned(persistent=True), 1024) is None
+    assert bench.traffic_for(_tuned(persistent_single_reduction=True, persistent=True),
+                             1024) is None
     assert bench.traffic_for(_tuned(l2_window="none"), 1024) is None
     assert bench.traffic_for(_tuned(), 512) is None
 
 
-def test_byte_counts_of_the_two_fp64_loops():
+def test_byte_counts_of_the_fp64_loops():
+    assert bench.BYTES_PER_CELL_ITER_METHOD == 108
     assert bench.BYTES_PER_CELL_ITER_FP64 == 117
     assert bench.BYTES_PER_CELL_ITER_FP64_1RED == 125
     assert sum(bench.BYTES_PER_CELL_CP2.values()) == 132 + 204 + 252
+
+
+def test_roofline_headline_uses_the_method_bytes_whatever_loop_runs():
+    nt, iters, secs, peak = 2_093_058, 13_144, 0.6254, 6782.4
+    for tf, loop in ((_tuned(), 117), (_tuned(stream_single_reduction=True,
+                                              l2_window="vectors5"), 125),
+                     (_tuned(persistent=True, persistent_single_reduction=True), 125)):
+        r = bench.roofline(tf, nt, iters, secs, peak, "measured", 1024)
+        assert r["bytes_per_cell_iter"] == 108
+        assert abs(r["achieved"] - 108 * nt * iters / secs / 1e9) < 1e-6
+        assert abs(r["frac"] - r["achieved"] / peak) < 1e-12
+        assert r["loop_bytes_per_cell_iter"] == loop
+        assert abs(r["loop_frac"] / r["frac"] - loop / 108) < 1e-12
+        assert r["traffic_source"].startswith("stored") == (r["traffic"] is not None)
 
 
 @pytest.mark.parametrize("mesh", ["lattice", "graded"])
@@ -56,12 +73,14 @@ def test_side_neighbours_match_the_oracle_topology(mesh):
 
 def test_reference_arm_prints_its_json_line():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                        "--n", "24", "--steps", "1", "--warmup", "0", "--cpu-iters", "20"],
+                        "--n", "24", "--steps", "2", "--warmup", "0"],
                        capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert r.returncode == 0, r.stderr
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["unit"] == "cell-iters/s"
-    assert line["value"] > 0 and line["cpu_baseline"]["cores"] == 1
+    assert line["value"] > 0 and line["cpu_baseline"]["cores"] == oracle.omp_threads()
     assert line["cpu_baseline"]["kind"] == "oracle"
+    # the same workload label as the GPU arm's line
+    assert line["config"]["workload"] == bench.workload_label(24, 1e-10)
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"],
                            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

@@ -283,12 +283,14 @@ def test_batched_solve_matches_oracle_per_system(ctx):
     bs[3] = torch.zeros_like(bs[3])
     xs = [torch.zeros_like(b) for b in bs]
     stats = cps.solve_batch(systems, bs, xs, rtol=1e-12, check=False)
+    xos = {}
     for i, (p, b, x, st) in enumerate(zip(probs, bs, xs, stats)):
         if i == 3:
             assert torch.all(x == 0) and st.iters == 0
             continue
         assert st.status in (0, cps._cps.ERR_NOT_CONVERGED) and st.rel_res < 1e-10
         xo, _, _ = oracle.solve_problem(p, b.cpu().numpy(), rtol=1e-13)
+        xos[i] = xo
         err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
         assert err < 1e-9, (i, err)
         # a single solve may take another recurrence (the tuner's single-
@@ -296,12 +298,21 @@ def test_batched_solve_matches_oracle_per_system(ctx):
         # at rtol 1e-12, near the FP64 floor, the counts drift a few percent
         x1, st1 = systems[i].solve(b, rtol=1e-12, check=False)
         assert abs(st1.iters - st.iters) <= max(8, 0.05 * st1.iters)
-    # a second batched call on the same handles (state reuse) and mixed mode
-    xs2 = [torch.zeros_like(b) for b in bs]
-    stats2 = cps.solve_batch(systems, bs, xs2, rtol=1e-10, precision=cps.MIXED, check=False)
-    for i, (x, st) in enumerate(zip(xs2, stats2)):
-        if i != 3:
-            assert st.rel_res <= 1e-10
+    # a second batched call on the same handles (state reuse) in mixed mode:
+    # every member against its own oracle solve at the mixed tolerance (the
+    # members' solves run concurrently, so a fault between them would show)
+    for rtol in (1e-10, 1e-12):
+        xs2 = [torch.zeros_like(b) for b in bs]
+        stats2 = cps.solve_batch(systems, bs, xs2, rtol=rtol, precision=cps.MIXED, check=False)
+        for i, (x, st) in enumerate(zip(xs2, stats2)):
+            if i == 3:
+                assert torch.all(x == 0) and st.iters == 0
+                continue
+            assert st.status in (0, cps._cps.ERR_NOT_CONVERGED)
+            assert st.rel_res <= (rtol if st.status == 0 else 1e-10)
+            if rtol == 1e-12:
+                err = np.linalg.norm(x.cpu().numpy() - xos[i]) / np.linalg.norm(xos[i])
+                assert err < 1e-8, (i, err)
     for s in systems:
         s.free()
 
@@ -449,9 +460,10 @@ def test_persistent_reduced_system_matches_oracle(ctx, name):
 
 def test_path_autotuner_reports_every_candidate(ctx):
     """On a system above the tuning threshold the first Jacobi solve times
-    streaming, streaming with the matrix in persisting L2 (where it fits) and
-    the persistent launch, and keeps the fastest; the first reduced-system
-    solve times streaming against persistent."""
+    streaming, streaming with the matrix or the vectors in persisting L2
+    (where they fit) and the persistent launches, textbook and
+    single-reduction, and keeps the fastest; the first reduced-system solve
+    times streaming against persistent."""
     p = synth.channel_block_problem(300, seed=8)
     s = assemble(ctx, p)
     b = torch.as_tensor(synth.rhs(p.mesh, 4), device="cuda")
@@ -460,15 +472,19 @@ def test_path_autotuner_reports_every_candidate(ctx):
     pr = tu["probe_us_per_iter"]
     assert pr["stream"] > 0 and pr["persistent"] > 0 and pr["cluster"] == 0
     assert pr["stream_1red"] > 0
+    assert pr["persistent_1red"] > 0
     chosen = [k for k in ("stream", "stream_l2_matrix", "stream_l2_vectors", "persistent",
-                          "persistent_l2_vectors", "stream_1red", "stream_1red_l2_vectors")
+                          "persistent_l2_vectors", "stream_1red", "stream_1red_l2_vectors",
+                          "persistent_1red", "persistent_1red_l2_vectors")
               if pr[k] > 0]
     best = min(chosen, key=lambda k: pr[k])
     assert tu["persistent"] == best.startswith("persistent")
+    assert tu["persistent_single_reduction"] == best.startswith("persistent_1red")
     assert tu["stream_single_reduction"] == best.startswith("stream_1red")
     want = {"stream_l2_matrix": ("matrix",), "stream_l2_vectors": ("vectors",),
             "persistent_l2_vectors": ("vectors",),
-            "stream_1red_l2_vectors": ("vectors", "vectors5")}.get(best, ("none",))
+            "stream_1red_l2_vectors": ("vectors", "vectors5"),
+            "persistent_1red_l2_vectors": ("vectors5",)}.get(best, ("none",))
     assert tu["l2_window"] in want
     s.set_precond(cps.PC_REDUCED)
     _, st = s.solve(b, rtol=1e-10)
@@ -485,10 +501,12 @@ def test_path_autotuner_reports_every_candidate(ctx):
 
 @pytest.mark.parametrize("name", ["channel64", "defect20", "ensemble", "channel300"])
 def test_stream_single_reduction_matches_oracle(ctx, name):
-    """The streaming single-reduction (Chronopoulos-Gear) FP64 Jacobi loop,
-    without and with r, p, q in persisting L2, against the oracle; the same
-    iterates as the textbook loop in exact arithmetic, so nearly the same
-    iteration count.  channel300 (178k cells) runs with tuned launch shapes."""
+    """The single-reduction (Chronopoulos-Gear) FP64 Jacobi loop -- streaming
+    and in one persistent launch, each without and with its vectors in
+    persisting L2 -- against the oracle; the same iterates as the textbook
+    loop in exact arithmetic, so nearly the same iteration count.  channel300
+    (178k cells, several hundred rows per persistent block, a ragged last
+    block) runs with tuned launch shapes."""
     p = PROBLEMS[name] if name in PROBLEMS else synth.channel_block_problem(300, seed=8)
     s = assemble(ctx, p)
     b = synth.rhs(p.mesh, 31)
@@ -496,18 +514,30 @@ def test_stream_single_reduction_matches_oracle(ctx, name):
     xo, _, A = oracle.solve_problem(p, b, rtol=1e-13)
     s.set_solver_path(cps.PATH_STREAM)
     _, st0 = s.solve(bt, rtol=1e-12, check=False)
-    for path in (cps.PATH_STREAM_1RED, cps.PATH_STREAM_1RED_L2):
+    for path in (cps.PATH_STREAM_1RED, cps.PATH_STREAM_1RED_L2, cps.PATH_PERSISTENT_1RED,
+                 cps.PATH_PERSISTENT_1RED_L2):
         try:
             s.set_solver_path(path)
         except cps.CpsError:
-            assert path == cps.PATH_STREAM_1RED_L2      # no persisting set-aside here
+            # no persisting set-aside for the vectors here
+            assert path in (cps.PATH_STREAM_1RED_L2, cps.PATH_PERSISTENT_1RED_L2)
             continue
         x, st = s.solve(bt, rtol=1e-12, check=False)
         assert st.status in (0, cps._cps.ERR_NOT_CONVERGED) and st.rel_res < 1e-10
         err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
         assert err < 1e-9, (path, err)
-        assert abs(st.iters - st0.iters) <= max(8, 0.05 * st0.iters)
-        assert s.tuning()["stream_single_reduction"]
+        # s = A p and w = A r are carried by recurrence, so near the FP64
+        # floor (rtol 1e-12 here) the recursive residual drifts from the true
+        # one sooner than in the textbook loop and the solve may restart from
+        # the true residual once or twice: a few percent more iterations
+        assert abs(st.iters - st0.iters) <= max(8, 0.08 * st0.iters), (path, st.iters, st0.iters)
+        tu = s.tuning()
+        persistent = path in (cps.PATH_PERSISTENT_1RED, cps.PATH_PERSISTENT_1RED_L2)
+        assert tu["stream_single_reduction"] == (not persistent)
+        assert tu["persistent_single_reduction"] == persistent
+        # the GPU's own residual claim, checked with the oracle's matrix
+        r = b - A.matvec(x.cpu().numpy())
+        assert np.linalg.norm(r) / np.linalg.norm(b) < 2 * max(st.rel_res, 1e-13)
         # warm start from the solution, and a zero right-hand side
         x2 = x.clone()
         _, st2 = s.solve(bt, x=x2, rtol=1e-8)
