@@ -7,8 +7,11 @@ the hot path: assemble (geometry, transmissibilities, ELL pack, Jacobi
 set-up) and one FP64 Jacobi-PCG solve to relative residual 1e-10.
 
 value = PCG cell-iterations per second of the whole step (cells x iterations
-/ step time), summed over ranks.  Extra keys report the mixed-precision
-time-to-1e-10, the iteration roofline and the oracle CPU baseline.
+/ step time), summed over ranks.  Extra keys report the mixed-precision and
+IC(0) time-to-1e-10, the iteration roofline (the method's 108 B/cell/iter), the
+CPU baseline (the oracle's PCG on all host cores), and compact summaries of the
+other workloads: the 7,938-cell latency case, the 256-system ensemble and the
+50-step differentiable chain.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--n 1024]
     python bench.py --impl reference   # the CPU oracle on the host cores
@@ -166,6 +169,9 @@ def parse():
     ap.add_argument("--rtol", type=float, default=1e-10)
     ap.add_argument("--impl", default="cps", choices=["cps", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default line only: skip the config 0 latency, config 3 ensemble and "
+                         "config 4 chain summaries")
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="seconds of multi-threaded oracle PCG in the CPU baseline sample")
     ap.add_argument("--batch", type=int, default=0,
@@ -390,15 +396,18 @@ def timed(fn, stream):
     return e0.elapsed_time(e1) / 1e3, out
 
 
-def run_batch(args):
-    """Uneven ensemble: sizes log-uniform in [2k, 500k] cells, random-Fourier
-    porosity in [0.3, 1], isotropic Kozeny-Carman K; FP64 Jacobi to rtol."""
+def batch_summary(n_systems: int, rtol: float, reps: int, loops: bool = True,
+                  mixed_loop: bool = True) -> dict:
+    """Uneven ensemble (config 3): n_systems systems with sizes log-uniform in
+    [2k, 500k] cells, random-Fourier porosity in [0.3, 1], isotropic
+    Kozeny-Carman K; FP64 and mixed Jacobi-PCG to rtol, batched (cps_solve_batch)
+    against a loop of single solves (best of `reps`)."""
     import torch
     import paper_2309_03543_gb300 as cps
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     ctx = cps.Context(0)
-    sizes = synth.ensemble_sizes(args.batch, 2000, 500000, seed=2024)
+    sizes = synth.ensemble_sizes(n_systems, 2000, 500000, seed=2024)
     systems, bs = [], []
     t0 = time.perf_counter()
     for i, nt in enumerate(sizes):
@@ -415,62 +424,82 @@ def run_batch(args):
         its = 0
         for s, b, x in zip(systems, bs, xs):
             x.zero_()
-            _, st = s.solve(b, x=x, rtol=args.rtol, precision=prec)
+            _, st = s.solve(b, x=x, rtol=rtol, precision=prec)
             its += st.iters * s.nt
         return its
 
     def batch(prec):
         for x in xs:
             x.zero_()
-        st = cps.solve_batch(systems, bs, xs, rtol=args.rtol, precision=prec)
+        st = cps.solve_batch(systems, bs, xs, rtol=rtol, precision=prec)
         return sum(t.iters * s.nt for t, s in zip(st, systems))
 
     loop(cps.FP64)
     batch(cps.FP64)   # warm-up (autotuning, graph capture)
-    loop(cps.MIXED)
     batch(cps.MIXED)
+    runs = [("batch_fp64", lambda: batch(cps.FP64)), ("batch_mixed", lambda: batch(cps.MIXED))]
+    if loops:
+        runs.append(("loop_fp64", lambda: loop(cps.FP64)))
+        if mixed_loop:
+            loop(cps.MIXED)
+            runs.append(("loop_mixed", lambda: loop(cps.MIXED)))
     res = {}
-    for name, fn in (("loop_fp64", lambda: loop(cps.FP64)), ("batch_fp64", lambda: batch(cps.FP64)),
-                     ("loop_mixed", lambda: loop(cps.MIXED)),
-                     ("batch_mixed", lambda: batch(cps.MIXED))):
+    for name, fn in runs:
         best = None
-        for _ in range(max(1, args.steps)):
+        for _ in range(max(1, reps)):
             t, ci = timed(fn, stream)
             best = (t, ci) if best is None or t < best[0] else best
         res[name] = {"seconds": best[0], "cell_iters": best[1],
                      "cell_iters_per_s": best[1] / best[0]}
+    for s in systems:
+        s.free()
+    ctx.close()
+    out = {"systems": n_systems, "cells": cells, "rtol": rtol, "host_setup_s": setup,
+           "variants": res,
+           "batch_mixed_vs_batch_fp64_seconds":
+               res["batch_mixed"]["seconds"] / res["batch_fp64"]["seconds"]}
+    if "loop_fp64" in res:
+        out["batch_speedup_vs_loop"] = res["loop_fp64"]["seconds"] / res["batch_fp64"]["seconds"]
+    if "loop_mixed" in res:
+        out["batch_mixed_speedup_vs_loop_mixed"] = \
+            res["loop_mixed"]["seconds"] / res["batch_mixed"]["seconds"]
+    return out
+
+
+def run_batch(args):
+    """--batch N: the ensemble as its own line."""
+    r = batch_summary(args.batch, args.rtol, args.steps)
     line = {"metric": "ensemble corrector solves: batched vs loop (FP64 Jacobi-PCG to rtol)",
-            "value": res["batch_fp64"]["cell_iters_per_s"], "unit": UNIT,
+            "value": r["variants"]["batch_fp64"]["cell_iters_per_s"], "unit": UNIT,
             "config": {"workload": f"{args.batch} systems, log-uniform 2k-500k cells",
-                       "cells": cells, "rtol": args.rtol, "host_setup_s": setup},
-            "variants": res,
-            "batch_speedup_vs_loop": res["loop_fp64"]["seconds"] / res["batch_fp64"]["seconds"],
-            "batch_mixed_speedup_vs_loop_mixed":
-                res["loop_mixed"]["seconds"] / res["batch_mixed"]["seconds"],
-            "batch_mixed_vs_batch_fp64_seconds":
-                res["batch_mixed"]["seconds"] / res["batch_fp64"]["seconds"]}
+                       "cells": r["cells"], "rtol": args.rtol,
+                       "host_setup_s": r["host_setup_s"]},
+            **{k: v for k, v in r.items() if k not in ("systems", "cells", "rtol",
+                                                        "host_setup_s")}}
     print(json.dumps(line), flush=True)
 
 
-def run_chain(args):
-    """Chained corrector solves x_t = A(theta)^-1 (n_t + 0.1 |n_t|/|x_{t-1}| x_{t-1}),
-    n_t = area N(0,1); loss = sum_t |x_t - x*_t|^2 with targets from theta*
-    (seed + 1000); gradient by the adjoint with checkpoints every 10 steps.
-    (With the unnormalised feedback 0.1 x_{t-1} the chain grows by
-    0.1 / lambda_min(A) ~ 1e7 per step on this matrix and overflows.)"""
+def chain_summary(n: int, steps: int, rtol: float) -> dict:
+    """Differentiable chain (config 4): x_t = A(theta)^-1 (n_t + 0.1 |n_t|/|x_{t-1}|
+    x_{t-1}), n_t = area N(0,1); loss = sum_t |x_t - x*_t|^2 with targets from
+    theta* (seed + 1000); gradient by the adjoint with checkpoints every 10
+    steps; forward, forward + backward and the same number of plain FP64
+    solves, each timed once after a warm-up.  (With the unnormalised feedback
+    0.1 x_{t-1} the chain grows by 0.1 / lambda_min(A) ~ 1e7 per step on this
+    matrix and overflows.)"""
     import torch
     import paper_2309_03543_gb300 as cps
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     ctx = cps.Context(0)
-    p, theta_np = synth.log_permeability_problem(args.n, seed=0)
-    _, theta_star = synth.log_permeability_problem(args.n, seed=1000)
+    p, theta_np = synth.log_permeability_problem(n, seed=0)
+    _, theta_star = synth.log_permeability_problem(n, seed=1000)
     m = p.mesh
     area = synth.triangle_areas(m)
     rhs = [torch.as_tensor(area * synth.normal_noise(m.nt, 100 + t), device=dev)
-           for t in range(args.chain)]
+           for t in range(steps)]
     model = cps.LogPermeabilityCorrector(ctx, m.xy, m.tri, m.dirichlet, p.eps, p.nu, p.dt,
-                                         rtol=args.chain_rtol)
+                                         rtol=rtol)
     with torch.no_grad():
         targets = [x.clone() for x in cps.chained_solve(
             model, torch.as_tensor(theta_star, device=dev), rhs, checkpoint_every=0,
@@ -493,9 +522,9 @@ def run_chain(args):
     def plain():
         its = 0
         x = torch.zeros(m.nt, dtype=torch.float64, device=dev)
-        for t in range(args.chain):
+        for t in range(steps):
             x.zero_()
-            _, st = sys_.solve(rhs[t], x=x, rtol=args.chain_rtol)
+            _, st = sys_.solve(rhs[t], x=x, rtol=rtol)
             its += st.iters
         return its
 
@@ -504,15 +533,70 @@ def run_chain(args):
     t_plain, its = timed(plain, stream)
     t_fwd, _ = timed(fwd_only, stream)
     t_fb, loss = timed(fwd_bwd, stream)
+    out = {"workload": f"log-permeability lattice n={n}", "cells": m.nt, "steps": steps,
+           "rtol": rtol, "checkpoint_every": 10,
+           "plain_fp64_solves_s": t_plain, "plain_iters": its, "forward_s": t_fwd,
+           "forward_backward_s": t_fb, "backward_s": t_fb - t_fwd,
+           "ratio_forward_backward_vs_plain": t_fb / t_plain, "loss": loss,
+           "grad_norm": float(theta.grad.norm())}
+    model.free()
+    ctx.close()
+    return out
+
+
+def run_chain(args):
+    """--chain T: the differentiable chain as its own line."""
+    r = chain_summary(args.n, args.chain, args.chain_rtol)
     line = {"metric": "differentiable chained corrector solves (adjoint backward, checkpoint 10)",
-            "value": t_fb, "unit": "s per forward+backward", "higher_is_better": False,
-            "config": {"workload": f"log-permeability lattice n={args.n}", "cells": m.nt,
-                       "steps": args.chain, "rtol": args.chain_rtol},
-            "plain_fp64_solves_s": t_plain, "plain_iters": its, "forward_s": t_fwd,
-            "forward_backward_s": t_fb, "backward_s": t_fb - t_fwd,
-            "ratio_forward_backward_vs_plain": t_fb / t_plain, "loss": loss,
-            "grad_norm": float(theta.grad.norm())}
+            "value": r["forward_backward_s"], "unit": "s per forward+backward",
+            "higher_is_better": False,
+            "config": {"workload": r["workload"], "cells": r["cells"], "steps": r["steps"],
+                       "rtol": r["rtol"]},
+            **{k: v for k, v in r.items() if k not in ("workload", "cells", "steps", "rtol")}}
     print(json.dumps(line), flush=True)
+
+
+def latency_summary(n: int, rtol: float, reps: int = 5) -> dict:
+    """Config 0: the centred-block lattice of n x n vertices (7,938 cells at
+    n = 64, isotropic Kozeny-Carman, Dirichlet on the right edge), FP64
+    Jacobi-PCG to rtol from x = 0, on the tuned path and on each forced path;
+    median of `reps` solve times.  At this size the system is cache-resident
+    and the loop is latency-bound: the figures are microseconds per
+    iteration, not bandwidth."""
+    import torch
+    import paper_2309_03543_gb300 as cps
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    ctx = cps.Context(0)
+    p = synth.centred_block_problem(n, seed=0)
+    m = p.mesh
+    s = ctx.assemble(m.xy, m.tri, m.dirichlet, p.eps, p.kinv, p.field_loc, cps.KIND_CP2,
+                     p.nu, p.dt)
+    b = torch.as_tensor(synth.rhs(m, seed=1), device=dev)
+    x = torch.zeros_like(b)
+    out = {"workload": f"centred-block lattice n={n}", "cells": m.nt, "rtol": rtol}
+    for name, path in (("tuned", cps.PATH_AUTO), ("cluster_1red", cps.PATH_CLUSTER_1RED),
+                       ("cluster", cps.PATH_CLUSTER), ("stream_1red", cps.PATH_STREAM_1RED),
+                       ("stream", cps.PATH_STREAM), ("persistent_1red", cps.PATH_PERSISTENT_1RED)):
+        try:
+            s.set_solver_path(path)
+        except cps.CpsError:
+            continue
+        x.zero_()
+        s.solve(b, x=x, rtol=rtol)       # tuning / warm-up
+        ts = []
+        for _ in range(reps):
+            x.zero_()
+            ts.append(timed(lambda: s.solve(b, x=x, rtol=rtol)[1], stream))
+        t, st = sorted(ts, key=lambda v: v[0])[len(ts) // 2]
+        out[name] = {"time_to_rtol_s": t, "iters": st.iters,
+                     "us_per_iter": 1e6 * t / max(st.iters, 1)}
+        if path == cps.PATH_AUTO:
+            tf = s.tuning(cps.FP64)
+            out["tuned_path"] = loop_name(tf)
+    s.free()
+    ctx.close()
+    return out
 
 
 def run_sequence(args):
@@ -958,7 +1042,8 @@ def main():
     tuning = {"fp64": s.tuning(cps.FP64), "mixed": s.tuning(cps.MIXED)}
     # each way of running the loop, forced: streaming kernels, the one-launch
     # cluster solve (small systems), the persistent grid-synchronised launch
-    for pc_name, pc in (("jacobi", cps.PC_JACOBI), ("reduced", cps.PC_REDUCED)):
+    for pc_name, pc in (("jacobi", cps.PC_JACOBI), ("reduced", cps.PC_REDUCED),
+                        ("ic0", cps.PC_IC0)):
         try:
             s.set_precond(pc)
         except cps.CpsError:
@@ -972,6 +1057,9 @@ def main():
             if pc == cps.PC_REDUCED and path in (cps.PATH_CLUSTER, cps.PATH_STREAM_1RED,
                                                  cps.PATH_STREAM_1RED_L2,
                                                  cps.PATH_PERSISTENT_1RED,
+                                                 cps.PATH_PERSISTENT_1RED_L2):
+                continue
+            if pc == cps.PC_IC0 and path not in (cps.PATH_STREAM, cps.PATH_PERSISTENT_1RED,
                                                  cps.PATH_PERSISTENT_1RED_L2):
                 continue
             try:
@@ -1012,6 +1100,21 @@ def main():
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    # the other workloads, compactly (each in its own context, after the
+    # headline measurement): config 0 latency, config 3 ensemble (batched
+    # FP64 and mixed against a loop of FP64 single solves), config 4 chain
+    if rank == 0 and world == 1 and not args.no_extras:
+        extras = (("n64_latency", lambda: latency_summary(64, args.rtol)),
+                  ("batch", lambda: batch_summary(256, args.rtol, 1, loops=True,
+                                                  mixed_loop=False)),
+                  ("chain", lambda: chain_summary(512, 50, 1e-8)))
+        for key, fn in extras:
+            t0 = time.perf_counter()
+            try:
+                line[key] = fn()
+            except Exception as e:      # an extra must not cost the headline line
+                line[key] = {"error": repr(e)[:400]}
+            line[key]["wall_s"] = time.perf_counter() - t0
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, b_np, seconds=args.cpu_seconds)
     if rank == 0:

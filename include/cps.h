@@ -327,12 +327,17 @@ int cps_cp2_kernel_times(cps_sys sys, float* ms);
  *     are carried so that both inner products of an iteration come from one
  *     SpMV (two cluster barriers per iteration instead of three; one more
  *     vector in shared memory, so a somewhat smaller size limit);
- *   CPS_PATH_PERSISTENT_1RED, CPS_PATH_PERSISTENT_1RED_L2 (FP64 Jacobi
- *     only): the persistent launch with the single-reduction recurrences --
- *     per iteration one wait on the neighbouring blocks and one grid
- *     reduction -- without / with its five vectors in persisting L2
- *     (CPS_ERR_ARG when the set-aside cannot hold them).
- * IC(0) and mixed precision always stream. */
+ *   CPS_PATH_PERSISTENT_1RED, CPS_PATH_PERSISTENT_1RED_L2 (FP64 Jacobi,
+ *     and FP64 IC(0) in a two-colour order): the persistent launch with the
+ *     single-reduction recurrences -- per iteration one grid reduction and
+ *     waits on the neighbouring blocks only (Jacobi: one; IC(0): three, around
+ *     the black forward and red backward sweeps) -- without / with its
+ *     vectors in persisting L2 (Jacobi: five, CPS_ERR_ARG when the set-aside
+ *     cannot hold them; IC(0): six where they fit).
+ * FP64 IC(0) in a two-colour order runs on the streaming kernels for every
+ * other pin, and CPS_PATH_AUTO times both ways on the first such solve; with
+ * more colours it always streams.
+ * Mixed precision always streams. */
 #define CPS_PATH_AUTO 0
 #define CPS_PATH_STREAM 1
 #define CPS_PATH_CLUSTER 2
@@ -375,21 +380,24 @@ int cps_test_inject(cps_sys sys, int fault);
  * (CPS_FP64 only) the direction update.  The tuner times every candidate on
  * the system's own data at its first solve; systems below 131072 cells keep
  * the defaults (unroll 2, 8 blocks per SM).  For CPS_FP64 Jacobi solves it
- * also times the ways of running the loop: flags (may be NULL, 7 entries)
+ * also times the ways of running the loop: flags (may be NULL, 8 entries)
  * receives {one-cluster launch chosen (0 no, 1 textbook recurrences, 2 the
  * single-reduction recurrences), persisting-L2 window (0 none, 1 the
  * matrix, 2 the vectors r, p, q, 3 the five vectors of the single-reduction
  * loop), persistent launch chosen (either recurrence), reduced system:
  * persistent launch chosen, reduced system: window (0 or 2), single-reduction
- * streaming chosen, single-reduction persistent launch chosen}, probe_us (may
- * be NULL, 14 entries) the microseconds per iteration measured for
- * {streaming, one cluster, streaming + matrix in L2, persistent, streaming +
- * vectors in L2, persistent + vectors in L2, reduced system: streaming,
- * persistent, streaming + vectors in L2, persistent + vectors in L2,
- * single-reduction streaming, single-reduction streaming + vectors in L2,
- * single-reduction persistent, single-reduction persistent + vectors in L2}
- * (0 where not tried; the persistent figures are the best over the grid sizes
- * tried, the one-cluster figure the better of its two recurrences).
+ * streaming chosen, single-reduction persistent launch chosen, IC(0):
+ * persistent single-reduction launch chosen (0 no, 1 without, 2 with its six
+ * vectors in persisting L2)}, flags then taking 8 entries; probe_us (may be
+ * NULL, 16 entries) the microseconds per iteration measured for {streaming,
+ * one cluster, streaming + matrix in L2, persistent, streaming + vectors in
+ * L2, persistent + vectors in L2, reduced system: streaming, persistent,
+ * streaming + vectors in L2, persistent + vectors in L2, single-reduction
+ * streaming, single-reduction streaming + vectors in L2, single-reduction
+ * persistent, single-reduction persistent + vectors in L2, IC(0): streaming,
+ * persistent single-reduction (the better window)} (0 where not tried; the
+ * persistent figures are the best over the grid sizes tried, the one-cluster
+ * figure the better of its two recurrences).
  * The context remembers what the tuner chose per mesh size (cells,
  * vertices): a system assembled later on the same context with the same
  * sizes starts from those choices and is not timed again.  A path forced by

@@ -139,8 +139,8 @@ class System:
         u = (ctypes.c_int32 * 3)()
         g = (ctypes.c_int32 * 3)()
         bl = (ctypes.c_int32 * 3)()
-        f = (ctypes.c_int32 * 7)()
-        pr = (ctypes.c_double * 14)()
+        f = (ctypes.c_int32 * 8)()
+        pr = (ctypes.c_double * 16)()
         self.ctx.check(self.ctx.lib.cps_get_tuning(self.handle, precision, u, g, bl, f, pr),
                        "cps_get_tuning")
         gu, gg, gb = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
@@ -155,6 +155,8 @@ class System:
                 "reduced_l2_window": ("none", "matrix", "vectors")[f[4]],
                 "stream_single_reduction": bool(f[5]),
                 "persistent_single_reduction": bool(f[6]),
+                "ic0_persistent": bool(f[7]),
+                "ic0_l2_window": ("none", "none", "vectors6")[f[7]],
                 "update_1red": [gu.value, gg.value, gb.value],
                 "probe_us_per_iter": {
                     "stream": pr[0], "cluster": pr[1], "stream_l2_matrix": pr[2],
@@ -162,7 +164,8 @@ class System:
                     "reduced_stream": pr[6], "reduced_persistent": pr[7],
                     "reduced_stream_l2_vectors": pr[8], "reduced_persistent_l2_vectors": pr[9],
                     "stream_1red": pr[10], "stream_1red_l2_vectors": pr[11],
-                    "persistent_1red": pr[12], "persistent_1red_l2_vectors": pr[13]}}
+                    "persistent_1red": pr[12], "persistent_1red_l2_vectors": pr[13],
+                    "ic0_stream": pr[14], "ic0_persistent": pr[15]}}
 
     def set_solver_path(self, path: int):
         """PATH_AUTO, PATH_STREAM, PATH_CLUSTER, PATH_CLUSTER_1RED,

@@ -210,7 +210,17 @@ int cps_adjoint(cps_sys sys, const double* x, const double* g, double* lambda, d
 int cps_set_solver_path(cps_sys sys, int path) {
     if (!sys) return CPS_ERR_ARG;
     cps::Tuning& t = sys->tune[CPS_FP64];
+    if (path >= CPS_PATH_STREAM && path <= CPS_PATH_PERSISTENT_1RED_L2) {
+        // IC(0) in a two-colour order: the persistent single-reduction loop
+        // for the CPS_PATH_PERSISTENT_1RED pins, the streaming kernels for
+        // the others
+        t.ic0_done = true;
+        t.ic0_path = (path == CPS_PATH_PERSISTENT_1RED || path == CPS_PATH_PERSISTENT_1RED_L2) ? 1 : 0;
+        t.ic0_win = (path == CPS_PATH_PERSISTENT_1RED_L2 && cps::l2_window_fits_mode(sys, 4)) ? 4 : 0;
+    }
     if (path == CPS_PATH_AUTO) {
+        t.ic0_done = false;
+        t.ic0_path = 0;
         t.path_done = false;
         t.path = 0;
         t.red_done = false;
@@ -346,6 +356,8 @@ int cps_get_tuning(cps_sys sys, int precision, int32_t* unroll, int32_t* grid, i
         flags[4] = t.red_done ? t.red_win : 0;
         flags[5] = t.path_done && t.path == 3;
         flags[6] = t.path_done && t.path == 4;
+        flags[7] = (t.ic0_done && t.ic0_path == 1 && sys->ncolours == 2) ? 1 + (t.ic0_win ? 1 : 0)
+                                                                          : 0;
     }
     if (probe_us) {
         for (int k = 0; k < 6; ++k) probe_us[k] = t.probe_us[k];
@@ -354,6 +366,8 @@ int cps_get_tuning(cps_sys sys, int precision, int32_t* unroll, int32_t* grid, i
         probe_us[11] = t.probe_us[7];
         probe_us[12] = t.probe_us[8];
         probe_us[13] = t.probe_us[9];
+        probe_us[14] = t.ic0_probe_us[0];
+        probe_us[15] = t.ic0_probe_us[1];
     }
     return CPS_OK;
 }

@@ -79,6 +79,12 @@ struct Tuning {
     int cluster_variant = 0; // one-cluster launch: 0 textbook CG, 1 single reduction
     KCfg kg;                 // single-reduction update kernel (if kg_set; else k[1])
     bool kg_set = false;
+    // FP64 IC(0) in a two-colour order: 0 graph-replayed streaming kernels,
+    // 1 one persistent launch of the single-reduction recurrences
+    int ic0_path = 0;
+    int ic0_win = 0;         // persisting L2 window of the persistent IC(0) loop (0 or 4)
+    bool ic0_done = false;
+    double ic0_probe_us[2] = {0, 0};   // us/iteration: streaming, persistent (best window)
 };
 
 // Device error flag written by the assembly kernels (first error wins).
@@ -372,7 +378,7 @@ int cluster_solve(cps_sys s, const double* b, const double* x, double* y, double
 int persistent_solve(cps_sys s, int reduced, const double* a, const int32_t* col,
                      const double* sc, double* y, double* r, double* p, double* q, double* t,
                      int64_t n, int64_t nR, const void* win_base, size_t win_bytes, int grid,
-                     cudaStream_t stream);
+                     cudaStream_t stream, double* z = nullptr, const double* dinv = nullptr);
 int persistent_max_grid(cps_sys s, int reduced);
 bool l2_vectors_fit(cps_sys s);
 bool l2_window_fits_mode(cps_sys s, int mode);

@@ -420,13 +420,14 @@ static int64_t enqueue_iteration(cps_sys s, const Run<V>& v, int prec, bool norm
 // written every iteration, 64 of the 117 bytes a row moves).  At a few
 // million cells either fits GB300's 129 MB L2 next to the streamed rest.
 // Mode 3, for the single-reduction loop, holds r, p, q (= s), y and p1
-// (= w): every vector that loop reads and writes (five contiguous slices).
+// (= w): every vector that loop reads and writes (five contiguous slices);
+// mode 4, for the single-reduction IC(0) loop, also z (six slices).
 static void* l2_window_base(cps_sys s, int mode) {
     return mode == 1 ? (void*)s->a : (void*)s->wr;
 }
 static size_t l2_window_bytes(cps_sys s, int mode) {
     if (mode == 1) return s->mat_bytes;
-    return (size_t)(mode == 3 ? 5 : 3) * s->vec_stride * sizeof(double);
+    return (size_t)(mode == 4 ? 6 : (mode == 3 ? 5 : 3)) * s->vec_stride * sizeof(double);
 }
 static bool l2_window_fits(cps_sys s, int mode) {
     return s->ctx->l2_persist_max > 0 && l2_window_bytes(s, mode) <= s->ctx->l2_persist_max;
@@ -792,6 +793,110 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
     return rc;
 }
 
+// One persistent single-reduction IC(0) run from the state k_init64 left
+// (colour order, two colours), with persisting L2 window `win` (the caller
+// holds its set-aside) on `grid` blocks (0: all that stay resident).
+static int persistent_ic0(cps_sys s, int win, cudaStream_t stream) {
+    return persistent_solve(s, 3, s->pa, s->pcol, s->ps, s->wy, s->wr, s->wp0, s->wq, s->wp1,
+                            s->nt, s->colour_start[1], win ? l2_window_base(s, win) : nullptr,
+                            win ? l2_window_bytes(s, win) : 0, 0, stream, s->wz, s->pdinv);
+}
+
+// For IC(0) on a two-colour order: times a short run (64 iterations; 256 on
+// large systems) of the graph-replayed streaming kernels and of the
+// persistent single-reduction launch (without and, where the set-aside holds
+// them, with its six vectors in persisting L2) and keeps the fastest.  bb is
+// the right-hand side in colour order.
+static int choose_ic0_path(cps_sys s, const Run<double>& v, const double* bb,
+                           cudaStream_t stream) {
+    Tuning& t = s->tune[CPS_FP64];
+    t.ic0_done = true;
+    t.ic0_path = 0;
+    t.ic0_win = 0;
+    if (s->ncolours != 2) return CPS_OK;
+    const long long probe = s->nt >= kTuneMinRows ? 256 : 64;
+    struct Cand {
+        int path, win;
+    };
+    Cand cands[3];
+    int nc = 0;
+    cands[nc++] = {0, 0};
+    if (persistent_max_grid(s, 3) > 0) {
+        cands[nc++] = {1, 0};
+        if (s->nt >= kTuneMinRows && l2_window_fits(s, 4)) cands[nc++] = {1, 4};
+    }
+    cudaEvent_t e0, e1;
+    CPS_CUDA_TRY(s->ctx, cudaEventCreate(&e0));
+    CPS_CUDA_TRY(s->ctx, cudaEventCreate(&e1));
+    double per_iter[2] = {0.0, 0.0};
+    double best_t = 0.0;
+    Cand best{0, 0};
+    int rc = CPS_OK;
+    int64_t dummy = 0;
+    for (int ci = 0; ci < nc && rc == CPS_OK; ++ci) {
+        const Cand c = cands[ci];
+        rc = l2_set_aside(s, c.win, stream);
+        double us = 0.0;
+        for (int rep = 0; rep < 2 && rc == CPS_OK; ++rep) {    // the first one warms up
+            if (cudaMemsetAsync(s->wx, 0, sizeof(double) * s->nt, stream) != cudaSuccess ||
+                cudaEventRecord(e0, stream) != cudaSuccess) {
+                rc = CPS_ERR_CUDA;
+                break;
+            }
+            k_init64<<<s->grid, kBlock, 0, stream>>>(bb, s->wx, v.s, v.a, v.col, s->nt, v.y, v.r,
+                                                     v.p0, 0.0, probe, 0, s->partials, s->st);
+            CgState h{};
+            if (c.path == 1) {
+                rc = persistent_ic0(s, c.win, stream);
+                if (rc == CPS_OK) rc = read_state(s, stream, &h);
+                if (rc == CPS_OK && h.status != CPS_OK) rc = CPS_ERR_ARG;   // not usable here
+            } else {
+                enqueue_precond<double>(s, v, stream);
+                k_copy<double><<<s->grid, kBlock, 0, stream>>>(v.p0, v.z, s->nt);
+                rc = run_chunks<double>(s, CPS_FP64, v, stream, &h, &dummy);
+            }
+            if (cudaEventRecord(e1, stream) != cudaSuccess ||
+                cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = CPS_ERR_CUDA;
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            us = rc == CPS_OK ? 1e3 * ms / (double)(h.iter > 0 ? h.iter : 1) : 0.0;
+        }
+        if (rc == CPS_ERR_ARG) {            // a candidate that cannot run here: skip it
+            rc = CPS_OK;
+            cudaGetLastError();
+            continue;
+        }
+        if (rc != CPS_OK || us <= 0.0) continue;
+        if (per_iter[c.path] == 0.0 || us < per_iter[c.path]) per_iter[c.path] = us;
+        if (best_t == 0.0 || us < best_t) {
+            best_t = us;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    {
+        const int rc2 = l2_set_aside(s, 0, stream);
+        if (rc == CPS_OK) rc = rc2;
+    }
+    if (rc != CPS_OK) return rc;
+    t.ic0_path = best.path;
+    t.ic0_win = best.win;
+    t.ic0_probe_us[0] = per_iter[0];
+    t.ic0_probe_us[1] = per_iter[1];
+    update_cached_tuning(s, CPS_FP64, [&](Tuning& cc) {
+        cc.ic0_done = true;
+        cc.ic0_path = t.ic0_path;
+        cc.ic0_win = t.ic0_win;
+        cc.ic0_probe_us[0] = per_iter[0];
+        cc.ic0_probe_us[1] = per_iter[1];
+    });
+    return CPS_OK;
+}
+
 static int solve_fp64(cps_sys s, const double* b, double* x, double rtol, int64_t max_iter,
                       cps_stats* stats, cudaStream_t stream) {
     const int64_t n = s->nt;
@@ -823,6 +928,21 @@ static int solve_fp64(cps_sys s, const double* b, double* x, double rtol, int64_
         ++launches;
         bb = s->wb;
         xx = s->wx;
+        if (!s->tune[CPS_FP64].ic0_done) {
+            // the probe runs from x = 0 in wx: keep the caller's start in wbest
+            CPS_CUDA_TRY(s->ctx, cudaMemcpyAsync(s->wbest, s->wx, sizeof(double) * n,
+                                                 cudaMemcpyDeviceToDevice, stream));
+            int rc = choose_ic0_path(s, v, bb, stream);
+            if (rc) return rc;
+            CPS_CUDA_TRY(s->ctx, cudaMemcpyAsync(s->wx, s->wbest, sizeof(double) * n,
+                                                 cudaMemcpyDeviceToDevice, stream));
+        }
+    }
+    const bool pic0 = ic0 && s->ncolours == 2 && s->tune[CPS_FP64].ic0_path == 1;
+    const int ic0_window = pic0 ? s->tune[CPS_FP64].ic0_win : 0;
+    if (ic0_window) {
+        int rc = l2_set_aside(s, ic0_window, stream);
+        if (rc) return rc;
     }
     CgState h{};
     int status = CPS_OK;
@@ -851,6 +971,24 @@ static int solve_fp64(cps_sys s, const double* b, double* x, double rtol, int64_
         k_init64<<<g, kBlock, 0, stream>>>(bb, xx, v.s, v.a, v.col, n, v.y, v.r, v.p0, rtol,
                                             budget, ic0 ? 0 : 1, s->partials, s->st);
         ++launches;
+        if (pic0) {
+            // one launch runs to the stop (it returns at once if init stopped)
+            int rc = persistent_ic0(s, ic0_window, stream);
+            if (rc) return rc;
+            ++launches;
+            rc = read_state(s, stream, &h);
+            if (rc) return rc;
+            total += h.iter;
+            status = h.status;
+            k_final64<<<g, kBlock, 0, stream>>>(bb, v.y, v.s, v.a, v.col, n, xx, s->partials,
+                                                s->st);
+            ++launches;
+            CPS_CUDA_TRY(s->ctx, cudaGetLastError());
+            rc = read_state(s, stream, &h);
+            if (rc) return rc;
+            if (status != CPS_OK || h.rnorm2 <= h.thresh2 || total >= max_iter) break;
+            continue;
+        }
         if (persistent) {
             if (pgear) {
                 k_gear_start<<<g, kBlock, 0, stream>>>(v.a, v.col, v.r, v.p1, v.p0, v.q, n,
@@ -910,7 +1048,7 @@ static int solve_fp64(cps_sys s, const double* b, double* x, double rtol, int64_
         CPS_CUDA_TRY(s->ctx, cudaGetLastError());
         CPS_CUDA_TRY(s->ctx, cudaStreamSynchronize(stream));
     }
-    if (window) {
+    if (window || ic0_window) {
         // release the lines and the set-aside: later work gets the whole L2
         int rc = l2_set_aside(s, 0, stream);
         if (rc) return rc;

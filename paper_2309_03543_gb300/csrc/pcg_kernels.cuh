@@ -326,7 +326,10 @@ __global__ void __launch_bounds__(BS) k_gear_spmv(const double* __restrict__ a,
             const double be = g / st->rho;
             const double den = d - be * g / st->alpha;
             if (!(den > 0.0) || !isfinite(den)) {
-                st->status = CPS_ERR_NOT_SPD;
+                // on a run's first iteration p.Ap <= 0: not SPD; later, the
+                // recurrence's difference lost its digits at the FP64 floor:
+                // stop, and let the true residual decide
+                if (it <= 1) st->status = CPS_ERR_NOT_SPD;
                 done = 1;
             } else {
                 st->beta = be;

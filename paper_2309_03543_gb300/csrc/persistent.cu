@@ -94,11 +94,11 @@ __device__ bool wait_geq(const unsigned long long* p, unsigned long long target,
 
 // Barriers passed by this block: reductions (k picks the partial buffer) and
 // the arrival count that completes the latest barrier (every barrier adds its
-// arrivals per block x the grid).
+// arrivals per block x the grid; the test hook starts it one arrival high, so
+// that every barrier waits for an arrival that never comes).
 struct Epoch {
-    unsigned long long k = 0;
+    unsigned int k = 0;
     unsigned long long target = 0;
-    unsigned long long extra = 0;   // test hook: arrivals a barrier waits for beyond the grid
 };
 
 __device__ __forceinline__ void named_barrier(int id, int threads) {
@@ -205,7 +205,7 @@ __device__ __forceinline__ bool grid_allreduce(double (*buf)[kPBlock], double (&
         if (NV > 1) named_barrier(1, NV * 32);
         if (warp == 0 && lane == 0) {
             red_release_add(&gs->count, 1ull);
-            s_ok = wait_geq(&gs->count, ep.target + ep.extra, gs) ? 1 : 0;
+            s_ok = wait_geq(&gs->count, ep.target, gs) ? 1 : 0;
         }
         if (NV > 1) named_barrier(1, NV * 32);
         else __syncwarp();
@@ -243,7 +243,7 @@ __device__ bool grid_barrier(GridSync* gs, Epoch& ep) {
     ep.target += gridDim.x;
     if (threadIdx.x == 0) {
         red_release_add(&gs->count, 1ull);
-        s_ok = wait_geq(&gs->count, ep.target + ep.extra, gs) ? 1 : 0;
+        s_ok = wait_geq(&gs->count, ep.target, gs) ? 1 : 0;
     }
     __syncthreads();
     return s_ok != 0;
@@ -317,7 +317,9 @@ struct PersistArgs {
     GridSync* gs;
     CgState* st;
     int stall;          // test hook: 1 makes every barrier wait for one arrival too many
-    double dmin;        // single-reduction Jacobi: smallest diagonal entry (stop-test gate)
+    double dmin;        // single-reduction loops: smallest diagonal entry (stop-test gate)
+    double* z;          // IC(0): preconditioned residual
+    const double* dinv; // IC(0): inverse pivots
 };
 
 // Rows per block for m rows over the grid: a multiple of 32.
@@ -376,7 +378,7 @@ __global__ void __launch_bounds__(kPBlock, 1) k_persistent_cg(PersistArgs P) {
     const int64_t lo = blockIdx.x * R < n ? blockIdx.x * R : n;
     const int64_t hi = lo + R < n ? lo + R : n;
     Epoch ep;
-    ep.extra = P.stall ? 1ull : 0ull;
+    ep.target = P.stall ? 1ull : 0ull;
     // the blocks whose rows this block's SpMV reads
     int dlo = blockIdx.x, dhi = blockIdx.x;
     {
@@ -549,7 +551,7 @@ __global__ void __launch_bounds__(kPBlock, 1) k_persistent_gear(PersistArgs P) {
     const int64_t lo = blockIdx.x * R < n ? blockIdx.x * R : n;
     const int64_t hi = lo + R < n ? lo + R : n;
     Epoch ep;
-    ep.extra = P.stall ? 1ull : 0ull;
+    ep.target = P.stall ? 1ull : 0ull;
     int dlo, dhi;
     column_blocks(C, n, lo, hi, 0, R, &dlo, &dhi);
     if (threadIdx.x == 0) {
@@ -670,7 +672,10 @@ __global__ void __launch_bounds__(kPBlock, 1) k_persistent_gear(PersistArgs P) {
             if (!halt) {
                 const double den = fma(-(g * g), sc[5], d);
                 if (!(den > 0.0) || !isfinite(den)) {
-                    f = 2;
+                    // on a run's first iteration p.Ap <= 0: not SPD; later, the
+                    // recurrence's difference lost its digits at the FP64
+                    // floor: stop, and let the true residual decide
+                    f = it > 0 ? 1 : 2;
                 } else {
                     const double ig = 1.0 / g;
                     sc[1] = g / den;
@@ -716,6 +721,270 @@ __global__ void __launch_bounds__(kPBlock, 1) k_persistent_gear(PersistArgs P) {
     }
 }
 
+// FP64 IC(0)-PCG in a two-colour order with the single-reduction
+// (Chronopoulos-Gear) recurrences, in one persistent launch.  Red rows
+// [0, nR) couple only to black rows [nR, n) and back, so the IC(0) factor of
+// the scaled matrix is L = [[I, 0], [E^T, I]], D = diag(I, D_B), with E the
+// red-black block of Ahat (L's off-diagonals are Ahat's own) and
+// D_B = I - diag(E^T E): z = M^-1 r is the black forward sweep
+// z_B = D_B^-1 (r_B - E^T r_R) and the red backward sweep z_R = r_R - E z_B,
+// read straight from the scaled matrix (an empty slot's zero value drops
+// out).  On the red rows w = Ahat z shares the backward sweep's sum:
+// with t = E z_B, z_R = r_R - t and w_R = z_R + t (equal to r_R in exact
+// arithmetic; computed, so that s = A p stays consistent in FP64).  Per
+// iteration, from the state k_init64 left (y, r, p = 0):
+//   red    p = z + beta p; s = w + beta s; y += alpha p; r -= alpha s     | post 0
+//   black  [wait: red owners updated r] the same update, then z_B;
+//          gamma_B = r.z                                                   | post 1
+//   red    [wait: black owners wrote z_B] z_R, w_R; gamma_R = r.z,
+//          delta_R = w.z                                                   | post 2
+//   black  [wait: red owners wrote z_R] w_B = z_B + E^T z_R; delta_B = w.z
+//   one grid reduction: stop test, beta = gamma / gamma_old,
+//   alpha = gamma / (delta - beta gamma / alpha_old)
+// Pass 0 skips the updates: it forms z_0, w_0 and alpha_0 = gamma_0 / delta_0
+// (the carried reciprocals start at 0, which turns the general step into
+// that).  The stop test (every 8th pass) sums ||S r||^2 in the two sweeps.  Block b owns red rows [b Rr, (b+1) Rr) and
+// black rows nR + [b Rb, (b+1) Rb).  About 11 FP64 operations a row per
+// iteration (red 9, black 13) against 9 for Jacobi; s lives in P.q, w in
+// P.t.
+__global__ void __launch_bounds__(kPBlock, 1) k_persistent_ic0(PersistArgs P) {
+    __shared__ double rbuf[3][kPBlock];
+    // rho, alpha, beta, ||S r||^2, 1/rho, 1/(rho alpha), stop threshold
+    __shared__ double sc[7];
+    __shared__ long long s_max_iter;
+    __shared__ int s_stop;        // 1 stop, 2 breakdown
+    __shared__ int s_dep[4];      // [lo, hi] owners for black rows, then for red rows
+    CgState* st = P.st;
+    if (st->done) return;                      // uniform: set before the launch
+    // row indices fit 32 bits (the columns are int32): fewer registers
+    const int n = (int)P.n, nR = (int)P.nR, nB = n - nR;
+    const double* __restrict__ A = P.a;
+    const int32_t* __restrict__ C = P.col;
+    double* __restrict__ y = P.y;
+    double* __restrict__ r = P.r;
+    double* __restrict__ p = P.p;
+    double* __restrict__ s = P.q;
+    double* __restrict__ w = P.t;
+    double* __restrict__ z = P.z;
+    GridSync* gs = P.gs;
+    const int Rr = (int)rows_per_block(nR), Rb = (int)rows_per_block(nB);
+    const int rlo = (int)blockIdx.x * Rr < nR ? (int)blockIdx.x * Rr : nR;
+    const int rhi = rlo + Rr < nR ? rlo + Rr : nR;
+    const int blo = nR + ((int)blockIdx.x * Rb < nB ? (int)blockIdx.x * Rb : nB);
+    const int bhi = blo + Rb < n ? blo + Rb : n;
+    Epoch ep;
+    ep.target = P.stall ? 1ull : 0ull;
+    {
+        int lo_, hi_;
+        column_blocks(C, n, blo, bhi, 0, Rr, &lo_, &hi_);
+        if (threadIdx.x == 0) {
+            s_dep[0] = lo_;
+            s_dep[1] = hi_;
+        }
+        column_blocks(C, n, rlo, rhi, nR, Rb, &lo_, &hi_);
+        if (threadIdx.x == 0) {
+            s_dep[2] = lo_;
+            s_dep[3] = hi_;
+        }
+        __syncthreads();          // every thread reads s_dep below
+    }
+    if (threadIdx.x == 0) {
+        sc[0] = 0.0;
+        sc[1] = 0.0;
+        sc[2] = 0.0;
+        sc[3] = st->rnorm2;
+        sc[4] = 0.0;
+        sc[5] = 0.0;
+        sc[6] = st->thresh2;
+        s_max_iter = st->max_iter;
+        s_stop = 0;
+    }
+    bool ok;
+    bool halo;
+    {
+        const bool wide = s_dep[1] - s_dep[0] + 1 > kMaxDeps || s_dep[3] - s_dep[2] + 1 > kMaxDeps;
+        double wv[1] = {wide ? 1.0 : 0.0};
+        double none[1];
+        int any = 0;
+        ok = grid_allreduce<1, 1>(rbuf, wv, none, any, P.partials, gs, ep,
+                                  [](const double (&t)[1], double* o, int& f) {
+                                      o[0] = 0.0;
+                                      f = t[0] > 0.0 ? 1 : 0;
+                                  });
+        halo = any == 0;
+    }
+    auto post = [&](int slot, int ps) {
+        if (halo) halo_post(gs, (unsigned long long)(ps + 1), slot);
+    };
+    // wait for phase `slot` of this pass at the owners of the black rows'
+    // columns (which = 0) or of the red rows' columns (which = 1)
+    auto wait = [&](int slot, int ps, int which) -> bool {
+        if (!halo) return grid_barrier(gs, ep);
+        return halo_wait(gs, s_dep[2 * which], s_dep[2 * which + 1],
+                         (unsigned long long)(ps + 1), slot);
+    };
+    int pass = 0;              // passes 1, 2, ... each begin with an update: iterations = pass
+    for (; ok; ++pass) {
+        const bool upd = pass > 0;
+        // the stop test every 8th pass, not gated: gamma = r.M^-1 r here, which
+        // bounds neither r.r nor ||S r||^2 from below
+        const bool check = upd && (pass % 8) == 0;
+        const double alpha = sc[1], beta = sc[2];
+        double sums[3] = {0.0, 0.0, 0.0};
+        if (upd) {   // red update
+            for (int e = rlo + (int)threadIdx.x; e < rhi; e += kPBlock) {
+                const double pe = p[e];
+                const double se = s[e];
+                const double we = w[e];
+                const double ze = z[e];
+                const double re = r[e];
+                const double ye = y[e];
+                const double pn = fma(beta, pe, ze);
+                const double sn = fma(beta, se, we);
+                p[e] = pn;
+                s[e] = sn;
+                y[e] = fma(alpha, pn, ye);
+                r[e] = fma(-alpha, sn, re);
+            }
+        } else {
+            // an empty slot of a red row points at the row itself with value
+            // 0: its z must be finite before the first backward sweep
+            for (int e = rlo + (int)threadIdx.x; e < rhi; e += kPBlock) z[e] = 0.0;
+        }
+        post(0, pass);
+        if (!(ok = wait(0, pass, 0))) break;
+        // black update, then z_B = D_B^-1 (r_B - E^T r_R); gamma_B = r.z
+        for (int e = blo + (int)threadIdx.x; e < bhi; e += kPBlock) {
+            double re = r[e];
+            if (upd) {
+                const double pe = p[e];
+                const double se = s[e];
+                const double we = w[e];
+                const double ze = z[e];
+                const double ye = y[e];
+                const double pn = fma(beta, pe, ze);
+                const double sn = fma(beta, se, we);
+                p[e] = pn;
+                s[e] = sn;
+                y[e] = fma(alpha, pn, ye);
+                re = fma(-alpha, sn, re);
+                r[e] = re;
+            } else {
+                s[e] = 0.0;
+            }
+            double v = fma(-A[e], r[C[e]], re);
+            v = fma(-A[n + e], r[C[n + e]], v);
+            v = fma(-A[2 * n + e], r[C[2 * n + e]], v);
+            const double ze = v * P.dinv[e];
+            z[e] = ze;
+            sums[0] = fma(re, ze, sums[0]);
+            if (check) {
+                const double tt = P.s[e] * re;
+                sums[2] = fma(tt, tt, sums[2]);
+            }
+        }
+        post(1, pass);
+        if (!(ok = wait(1, pass, 1))) break;
+        // t = E z_B, z_R = r_R - t, w_R = z_R + t; gamma_R = r.z, delta_R = w.z
+        {
+            double re[2], a0[2], a1[2], a2[2];
+            int c0[2], c1[2], c2[2];
+            CPS_B_LOOP(rlo, rhi, 2,
+                (re[u] = r[e], a0[u] = A[e], a1[u] = A[n + e], a2[u] = A[2 * n + e],
+                 c0[u] = C[e], c1[u] = C[n + e], c2[u] = C[2 * n + e]),
+                {
+                    if (!upd) s[e] = 0.0;
+                    double t = a0[u] * z[c0[u]];
+                    t = fma(a1[u], z[c1[u]], t);
+                    t = fma(a2[u], z[c2[u]], t);
+                    const double ze = re[u] - t;
+                    const double we = ze + t;
+                    z[e] = ze;
+                    w[e] = we;
+                    sums[0] = fma(re[u], ze, sums[0]);
+                    sums[1] = fma(we, ze, sums[1]);
+                    if (check) {
+                        const double tt = P.s[e] * re[u];
+                        sums[2] = fma(tt, tt, sums[2]);
+                    }
+                })
+        }
+        post(2, pass);
+        if (!(ok = wait(2, pass, 0))) break;
+        // w_B = z_B + E^T z_R; delta_B = w.z
+        {
+            double ze[2], a0[2], a1[2], a2[2];
+            int c0[2], c1[2], c2[2];
+            CPS_B_LOOP(blo, bhi, 2,
+                (ze[u] = z[e], a0[u] = A[e], a1[u] = A[n + e], a2[u] = A[2 * n + e],
+                 c0[u] = C[e], c1[u] = C[n + e], c2[u] = C[2 * n + e]),
+                {
+                    double v = fma(a0[u], z[c0[u]], ze[u]);
+                    v = fma(a1[u], z[c1[u]], v);
+                    v = fma(a2[u], z[c2[u]], v);
+                    w[e] = v;
+                    sums[1] = fma(v, ze[u], sums[1]);
+                })
+        }
+        auto step = [&](const double* t, bool chk, int& f) {
+            const double g = t[0], d = t[1];
+            bool halt = !(g > 0.0) || (upd && pass >= s_max_iter);   // exact, budget
+            if (chk) {
+                sc[3] = t[2];
+                if (t[2] <= sc[6]) halt = true;
+            }
+            f = halt ? 1 : 0;
+            if (!halt) {
+                const double den = fma(-(g * g), sc[5], d);
+                if (!(den > 0.0) || !isfinite(den)) {
+                    // on pass 0 z.Az <= 0: not SPD; later, the recurrence's
+                    // difference lost its digits at the FP64 floor: stop, and
+                    // let the true residual decide (restart or not converged)
+                    f = upd ? 1 : 2;
+                } else {
+                    const double ig = 1.0 / g;
+                    sc[1] = g / den;
+                    sc[2] = g * sc[4];
+                    sc[4] = ig;
+                    sc[5] = den * ig * ig;
+                }
+            }
+            sc[0] = g;
+        };
+        double none[1];
+        int flag = 0;
+        if (check) {
+            double v3[3] = {sums[0], sums[1], sums[2]};
+            ok = grid_allreduce<3, 1>(rbuf, v3, none, flag, P.partials, gs, ep,
+                                      [&](const double (&t)[3], double* o, int& f) {
+                                          o[0] = 0.0;
+                                          step(t, true, f);
+                                      });
+        } else {
+            double v2[2] = {sums[0], sums[1]};
+            ok = grid_allreduce<2, 1>(rbuf, v2, none, flag, P.partials, gs, ep,
+                                      [&](const double (&t)[2], double* o, int& f) {
+                                          o[0] = 0.0;
+                                          step(t, false, f);
+                                      });
+        }
+        if (!ok) break;
+        if (flag) {
+            if (threadIdx.x == 0) s_stop = flag;
+            break;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->iter = pass;
+        st->rho = sc[0];
+        st->alpha = sc[1];
+        st->beta = sc[2];
+        st->rnorm2 = sc[3];
+        st->status = ok ? (s_stop == 2 ? CPS_ERR_NOT_SPD : CPS_OK) : CPS_ERR_TIMEOUT;
+        st->done = 2;
+    }
+}
+
 // Reduced system (two colours, colour order): CG on S = I - E^T E over the
 // black rows [nR, n) from the state k_black_init left.  Block b owns red rows
 // [b Rr, (b+1) Rr) and black rows nR + [b Rb, (b+1) Rb).
@@ -736,11 +1005,12 @@ __global__ void __launch_bounds__(kPBlock, 1) k_persistent_reduced(PersistArgs P
     double* __restrict__ y = P.y;
     double* __restrict__ t = P.t;
     GridSync* gs = P.gs;
-    const int64_t Rr = rows_per_block(nR), Rb = rows_per_block(nB);
-    const int64_t rlo = blockIdx.x * Rr < nR ? blockIdx.x * Rr : nR;
-    const int64_t rhi = rlo + Rr < nR ? rlo + Rr : nR;
-    const int64_t blo = nR + (blockIdx.x * Rb < nB ? blockIdx.x * Rb : nB);
-    const int64_t bhi = blo + Rb < n ? blo + Rb : n;
+    // row ranges fit 32 bits (the columns are int32): fewer registers
+    const int Rr = (int)rows_per_block(nR), Rb = (int)rows_per_block(nB);
+    const int rlo = (int)blockIdx.x * Rr < nR ? (int)blockIdx.x * Rr : (int)nR;
+    const int rhi = rlo + Rr < nR ? rlo + Rr : (int)nR;
+    const int blo = (int)nR + ((int)blockIdx.x * Rb < nB ? (int)blockIdx.x * Rb : (int)nB);
+    const int bhi = blo + Rb < n ? blo + Rb : (int)n;
     if (threadIdx.x == 0) {
         sc[0] = st->rho;
         sc[1] = st->rnorm2;
@@ -749,7 +1019,7 @@ __global__ void __launch_bounds__(kPBlock, 1) k_persistent_reduced(PersistArgs P
     int status = CPS_OK;
     bool ok = true;
     Epoch ep;
-    ep.extra = P.stall ? 1ull : 0ull;
+    ep.target = P.stall ? 1ull : 0ull;
     // The red phase reads p at black rows, the black phase t at red rows:
     // on banded numberings both lie in a few neighbouring blocks, and the
     // two grid barriers become waits on those blocks' flags (slot 0: p
@@ -883,9 +1153,15 @@ __global__ void __launch_bounds__(kPBlock, 1) k_persistent_reduced(PersistArgs P
 }  // namespace
 
 // The persistent kernel of a solve kind: 0 textbook Jacobi, 1 the reduced
-// system, 2 single-reduction Jacobi.
+// system, 2 single-reduction Jacobi, 3 single-reduction IC(0) in a
+// two-colour order.
 static void (*persistent_kernel(int kind))(PersistArgs) {
-    return kind == 1 ? k_persistent_reduced : (kind == 2 ? k_persistent_gear : k_persistent_cg);
+    switch (kind) {
+        case 1: return k_persistent_reduced;
+        case 2: return k_persistent_gear;
+        case 3: return k_persistent_ic0;
+        default: return k_persistent_cg;
+    }
 }
 
 // Largest grid of a persistent launch on this device (blocks that stay
@@ -903,15 +1179,16 @@ int persistent_max_grid(cps_sys s, int reduced) {
 
 // Launches the persistent solve (reduced = 0: Jacobi on all rows; 1: the
 // reduced system; 2: single-reduction Jacobi on all rows, after k_init64 and
-// k_gear_start, with s = A p in q and w = A r in t) after the caller's init
-// kernel; state in s->st.  With
+// k_gear_start, with s = A p in q and w = A r in t; 3: single-reduction IC(0)
+// in the two-colour order after k_init64, s in q, w in t, z and the inverse
+// pivots in z, dinv) after the caller's init kernel; state in s->st.  With
 // win_bytes > 0 the launch carries a persisting L2 access-policy window over
 // [win_base, win_base + win_bytes) (the caller holds the set-aside).  grid:
 // blocks of the launch, at most what stays resident (0: that maximum).
 int persistent_solve(cps_sys s, int reduced, const double* a, const int32_t* col,
                      const double* sc, double* y, double* r, double* p, double* q, double* t,
                      int64_t n, int64_t nR, const void* win_base, size_t win_bytes, int grid,
-                     cudaStream_t stream) {
+                     cudaStream_t stream, double* z, const double* dinv) {
     if (!s->gsync) {
         cudaError_t e = cudaMalloc((void**)&s->gsync, sizeof(GridSync));
         if (e != cudaSuccess) {
@@ -939,7 +1216,7 @@ int persistent_solve(cps_sys s, int reduced, const double* a, const int32_t* col
     const int stall = s->inject == CPS_TEST_STALL_BARRIER ? 1 : 0;
     s->inject = 0;
     PersistArgs P{a, col, sc, y, r, p, q, t, n, nR, s->partials,
-                  reinterpret_cast<GridSync*>(s->gsync), s->st, stall, s->diag_min};
+                  reinterpret_cast<GridSync*>(s->gsync), s->st, stall, s->diag_min, z, dinv};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(G, 1, 1);
     cfg.blockDim = dim3(kPBlock, 1, 1);

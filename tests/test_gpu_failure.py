@@ -26,7 +26,8 @@ def ctx(cuda_device):
     c.close()
 
 
-@pytest.mark.parametrize("precond", ["jacobi", "jacobi_single_reduction", "reduced"])
+@pytest.mark.parametrize("precond", ["jacobi", "jacobi_single_reduction", "ic0_single_reduction",
+                                     "reduced"])
 def test_stalled_grid_barrier_times_out_and_recovers(ctx, precond):
     p = synth.channel_block_problem(64, seed=5)
     m = p.mesh
@@ -34,7 +35,9 @@ def test_stalled_grid_barrier_times_out_and_recovers(ctx, precond):
                      p.nu, p.dt)
     if precond == "reduced":
         s.set_precond(cps.PC_REDUCED)
-    s.set_solver_path(cps.PATH_PERSISTENT_1RED if precond == "jacobi_single_reduction"
+    if precond == "ic0_single_reduction":
+        s.set_precond(cps.PC_IC0)
+    s.set_solver_path(cps.PATH_PERSISTENT_1RED if precond.endswith("single_reduction")
                       else cps.PATH_PERSISTENT)
     b = synth.rhs(m, 3)
     bt = torch.as_tensor(b, device="cuda")

@@ -548,6 +548,54 @@ def test_stream_single_reduction_matches_oracle(ctx, name):
     s.free()
 
 
+@pytest.mark.parametrize("name", ["block37", "channel64", "logperm29", "ensemble", "defect20",
+                                  "channel300"])
+def test_persistent_ic0_matches_oracle(ctx, name):
+    """IC(0) in the colour order as one persistent launch of the single-
+    reduction recurrences (black forward and red backward sweeps read from
+    the scaled matrix), without and with its vectors in persisting L2,
+    against the oracle's solution and against the streaming IC(0) loop (the
+    same preconditioned iterates in exact arithmetic).  On a graph that
+    needs more than two colours the pin falls back to the streaming
+    kernels."""
+    p = PROBLEMS[name] if name in PROBLEMS else synth.channel_block_problem(300, seed=8)
+    s = assemble(ctx, p)
+    s.set_precond(cps.PC_IC0)
+    b = synth.rhs(p.mesh, 37)
+    bt = torch.as_tensor(b, device="cuda")
+    xo, _, A = oracle.solve_problem(p, b, rtol=1e-13)
+    s.set_solver_path(cps.PATH_STREAM)
+    x0, st0 = s.solve(bt, rtol=1e-12, max_iter=100_000, check=False)
+    assert not s.tuning()["ic0_persistent"]
+    for path in (cps.PATH_PERSISTENT_1RED, cps.PATH_PERSISTENT_1RED_L2):
+        s.set_solver_path(path)
+        x, st = s.solve(bt, rtol=1e-12, max_iter=100_000, check=False)
+        assert st.status in (0, cps._cps.ERR_NOT_CONVERGED) and st.rel_res < 1e-10
+        err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
+        assert err < 1e-9, (path, err)
+        assert abs(st.iters - st0.iters) <= max(8, 0.08 * st0.iters), (path, st.iters, st0.iters)
+        r = b - A.matvec(x.cpu().numpy())
+        assert np.linalg.norm(r) / np.linalg.norm(b) < 2 * max(st.rel_res, 1e-13)
+        persistent = s.tuning()["ic0_persistent"]
+        if name != "defect20":                  # the lattices are two-coloured
+            assert persistent
+    # warm start from the solution; a zero right-hand side
+    s.set_solver_path(cps.PATH_PERSISTENT_1RED)
+    x2 = x.clone()
+    _, st2 = s.solve(bt, x=x2, rtol=1e-8)
+    assert st2.iters == 0
+    z = torch.ones_like(bt)
+    s.solve(torch.zeros_like(bt), x=z)
+    assert torch.all(z == 0)
+    # the tuner times both ways on a fresh pin
+    s.set_solver_path(cps.PATH_AUTO)
+    x3, st3 = s.solve(bt, rtol=1e-12, max_iter=100_000, check=False)
+    assert np.linalg.norm(x3.cpu().numpy() - xo) / np.linalg.norm(xo) < 1e-9
+    pr = s.tuning()["probe_us_per_iter"]
+    assert (pr["ic0_stream"] > 0) == (name != "defect20")   # probed on two colours only
+    s.free()
+
+
 def test_pinned_shapes_and_stream_l2_path(ctx):
     """Launch shapes pinned instead of tuned, and the streaming path with
     r, p, q in persisting L2, on a system above the tuning threshold: the
