@@ -75,6 +75,11 @@ TRAFFIC_CAPTURES = [
       "persistent": False, "cluster": False, "stream_single_reduction": True,
       "update_1red_grid_block": [152, 1024]},
      (108.3 + 124.5) * 1e6),
+    # single-reduction persistent launch (k_persistent_gear, 152 x 1024, the
+    # five vectors in persisting L2): 45.07 GB over a 200-iteration solve
+    ({"l2_window": "vectors5", "persistent": True, "persistent_single_reduction": True,
+      "cluster": False},
+     (141.7 + 83.6) * 1e6),
 ]
 # Algorithmic bytes per cell of the CP2 step kernels (each array counted once):
 # mean flux: u 16, per side col 4 + area weight 8 + l n 16, Fbar out 24, B1 out 8;
@@ -428,10 +433,14 @@ def batch_summary(n_systems: int, rtol: float, reps: int, loops: bool = True,
             its += st.iters * s.nt
         return its
 
+    status = {}
+
     def batch(prec):
         for x in xs:
             x.zero_()
-        st = cps.solve_batch(systems, bs, xs, rtol=rtol, precision=prec)
+        st = cps.solve_batch(systems, bs, xs, rtol=rtol, precision=prec, check=False)
+        status[prec] = {"members_not_converged": sum(1 for t in st if t.status != 0),
+                        "max_rel_res": max(t.rel_res for t in st)}
         return sum(t.iters * s.nt for t, s in zip(st, systems))
 
     loop(cps.FP64)
@@ -455,7 +464,8 @@ def batch_summary(n_systems: int, rtol: float, reps: int, loops: bool = True,
         s.free()
     ctx.close()
     out = {"systems": n_systems, "cells": cells, "rtol": rtol, "host_setup_s": setup,
-           "variants": res,
+           "variants": res, "fp64_status": status.get(cps.FP64),
+           "mixed_status": status.get(cps.MIXED),
            "batch_mixed_vs_batch_fp64_seconds":
                res["batch_mixed"]["seconds"] / res["batch_fp64"]["seconds"]}
     if "loop_fp64" in res:

@@ -1364,8 +1364,9 @@ static int solve_mixed(cps_sys s, const double* b, double* x, double rtol, int64
             break;
         }
         // A replaced residual that stops falling (no 10% gain over 8
-        // replacements) or that rose since the last replacement: restart
-        // the search directions.
+        // replacements): restart the search directions, at most 4 times.  One
+        // that rose since the last replacement restarts them too, without
+        // counting against that limit (the stall count still runs).
         if (h.rnorm2 < 0.81 * prev) {
             prev = h.rnorm2;
             stall = 0;
@@ -1374,7 +1375,7 @@ static int solve_mixed(cps_sys s, const double* b, double* x, double rtol, int64
         }
         const bool rose = h.rnorm2 > last;
         last = h.rnorm2;
-        if ((stall >= 8 || rose) && !first) {
+        if (stall >= 8 && !first) {
             if (++restarts > 4) {
                 status = CPS_ERR_NOT_CONVERGED;
                 restore = h.rnorm2 > best;
@@ -1383,6 +1384,11 @@ static int solve_mixed(cps_sys s, const double* b, double* x, double rtol, int64
             base += h.iter;
             first = 1;
             stall = 0;
+            continue;
+        }
+        if (rose && !first) {
+            base += h.iter;
+            first = 1;
             continue;
         }
         first = 0;

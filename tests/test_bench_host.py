@@ -26,7 +26,7 @@ def _tuned(**kw):
 
 
 def test_traffic_is_reported_only_for_captured_configurations():
-    textbook, gear = (t for _, t in bench.TRAFFIC_CAPTURES)
+    textbook, gear, pgear = (t for _, t in bench.TRAFFIC_CAPTURES)
     assert bench.traffic_for(_tuned(), 1024) == textbook
     g = _tuned(stream_single_reduction=True, l2_window="vectors5")
     assert bench.traffic_for(g, 1024) == gear
@@ -35,7 +35,9 @@ def test_traffic_is_reported_only_for_captured_configurations():
     assert bench.traffic_for(dict(g, update_1red=[2, 608, 256]), 1024) is None
     assert bench.traffic_for(_tuned(persistent=True), 1024) is None
     assert bench.traffic_for(_tuned(persistent_single_reduction=True, persistent=True),
-                             1024) is None
+                             1024) is None            # r, p, q window only: not captured
+    assert bench.traffic_for(_tuned(persistent_single_reduction=True, persistent=True,
+                                    l2_window="vectors5"), 1024) == pgear
     assert bench.traffic_for(_tuned(l2_window="none"), 1024) is None
     assert bench.traffic_for(_tuned(), 512) is None
 
