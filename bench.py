@@ -187,11 +187,14 @@ def parse():
                          "--n lattice with checkpointed adjoint backward (own line)")
     ap.add_argument("--chain-rtol", type=float, default=1e-8,
                     help="relative residual of the chained forward and adjoint solves")
-    ap.add_argument("--sequence", type=int, default=0,
-                    help="sequence mode: this many warm-started solves on one fixed matrix "
-                         "of the --n lattice (4096: 33.5M cells), right-hand side redrawn each "
-                         "step, FP64 and mixed, each solve capped at --seq-iters (own line)")
-    ap.add_argument("--seq-iters", type=int, default=500)
+    ap.add_argument("--sequence", action="store_true",
+                    help="sequence mode: warm-started solves to --rtol on one fixed matrix of "
+                         "the --n lattice (4096: 33.5M cells), right-hand side redrawn each "
+                         "step, --seq-solves per variant (own line)")
+    ap.add_argument("--seq-iters", type=int, default=0,
+                    help="sequence mode: iteration cap per solve (0: none, run to --rtol)")
+    ap.add_argument("--seq-solves", default="reduced:3,jacobi:2,mixed:2,ic0:1",
+                    help="sequence mode: solves per variant (reduced, jacobi, mixed, ic0)")
     ap.add_argument("--cp2-step", type=int, default=0,
                     help="CP2-step mode: this many timed CP2 steps (mean flux, two PCG solves, "
                          "tangential flux, RT0 velocity, eps grad Psi) on the --n lattice, "
@@ -610,53 +613,74 @@ def latency_summary(n: int, rtol: float, reps: int = 5) -> dict:
 
 
 def run_sequence(args):
-    """Warm-started corrector sequence on one fixed matrix: x_t starts from
-    x_{t-1}, b_t = area N(0,1) drawn from seed t.  At 33.5M cells a full solve
-    to 1e-10 takes tens of thousands of iterations, so each solve is capped at
-    --seq-iters iterations and the line reports per-iteration throughput (cells x
-    iterations / time, and the algorithmic bytes of the iteration against the
-    measured copy bandwidth) for FP64 and for mixed precision."""
+    """Warm-started corrector sequence on one fixed matrix (config 2): the
+    matrix is assembled once (Sec. 3.1: assembled and factored once, solved
+    every step), b_t = area N(0,1) from seed t, and each solve starts from the
+    previous solution and runs to --rtol.  At 33.5M cells a Jacobi solve to
+    1e-10 takes tens of thousands of iterations, so every variant runs its own
+    number of solves (--seq-solves, e.g. "reduced:3,jacobi:2,mixed:2,ic0:1"),
+    stated in the line.  Per variant: seconds per solve to rtol, iterations,
+    microseconds per iteration and the method's algorithmic bytes against the
+    measured copy bandwidth (108 B/cell/iter for Jacobi; 148 for IC(0); the
+    reduced system's own 160 B per black-row pair)."""
     import torch
     import paper_2309_03543_gb300 as cps
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     ctx = cps.Context(0)
+    t0 = time.perf_counter()
     p = synth.channel_block_problem(args.n, seed=0)
     m = p.mesh
     nt = m.nt
     s = ctx.assemble(m.xy, m.tri, m.dirichlet, p.eps, p.kinv, p.field_loc, cps.KIND_CP2,
                      p.nu, p.dt)
-    rhs = [torch.as_tensor(synth.rhs(m, seed=t), device=dev) for t in range(args.sequence + 1)]
+    counts = {k: int(v) for k, v in (kv.split(":") for kv in args.seq_solves.split(","))}
+    total = max(counts.values()) + 1
+    rhs = [torch.as_tensor(synth.rhs(m, seed=t), device=dev) for t in range(total)]
+    setup = time.perf_counter() - t0
     peak, peak_kind = measured_peaks()
+    max_iter = args.seq_iters if args.seq_iters > 0 else 1_000_000
+    # (name, preconditioner, precision, algorithmic bytes per cell per iteration)
+    table = {"reduced": (cps.PC_REDUCED, cps.FP64, 160 / 2),
+             "jacobi": (cps.PC_JACOBI, cps.FP64, BYTES_PER_CELL_ITER_METHOD),
+             "mixed": (cps.PC_JACOBI, cps.MIXED, BYTES_PER_CELL_ITER_MIXED),
+             "ic0": (cps.PC_IC0, cps.FP64, BYTES_PER_CELL_ITER_METHOD + 40)}
     out = {}
-    for name, prec, bpc in (("fp64", cps.FP64, BYTES_PER_CELL_ITER_FP64),
-                            ("mixed", cps.MIXED, BYTES_PER_CELL_ITER_MIXED)):
+    for name, k in counts.items():
+        pc, prec, bpc = table[name]
+        s.set_precond(pc)
         x = torch.zeros(nt, dtype=torch.float64, device=dev)
-        # warm-up solve: autotuning and path probes of this precision
-        s.solve(rhs[-1], x=x, rtol=1e-10, max_iter=args.seq_iters, precision=prec, check=False)
-        x.zero_()
-        t_tot, it_tot, rel = 0.0, 0, []
-        for t in range(args.sequence):
-            dt_, st = timed(lambda: s.solve(rhs[t], x=x, rtol=1e-10, max_iter=args.seq_iters,
+        t_tot, it_tot, rel, status, per = 0.0, 0, [], [], []
+        for t in range(k + 1):          # solve 0 also tunes: not timed
+            dt_, st = timed(lambda: s.solve(rhs[t], x=x, rtol=args.rtol, max_iter=max_iter,
                                             precision=prec, check=False)[1], stream)
+            if t == 0:
+                continue
             t_tot += dt_
             it_tot += st.iters
             rel.append(st.rel_res)
+            status.append(st.status)
+            per.append(dt_)
+        # reduced system: iterations run over the black half of the cells
+        units = nt // 2 if pc == cps.PC_REDUCED else nt
         gbs = bpc * nt * it_tot / t_tot / 1e9
-        out[name] = {"cell_iters_per_s": nt * it_tot / t_tot, "us_per_iter": 1e6 * t_tot / it_tot,
-                     "iters": it_tot, "seconds": t_tot, "algorithmic_gbs": gbs,
+        out[name] = {"solves": k, "seconds_per_solve": t_tot / k, "seconds_each": per,
+                     "iters": it_tot, "us_per_iter": 1e6 * t_tot / max(it_tot, 1),
+                     "cell_iters_per_s": units * it_tot / t_tot, "algorithmic_gbs": gbs,
                      "bytes_per_cell_iter": bpc, "frac_of_peak": gbs / peak,
-                     "rel_res_after_each_solve": rel}
-    tuned = s.tuning(cps.FP64)
+                     "rel_res_each": rel, "status_each": status,
+                     "path": loop_name(s.tuning(cps.FP64)) if name == "jacobi" else None}
     s.free()
-    line = {"metric": "warm-started corrector sequence, per-iteration throughput (capped solves)",
-            "value": out["fp64"]["cell_iters_per_s"], "unit": "cell-iters/s",
+    ctx.close()
+    first = out.get("jacobi") or next(iter(out.values()))
+    line = {"metric": "warm-started corrector sequence: time per solve to rtol",
+            "value": first["cell_iters_per_s"], "unit": "cell-iters/s",
             "higher_is_better": True, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"channel-block-aniso lattice n={args.n}", "cells": nt,
-                       "solves": args.sequence, "iters_cap_per_solve": args.seq_iters,
-                       "rhs": "area N(0,1) from seed t, warm start from x_{t-1}"},
-            "peak": peak, "peak_kind": peak_kind, "fp64": out["fp64"], "mixed": out["mixed"],
-            "fp64_tuning": tuned}
+                       "rtol": args.rtol, "solves": counts,
+                       "rhs": "area N(0,1) from seed t, warm start from x_{t-1}",
+                       "host_setup_s": setup},
+            "peak": peak, "peak_kind": peak_kind, "variants": out}
     print(json.dumps(line), flush=True)
 
 
@@ -909,9 +933,9 @@ def main():
     if args.profile_iters:
         # every variant once (autotuning, path probes), then the FP64 Jacobi
         # solve again inside the NVTX range "cps_profile", the mixed Jacobi
-        # solve inside "cps_profile_mixed" and the reduced-system solve inside
-        # "cps_profile_reduced" (the launches a profiler should select: ncu
-        # --nvtx --nvtx-include "cps_profile/")
+        # solve inside "cps_profile_mixed", IC(0) inside "cps_profile_ic0" and
+        # the reduced-system solve inside "cps_profile_reduced" (the launches a
+        # profiler should select: ncu --nvtx --nvtx-include "cps_profile/")
         s = ctx.assemble(d["xy"], d["tri"], d["dir"], d["eps"], d["kinv"], cps.PER_VERTEX,
                          cps.KIND_CP2, p.nu, p.dt)
         if args.pin:
@@ -941,6 +965,14 @@ def main():
         torch.cuda.nvtx.range_push("cps_profile_mixed")
         s.solve(d["b"], x=x, rtol=args.rtol, max_iter=args.profile_iters, precision=cps.MIXED,
                 check=False)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        # IC(0) (tuned or pinned loop), marked "cps_profile_ic0"
+        s.set_precond(cps.PC_IC0)
+        x.zero_()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("cps_profile_ic0")
+        s.solve(d["b"], x=x, rtol=args.rtol, max_iter=args.profile_iters, check=False)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         # the reduced system: first solve tunes its path, the second is marked
