@@ -183,10 +183,21 @@ int cps_solve(cps_sys sys, const double* b, double* x, double rtol, int64_t max_
  * systems, b, x and stats are HOST arrays of length nsys holding handles and
  * device pointers (b[i], x[i] of system i's size; x[i] is the initial guess
  * and receives the solution).  All systems must come from the same context.
- * CPS_FP64: one launch per phase for all systems (Jacobi, whatever each
- * system's preconditioner setting), a per-system convergence mask, and
- * iteration chunks replayed from a CUDA graph; a system of more than
- * 33,554,432 cells is rejected (CPS_ERR_ARG) -- solve it alone.  CPS_MIXED:
+ * CPS_FP64 (Jacobi, whatever each system's preconditioner setting): by
+ * default one cooperative kernel launch for the whole ensemble -- the
+ * largest systems (estimated work cells^1.5 above twice a block's fair
+ * share) are each solved by a static team of blocks that split the rows and
+ * combine their sums through bounded device-side waits, and every other
+ * block takes whole systems from a device work queue (largest first) and
+ * solves each with block-level reductions only; a team's blocks join the
+ * queue when their system is done, and every system stops as soon as it
+ * converges.  The iteration is the single-reduction (Chronopoulos-Gear) form
+ * of Jacobi CG, restarted from the true residual up to 8 times.  A team
+ * wait that runs out (about one second) gives CPS_ERR_TIMEOUT.  With
+ * cps_set_batch_path(ctx, CPS_BATCH_GRAPH) instead one launch per phase for
+ * all systems, a per-system convergence mask, and iteration chunks replayed
+ * from a CUDA graph (a system of more than 33,554,432 cells is rejected there
+ * with CPS_ERR_ARG -- solve it alone).  CPS_MIXED:
  * each system's solve (whose residual replacements are decided on the host)
  * runs whole on one of up to 8 internal streams, fed by as many host threads,
  * so that the systems' launches overlap on the GPU; the call returns after
@@ -196,6 +207,13 @@ int cps_solve(cps_sys sys, const double* b, double* x, double rtol, int64_t max_
 int cps_solve_batch(const cps_sys* systems, int nsys, const double* const* b,
                     double* const* x, double rtol, int64_t max_iter, int precision,
                     cps_stats* stats, void* stream);
+
+/* How cps_solve_batch runs FP64 ensembles on this context (no counterpart in
+ * the paper; both are for the ensemble workload): CPS_BATCH_ONE_LAUNCH (the
+ * default) or CPS_BATCH_GRAPH (see cps_solve_batch).  Errors: CPS_ERR_ARG. */
+#define CPS_BATCH_ONE_LAUNCH 0
+#define CPS_BATCH_GRAPH 1
+int cps_set_batch_path(cps_ctx ctx, int path);
 
 /* Adjoint of one solve x = A^-1 b (A symmetric, so the same matrix and
  * preconditioner serve): lambda = A^-1 g, then for every local side slot

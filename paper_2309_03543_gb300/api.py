@@ -69,6 +69,11 @@ class Context:
         t = torch.as_tensor(t)
         return t.to(device=self.device, dtype=dtype).contiguous()
 
+    def set_batch_path(self, path: int):
+        """BATCH_ONE_LAUNCH (default) or BATCH_GRAPH: how solve_batch runs FP64
+        ensembles on this context."""
+        self.check(self.lib.cps_set_batch_path(self.handle, path), "cps_set_batch_path")
+
     def close(self):
         if getattr(self, "handle", None):
             for s in list(self._systems):

@@ -207,6 +207,12 @@ int cps_adjoint(cps_sys sys, const double* x, const double* g, double* lambda, d
                              as_stream(stream));
 }
 
+int cps_set_batch_path(cps_ctx ctx, int path) {
+    if (!ctx || (path != CPS_BATCH_ONE_LAUNCH && path != CPS_BATCH_GRAPH)) return CPS_ERR_ARG;
+    ctx->batch_path = path;
+    return CPS_OK;
+}
+
 int cps_set_solver_path(cps_sys sys, int path) {
     if (!sys) return CPS_ERR_ARG;
     cps::Tuning& t = sys->tune[CPS_FP64];

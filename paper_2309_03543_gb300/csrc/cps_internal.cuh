@@ -244,6 +244,7 @@ struct cps_ctx_s {
     std::mutex mu;               // guards last_error and tune_cache (solves may run on threads)
     std::mutex l2_mu;            // guards the persisting-L2 set-aside
     std::unordered_set<cps_sys_s*> systems;   // live systems, freed with the context
+    int batch_path = CPS_BATCH_ONE_LAUNCH;   // FP64 cps_solve_batch: one launch or graph chunks
     // Tuned launch choices by mesh size (cells, vertices): a system assembled
     // later on a mesh of the same size starts from them instead of re-timing.
     std::map<std::pair<int64_t, int64_t>, std::array<cps::Tuning, 2>> tune_cache;

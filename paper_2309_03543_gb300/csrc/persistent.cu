@@ -30,6 +30,7 @@
 // block whose wait runs out records CPS_ERR_TIMEOUT and leaves; the blocks
 // waiting on it then run out too, so the kernel always ends.
 #include "cps_internal.cuh"
+#include "exact_sum.cuh"
 
 #include <cmath>
 #include <cstddef>
@@ -103,56 +104,6 @@ struct Epoch {
 
 __device__ __forceinline__ void named_barrier(int id, int threads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
-}
-
-// ---- Exact sums in integer arithmetic.  GB300 issues FP64 at 2 per SM per
-// clock, and a chain of dependent FP64 adds pays the FP64 latency per add: a
-// block sum of 1024 doubles took about 2 us that way.  Here a set of doubles
-// is summed by aligning every value to the set's largest exponent E
-// (rounding to the nearest multiple of 2^(E - 1075 + h), h bits of headroom)
-// and adding the aligned integers exactly, with warp integer reductions on
-// 18-20-bit limbs.  The result depends on the set only, not on the order of
-// the values (deterministic, bit-identical in every block that sums the same
-// set); each value is off by at most half a unit of 2^(E - 1075 + h).
-
-// Biased exponent of v's binade (1 for zero and subnormals).
-__device__ __forceinline__ int align_exp(double v) {
-    const int e = (int)((__double_as_longlong(v) >> 52) & 0x7FF);
-    return e > 0 ? e : 1;
-}
-
-// round(v / 2^(E - 1075 + h)) for |v| < 2^(E - 1022), h >= 1: at most 2^(53 - h)
-// in magnitude.
-__device__ __forceinline__ long long align_fixed(double v, int E, int h) {
-    const long long bits = __double_as_longlong(v);
-    const int e = (int)((bits >> 52) & 0x7FF);
-    long long m = bits & 0xFFFFFFFFFFFFFLL;
-    if (e) m |= 1LL << 52;
-    const int sh = E - (e > 0 ? e : 1) + h;
-    const long long f = sh > 62 ? 0 : ((m + (1LL << (sh - 1))) >> sh);
-    return bits < 0 ? -f : f;
-}
-
-// T 2^(E - 1075 + h) as a double (NaN if the set held an infinity or NaN).
-__device__ __forceinline__ double fixed_to_double(long long T, int E, int h) {
-    if (E >= 2047) return __longlong_as_double(0x7FF8000000000000LL);
-    return ldexp(__ll2double_rn(T), E - 1075 + h);
-}
-
-// Exact sum over the warp of x, |x| <= 2^B (B <= 57): the biased value
-// x + 2^B is split into three limbs whose 32-lane sums fit 32 bits; the
-// recombination runs modulo 2^64, exact because the true sum (at most
-// 2^(B + 5)) fits a signed 64-bit integer.
-template <int B>
-__device__ __forceinline__ long long warp_sum_fixed(long long x) {
-    constexpr int L = (B + 4) / 3;
-    static_assert(B <= 57 && L <= 26 && 3 * L >= B + 2, "limbs of the biased value");
-    const unsigned long long u = (unsigned long long)x + (1ULL << B);
-    const unsigned mask = (1u << L) - 1u;
-    const unsigned long long s0 = __reduce_add_sync(0xffffffffu, (unsigned)(u & mask));
-    const unsigned long long s1 = __reduce_add_sync(0xffffffffu, (unsigned)((u >> L) & mask));
-    const unsigned long long s2 = __reduce_add_sync(0xffffffffu, (unsigned)(u >> (2 * L)));
-    return (long long)(s0 + (s1 << L) + (s2 << (2 * L)) - (32ULL << B));
 }
 
 // Grid-wide sum of v[0..NV) (NV <= 4), every stage in exact integer sums:

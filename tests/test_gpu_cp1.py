@@ -95,6 +95,23 @@ def test_cp1_step_matches_oracle_fp64(ctx, name):
     sy.free()
 
 
+@pytest.mark.parametrize("beta", [1.0, 1.5, 2.0])
+def test_cp1_weak_anisotropy_takes_the_papers_sweep_count(ctx, beta):
+    """App. B's 3-4 outer sweeps: an isotropic tensor needs one sweep (no
+    coupling), a weakly anisotropic one (beta <= 2) at most four, the same
+    count as the oracle's, with the same increments."""
+    p = _with_walls(synth.channel_block_problem(40, seed=2, beta=beta))
+    du_b = synth.cell_vector_field(p.mesh, 5, mean=(0.05, 0.01), scale=0.02)
+    o = oracle.cp1_step(p, du_b, toll=1e-4, rtol=1e-13)
+    sx, sy = _systems(ctx, p, None)
+    du, st = cps.cp1_step(sx, sy, du_b, toll=1e-4, rtol=1e-12)
+    assert st["outer"] == o.outer
+    assert st["outer"] == 1 if beta == 1.0 else 2 <= st["outer"] <= 4
+    assert _rel(du.cpu().numpy(), o.du) <= 1e-9
+    sx.free()
+    sy.free()
+
+
 @pytest.mark.parametrize("name", ["vertex_aniso_n20", "defect_n12", "two_cells"])
 def test_cp1_step_matches_oracle_mixed(ctx, name):
     p, theta = CASES[name]

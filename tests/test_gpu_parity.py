@@ -272,10 +272,13 @@ def test_autotuned_solves_on_a_large_system(ctx):
     s.free()
 
 
-def test_batched_solve_matches_oracle_per_system(ctx):
-    """Uneven ensemble solved together (one launch per phase, per-system
-    convergence): every member against its own oracle solve; a zero RHS
-    member returns zeros; the result equals the loop of single solves."""
+@pytest.mark.parametrize("batch_path", ["one_launch", "graph"])
+def test_batched_solve_matches_oracle_per_system(ctx, batch_path):
+    """Uneven ensemble solved together (in one launch whose blocks take whole
+    systems, or one launch per phase with per-system convergence masks):
+    every member against its own oracle solve; a zero RHS member returns
+    zeros; the result equals the loop of single solves."""
+    ctx.set_batch_path(cps.BATCH_ONE_LAUNCH if batch_path == "one_launch" else cps.BATCH_GRAPH)
     sizes = [600, 2500, 9000, 1200, 30000]
     probs = [synth.ensemble_member_problem(nt, seed=40 + i) for i, nt in enumerate(sizes)]
     systems = [assemble(ctx, p) for p in probs]
@@ -315,6 +318,7 @@ def test_batched_solve_matches_oracle_per_system(ctx):
                 assert err < 1e-8, (i, err)
     for s in systems:
         s.free()
+    ctx.set_batch_path(cps.BATCH_ONE_LAUNCH)
 
 
 @pytest.mark.parametrize("path", ["textbook", "single_reduction"])

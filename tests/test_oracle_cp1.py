@@ -132,3 +132,24 @@ def test_converged_outer_iteration_solves_the_coupled_system():
     # the paper's stopping rule (min of the two changes, toll 1e-4) stops earlier
     r4 = oracle.cp1_step(p, du_b, toll=1e-4)
     assert 1 <= r4.outer <= r.outer and r4.err <= 1e-4
+
+
+def test_outer_sweeps_grow_with_the_anisotropy_and_stay_at_the_papers_count_when_weak():
+    """App. B reports 3-4 outer sweeps (toll 1e-4 to 1e-3).  The outer
+    iteration is block Jacobi between the x and y systems, coupled only by
+    Mbar_12 A_e, which vanishes for an isotropic tensor and grows with the
+    principal ratio beta: one sweep when isotropic, at most 4 for beta <= 2,
+    and more as beta grows (the channel workload's beta = 100 needs tens)."""
+    import dataclasses
+    sweeps = {}
+    for beta in (1.0, 2.0, 10.0, 100.0):
+        p = synth.channel_block_problem(24, seed=2, beta=beta)
+        m = p.mesh
+        nbr = oracle.topology(m.tri)
+        e, j = np.nonzero(nbr < 0)
+        p = dataclasses.replace(p, mesh=dataclasses.replace(m, dirichlet=(e * 3 + j).astype(np.int32)))
+        du_b = synth.cell_vector_field(m, 5, mean=(0.05, 0.01), scale=0.02)
+        sweeps[beta] = oracle.cp1_step(p, du_b, toll=1e-4).outer
+    assert sweeps[1.0] == 1
+    assert 2 <= sweeps[2.0] <= 4
+    assert sweeps[2.0] < sweeps[10.0] < sweeps[100.0]
