@@ -446,19 +446,27 @@ def batch_summary(n_systems: int, rtol: float, reps: int, loops: bool = True,
                         "max_rel_res": max(t.rel_res for t in st)}
         return sum(t.iters * s.nt for t, s in zip(st, systems))
 
-    def batch_graph():
+    def batch_graph(prec):
+        # FP64: one launch per phase in graph chunks; mixed: whole per-system
+        # solves on worker streams (the designs the one launch replaces)
         ctx.set_batch_path(cps.BATCH_GRAPH)
         try:
-            return batch(cps.FP64)
+            for x in xs:
+                x.zero_()
+            st = cps.solve_batch(systems, bs, xs, rtol=rtol, precision=prec, check=False)
+            return sum(t.iters * s.nt for t, s in zip(st, systems))
         finally:
             ctx.set_batch_path(cps.BATCH_ONE_LAUNCH)
 
     loop(cps.FP64)
     batch(cps.FP64)   # warm-up (autotuning, graph capture)
-    batch_graph()
+    batch_graph(cps.FP64)
     batch(cps.MIXED)
-    runs = [("batch_fp64", lambda: batch(cps.FP64)), ("batch_fp64_graph", batch_graph),
-            ("batch_mixed", lambda: batch(cps.MIXED))]
+    batch_graph(cps.MIXED)
+    runs = [("batch_fp64", lambda: batch(cps.FP64)),
+            ("batch_fp64_graph", lambda: batch_graph(cps.FP64)),
+            ("batch_mixed", lambda: batch(cps.MIXED)),
+            ("batch_mixed_streams", lambda: batch_graph(cps.MIXED))]
     if loops:
         runs.append(("loop_fp64", lambda: loop(cps.FP64)))
         if mixed_loop:
@@ -482,6 +490,8 @@ def batch_summary(n_systems: int, rtol: float, reps: int, loops: bool = True,
                res["batch_mixed"]["seconds"] / res["batch_fp64"]["seconds"]}
     out["one_launch_speedup_vs_graph_chunks"] = \
         res["batch_fp64_graph"]["seconds"] / res["batch_fp64"]["seconds"]
+    out["mixed_one_launch_speedup_vs_streams"] = \
+        res["batch_mixed_streams"]["seconds"] / res["batch_mixed"]["seconds"]
     if "loop_fp64" in res:
         out["batch_speedup_vs_loop"] = res["loop_fp64"]["seconds"] / res["batch_fp64"]["seconds"]
     if "loop_mixed" in res:

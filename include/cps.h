@@ -197,18 +197,22 @@ int cps_solve(cps_sys sys, const double* b, double* x, double rtol, int64_t max_
  * cps_set_batch_path(ctx, CPS_BATCH_GRAPH) instead one launch per phase for
  * all systems, a per-system convergence mask, and iteration chunks replayed
  * from a CUDA graph (a system of more than 33,554,432 cells is rejected there
- * with CPS_ERR_ARG -- solve it alone).  CPS_MIXED:
- * each system's solve (whose residual replacements are decided on the host)
- * runs whole on one of up to 8 internal streams, fed by as many host threads,
- * so that the systems' launches overlap on the GPU; the call returns after
- * ordering `stream` behind all of them (it blocks the calling thread until
- * every system has finished).  The return value is the first non-OK
- * per-system status, or CPS_OK. */
+ * with CPS_ERR_ARG -- solve it alone).  CPS_MIXED: by default the same one
+ * launch, each system (or team) running the single solve's refinement with
+ * every decision on the device -- binary32 textbook CG inner iterations with
+ * FP64 inner products, an FP64 true residual after each, the best FP64
+ * iterate kept (stats.refinements = residual replacements); with
+ * CPS_BATCH_GRAPH instead each system's solve (whose residual replacements
+ * are decided on the host) runs whole on one of up to 8 internal streams,
+ * fed by as many host threads, so that the systems' launches overlap on the
+ * GPU; the call returns after ordering `stream` behind all of them (it
+ * blocks the calling thread until every system has finished).  The return
+ * value is the first non-OK per-system status, or CPS_OK. */
 int cps_solve_batch(const cps_sys* systems, int nsys, const double* const* b,
                     double* const* x, double rtol, int64_t max_iter, int precision,
                     cps_stats* stats, void* stream);
 
-/* How cps_solve_batch runs FP64 ensembles on this context (no counterpart in
+/* How cps_solve_batch runs ensembles on this context (no counterpart in
  * the paper; both are for the ensemble workload): CPS_BATCH_ONE_LAUNCH (the
  * default) or CPS_BATCH_GRAPH (see cps_solve_batch).  Errors: CPS_ERR_ARG. */
 #define CPS_BATCH_ONE_LAUNCH 0

@@ -48,6 +48,9 @@ struct BatchDesc {
     double* p;
     double* q;
     double* t;                    // one-launch solve only: w = Ahat r
+    const float* a32;             // one-launch mixed solve: binary32 matrix and S
+    const float* s32;
+    double* best;                 // one-launch mixed solve: the best FP64 iterate
     double* partials;
     CgState* st;
     int64_t n;
@@ -384,7 +387,7 @@ struct TeamSync {
     unsigned long long count;   // arrivals since the launch
     int timeout;
     int pad[13];
-    double partials[2][3][kMaxTeam];
+    double partials[2][4][kMaxTeam];
 };
 
 // Blocks [first, first + k) solve system sys as one team.
@@ -448,13 +451,13 @@ __device__ __noinline__ int team_arrive_wait(TeamCtx& tc) {
     return team_wait(tc.ts, tc.target) ? par : -1;
 }
 
-// Team-wide exact sum of v[0..NV) (NV <= 3): the block's exact total, then
+// Team-wide exact sum of v[0..NV) (NV <= 4): the block's exact total, then
 // the k members' totals aligned to their largest exponent and summed in
 // integers by warp 0 (the same set in every member: bit-identical results,
 // so all members take the same decisions).  Also a team barrier.
 template <int NV>
 __device__ __forceinline__ bool team_sum(double (&v)[NV], TeamCtx& tc) {
-    static_assert(NV >= 1 && NV <= 3, "team sum width");
+    static_assert(NV >= 1 && NV <= 4, "team sum width");
     __shared__ double s_tot[NV];
     __shared__ int s_par;
     block_sum_exact<NV, kBB>(v);
@@ -763,10 +766,300 @@ __device__ __forceinline__ void kbp_solve(const BatchDesc& d, int64_t lo, int64_
     __syncthreads();
 }
 
+// ---- Mixed precision in the one launch.  The single solve's reliable-update
+// refinement with every decision taken on the device: binary32 matrix,
+// vectors and SpMV in the inner iteration (the textbook recurrences, as in the
+// single solve: the single-reduction ones carry s = Ahat p by recurrence,
+// which drifts in binary32; FP64 inner products and scalars), an FP64 true
+// residual after every run, the best FP64 iterate kept, and the same stop,
+// divergence and restart rules.  Two passes an iteration: the direction
+// update is fused into the SpMV (q = Ahat (r + beta p_old) gathered from r
+// and the old direction at the neighbours; p double-buffered), then the
+// residual and correction update.
+constexpr double kMxDelta = 0.5;      // residual drop between replacements
+constexpr int kMxMaxUpdates = 2000;
+constexpr double kMxDiverge = 1e4;
+
+// Thread 0's refinement state of one mixed solve.
+struct MixedScalars {
+    double rho, rho_prev, alpha, beta;    // inner scalars (rho = r.r, rho_prev its last value)
+    double bnorm2, rnorm2, thresh2, outer2, rho_rep;
+    double best, prev, last;
+    long long total, it;                  // inner iterations: whole solve, this run
+    int updates, stall, restarts;
+    int first;                            // next run starts from p = 0
+    int par;                              // which buffer holds the current direction
+    int flag;                             // per phase: 0 go on, 1 stop
+    int action;                           // after a residual: 0 run, 1 end, 2 end + restore
+    int copy;                             // keep x as the best iterate
+    int status;
+};
+
+// One system by this block (tc null) or this member's rows of a team's
+// system: Jacobi PCG on the scaled matrix, binary32 inner iteration with FP64
+// residual replacement.  x receives the final (or best) FP64 iterate; the
+// result goes to the system's CgState (iter, rnorm2, bnorm2, status,
+// updates; done = 2) from the block that holds row 0.
+__device__ __forceinline__ void kbp_solve_mixed(const BatchDesc& d, int64_t lo, int64_t hi,
+                                                TeamCtx* tc, double rtol, long long max_iter) {
+    __shared__ MixedScalars sm;
+    const int64_t n = d.n;
+    const double* __restrict__ A = d.a;       // FP64 scaled matrix (residuals)
+    const int32_t* __restrict__ C = d.col;
+    const double* __restrict__ S = d.s;
+    const float* __restrict__ A32 = d.a32;
+    const float* __restrict__ S32 = d.s32;
+    double* __restrict__ x = d.x;
+    float* __restrict__ r = reinterpret_cast<float*>(d.r);
+    float* __restrict__ pb0 = reinterpret_cast<float*>(d.p);
+    float* __restrict__ pb1 = reinterpret_cast<float*>(d.t);
+    float* __restrict__ q = reinterpret_cast<float*>(d.q);
+    float* __restrict__ dy = reinterpret_cast<float*>(d.y);
+    bool ok = true;
+    auto sum1 = [&](double (&v)[1]) {
+        if (tc) ok = team_sum<1>(v, *tc) && ok;
+        else block_sum_exact<1, kBB>(v);
+    };
+    auto sum2 = [&](double (&v)[2]) {
+        if (tc) ok = team_sum<2>(v, *tc) && ok;
+        else block_sum_exact<2, kBB>(v);
+    };
+    auto sum3 = [&](double (&v)[3]) {
+        if (tc) ok = team_sum<3>(v, *tc) && ok;
+        else block_sum_exact<3, kBB>(v);
+    };
+    auto barrier = [&]() {
+        if (tc) ok = team_barrier(*tc) && ok;
+        else __syncthreads();
+    };
+    if (threadIdx.x == 0) {
+        sm.total = 0;
+        sm.it = 0;
+        sm.updates = sm.stall = sm.restarts = 0;
+        sm.first = 1;
+        sm.best = sm.prev = sm.last = INFINITY;
+        sm.bnorm2 = sm.rnorm2 = sm.thresh2 = 0.0;
+        sm.rho = sm.rho_prev = 0.0;
+        sm.par = 0;
+        sm.status = CPS_OK;
+    }
+    __syncthreads();
+    for (;;) {
+        // FP64 true residual of x: r = S^-1 b - Ahat (S x), rounded to
+        // binary32; the correction d = 0
+        {
+            double v3[3] = {0.0, 0.0, 0.0};   // r32.r32, b.b, ||S r||^2
+            for (int64_t e = lo + threadIdx.x; e < hi; e += kBB) {
+                const double se = S[e];
+                double ay = se * x[e];
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const int32_t c = C[j * n + e];
+                    ay = fma(A[j * n + e], S[c] * x[c], ay);
+                }
+                const double be = d.b[e];
+                const double re = be / se - ay;
+                const float rf = (float)re;
+                r[e] = rf;
+                dy[e] = 0.0f;
+                v3[0] = fma((double)rf, (double)rf, v3[0]);
+                v3[1] = fma(be, be, v3[1]);
+                const double t = se * re;
+                v3[2] = fma(t, t, v3[2]);
+            }
+            sum3(v3);
+            if (!ok) break;
+            if (threadIdx.x == 0) {
+                const double rr = v3[0], bb = v3[1], nn = v3[2];
+                sm.bnorm2 = bb;
+                sm.outer2 = rtol * rtol * bb;
+                sm.rnorm2 = nn;
+                sm.copy = 0;
+                int act = 0;
+                if (bb == 0.0 || nn <= sm.outer2) {
+                    act = 1;                              // converged (b = 0: x = 0 below)
+                } else {
+                    if (nn < sm.best) {
+                        sm.best = nn;
+                        sm.copy = 1;
+                    } else if (!(nn <= kMxDiverge * sm.best)) {
+                        sm.status = CPS_ERR_NOT_CONVERGED;  // refinement diverging
+                        act = 2;
+                    }
+                    if (act == 0 && (sm.total >= max_iter || sm.updates >= kMxMaxUpdates)) {
+                        sm.status = CPS_ERR_NOT_CONVERGED;
+                        act = nn > sm.best ? 2 : 1;
+                    }
+                    if (act == 0) {
+                        // a replaced residual that stops falling (no 10% gain
+                        // over 8 replacements) restarts the directions, at
+                        // most 4 times; one that rose since the last
+                        // replacement restarts them without counting
+                        if (nn < 0.81 * sm.prev) {
+                            sm.prev = nn;
+                            sm.stall = 0;
+                        } else {
+                            ++sm.stall;
+                        }
+                        const bool rose = nn > sm.last;
+                        sm.last = nn;
+                        if (sm.stall >= 8 && !sm.first) {
+                            if (++sm.restarts > 4) {
+                                sm.status = CPS_ERR_NOT_CONVERGED;
+                                act = nn > sm.best ? 2 : 1;
+                            } else {
+                                sm.first = 1;
+                                sm.stall = 0;
+                            }
+                        } else if (rose && !sm.first) {
+                            sm.first = 1;
+                        }
+                    }
+                    if (act == 0) {
+                        const double inner2 = kMxDelta * kMxDelta * nn;
+                        sm.thresh2 = inner2 > 0.25 * sm.outer2 ? inner2 : 0.25 * sm.outer2;
+                        sm.rho_rep = rr;
+                        // continue the directions: p = r_true + beta p_k with
+                        // beta = rho_true / rho_k (0 on a fresh start)
+                        sm.beta = sm.first || !(sm.rho_prev > 0.0) ? 0.0 : rr / sm.rho_prev;
+                        sm.rho = rr;
+                        sm.it = 0;
+                        ++sm.updates;
+                        if (!(rr > 0.0)) act = 1;
+                    }
+                }
+                sm.action = act;
+            }
+            __syncthreads();
+        }
+        const int act = sm.action;
+        if (act != 0) {
+            if (sm.bnorm2 == 0.0) {
+                for (int64_t e = lo + threadIdx.x; e < hi; e += kBB) x[e] = 0.0;
+                if (threadIdx.x == 0) sm.rnorm2 = 0.0;
+            } else if (act == 2) {
+                for (int64_t e = lo + threadIdx.x; e < hi; e += kBB) x[e] = d.best[e];
+                if (threadIdx.x == 0) sm.rnorm2 = sm.best;
+            }
+            break;
+        }
+        if (sm.copy)
+            for (int64_t e = lo + threadIdx.x; e < hi; e += kBB) d.best[e] = x[e];
+        if (sm.first) {       // a fresh start: clear the direction
+            float* pz = sm.par ? pb1 : pb0;
+            for (int64_t e = lo + threadIdx.x; e < hi; e += kBB) pz[e] = 0.0f;
+        }
+        if (threadIdx.x == 0) sm.flag = 0;
+        barrier();            // r and the direction final everywhere
+        if (!ok) break;
+        if (threadIdx.x == 0) sm.first = 0;
+        while (sm.flag == 0) {
+            const int par = sm.par;
+            const float* __restrict__ po = par ? pb1 : pb0;
+            float* __restrict__ pn = par ? pb0 : pb1;
+            // p = r + beta p_old; q = Ahat p (gathered); gamma = p.q
+            double g[1] = {0.0};
+            {
+                const float beta = (float)sm.beta;
+                float ro[2], pol[2], a0[2], a1[2], a2[2];
+                int32_t c0[2], c1[2], c2[2];
+                CPS_BLK_LOOP(lo, hi, 2,
+                    (pf_l1(r + f), pf_l1(po + f), pf_l1(A32 + f), pf_l1(A32 + n + f),
+                     pf_l1(A32 + 2 * n + f), pf_l1(C + f), pf_l1(C + n + f), pf_l1(C + 2 * n + f)),
+                    (ro[u] = r[e], pol[u] = po[e], a0[u] = A32[e], a1[u] = A32[n + e],
+                     a2[u] = A32[2 * n + e], c0[u] = C[e], c1[u] = C[n + e], c2[u] = C[2 * n + e]),
+                    {
+                        const float pe = fmaf(beta, pol[u], ro[u]);
+                        float v = fmaf(a0[u], fmaf(beta, po[c0[u]], r[c0[u]]), pe);
+                        v = fmaf(a1[u], fmaf(beta, po[c1[u]], r[c1[u]]), v);
+                        v = fmaf(a2[u], fmaf(beta, po[c2[u]], r[c2[u]]), v);
+                        pn[e] = pe;
+                        q[e] = v;
+                        g[0] = fma((double)pe, (double)v, g[0]);
+                    })
+            }
+            sum1(g);
+            if (!ok) break;
+            if (threadIdx.x == 0) {
+                const double gamma = g[0];
+                if (!(gamma > 0.0) || !isfinite(gamma)) {
+                    sm.status = CPS_ERR_NOT_SPD;
+                    sm.flag = 2;
+                } else {
+                    sm.alpha = sm.rho / gamma;
+                }
+                sm.par = par ^ 1;
+            }
+            __syncthreads();
+            if (sm.flag == 2) break;
+            // r -= alpha q, d += alpha p; rho' = r.r (every 8th: ||S r||^2)
+            const bool check = ((sm.it + 1) % 8) == 0;
+            double rr[2] = {0.0, 0.0};
+            {
+                const float alpha = (float)sm.alpha;
+                float qe[2], re[2], pe[2], ye[2];
+                CPS_BLK_LOOP(lo, hi, 2,
+                    (pf_l1(q + f), pf_l1(r + f), pf_l1(pn + f), pf_l1(dy + f)),
+                    (qe[u] = q[e], re[u] = r[e], pe[u] = pn[e], ye[u] = dy[e]),
+                    {
+                        const float rv = fmaf(-alpha, qe[u], re[u]);
+                        r[e] = rv;
+                        dy[e] = fmaf(alpha, pe[u], ye[u]);
+                        rr[0] = fma((double)rv, (double)rv, rr[0]);
+                        if (check) {
+                            const double tt = (double)S32[e] * (double)rv;
+                            rr[1] = fma(tt, tt, rr[1]);
+                        }
+                    })
+            }
+            sum2(rr);
+            if (!ok) break;
+            if (threadIdx.x == 0) {
+                const long long it = ++sm.it;
+                const double rho_new = rr[0];
+                // stop the run: the recursive residual fell below the
+                // replacement threshold, the budget is spent, or r.r reached
+                // the binary32 rounding floor (1e-13 of the replaced one)
+                bool halt = !(rho_new > 0.0) || sm.total + it >= max_iter ||
+                            rho_new <= 1e-13 * sm.rho_rep;
+                if (check && rr[1] <= sm.thresh2) halt = true;
+                sm.beta = rho_new / sm.rho;
+                sm.rho_prev = sm.rho;
+                sm.rho = rho_new;
+                sm.flag = halt ? 1 : 0;
+            }
+            __syncthreads();
+        }
+        if (!ok || sm.flag == 2) break;
+        // x += S^-1 d in FP64 (own rows), then every member's x is final
+        // before the next residual reads it at neighbours
+        for (int64_t e = lo + threadIdx.x; e < hi; e += kBB) x[e] += (double)dy[e] / S[e];
+        if (threadIdx.x == 0) {
+            sm.total += sm.it;
+            sm.it = 0;
+        }
+        barrier();
+        if (!ok) break;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && lo == 0) {
+        CgState* st = d.st;
+        st->iter = sm.total + sm.it;
+        st->rnorm2 = sm.rnorm2;
+        st->bnorm2 = sm.bnorm2;
+        st->thresh2 = sm.outer2;
+        st->updates = sm.updates;
+        st->status = ok ? sm.status : CPS_ERR_TIMEOUT;
+        st->done = 2;
+    }
+    __syncthreads();
+}
+
 // First the static teams: block b of team t solves its slice of system
 // teams[t].sys (rows split in multiples of 32).  Then every block takes whole
 // systems in the order `order` (largest estimated work first) from the
-// counter *next until none is left.
+// counter *next until none is left.  FP64 or mixed precision.
+template <bool MIXED>
 __global__ void __launch_bounds__(kBB, 2) kb_one_launch(const BatchDesc* __restrict__ dd,
                                                         const int* __restrict__ order, int nqueue,
                                                         int* next,
@@ -785,7 +1078,8 @@ __global__ void __launch_bounds__(kBB, 2) kb_one_launch(const BatchDesc* __restr
         const int64_t hi = min(d.n, lo + rows);
         if (threadIdx.x == 0) s_tc = TeamCtx{sync + t, 0ull, rank, tp.k, 0u};
         __syncthreads();
-        kbp_solve(d, lo, hi, &s_tc, rtol, max_iter);
+        if (MIXED) kbp_solve_mixed(d, lo, hi, &s_tc, rtol, max_iter);
+        else kbp_solve(d, lo, hi, &s_tc, rtol, max_iter);
         break;
     }
     for (;;) {
@@ -795,7 +1089,8 @@ __global__ void __launch_bounds__(kBB, 2) kb_one_launch(const BatchDesc* __restr
         const int k = s_k;
         if (k >= nqueue) return;
         const BatchDesc& d = dd[order[k]];
-        kbp_solve(d, 0, d.n, nullptr, rtol, max_iter);
+        if (MIXED) kbp_solve_mixed(d, 0, d.n, nullptr, rtol, max_iter);
+        else kbp_solve(d, 0, d.n, nullptr, rtol, max_iter);
     }
 }
 
@@ -930,13 +1225,14 @@ static void plan_teams(const std::vector<BatchDesc>& hd, int G, std::vector<Team
     }
 }
 
-// FP64 ensemble in one cooperative launch of kb_one_launch: two blocks per SM;
-// the static teams solve the largest systems while the other blocks take the
-// rest from the work queue, largest first, each to rtol, and every team's
-// blocks join the queue when their system is done.
+// The ensemble in one cooperative launch of kb_one_launch (FP64 or mixed
+// precision): two blocks per SM; the static teams solve the largest systems
+// while the other blocks take the rest from the work queue, largest first,
+// each to rtol, and every team's blocks join the queue when their system is
+// done.
 static int solve_batch_one_launch(const cps_sys* systems, int nsys, const double* const* b,
                                   double* const* x, double rtol, int64_t max_iter,
-                                  cps_stats* stats, cudaStream_t stream) {
+                                  bool mixed, cps_stats* stats, cudaStream_t stream) {
     cps_ctx ctx = systems[0]->ctx;
     std::vector<BatchDesc> hd(nsys);
     for (int i = 0; i < nsys; ++i) {
@@ -953,12 +1249,16 @@ static int solve_batch_one_launch(const cps_sys* systems, int nsys, const double
         d.p = s->wp0;
         d.q = s->wq;
         d.t = s->wp1;
+        d.a32 = s->a32;
+        d.s32 = s->s32;
+        d.best = s->wbest;
         d.partials = s->partials;
         d.st = s->st;
         d.n = s->nt;
     }
+    const void* kernel = mixed ? (const void*)kb_one_launch<true> : (const void*)kb_one_launch<false>;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_one_launch, kBB, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBB, 0) !=
             cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         cps::set_error(ctx, "solve_batch: the one-launch kernel does not fit an SM");
@@ -1001,7 +1301,7 @@ static int solve_batch_one_launch(const cps_sys* systems, int nsys, const double
         long long mi = (long long)max_iter;
         void* args[] = {(void*)&dd, (void*)&dorder, (void*)&nqueue, (void*)&dnext,
                         (void*)&dteams, (void*)&nteams, (void*)&dsync, (void*)&rtol, (void*)&mi};
-        if (cudaLaunchCooperativeKernel((const void*)kb_one_launch, dim3(grid), dim3(kBB), args,
+        if (cudaLaunchCooperativeKernel(kernel, dim3(grid), dim3(kBB), args,
                                         0, stream) != cudaSuccess)
             rc = CPS_ERR_CUDA;
     }
@@ -1025,7 +1325,7 @@ static int solve_batch_one_launch(const cps_sys* systems, int nsys, const double
                 stats[i].iters = h.iter;
                 stats[i].rel_res = rel;
                 stats[i].status = st;
-                stats[i].refinements = 1;
+                stats[i].refinements = mixed ? h.updates : 1;
                 stats[i].launches = 2;
             }
         }
@@ -1043,7 +1343,11 @@ static int solve_batch_one_launch(const cps_sys* systems, int nsys, const double
                                                 : "solve_batch: CUDA failure");
         return rc;
     }
-    if (first == CPS_ERR_NOT_CONVERGED) cps::set_error(ctx, "solve_batch: max_iter reached");
+    if (first == CPS_ERR_NOT_CONVERGED)
+        cps::set_error(ctx, mixed ? "solve_batch: a member did not reach rtol in mixed precision "
+                                    "(max_iter, or binary32 refinement stopped reducing its "
+                                    "residual: its x holds the iterate with the least residual)"
+                                  : "solve_batch: max_iter reached");
     if (first == CPS_ERR_NOT_SPD) cps::set_error(ctx, "solve_batch: p.Ap <= 0");
     if (first == CPS_ERR_TIMEOUT)
         cps::set_error(ctx, "solve_batch: a team wait ran out (blocks not co-resident?)");
@@ -1064,10 +1368,15 @@ int solve_batch_impl(const cps_sys* systems, int nsys, const double* const* b,
         cps::set_error(ctx, "solve_batch: bad argument");
         return CPS_ERR_ARG;
     }
+    if (precision != CPS_FP64 && precision != CPS_MIXED) {
+        cps::set_error(ctx, "solve_batch: bad precision");
+        return CPS_ERR_ARG;
+    }
+    if (ctx->batch_path == CPS_BATCH_ONE_LAUNCH)
+        return solve_batch_one_launch(systems, nsys, b, x, rtol, max_iter,
+                                      precision == CPS_MIXED, stats, stream);
     if (precision != CPS_FP64) return solve_batch_mixed(systems, nsys, b, x, rtol, max_iter,
                                                         precision, stats, stream);
-    if (ctx->batch_path == CPS_BATCH_ONE_LAUNCH)
-        return solve_batch_one_launch(systems, nsys, b, x, rtol, max_iter, stats, stream);
     std::vector<BatchDesc> hd(nsys);
     int64_t total_tiles = 0;
     for (int i = 0; i < nsys; ++i) {

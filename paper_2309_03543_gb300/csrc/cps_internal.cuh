@@ -39,7 +39,8 @@ struct CgState {
     int status;        // CPS_OK or an error code set on the device
     unsigned int arrive[4];   // arrival counters of the grid reductions
     double rho_rep;    // mixed precision: r.r of the last residual replacement
-    int pad[2];
+    int updates;       // mixed one-launch batch: residual replacements of the solve
+    int pad;
 };
 
 // Launch configuration of one iteration kernel: rows per thread per trip of
