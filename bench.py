@@ -771,18 +771,19 @@ def run_cp2_step(args):
     print(json.dumps(line), flush=True)
 
 
-def run_cp1_step(args):
+def cp1_summary(n: int, steps: int, warmup: int, toll: float, rtol: float) -> dict:
     """Whole CP1 steps on the channel-block workload with no-slip walls: each
     step takes a new predictor increment (seeded random-Fourier field) and
-    runs the outer iteration of App. B to --cp1-toll; the line reports steps
-    per second, outer sweeps and PCG iterations per step."""
+    runs the outer iteration of App. B to toll, in one launch (the default
+    path) and as host-driven sweeps of single solves; per path ms per step,
+    outer sweeps and PCG iterations per step."""
     import dataclasses
     import torch
     import paper_2309_03543_gb300 as cps
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     ctx = cps.Context(0)
-    p = synth.channel_block_problem(args.n, seed=0)
+    p = synth.channel_block_problem(n, seed=0)
     m = p.mesh
     nbr = side_neighbours(m.tri)
     e, j = np.nonzero(nbr < 0)
@@ -793,30 +794,48 @@ def run_cp1_step(args):
     sy = ctx.assemble(m.xy, m.tri, m.dirichlet, p.eps, p.kinv, p.field_loc, cps.KIND_CP1_Y,
                       p.nu, p.dt)
     cps.cp1_setup(sx, sy, m.xy, m.tri, p.eps, p.kinv)
-    total = args.warmup + args.cp1_step
+    total = warmup + steps
     dus = [torch.as_tensor(synth.cell_vector_field(m, 200 + t, mean=(0.01, -0.02), scale=0.05),
                            device=dev) for t in range(total)]
-    secs, outer, iters = [], [], []
-    for t in range(total):
-        dt_, (du, st) = timed(lambda: cps.cp1_step(sx, sy, dus[t], toll=args.cp1_toll,
-                                                   rtol=args.rtol, check=False), stream)
-        if t >= args.warmup:
-            secs.append(dt_)
-            outer.append(st["outer"])
-            iters.append(st["solve_iters"])
-    t_step = sum(secs) / len(secs)
+    out = {"workload": f"channel-block-aniso lattice n={n}, no-slip walls", "cells": nt,
+           "toll": toll, "rtol": rtol, "steps": steps,
+           "du_breve": "random-Fourier field + mean, seed 200+t"}
+    for name, path in (("one_launch", cps.CP1_ONE_LAUNCH), ("host_sweeps", cps.CP1_HOST)):
+        cps.set_cp1_path(sx, path)
+        secs, outer, iters, status = [], [], [], []
+        for t in range(total):
+            dt_, (du, st) = timed(lambda: cps.cp1_step(sx, sy, dus[t], toll=toll, rtol=rtol,
+                                                       check=False), stream)
+            if t >= warmup:
+                secs.append(dt_)
+                outer.append(st["outer"])
+                iters.append(st["solve_iters"])
+                status.append(st["status"])
+        t_step = sum(secs) / len(secs)
+        out[name] = {"ms_per_step": 1e3 * t_step, "outer_sweeps": outer, "solve_iters": iters,
+                     "status": status,
+                     "us_per_solve_iter": 1e6 * sum(secs) / max(sum(iters), 1)}
+    out["one_launch_speedup"] = (out["host_sweeps"]["ms_per_step"]
+                                 / out["one_launch"]["ms_per_step"])
     sx.free()
     sy.free()
+    ctx.close()
+    return out
+
+
+def run_cp1_step(args):
+    """--cp1-step K: the CP1 step as its own line (steps per second of the
+    default one-launch path; the host-driven sweeps beside it)."""
+    r = cp1_summary(args.n, args.cp1_step, args.warmup, args.cp1_toll, args.rtol)
+    t_step = r["one_launch"]["ms_per_step"] / 1e3
     line = {"metric": "CP1 steps per second (x and y solves coupled through Mbar_12, outer "
                       "iteration of App. B)",
             "value": 1.0 / t_step, "unit": "steps/s", "higher_is_better": True,
             "ms_per_step": 1e3 * t_step, "steps": args.cp1_step, "warmup": args.warmup,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"channel-block-aniso lattice n={args.n}, no-slip walls",
-                       "cells": nt, "toll": args.cp1_toll, "rtol": args.rtol,
-                       "du_breve": "random-Fourier field + mean, seed 200+t"},
-            "outer_sweeps": outer, "solve_iters": iters,
-            "us_per_solve_iter": 1e6 * sum(secs) / max(sum(iters), 1)}
+            "config": {k: r[k] for k in ("workload", "cells", "toll", "rtol", "du_breve")},
+            "paths": {k: r[k] for k in ("one_launch", "host_sweeps")},
+            "one_launch_speedup": r["one_launch_speedup"]}
     print(json.dumps(line), flush=True)
 
 
@@ -1165,12 +1184,14 @@ def main():
     }
     # the other workloads, compactly (each in its own context, after the
     # headline measurement): config 0 latency, config 3 ensemble (batched
-    # FP64 and mixed against a loop of FP64 single solves), config 4 chain
+    # FP64 and mixed against a loop of FP64 single solves), config 4 chain,
+    # and the CP1 step on the headline lattice (one launch and host sweeps)
     if rank == 0 and world == 1 and not args.no_extras:
         extras = (("n64_latency", lambda: latency_summary(64, args.rtol)),
                   ("batch", lambda: batch_summary(256, args.rtol, 1, loops=True,
                                                   mixed_loop=False)),
-                  ("chain", lambda: chain_summary(512, 50, 1e-8)))
+                  ("chain", lambda: chain_summary(512, 50, 1e-8)),
+                  ("cp1_step", lambda: cp1_summary(args.n, 3, 2, 1e-4, args.rtol)))
         for key, fn in extras:
             t0 = time.perf_counter()
             try:

@@ -309,12 +309,27 @@ int cps_cp1_setup(cps_sys sys_x, cps_sys sys_y, const double* xy, const int32_t*
  * (Eq. cs1_sys2, Eq. CS1_sys_coeff with the sign of Eq. CS1_2).  Sweep 0 drops
  * the coupling; each later sweep solves both components with the other's
  * previous iterate, warm-started, until min(err_x, err_y) <= toll, err_k =
- * ||du_k^{i+1} - du_k^i||_2 / ||du_k^i||_2.  Needs cps_cp1_setup.  Errors: as
- * cps_solve; CPS_ERR_NOT_CONVERGED also when max_outer sweeps end above toll
- * (du holds the last iterate). */
+ * ||du_k^{i+1} - du_k^i||_2 / ||du_k^i||_2.  Needs cps_cp1_setup.  When both
+ * systems use the Jacobi preconditioner the whole outer iteration runs by
+ * default in one cooperative launch: each sweep's right-hand sides, both
+ * solves (the single-reduction Jacobi CG of cps_solve_batch, FP64 or mixed,
+ * by all the launch's blocks), the change test and the stop decision on the
+ * device, the statistics read once at the end; otherwise (or after
+ * cps_set_cp1_path(sys_x, CPS_CP1_HOST)) each solve is a cps_solve and the
+ * change sums are read back after every sweep.  Errors: as cps_solve
+ * (CPS_ERR_TIMEOUT: a device-side wait of the one launch ran out);
+ * CPS_ERR_NOT_CONVERGED also when max_outer sweeps end above toll (du holds
+ * the last iterate). */
 int cps_cp1_step(cps_sys sys_x, cps_sys sys_y, const double* du_breve, double* du, double toll,
                  int64_t max_outer, double rtol, int64_t max_iter, int precision,
                  cps_cp1_stats* stats, void* stream);
+
+/* How cps_cp1_step runs on the pair prepared on sys_x (no counterpart in the
+ * paper): CPS_CP1_ONE_LAUNCH (the default; Jacobi systems) or CPS_CP1_HOST
+ * (see cps_cp1_step).  Errors: CPS_ERR_ARG (bad path, or no cps_cp1_setup). */
+#define CPS_CP1_ONE_LAUNCH 0
+#define CPS_CP1_HOST 1
+int cps_set_cp1_path(cps_sys sys_x, int path);
 
 /* Device durations in milliseconds (host ms[3]) of the last cps_cp2_step's
  * three step kernels -- mean flux, tangential flux, update -- from CUDA events

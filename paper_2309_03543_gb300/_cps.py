@@ -33,6 +33,7 @@ PATH_CLUSTER_1RED = 6
 PATH_STREAM_1RED, PATH_STREAM_1RED_L2 = 7, 8
 PATH_PERSISTENT_1RED, PATH_PERSISTENT_1RED_L2 = 9, 10
 BATCH_ONE_LAUNCH, BATCH_GRAPH = 0, 1
+CP1_ONE_LAUNCH, CP1_HOST = 0, 1
 
 ERROR_NAMES = {
     ERR_ARG: "CPS_ERR_ARG", ERR_NONMANIFOLD: "CPS_ERR_NONMANIFOLD",
@@ -86,6 +87,7 @@ SIGNATURES = {
     "cps_get_gear_shape": (_I, [_P, _P, _P, _P]),
     "cps_set_solver_path": (_I, [_P, _I]),
     "cps_set_batch_path": (_I, [_P, _I]),
+    "cps_set_cp1_path": (_I, [_P, _I]),
     "cps_set_kernel_shapes": (_I, [_P, _I, _P, _P, _P]),
     "cps_test_inject": (_I, [_P, _I]),
     "cps_solve_ell_noalloc": (_I, [_I64, _P, _P, _P, _P, _P, _D, _I64, ctypes.POINTER(Stats),

@@ -301,6 +301,13 @@ def cp1_setup(sys_x: System, sys_y: System, xy, tri, eps, kinv):
     sys_x.ctx.check(rc, "cps_cp1_setup")
 
 
+def set_cp1_path(sys_x: System, path: int):
+    """CP1_ONE_LAUNCH (default: the whole outer iteration in one launch for
+    Jacobi systems) or CP1_HOST (a cps_solve per solve, the change sums read
+    back per sweep), for the pair prepared on sys_x."""
+    sys_x.ctx.check(sys_x.ctx.lib.cps_set_cp1_path(sys_x.handle, path), "cps_set_cp1_path")
+
+
 def cp1_step(sys_x: System, sys_y: System, du_breve, du=None, toll: float = 1e-4,
              max_outer: int = 1000, rtol: float = 1e-10, max_iter: int = 1_000_000,
              precision: int = _cps.FP64, check: bool = True):

@@ -192,6 +192,13 @@ int cps_cp1_step(cps_sys sys_x, cps_sys sys_y, const double* du_breve, double* d
                               precision, stats, as_stream(stream));
 }
 
+int cps_set_cp1_path(cps_sys sys_x, int path) {
+    if (!sys_x || !sys_x->cp1 || (path != CPS_CP1_ONE_LAUNCH && path != CPS_CP1_HOST))
+        return CPS_ERR_ARG;
+    sys_x->cp1->path = path;
+    return CPS_OK;
+}
+
 int cps_cp2_kernel_times(cps_sys sys, float* ms) {
     if (!sys) return CPS_ERR_ARG;
     return cps::cp2_kernel_times(sys, ms);

@@ -11,12 +11,18 @@
 // component takes the other's previous iterate, until
 // min(err_x, err_y) <= toll with err_k = ||du_k^{i+1} - du_k^i|| / ||du_k^i||.
 //
-// The solves are the library's PCG on the two assembled systems; around them
-// three small kernels: -nu L du_breve (once), the coupled right-hand sides with
-// a copy of the iterate (per sweep), and the four sums of the change test
-// (per sweep, deterministic block sums).
+// By default the whole outer iteration runs in one cooperative launch
+// (k_cp1_step) after -nu L du_breve: per sweep the right-hand sides, the x and
+// the y solve (Jacobi PCG, FP64 or mixed, by the whole grid as one team of
+// blocks, block_solve.cuh), the change test as an exact team sum, and the
+// stop decision, all on the device; the host reads the statistics once.  The
+// host-driven loop (the library's PCG per solve, with the change sums read
+// back after every sweep) serves systems with another preconditioner and can
+// be chosen with cps_set_cp1_path.
+#include "block_solve.cuh"
 #include "cps_internal.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <string>
 
@@ -143,6 +149,137 @@ k_cp1_change_total(const double* __restrict__ partials, int nblocks, double* __r
         for (int k = 0; k < 4; ++k) out[k] = v[k];
 }
 
+// ---- The one-launch step.  Statistics written by block 0, thread 0.
+struct Cp1DevStats {
+    long long outer;
+    long long solve_iters;
+    double err;
+    double rel_res_max;
+    int worst;          // first CPS_ERR_NOT_CONVERGED of a solve, else CPS_OK
+    int fatal;          // a solve status other than OK / NOT_CONVERGED
+    int settled;
+    int pad;
+};
+
+// Layout of Cp1Data::dev: the team state, its partials, the two system
+// descriptors and the statistics.
+constexpr size_t kCp1SyncOff = 0;
+constexpr size_t kCp1PartOff = 256;
+constexpr size_t kCp1DescOff = kCp1PartOff + 8 * sizeof(double) * kMaxTeam;
+constexpr size_t kCp1StatOff = kCp1DescOff + (2 * sizeof(BatchDesc) + 255) / 256 * 256;
+constexpr size_t kCp1DevBytes = kCp1StatOff + 256;
+static_assert(sizeof(TeamSync) <= 256 && sizeof(Cp1DevStats) <= 256, "one-launch CP1 layout");
+
+struct Cp1DevArgs {
+    const double* lap;       // [2][nt] -nu L du_breve
+    const double* m12;       // [nt] Mbar_12 A_e
+    double* du;              // [2][nt]
+    double* prev;            // [2][nt]
+    double* rhs;             // [2][nt]
+    const BatchDesc* sys;    // [2]: the x and y systems (b = rhs_k, x = du_k)
+    TeamSync* ts;            // the grid as one team
+    Cp1DevStats* out;
+    double toll, rtol;
+    long long max_outer, max_iter;
+    int64_t nt;
+};
+
+template <bool MIXED>
+__global__ void __launch_bounds__(kBB, 2) k_cp1_step(Cp1DevArgs P) {
+    __shared__ TeamCtx s_tc;
+    __shared__ int s_stop;
+    const int G = gridDim.x;
+    const int64_t nt = P.nt;
+    const int64_t rows = ((nt + G - 1) / G + 31) / 32 * 32;
+    const int64_t lo = min(nt, (int64_t)blockIdx.x * rows);
+    const int64_t hi = min(nt, lo + rows);
+    if (threadIdx.x == 0) {
+        s_tc = TeamCtx{P.ts, 0ull, (int)blockIdx.x, G, 0u};
+        if (blockIdx.x == 0) *P.out = Cp1DevStats{0, 0, INFINITY, 0.0, CPS_OK, CPS_OK, 0, 0};
+    }
+    __syncthreads();
+    const double* __restrict__ lap = P.lap;
+    const double* __restrict__ m12 = P.m12;
+    double* __restrict__ du = P.du;
+    double* __restrict__ prev = P.prev;
+    double* __restrict__ rhs = P.rhs;
+    bool ok = true;
+    for (long long sweep = 0;; ++sweep) {
+        // right-hand sides (sweep 0 without the coupling) and prev = du
+        const bool coupled = sweep > 0;
+        for (int64_t e = lo + threadIdx.x; e < hi; e += kBB) {
+            const double ux = du[e], uy = du[nt + e];
+            const double c = coupled ? m12[e] : 0.0;
+            rhs[e] = lap[e] - c * uy;
+            rhs[nt + e] = lap[nt + e] - c * ux;
+            prev[e] = ux;
+            prev[nt + e] = uy;
+        }
+        ok = team_barrier(s_tc) && ok;
+        if (!ok) break;
+        // the two solves, each by the whole grid, warm-started from du
+        for (int k = 0; k < 2 && ok; ++k)
+            ok = (MIXED ? kbp_solve_mixed(P.sys[k], lo, hi, &s_tc, P.rtol, P.max_iter)
+                        : kbp_solve(P.sys[k], lo, hi, &s_tc, P.rtol, P.max_iter)) && ok;
+        if (!ok) break;
+        // every block: the change sums of its rows (du final everywhere after
+        // the team sum that ends each solve), one exact team sum; the solves'
+        // states, written by block 0 before that sum, are final after it
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        if (coupled) {
+            for (int64_t e = lo + threadIdx.x; e < hi; e += kBB) {
+                const double px = prev[e], py = prev[nt + e];
+                const double dx = du[e] - px, dy = du[nt + e] - py;
+                v[0] = fma(dx, dx, v[0]);
+                v[1] = fma(px, px, v[1]);
+                v[2] = fma(dy, dy, v[2]);
+                v[3] = fma(py, py, v[3]);
+            }
+        }
+        ok = team_sum<4>(v, s_tc) && ok;
+        if (!ok) break;
+        if (threadIdx.x == 0) {
+            // the same decision in every block (the same totals and states)
+            int worst = CPS_OK, fatal = CPS_OK;
+            long long iters = 0;
+            double relmax = 0.0;
+            for (int k = 0; k < 2; ++k) {
+                const CgState* st = P.sys[k].st;
+                const double b2 = __ldcg(&st->bnorm2), r2 = __ldcg(&st->rnorm2);
+                const double rel = b2 > 0.0 ? sqrt(r2 / b2) : 0.0;
+                int sk = __ldcg(&st->status);
+                if (sk == CPS_OK && b2 > 0.0 && !(rel <= P.rtol)) sk = CPS_ERR_NOT_CONVERGED;
+                if (sk == CPS_ERR_NOT_CONVERGED && worst == CPS_OK) worst = sk;
+                if (sk != CPS_OK && sk != CPS_ERR_NOT_CONVERGED && fatal == CPS_OK) fatal = sk;
+                iters += __ldcg(&st->iter);
+                relmax = fmax(relmax, rel);
+            }
+            auto rel_change = [](double d2, double p2) {
+                return d2 == 0.0 ? 0.0 : (p2 > 0.0 ? sqrt(d2) / sqrt(p2) : INFINITY);
+            };
+            const double err = coupled ? fmin(rel_change(v[0], v[1]), rel_change(v[2], v[3]))
+                                       : INFINITY;
+            const bool settled = coupled ? err <= P.toll : P.max_outer == 0;
+            s_stop = (fatal != CPS_OK || settled || sweep >= P.max_outer) ? 1 : 0;
+            if (blockIdx.x == 0) {
+                Cp1DevStats* o = P.out;
+                o->solve_iters += iters;
+                o->rel_res_max = fmax(o->rel_res_max, relmax);
+                if (o->worst == CPS_OK) o->worst = worst;
+                o->fatal = fatal;
+                if (coupled) {
+                    o->outer = sweep;
+                    o->err = err;
+                }
+                o->settled = settled ? 1 : 0;
+            }
+        }
+        __syncthreads();
+        if (s_stop) break;
+    }
+    if (!ok && blockIdx.x == 0 && threadIdx.x == 0) P.out->fatal = CPS_ERR_TIMEOUT;
+}
+
 int fail(cps_sys s, int code, const std::string& msg) {
     set_error(s->ctx, msg);
     return code;
@@ -158,6 +295,8 @@ double rel_change(double d2, double p2) {
 void free_cp1(cps_sys s) {
     if (!s || !s->cp1) return;
     if (s->cp1->buf) cudaFree(s->cp1->buf);
+    if (s->cp1->dev) cudaFree(s->cp1->dev);
+    if (s->cp1->hstats) cudaFreeHost(s->cp1->hstats);
     delete s->cp1;
     s->cp1 = nullptr;
 }
@@ -181,6 +320,14 @@ int cp1_setup_impl(cps_sys sx, cps_sys sy, const double* xy, const int32_t* tri,
     if (ce != cudaSuccess) {
         delete c;
         return fail(sx, CPS_ERR_NOMEM, std::string("cp1_setup: cudaMalloc: ") + cudaGetErrorString(ce));
+    }
+    ce = cudaMalloc(&c->dev, kCp1DevBytes);
+    if (ce == cudaSuccess) ce = cudaMallocHost(&c->hstats, sizeof(Cp1DevStats));
+    if (ce != cudaSuccess) {
+        cudaFree(c->buf);
+        if (c->dev) cudaFree(c->dev);
+        delete c;
+        return fail(sx, CPS_ERR_NOMEM, std::string("cp1_setup: ") + cudaGetErrorString(ce));
     }
     double* d = static_cast<double*>(c->buf);
     c->T = d;
@@ -228,6 +375,86 @@ int cp1_setup_impl(cps_sys sx, cps_sys sy, const double* xy, const int32_t* tri,
     return CPS_OK;
 }
 
+// The step in one cooperative launch of k_cp1_step (both systems Jacobi).
+static int cp1_step_one_launch(cps_sys sx, cps_sys sy, double* du, double toll,
+                               int64_t max_outer, double rtol, int64_t max_iter, bool mixed,
+                               cps_cp1_stats* stats, cudaStream_t stream) {
+    Cp1Data* c = sx->cp1;
+    const int64_t nt = sx->nt;
+    const void* kernel = mixed ? (const void*)k_cp1_step<true> : (const void*)k_cp1_step<false>;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBB, 0) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        return fail(sx, CPS_ERR_CUDA, "cp1_step: the one-launch kernel does not fit an SM");
+    }
+    const int grid = std::min(sx->ctx->num_sms * per_sm, kMaxTeam);
+    char* dev = static_cast<char*>(c->dev);
+    TeamSync hs{};
+    hs.partials = reinterpret_cast<double*>(dev + kCp1PartOff);
+    BatchDesc hd[2];
+    cps_sys sys[2] = {sx, sy};
+    for (int k = 0; k < 2; ++k) {
+        cps_sys s = sys[k];
+        BatchDesc& d = hd[k];
+        d = BatchDesc{};
+        d.a = s->a;
+        d.col = s->col;
+        d.s = s->s;
+        d.b = c->rhs + k * nt;
+        d.x = du + k * nt;
+        d.y = s->wy;
+        d.r = s->wr;
+        d.p = s->wp0;
+        d.q = s->wq;
+        d.t = s->wp1;
+        d.a32 = s->a32;
+        d.s32 = s->s32;
+        d.best = s->wbest;
+        d.partials = s->partials;
+        d.st = s->st;
+        d.n = nt;
+    }
+    Cp1DevArgs a{};
+    a.lap = c->lap;
+    a.m12 = c->mass + nt;
+    a.du = du;
+    a.prev = c->prev;
+    a.rhs = c->rhs;
+    a.sys = reinterpret_cast<const BatchDesc*>(dev + kCp1DescOff);
+    a.ts = reinterpret_cast<TeamSync*>(dev + kCp1SyncOff);
+    a.out = reinterpret_cast<Cp1DevStats*>(dev + kCp1StatOff);
+    a.toll = toll;
+    a.rtol = rtol;
+    a.max_outer = (long long)max_outer;
+    a.max_iter = (long long)max_iter;
+    a.nt = nt;
+    Cp1DevStats* h = static_cast<Cp1DevStats*>(c->hstats);
+    cudaError_t ce = cudaMemcpyAsync(dev + kCp1SyncOff, &hs, sizeof(hs), cudaMemcpyHostToDevice,
+                                     stream);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(dev + kCp1DescOff, hd, sizeof(hd), cudaMemcpyHostToDevice, stream);
+    if (ce == cudaSuccess) {
+        void* args[] = {(void*)&a};
+        ce = cudaLaunchCooperativeKernel(kernel, dim3(grid), dim3(kBB), args, 0, stream);
+    }
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(h, a.out, sizeof(Cp1DevStats), cudaMemcpyDeviceToHost, stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return fail(sx, CPS_ERR_CUDA, std::string("cp1_step: ") + cudaGetErrorString(ce));
+    }
+    if (stats) *stats = cps_cp1_stats{h->outer, h->solve_iters, h->err, h->rel_res_max};
+    if (h->fatal == CPS_ERR_TIMEOUT)
+        return fail(sx, CPS_ERR_TIMEOUT, "cp1_step: a device-side wait ran out");
+    if (h->fatal == CPS_ERR_NOT_SPD) return fail(sx, CPS_ERR_NOT_SPD, "cp1_step: p.Ap <= 0");
+    if (h->fatal != CPS_OK) return fail(sx, h->fatal, "cp1_step: a solve failed");
+    if (h->worst != CPS_OK) return fail(sx, h->worst, "cp1_step: a solve did not reach rtol");
+    if (!h->settled) return fail(sx, CPS_ERR_NOT_CONVERGED, "cp1_step: outer iteration above toll");
+    return CPS_OK;
+}
+
 int cp1_step_impl(cps_sys sx, cps_sys sy, const double* du_breve, double* du, double toll,
                   int64_t max_outer, double rtol, int64_t max_iter, int precision,
                   cps_cp1_stats* stats, cudaStream_t stream) {
@@ -237,8 +464,18 @@ int cp1_step_impl(cps_sys sx, cps_sys sy, const double* du_breve, double* du, do
         return fail(sx, CPS_ERR_ARG, "cp1_step: sys_y is not the CP1_Y partner");
     if (!du_breve || !du || !(toll >= 0.0) || max_outer < 0)
         return fail(sx, CPS_ERR_ARG, "cp1_step: bad argument");
+    if (precision != CPS_FP64 && precision != CPS_MIXED)
+        return fail(sx, CPS_ERR_ARG, "cp1_step: bad precision");
     const int64_t nt = sx->nt;
     const int g1 = (int)((nt + kBlock - 1) / kBlock);
+    const bool jacobi = sx->precond == CPS_PC_JACOBI && sy->precond == CPS_PC_JACOBI;
+    if (c->path == 0 && jacobi && nt > 0) {
+        k_cp1_laplacian<<<g1, kBlock, 0, stream>>>(du_breve, sx->col, c->T, nt, c->lap);
+        const cudaError_t le = cudaGetLastError();
+        if (le != cudaSuccess) return fail(sx, CPS_ERR_CUDA, std::string("cp1_step: ") + cudaGetErrorString(le));
+        return cp1_step_one_launch(sx, sy, du, toll, max_outer, rtol, max_iter,
+                                   precision == CPS_MIXED, stats, stream);
+    }
     const int gr = sx->grid;   // <= kMaxGrid blocks for the change sums
     cps_cp1_stats st{0, 0, INFINITY, 0.0};
     int worst = CPS_OK;

@@ -148,6 +148,9 @@ struct Cp1Data {
     double* rhs = nullptr;    // [2][nt]
     double* prev = nullptr;   // [2][nt] previous iterate
     double* partials = nullptr;  // [kMaxGrid][4] + [4] error sums
+    void* dev = nullptr;         // one-launch step: team state, system descriptors, statistics
+    void* hstats = nullptr;      // pinned copy of the one-launch statistics
+    int path = 0;                // 0 one launch (Jacobi systems), 1 host-driven sweeps
     int64_t nt = 0;
 };
 

@@ -81,12 +81,16 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
+@pytest.mark.parametrize("path", ["one_launch", "host"])
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_cp1_step_matches_oracle_fp64(ctx, name):
+def test_cp1_step_matches_oracle_fp64(ctx, name, path):
+    """Both ways of running the step: the whole outer iteration in one launch
+    (the default) and the host-driven sweeps of single solves."""
     p, theta = CASES[name]
     du_b = synth.cell_vector_field(p.mesh, 9, mean=(0.01, -0.02), scale=0.05)
     o = oracle.cp1_step(p, du_b, toll=1e-4, rtol=1e-13)
     sx, sy = _systems(ctx, p, theta)
+    cps.set_cp1_path(sx, cps.CP1_ONE_LAUNCH if path == "one_launch" else cps.CP1_HOST)
     du, st = cps.cp1_step(sx, sy, du_b, toll=1e-4, rtol=1e-12)
     assert st["outer"] == o.outer
     assert st["err"] <= 1e-4
@@ -112,12 +116,14 @@ def test_cp1_weak_anisotropy_takes_the_papers_sweep_count(ctx, beta):
     sy.free()
 
 
+@pytest.mark.parametrize("path", ["one_launch", "host"])
 @pytest.mark.parametrize("name", ["vertex_aniso_n20", "defect_n12", "two_cells"])
-def test_cp1_step_matches_oracle_mixed(ctx, name):
+def test_cp1_step_matches_oracle_mixed(ctx, name, path):
     p, theta = CASES[name]
     du_b = synth.cell_vector_field(p.mesh, 19, scale=0.05)
     o = oracle.cp1_step(p, du_b, toll=1e-4, rtol=1e-13)
     sx, sy = _systems(ctx, p, theta)
+    cps.set_cp1_path(sx, cps.CP1_ONE_LAUNCH if path == "one_launch" else cps.CP1_HOST)
     du, st = cps.cp1_step(sx, sy, du_b, toll=1e-4, rtol=1e-12, precision=cps.MIXED)
     assert st["outer"] == o.outer
     assert _rel(du.cpu().numpy(), o.du) <= 1e-8
@@ -134,6 +140,8 @@ def test_cp1_entry_points_reject_bad_use(ctx):
                       p.nu, p.dt)
     with pytest.raises(cps.CpsError):
         cps.cp1_setup(sx, s2, m.xy, m.tri, p.eps, p.kinv)        # partner is not CP1_Y
+    with pytest.raises(cps.CpsError):
+        cps.set_cp1_path(sx, cps.CP1_HOST)                        # no set-up
     _, st = cps.cp1_step(sx, s2, np.zeros((2, m.nt)), check=False)  # no set-up
     assert st["status"] == cps._cps.ERR_ARG
     sx.free()
