@@ -403,9 +403,12 @@ int cps_set_kernel_shapes(cps_sys sys, int precision, const int32_t* unroll, con
  * CPS_TEST_STALL_BARRIER, the next persistent launch on this system (see
  * CPS_PATH_PERSISTENT) waits at its first grid barrier for one arrival that
  * never comes: every block's bounded wait runs out after about a second, the
- * kernel ends, and the solve returns CPS_ERR_TIMEOUT.  The context stays
- * usable.  One-shot; 0 clears a pending fault.  CPS_ERR_ARG for an unknown
- * fault. */
+ * kernel ends, and the solve returns CPS_ERR_TIMEOUT.  The same holds for the
+ * team waits of the next one-launch cps_solve_batch whose first system this
+ * is (every team of blocks stalls; systems solved by single blocks finish),
+ * and of the next one-launch cps_cp1_step whose sys_x this is.  The context
+ * stays usable.  One-shot; 0 clears a pending fault.  CPS_ERR_ARG for an
+ * unknown fault. */
 #define CPS_TEST_STALL_BARRIER 1
 int cps_test_inject(cps_sys sys, int fault);
 

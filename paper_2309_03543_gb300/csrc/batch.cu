@@ -374,7 +374,8 @@ __global__ void __launch_bounds__(kBB, 2) kb_one_launch(const BatchDesc* __restr
         const int64_t rows = ((d.n + tp.k - 1) / tp.k + 31) / 32 * 32;
         const int64_t lo = min(d.n, (int64_t)rank * rows);
         const int64_t hi = min(d.n, lo + rows);
-        if (threadIdx.x == 0) s_tc = TeamCtx{sync + t, 0ull, rank, tp.k, 0u};
+        if (threadIdx.x == 0)
+            s_tc = TeamCtx{sync + t, (unsigned long long)sync[t].stall, rank, tp.k, 0u};
         __syncthreads();
         if (MIXED) kbp_solve_mixed(d, lo, hi, &s_tc, rtol, max_iter);
         else kbp_solve(d, lo, hi, &s_tc, rtol, max_iter);
@@ -596,10 +597,15 @@ static int solve_batch_one_launch(const cps_sys* systems, int nsys, const double
          cudaMemsetAsync(dorder + nqueue, 0, sizeof(int), stream) != cudaSuccess))
         rc = CPS_ERR_CUDA;
     if (rc == CPS_OK) {
+        // test hook (cps_test_inject on the first system): every team's waits
+        // expect one arrival that never comes
+        const int stall = systems[0]->inject == CPS_TEST_STALL_BARRIER ? 1 : 0;
+        systems[0]->inject = 0;
         std::vector<TeamSync> hs(nt_alloc);
         double* part = reinterpret_cast<double*>(dsync + nt_alloc);
         for (int t = 0; t < nteams; ++t) {
             hs[t] = TeamSync{};
+            hs[t].stall = stall;
             hs[t].partials = part;
             part += 8 * (size_t)teams[t].k;
         }

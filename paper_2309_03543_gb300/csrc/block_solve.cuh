@@ -61,7 +61,7 @@ constexpr unsigned long long kTeamWaitNs = 1000000000ull;
 struct TeamSync {
     unsigned long long count;   // arrivals since the launch
     int timeout;
-    int pad0;
+    int stall;                  // test hook: every wait expects one more arrival
     double* partials;           // [2][4][k]: per sync parity, quantity, member
     int pad[10];
 };

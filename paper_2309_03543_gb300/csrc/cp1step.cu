@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kBB, 2) k_cp1_step(Cp1DevArgs P) {
     const int64_t lo = min(nt, (int64_t)blockIdx.x * rows);
     const int64_t hi = min(nt, lo + rows);
     if (threadIdx.x == 0) {
-        s_tc = TeamCtx{P.ts, 0ull, (int)blockIdx.x, G, 0u};
+        s_tc = TeamCtx{P.ts, (unsigned long long)P.ts->stall, (int)blockIdx.x, G, 0u};
         if (blockIdx.x == 0) *P.out = Cp1DevStats{0, 0, INFINITY, 0.0, CPS_OK, CPS_OK, 0, 0};
     }
     __syncthreads();
@@ -392,6 +392,8 @@ static int cp1_step_one_launch(cps_sys sx, cps_sys sy, double* du, double toll,
     char* dev = static_cast<char*>(c->dev);
     TeamSync hs{};
     hs.partials = reinterpret_cast<double*>(dev + kCp1PartOff);
+    hs.stall = sx->inject == CPS_TEST_STALL_BARRIER ? 1 : 0;   // test hook, one-shot
+    sx->inject = 0;
     BatchDesc hd[2];
     cps_sys sys[2] = {sx, sy};
     for (int k = 0; k < 2; ++k) {
