@@ -182,6 +182,13 @@ def parse():
     ap.add_argument("--batch", type=int, default=0,
                     help="ensemble mode: this many systems of log-uniform 2k-500k cells, "
                          "batched solve vs a loop of single solves (prints its own line)")
+    ap.add_argument("--batch-max-cells", type=int, default=500000,
+                    help="ensemble mode: largest member (log-uniform from 2k cells)")
+    ap.add_argument("--batch-no-loops", action="store_true",
+                    help="ensemble mode: batched designs only, no loop of single solves")
+    ap.add_argument("--batch-one-launch-only", action="store_true",
+                    help="ensemble mode: the one-launch batch (FP64 and mixed) only, for "
+                         "profiling (no graph chunks, streams or loops)")
     ap.add_argument("--chain", type=int, default=0,
                     help="adjoint mode: this many chained log-permeability solves on the "
                          "--n lattice with checkpointed adjoint backward (own line)")
@@ -405,9 +412,10 @@ def timed(fn, stream):
 
 
 def batch_summary(n_systems: int, rtol: float, reps: int, loops: bool = True,
-                  mixed_loop: bool = True) -> dict:
+                  mixed_loop: bool = True, max_cells: int = 500000,
+                  one_launch_only: bool = False) -> dict:
     """Uneven ensemble (config 3): n_systems systems with sizes log-uniform in
-    [2k, 500k] cells, random-Fourier porosity in [0.3, 1], isotropic
+    [2k, max_cells] cells, random-Fourier porosity in [0.3, 1], isotropic
     Kozeny-Carman K; FP64 and mixed Jacobi-PCG to rtol, batched (cps_solve_batch)
     against a loop of single solves (best of `reps`)."""
     import torch
@@ -415,7 +423,7 @@ def batch_summary(n_systems: int, rtol: float, reps: int, loops: bool = True,
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     ctx = cps.Context(0)
-    sizes = synth.ensemble_sizes(n_systems, 2000, 500000, seed=2024)
+    sizes = synth.ensemble_sizes(n_systems, 2000, max_cells, seed=2024)
     systems, bs = [], []
     t0 = time.perf_counter()
     for i, nt in enumerate(sizes):
@@ -458,15 +466,22 @@ def batch_summary(n_systems: int, rtol: float, reps: int, loops: bool = True,
         finally:
             ctx.set_batch_path(cps.BATCH_ONE_LAUNCH)
 
-    loop(cps.FP64)
-    batch(cps.FP64)   # warm-up (autotuning, graph capture)
-    batch_graph(cps.FP64)
-    batch(cps.MIXED)
-    batch_graph(cps.MIXED)
-    runs = [("batch_fp64", lambda: batch(cps.FP64)),
-            ("batch_fp64_graph", lambda: batch_graph(cps.FP64)),
-            ("batch_mixed", lambda: batch(cps.MIXED)),
-            ("batch_mixed_streams", lambda: batch_graph(cps.MIXED))]
+    if one_launch_only:
+        loops = False
+        batch(cps.FP64)   # warm-up
+        batch(cps.MIXED)
+        runs = [("batch_fp64", lambda: batch(cps.FP64)), ("batch_mixed", lambda: batch(cps.MIXED))]
+    else:
+        if loops:
+            loop(cps.FP64)
+        batch(cps.FP64)   # warm-up (autotuning, graph capture)
+        batch_graph(cps.FP64)
+        batch(cps.MIXED)
+        batch_graph(cps.MIXED)
+        runs = [("batch_fp64", lambda: batch(cps.FP64)),
+                ("batch_fp64_graph", lambda: batch_graph(cps.FP64)),
+                ("batch_mixed", lambda: batch(cps.MIXED)),
+                ("batch_mixed_streams", lambda: batch_graph(cps.MIXED))]
     if loops:
         runs.append(("loop_fp64", lambda: loop(cps.FP64)))
         if mixed_loop:
@@ -488,10 +503,11 @@ def batch_summary(n_systems: int, rtol: float, reps: int, loops: bool = True,
            "mixed_status": status.get(cps.MIXED),
            "batch_mixed_vs_batch_fp64_seconds":
                res["batch_mixed"]["seconds"] / res["batch_fp64"]["seconds"]}
-    out["one_launch_speedup_vs_graph_chunks"] = \
-        res["batch_fp64_graph"]["seconds"] / res["batch_fp64"]["seconds"]
-    out["mixed_one_launch_speedup_vs_streams"] = \
-        res["batch_mixed_streams"]["seconds"] / res["batch_mixed"]["seconds"]
+    if "batch_fp64_graph" in res:
+        out["one_launch_speedup_vs_graph_chunks"] = \
+            res["batch_fp64_graph"]["seconds"] / res["batch_fp64"]["seconds"]
+        out["mixed_one_launch_speedup_vs_streams"] = \
+            res["batch_mixed_streams"]["seconds"] / res["batch_mixed"]["seconds"]
     if "loop_fp64" in res:
         out["batch_speedup_vs_loop"] = res["loop_fp64"]["seconds"] / res["batch_fp64"]["seconds"]
     if "loop_mixed" in res:
@@ -502,10 +518,12 @@ def batch_summary(n_systems: int, rtol: float, reps: int, loops: bool = True,
 
 def run_batch(args):
     """--batch N: the ensemble as its own line."""
-    r = batch_summary(args.batch, args.rtol, args.steps)
+    r = batch_summary(args.batch, args.rtol, args.steps, loops=not args.batch_no_loops,
+                      max_cells=args.batch_max_cells, one_launch_only=args.batch_one_launch_only)
     line = {"metric": "ensemble corrector solves: batched vs loop (FP64 Jacobi-PCG to rtol)",
             "value": r["variants"]["batch_fp64"]["cell_iters_per_s"], "unit": UNIT,
-            "config": {"workload": f"{args.batch} systems, log-uniform 2k-500k cells",
+            "config": {"workload": f"{args.batch} systems, log-uniform 2k-"
+                                   f"{args.batch_max_cells // 1000}k cells",
                        "cells": r["cells"], "rtol": args.rtol,
                        "host_setup_s": r["host_setup_s"]},
             **{k: v for k, v in r.items() if k not in ("systems", "cells", "rtol",
