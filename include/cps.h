@@ -367,10 +367,12 @@ int cps_cp2_kernel_times(cps_sys sys, float* ms);
  *   CPS_PATH_PERSISTENT_1RED, CPS_PATH_PERSISTENT_1RED_L2 (FP64 Jacobi,
  *     and FP64 IC(0) in a two-colour order): the persistent launch with the
  *     single-reduction recurrences -- per iteration one grid reduction and
- *     waits on the neighbouring blocks only (Jacobi: one; IC(0): three, around
- *     the black forward and red backward sweeps) -- without / with its
- *     vectors in persisting L2 (Jacobi: five, CPS_ERR_ARG when the set-aside
- *     cannot hold them; IC(0): six where they fit).
+ *     waits on the neighbouring blocks only (Jacobi: one; IC(0): two, in
+ *     Eisenstat's form of the preconditioned iteration, which applies the
+ *     two-colour IC(0) factor and the matrix in one pass over the matrix,
+ *     with the same iterates) -- without / with its vectors in persisting L2
+ *     (Jacobi: five, CPS_ERR_ARG when the set-aside cannot hold them; IC(0):
+ *     six where they fit, else five, else none).
  * FP64 IC(0) in a two-colour order runs on the streaming kernels for every
  * other pin, and CPS_PATH_AUTO times both ways on the first such solve; with
  * more colours it always streams.
@@ -427,8 +429,9 @@ int cps_test_inject(cps_sys sys, int fault);
  * loop), persistent launch chosen (either recurrence), reduced system:
  * persistent launch chosen, reduced system: window (0 or 2), single-reduction
  * streaming chosen, single-reduction persistent launch chosen, IC(0):
- * persistent single-reduction launch chosen (0 no, 1 without, 2 with its six
- * vectors in persisting L2)}, flags then taking 8 entries; probe_us (may be
+ * persistent single-reduction launch chosen (0 no, 1 without a window, 2
+ * with its first five vectors, 3 with all six in persisting L2)}, flags
+ * then taking 8 entries; probe_us (may be
  * NULL, 16 entries) the microseconds per iteration measured for {streaming,
  * one cluster, streaming + matrix in L2, persistent, streaming + vectors in
  * L2, persistent + vectors in L2, reduced system: streaming, persistent,

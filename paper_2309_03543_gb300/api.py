@@ -161,7 +161,7 @@ class System:
                 "stream_single_reduction": bool(f[5]),
                 "persistent_single_reduction": bool(f[6]),
                 "ic0_persistent": bool(f[7]),
-                "ic0_l2_window": ("none", "none", "vectors6")[f[7]],
+                "ic0_l2_window": ("none", "none", "vectors5", "vectors6")[f[7]],
                 "update_1red": [gu.value, gg.value, gb.value],
                 "probe_us_per_iter": {
                     "stream": pr[0], "cluster": pr[1], "stream_l2_matrix": pr[2],

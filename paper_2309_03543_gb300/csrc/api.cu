@@ -229,7 +229,9 @@ int cps_set_solver_path(cps_sys sys, int path) {
         // the others
         t.ic0_done = true;
         t.ic0_path = (path == CPS_PATH_PERSISTENT_1RED || path == CPS_PATH_PERSISTENT_1RED_L2) ? 1 : 0;
-        t.ic0_win = (path == CPS_PATH_PERSISTENT_1RED_L2 && cps::l2_window_fits_mode(sys, 4)) ? 4 : 0;
+        t.ic0_win = path != CPS_PATH_PERSISTENT_1RED_L2 ? 0
+                    : cps::l2_window_fits_mode(sys, 4) ? 4
+                    : cps::l2_window_fits_mode(sys, 3) ? 3 : 0;
     }
     if (path == CPS_PATH_AUTO) {
         t.ic0_done = false;
@@ -369,8 +371,9 @@ int cps_get_tuning(cps_sys sys, int precision, int32_t* unroll, int32_t* grid, i
         flags[4] = t.red_done ? t.red_win : 0;
         flags[5] = t.path_done && t.path == 3;
         flags[6] = t.path_done && t.path == 4;
-        flags[7] = (t.ic0_done && t.ic0_path == 1 && sys->ncolours == 2) ? 1 + (t.ic0_win ? 1 : 0)
-                                                                          : 0;
+        flags[7] = (t.ic0_done && t.ic0_path == 1 && sys->ncolours == 2)
+                       ? (t.ic0_win == 4 ? 3 : (t.ic0_win == 3 ? 2 : 1))
+                       : 0;
     }
     if (probe_us) {
         for (int k = 0; k < 6; ++k) probe_us[k] = t.probe_us[k];

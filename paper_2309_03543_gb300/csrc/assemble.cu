@@ -350,7 +350,7 @@ void free_sys(cps_sys s) {
     // s->col lives inside s->a's allocation (one range for the L2 window)
     void* bufs[] = {s->s,     s->diag,  s->a,     s->a32,     s->s32,      s->gfac,
                     s->dxi,   s->slot_kind, s->perm, s->iperm, s->pa,  s->pcol,     s->pl,
-                    s->pdinv, s->ps,    s->pa32,  s->pl32,  s->pdinv32, s->ps32,     s->wvec,
+                    s->pdinv, s->pdiag, s->ps, s->pa32, s->pl32, s->pdinv32, s->ps32,   s->wvec,
                     s->partials, s->st, s->gsync};
     for (void* b : bufs)
         if (b) cudaFree(b);

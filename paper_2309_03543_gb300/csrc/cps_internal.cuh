@@ -301,6 +301,7 @@ struct cps_sys_s {
     int32_t* pcol = nullptr;    // [3*nt] permuted columns
     double* pl = nullptr;       // [3*nt] IC(0) factor entries per slot
     double* pdinv = nullptr;    // [nt] inverse IC(0) pivots
+    double* pdiag = nullptr;    // [nt] the IC(0) pivots themselves
     double* ps = nullptr;       // [nt] s in colour order
     float* pa32 = nullptr;
     float* pl32 = nullptr;
@@ -383,7 +384,8 @@ int cluster_solve(cps_sys s, const double* b, const double* x, double* y, double
 int persistent_solve(cps_sys s, int reduced, const double* a, const int32_t* col,
                      const double* sc, double* y, double* r, double* p, double* q, double* t,
                      int64_t n, int64_t nR, const void* win_base, size_t win_bytes, int grid,
-                     cudaStream_t stream, double* z = nullptr, const double* dinv = nullptr);
+                     cudaStream_t stream, double* z = nullptr, const double* dinv = nullptr,
+                     const double* dpiv = nullptr);
 int persistent_max_grid(cps_sys s, int reduced);
 bool l2_vectors_fit(cps_sys s);
 bool l2_window_fits_mode(cps_sys s, int mode);

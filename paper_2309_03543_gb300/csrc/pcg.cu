@@ -799,7 +799,8 @@ static int choose_fp64_path(cps_sys s, const Run<double>& v, const double* b,
 static int persistent_ic0(cps_sys s, int win, cudaStream_t stream) {
     return persistent_solve(s, 3, s->pa, s->pcol, s->ps, s->wy, s->wr, s->wp0, s->wq, s->wp1,
                             s->nt, s->colour_start[1], win ? l2_window_base(s, win) : nullptr,
-                            win ? l2_window_bytes(s, win) : 0, 0, stream, s->wz, s->pdinv);
+                            win ? l2_window_bytes(s, win) : 0, 0, stream, s->wz, s->pdinv,
+                            s->pdiag);
 }
 
 // For IC(0) on a two-colour order: times a short run (64 iterations; 256 on
@@ -823,7 +824,10 @@ static int choose_ic0_path(cps_sys s, const Run<double>& v, const double* bb,
     cands[nc++] = {0, 0};
     if (persistent_max_grid(s, 3) > 0) {
         cands[nc++] = {1, 0};
+        // six vectors in persisting L2 where they fit, else the first five
+        // (xh, rh, p, s, w: all but v / z)
         if (s->nt >= kTuneMinRows && l2_window_fits(s, 4)) cands[nc++] = {1, 4};
+        else if (s->nt >= kTuneMinRows && l2_window_fits(s, 3)) cands[nc++] = {1, 3};
     }
     cudaEvent_t e0, e1;
     CPS_CUDA_TRY(s->ctx, cudaEventCreate(&e0));

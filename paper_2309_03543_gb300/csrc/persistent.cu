@@ -271,6 +271,7 @@ struct PersistArgs {
     double dmin;        // single-reduction loops: smallest diagonal entry (stop-test gate)
     double* z;          // IC(0): preconditioned residual
     const double* dinv; // IC(0): inverse pivots
+    const double* dpiv; // IC(0), Eisenstat form: the pivots themselves
 };
 
 // Rows per block for m rows over the grid: a multiple of 32.
@@ -672,45 +673,49 @@ __global__ void __launch_bounds__(kPBlock, 1) k_persistent_gear(PersistArgs P) {
     }
 }
 
-// FP64 IC(0)-PCG in a two-colour order with the single-reduction
-// (Chronopoulos-Gear) recurrences, in one persistent launch.  Red rows
-// [0, nR) couple only to black rows [nR, n) and back, so the IC(0) factor of
-// the scaled matrix is L = [[I, 0], [E^T, I]], D = diag(I, D_B), with E the
-// red-black block of Ahat (L's off-diagonals are Ahat's own) and
-// D_B = I - diag(E^T E): z = M^-1 r is the black forward sweep
-// z_B = D_B^-1 (r_B - E^T r_R) and the red backward sweep z_R = r_R - E z_B,
-// read straight from the scaled matrix (an empty slot's zero value drops
-// out).  On the red rows w = Ahat z shares the backward sweep's sum:
-// with t = E z_B, z_R = r_R - t and w_R = z_R + t (equal to r_R in exact
-// arithmetic; computed, so that s = A p stays consistent in FP64).  Per
-// iteration, from the state k_init64 left (y, r, p = 0):
-//   red    p = z + beta p; s = w + beta s; y += alpha p; r -= alpha s     | post 0
-//   black  [wait: red owners updated r] the same update, then z_B;
-//          gamma_B = r.z                                                   | post 1
-//   red    [wait: black owners wrote z_B] z_R, w_R; gamma_R = r.z,
-//          delta_R = w.z                                                   | post 2
-//   black  [wait: red owners wrote z_R] w_B = z_B + E^T z_R; delta_B = w.z
+// FP64 IC(0)-PCG in a two-colour order by Eisenstat's form of the
+// preconditioned iteration (S. C. Eisenstat, SIAM J. Sci. Stat. Comput. 2,
+// 1981), in one persistent launch with the single-reduction recurrences.
+// With Ahat = [[I, E], [E^T, I]] (red rows [0, nR) first), the strictly lower
+// part Lt = [[0, 0], [E^T, 0]] and Dt = diag(I, D_B), the IC(0) factor is
+// M = (Dt + Lt) Dt^-1 (Dt + Lt^T).  PCG on Ahat with M gives the same
+// iterates as PCG on T = (Dt + Lt)^-1 Ahat (Dt + Lt^T)^-1 (symmetric) with
+// the diagonal preconditioner Dt, under xh = (Dt + Lt^T) y and
+// rh = (Dt + Lt)^-1 r; and from Ahat = (Dt + Lt) + (Dt + Lt^T) - (2 Dt - I),
+//   T = diag(I, D_B^-1 (I - E^T E) D_B^-1):
+// the red block is the identity, the black one needs E then E^T once.  One
+// pass over the matrix per iteration instead of two sweeps and an SpMV.  With
+// z = Dt rh (z_R = rh_R, z_B = D_B rh_B) and w = T z:
+//   w_R = z_R, and w_B = D_B^-1 (rh_B - E^T v) with v_R = E rh_B,
+// so in the recurrences s = T p stays equal to p on the red rows.  Per
+// iteration, from the state k_init64 left (y, r):
+//   all    p = z + beta p; s = w + beta s (black; red s = p);
+//          xh += alpha p; rh -= alpha s                                   | post 0
+//   red    [wait: black owners' rh_B] v_R = E rh_B; gamma_R = delta_R = rh_R.rh_R | post 1
+//   black  [wait: red owners' v] w_B = D_B^-1 (rh_B - E^T v), z_B = D_B rh_B;
+//          gamma_B = rh_B.z_B, delta_B = (rh_B - E^T v).rh_B
 //   one grid reduction: stop test, beta = gamma / gamma_old,
 //   alpha = gamma / (delta - beta gamma / alpha_old)
-// Pass 0 skips the updates: it forms z_0, w_0 and alpha_0 = gamma_0 / delta_0
-// (the carried reciprocals start at 0, which turns the general step into
-// that).  The stop test (every 8th pass) sums ||S r||^2 in the two sweeps.  Block b owns red rows [b Rr, (b+1) Rr) and
-// black rows nR + [b Rb, (b+1) Rb).  About 11 FP64 operations a row per
-// iteration (red 9, black 13) against 9 for Jacobi; s lives in P.q, w in
-// P.t.
+// Pass 0 transforms instead of updating (xh_R = y_R + E y_B, rh_B =
+// D_B^-1 (r_B - E^T r_R), p = s = 0; xh_B = D_B y_B after the red rows have
+// read y_B); after the stop, y = (Dt + Lt^T)^-1 xh: y_B = D_B^-1 xh_B, then
+// y_R = xh_R - E y_B.  The stop test (every 8th pass) sums ||S r||^2 of the
+// true-form residual r = (Dt + Lt) rh: r_R = rh_R, r_B = z_B + E^T rh_R.
+// xh lives in P.y, rh in P.r, s_B in P.q, w_B in P.t, v_R and z_B in P.z.
 __global__ void __launch_bounds__(kPBlock, 1) k_persistent_ic0(PersistArgs P) {
     __shared__ double rbuf[3][kPBlock];
-    // rho, alpha, beta, ||S r||^2, 1/rho, 1/(rho alpha), stop threshold
+    // gamma, alpha, beta, ||S r||^2, 1/gamma, 1/(gamma alpha), stop threshold
     __shared__ double sc[7];
     __shared__ long long s_max_iter;
     __shared__ int s_stop;        // 1 stop, 2 breakdown
     __shared__ int s_dep[4];      // [lo, hi] owners for black rows, then for red rows
     CgState* st = P.st;
     if (st->done) return;                      // uniform: set before the launch
-    // row indices fit 32 bits (the columns are int32): fewer registers
     const int n = (int)P.n, nR = (int)P.nR, nB = n - nR;
     const double* __restrict__ A = P.a;
     const int32_t* __restrict__ C = P.col;
+    const double* __restrict__ dinv = P.dinv;
+    const double* __restrict__ dpiv = P.dpiv;
     double* __restrict__ y = P.y;
     double* __restrict__ r = P.r;
     double* __restrict__ p = P.p;
@@ -777,66 +782,72 @@ __global__ void __launch_bounds__(kPBlock, 1) k_persistent_ic0(PersistArgs P) {
     int pass = 0;              // passes 1, 2, ... each begin with an update: iterations = pass
     for (; ok; ++pass) {
         const bool upd = pass > 0;
-        // the stop test every 8th pass, not gated: gamma = r.M^-1 r here, which
-        // bounds neither r.r nor ||S r||^2 from below
         const bool check = upd && (pass % 8) == 0;
         const double alpha = sc[1], beta = sc[2];
         double sums[3] = {0.0, 0.0, 0.0};
-        if (upd) {   // red update
-            for (int e = rlo + (int)threadIdx.x; e < rhi; e += kPBlock) {
-                const double pe = p[e];
-                const double se = s[e];
-                const double we = w[e];
-                const double ze = z[e];
-                const double re = r[e];
-                const double ye = y[e];
-                const double pn = fma(beta, pe, ze);
-                const double sn = fma(beta, se, we);
-                p[e] = pn;
-                s[e] = sn;
-                y[e] = fma(alpha, pn, ye);
-                r[e] = fma(-alpha, sn, re);
+        if (upd) {
+            // red: z = w = rh (old), so s = p: p = rh + beta p, xh += alpha p,
+            // rh -= alpha p
+            {
+                double re[2], pe[2], ye[2];
+                CPS_B_LOOP(rlo, rhi, 2, (re[u] = r[e], pe[u] = p[e], ye[u] = y[e]), {
+                    const double pn = fma(beta, pe[u], re[u]);
+                    p[e] = pn;
+                    y[e] = fma(alpha, pn, ye[u]);
+                    r[e] = fma(-alpha, pn, re[u]);
+                })
             }
+            // black: p = z + beta p, s = w + beta s, xh += alpha p,
+            // rh -= alpha s
+            double pe[2], se[2], we[2], ze[2], re[2], ye[2];
+            CPS_B_LOOP(blo, bhi, 2,
+                (pe[u] = p[e], se[u] = s[e], we[u] = w[e], ze[u] = z[e], re[u] = r[e],
+                 ye[u] = y[e]),
+                {
+                    const double pn = fma(beta, pe[u], ze[u]);
+                    const double sn = fma(beta, se[u], we[u]);
+                    p[e] = pn;
+                    s[e] = sn;
+                    y[e] = fma(alpha, pn, ye[u]);
+                    r[e] = fma(-alpha, sn, re[u]);
+                })
         } else {
-            // an empty slot of a red row points at the row itself with value
-            // 0: its z must be finite before the first backward sweep
-            for (int e = rlo + (int)threadIdx.x; e < rhi; e += kPBlock) z[e] = 0.0;
-        }
-        post(0, pass);
-        if (!(ok = wait(0, pass, 0))) break;
-        // black update, then z_B = D_B^-1 (r_B - E^T r_R); gamma_B = r.z
-        for (int e = blo + (int)threadIdx.x; e < bhi; e += kPBlock) {
-            double re = r[e];
-            if (upd) {
-                const double pe = p[e];
-                const double se = s[e];
-                const double we = w[e];
-                const double ze = z[e];
-                const double ye = y[e];
-                const double pn = fma(beta, pe, ze);
-                const double sn = fma(beta, se, we);
-                p[e] = pn;
-                s[e] = sn;
-                y[e] = fma(alpha, pn, ye);
-                re = fma(-alpha, sn, re);
-                r[e] = re;
-            } else {
+            // xh_R = y_R + E y_B (y_B still the untransformed iterate)
+            for (int e = rlo + (int)threadIdx.x; e < rhi; e += kPBlock) {
+                double v = fma(A[e], y[C[e]], y[e]);
+                v = fma(A[n + e], y[C[n + e]], v);
+                v = fma(A[2 * n + e], y[C[2 * n + e]], v);
+                y[e] = v;
+                p[e] = 0.0;
+            }
+            // rh_B = D_B^-1 (r_B - E^T r_R) (r_R is never written here)
+            for (int e = blo + (int)threadIdx.x; e < bhi; e += kPBlock) {
+                double v = fma(-A[e], r[C[e]], r[e]);
+                v = fma(-A[n + e], r[C[n + e]], v);
+                v = fma(-A[2 * n + e], r[C[2 * n + e]], v);
+                r[e] = v * dinv[e];
+                p[e] = 0.0;
                 s[e] = 0.0;
             }
-            double v = fma(-A[e], r[C[e]], re);
-            v = fma(-A[n + e], r[C[n + e]], v);
-            v = fma(-A[2 * n + e], r[C[2 * n + e]], v);
-            const double ze = v * P.dinv[e];
-            z[e] = ze;
-            sums[0] = fma(re, ze, sums[0]);
-            if (check) {
-                const double tt = P.s[e] * re;
-                sums[2] = fma(tt, tt, sums[2]);
+        }
+        post(0, pass);
+        // the red phase's first trip reads this block's rows up to the
+        // gathers: fetch them into L1 while waiting on the neighbours
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int e = rlo + (int)threadIdx.x + u * kPBlock;
+            if (e < rhi) {
+                prefetch_l1(r + e);
+                prefetch_l1(A + e);
+                prefetch_l1(A + n + e);
+                prefetch_l1(A + 2 * n + e);
+                prefetch_l1(C + e);
+                prefetch_l1(C + n + e);
+                prefetch_l1(C + 2 * n + e);
             }
         }
-        post(1, pass);
-        if (!(ok = wait(1, pass, 1))) break;
-        // t = E z_B, z_R = r_R - t, w_R = z_R + t; gamma_R = r.z, delta_R = w.z
+        if (!(ok = wait(0, pass, 1))) break;
+        // red: v_R = E rh_B; gamma_R = delta_R = rh_R.rh_R
         {
             double re[2], a0[2], a1[2], a2[2];
             int c0[2], c1[2], c2[2];
@@ -844,38 +855,73 @@ __global__ void __launch_bounds__(kPBlock, 1) k_persistent_ic0(PersistArgs P) {
                 (re[u] = r[e], a0[u] = A[e], a1[u] = A[n + e], a2[u] = A[2 * n + e],
                  c0[u] = C[e], c1[u] = C[n + e], c2[u] = C[2 * n + e]),
                 {
-                    if (!upd) s[e] = 0.0;
-                    double t = a0[u] * z[c0[u]];
-                    t = fma(a1[u], z[c1[u]], t);
-                    t = fma(a2[u], z[c2[u]], t);
-                    const double ze = re[u] - t;
-                    const double we = ze + t;
-                    z[e] = ze;
-                    w[e] = we;
-                    sums[0] = fma(re[u], ze, sums[0]);
-                    sums[1] = fma(we, ze, sums[1]);
+                    double v = a0[u] * r[c0[u]];
+                    v = fma(a1[u], r[c1[u]], v);
+                    v = fma(a2[u], r[c2[u]], v);
+                    z[e] = v;
+                    sums[0] = fma(re[u], re[u], sums[0]);
                     if (check) {
                         const double tt = P.s[e] * re[u];
                         sums[2] = fma(tt, tt, sums[2]);
                     }
                 })
         }
-        post(2, pass);
-        if (!(ok = wait(2, pass, 0))) break;
-        // w_B = z_B + E^T z_R; delta_B = w.z
+        sums[1] = sums[0];
+        post(1, pass);
+        // likewise the black phase's first trip
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int e = blo + (int)threadIdx.x + u * kPBlock;
+            if (e < bhi) {
+                prefetch_l1(r + e);
+                prefetch_l1(A + e);
+                prefetch_l1(A + n + e);
+                prefetch_l1(A + 2 * n + e);
+                prefetch_l1(C + e);
+                prefetch_l1(C + n + e);
+                prefetch_l1(C + 2 * n + e);
+                prefetch_l1(dpiv + e);
+                prefetch_l1(dinv + e);
+            }
+        }
+        if (!(ok = wait(1, pass, 0))) break;
+        // black: w_B = D_B^-1 (rh_B - E^T v), z_B = D_B rh_B; gamma_B, delta_B
         {
-            double ze[2], a0[2], a1[2], a2[2];
+            double re[2], a0[2], a1[2], a2[2];
             int c0[2], c1[2], c2[2];
             CPS_B_LOOP(blo, bhi, 2,
-                (ze[u] = z[e], a0[u] = A[e], a1[u] = A[n + e], a2[u] = A[2 * n + e],
+                (re[u] = r[e], a0[u] = A[e], a1[u] = A[n + e], a2[u] = A[2 * n + e],
                  c0[u] = C[e], c1[u] = C[n + e], c2[u] = C[2 * n + e]),
                 {
-                    double v = fma(a0[u], z[c0[u]], ze[u]);
-                    v = fma(a1[u], z[c1[u]], v);
-                    v = fma(a2[u], z[c2[u]], v);
-                    w[e] = v;
-                    sums[1] = fma(v, ze[u], sums[1]);
+                    double t = fma(-a0[u], z[c0[u]], re[u]);
+                    t = fma(-a1[u], z[c1[u]], t);
+                    t = fma(-a2[u], z[c2[u]], t);
+                    const double d = dpiv[e];
+                    const double ze = d * re[u];
+                    w[e] = t * dinv[e];
+                    z[e] = ze;
+                    if (!upd) y[e] = d * y[e];        // xh_B = D_B y_B
+                    sums[0] = fma(re[u], ze, sums[0]);
+                    sums[1] = fma(t, re[u], sums[1]);
+                    if (check) {
+                        double rb = fma(a0[u], r[c0[u]], ze);
+                        rb = fma(a1[u], r[c1[u]], rb);
+                        rb = fma(a2[u], r[c2[u]], rb);
+                        const double tt = P.s[e] * rb;
+                        sums[2] = fma(tt, tt, sums[2]);
+                    }
                 })
+        }
+        // the next update's first trips read only this block's own rows,
+        // final now: fetch them into L1 during the reduction
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int er = rlo + (int)threadIdx.x + u * kPBlock;
+            if (er < rhi) {
+                prefetch_l1(r + er);
+                prefetch_l1(p + er);
+                prefetch_l1(y + er);
+            }
         }
         auto step = [&](const double* t, bool chk, int& f) {
             const double g = t[0], d = t[1];
@@ -888,9 +934,9 @@ __global__ void __launch_bounds__(kPBlock, 1) k_persistent_ic0(PersistArgs P) {
             if (!halt) {
                 const double den = fma(-(g * g), sc[5], d);
                 if (!(den > 0.0) || !isfinite(den)) {
-                    // on pass 0 z.Az <= 0: not SPD; later, the recurrence's
-                    // difference lost its digits at the FP64 floor: stop, and
-                    // let the true residual decide (restart or not converged)
+                    // pass 0: z.Tz <= 0, not SPD; later the recurrence's
+                    // difference lost its digits at the FP64 floor: stop,
+                    // and let the true residual decide
                     f = upd ? 1 : 2;
                 } else {
                     const double ig = 1.0 / g;
@@ -923,6 +969,20 @@ __global__ void __launch_bounds__(kPBlock, 1) k_persistent_ic0(PersistArgs P) {
         if (flag) {
             if (threadIdx.x == 0) s_stop = flag;
             break;
+        }
+    }
+    if (ok) {
+        // y = (Dt + Lt^T)^-1 xh: y_B = D_B^-1 xh_B, then y_R = xh_R - E y_B
+        for (int e = blo + (int)threadIdx.x; e < bhi; e += kPBlock) y[e] *= dinv[e];
+        post(2, 0);
+        ok = wait(2, 0, 1);
+        if (ok) {
+            for (int e = rlo + (int)threadIdx.x; e < rhi; e += kPBlock) {
+                double v = fma(-A[e], y[C[e]], y[e]);
+                v = fma(-A[n + e], y[C[n + e]], v);
+                v = fma(-A[2 * n + e], y[C[2 * n + e]], v);
+                y[e] = v;
+            }
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1139,7 +1199,7 @@ int persistent_max_grid(cps_sys s, int reduced) {
 int persistent_solve(cps_sys s, int reduced, const double* a, const int32_t* col,
                      const double* sc, double* y, double* r, double* p, double* q, double* t,
                      int64_t n, int64_t nR, const void* win_base, size_t win_bytes, int grid,
-                     cudaStream_t stream, double* z, const double* dinv) {
+                     cudaStream_t stream, double* z, const double* dinv, const double* dpiv) {
     if (!s->gsync) {
         cudaError_t e = cudaMalloc((void**)&s->gsync, sizeof(GridSync));
         if (e != cudaSuccess) {
@@ -1167,7 +1227,8 @@ int persistent_solve(cps_sys s, int reduced, const double* a, const int32_t* col
     const int stall = s->inject == CPS_TEST_STALL_BARRIER ? 1 : 0;
     s->inject = 0;
     PersistArgs P{a, col, sc, y, r, p, q, t, n, nR, s->partials,
-                  reinterpret_cast<GridSync*>(s->gsync), s->st, stall, s->diag_min, z, dinv};
+                  reinterpret_cast<GridSync*>(s->gsync), s->st, stall, s->diag_min, z, dinv,
+                  dpiv};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(G, 1, 1);
     cfg.blockDim = dim3(kPBlock, 1, 1);

@@ -249,7 +249,7 @@ __global__ void k_permute_matrix(const double* __restrict__ a, const int32_t* __
 // IC(0) rows of one colour [cs, ce): lower slots have pcol < i.
 __global__ void k_ic0_factor(const double* __restrict__ pa, const int32_t* __restrict__ pcol,
                              int64_t n, int64_t cs, int64_t ce, double* __restrict__ pl,
-                             double* __restrict__ pdinv, int* err) {
+                             double* __restrict__ pdinv, double* __restrict__ pdiag, int* err) {
     for (int64_t i = cs + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ce;
          i += (int64_t)gridDim.x * blockDim.x) {
         int kk[3], sl[3], m = 0;
@@ -291,8 +291,10 @@ __global__ void k_ic0_factor(const double* __restrict__ pa, const int32_t* __res
         if (!(d > 0.0) || !isfinite(d)) {
             set_error(err, CPS_ERR_NOT_SPD);
             pdinv[i] = 1.0;
+            pdiag[i] = 1.0;
         } else {
             pdinv[i] = 1.0 / d;
+            pdiag[i] = d;
         }
     }
 }
@@ -335,6 +337,7 @@ static int alloc_ic0(cps_sys s) {
     } req[] = {{(void**)&s->perm, 4 * (size_t)n},       {(void**)&s->iperm, 4 * (size_t)n},
                {(void**)&s->pa, 24 * (size_t)n},        {(void**)&s->pcol, 12 * (size_t)n},
                {(void**)&s->pl, 24 * (size_t)n},        {(void**)&s->pdinv, 8 * (size_t)n},
+               {(void**)&s->pdiag, 8 * (size_t)n},
                {(void**)&s->ps, 8 * (size_t)n},         {(void**)&s->pa32, 12 * (size_t)n},
                {(void**)&s->pl32, 12 * (size_t)n},      {(void**)&s->pdinv32, 4 * (size_t)n},
                {(void**)&s->ps32, 4 * (size_t)n}};
@@ -454,7 +457,7 @@ int precond_impl(cps_sys s, int precond, cudaStream_t stream) {
                 for (int c = 0; c < ncol; ++c)
                     k_ic0_factor<<<g, kBlock, 0, stream>>>(s->pa, s->pcol, n, s->colour_start[c],
                                                            s->colour_start[c + 1], s->pl, s->pdinv,
-                                                           err);
+                                                           s->pdiag, err);
                 k_ic0_upper<<<g, kBlock, 0, stream>>>(s->pcol, n, s->pl, s->pdinv, s->pl32,
                                                       s->pdinv32);
                 k_to_float<<<grid_for(s->ctx, 3 * n), kBlock, 0, stream>>>(s->pl, 3 * n, s->pl32);
