@@ -185,7 +185,7 @@ int cps_solve(cps_sys sys, const double* b, double* x, double rtol, int64_t max_
  * and receives the solution).  All systems must come from the same context.
  * CPS_FP64 (Jacobi, whatever each system's preconditioner setting): by
  * default one cooperative kernel launch for the whole ensemble -- the
- * largest systems (estimated work cells^1.5 above twice a block's fair
+ * larger systems (estimated work cells^1.5 above half a block's fair
  * share) are each solved by a static team of blocks that split the rows and
  * combine their sums through bounded device-side waits, and every other
  * block takes whole systems from a device work queue (largest first) and
