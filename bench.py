@@ -116,7 +116,12 @@ def loop_name(tf: dict) -> str:
     elif tf["persistent"]:
         kname = "k_persistent_cg (whole Jacobi-PCG solve in one cooperative launch)"
     elif tf["cluster"]:
-        kname = "k_cluster_cg (whole Jacobi-PCG solve in one thread-block cluster)"
+        kname = {"single_reduction": "k_cluster_cg1 (whole Jacobi-PCG solve in one thread-block "
+                                     "cluster, Chronopoulos-Gear recurrences)",
+                 "pipelined": "k_cluster_cgp (whole Jacobi-PCG solve in one thread-block "
+                              "cluster, pipelined Ghysels-Vanroose recurrences)"}.get(
+            tf.get("cluster_recurrence"),
+            "k_cluster_cg (whole Jacobi-PCG solve in one thread-block cluster)")
     elif tf["stream_single_reduction"]:
         kname = ("pcg_iteration_fp64_single_reduction (k_gear_update + k_gear_spmv, Jacobi, "
                  "Chronopoulos-Gear recurrences)")
@@ -628,6 +633,7 @@ def latency_summary(n: int, rtol: float, reps: int = 5) -> dict:
     x = torch.zeros_like(b)
     out = {"workload": f"centred-block lattice n={n}", "cells": m.nt, "rtol": rtol}
     for name, path in (("tuned", cps.PATH_AUTO), ("cluster_1red", cps.PATH_CLUSTER_1RED),
+                       ("cluster_pipelined", cps.PATH_CLUSTER_PIPE),
                        ("cluster", cps.PATH_CLUSTER), ("stream_1red", cps.PATH_STREAM_1RED),
                        ("stream", cps.PATH_STREAM), ("persistent_1red", cps.PATH_PERSISTENT_1RED)):
         try:

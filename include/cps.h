@@ -364,6 +364,13 @@ int cps_cp2_kernel_times(cps_sys sys, float* ms);
  *     are carried so that both inner products of an iteration come from one
  *     SpMV (two cluster barriers per iteration instead of three; one more
  *     vector in shared memory, so a somewhat smaller size limit);
+ *   CPS_PATH_CLUSTER_PIPE (FP64 Jacobi only): the one-cluster launch with the
+ *     pipelined (Ghysels-Vanroose) single-reduction recurrences -- z = A s
+ *     is carried as well, so that the SpMV of an iteration runs while its
+ *     reduction is in flight: one split cluster barrier per iteration (two
+ *     more vectors in shared memory, a smaller size limit).  Pinned only:
+ *     CPS_PATH_AUTO does not take it, since its recurrences lose accuracy
+ *     sooner and need more iterations than the per-iteration gain repays;
  *   CPS_PATH_PERSISTENT_1RED, CPS_PATH_PERSISTENT_1RED_L2 (FP64 Jacobi,
  *     and FP64 IC(0) in a two-colour order): the persistent launch with the
  *     single-reduction recurrences -- per iteration one grid reduction and
@@ -388,6 +395,7 @@ int cps_cp2_kernel_times(cps_sys sys, float* ms);
 #define CPS_PATH_STREAM_1RED_L2 8
 #define CPS_PATH_PERSISTENT_1RED 9
 #define CPS_PATH_PERSISTENT_1RED_L2 10
+#define CPS_PATH_CLUSTER_PIPE 11
 int cps_set_solver_path(cps_sys sys, int path);
 
 /* Pin the launch shapes of the iteration kernels of one precision instead of
@@ -424,7 +432,7 @@ int cps_test_inject(cps_sys sys, int fault);
  * the defaults (unroll 2, 8 blocks per SM).  For CPS_FP64 Jacobi solves it
  * also times the ways of running the loop: flags (may be NULL, 8 entries)
  * receives {one-cluster launch chosen (0 no, 1 textbook recurrences, 2 the
- * single-reduction recurrences), persisting-L2 window (0 none, 1 the
+ * single-reduction recurrences, 3 the pipelined ones), persisting-L2 window (0 none, 1 the
  * matrix, 2 the vectors r, p, q, 3 the five vectors of the single-reduction
  * loop), persistent launch chosen (either recurrence), reduced system:
  * persistent launch chosen, reduced system: window (0 or 2), single-reduction
@@ -433,7 +441,7 @@ int cps_test_inject(cps_sys sys, int fault);
  * with its first five vectors, 3 with all six in persisting L2)}, flags
  * then taking 8 entries; probe_us (may be
  * NULL, 16 entries) the microseconds per iteration measured for {streaming,
- * one cluster, streaming + matrix in L2, persistent, streaming + vectors in
+ * one cluster (the best of its three recurrences), streaming + matrix in L2, persistent, streaming + vectors in
  * L2, persistent + vectors in L2, reduced system: streaming, persistent,
  * streaming + vectors in L2, persistent + vectors in L2, single-reduction
  * streaming, single-reduction streaming + vectors in L2, single-reduction

@@ -303,8 +303,9 @@ int cps_set_solver_path(cps_sys sys, int path) {
         t.red_done = true;
         t.red_path = 0;
         t.red_win = 2;
-    } else if (path == CPS_PATH_CLUSTER || path == CPS_PATH_CLUSTER_1RED) {
-        const int var = path == CPS_PATH_CLUSTER_1RED ? 1 : 0;
+    } else if (path == CPS_PATH_CLUSTER || path == CPS_PATH_CLUSTER_1RED ||
+               path == CPS_PATH_CLUSTER_PIPE) {
+        const int var = path == CPS_PATH_CLUSTER_PIPE ? 2 : (path == CPS_PATH_CLUSTER_1RED ? 1 : 0);
         if (sys->nt > cps::cluster_max_rows(sys->ctx, var)) {
             cps::set_error(sys->ctx, "set_solver_path: system too large for one cluster");
             return CPS_ERR_ARG;

@@ -425,7 +425,267 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_cluster_cg1(ClusterArgs 
     cluster.sync();         // no CTA leaves while others may still read its memory
 }
 
+// Pipelined variant (Ghysels-Vanroose recurrences; one split cluster barrier
+// per iteration): besides s = Ahat p and w = Ahat r the CTA keeps
+// z = Ahat s, so that the SpMV of an iteration, q = Ahat w, needs only the
+// current w and can run while the iteration's reduction is in flight:
+//   gamma = r.r, delta = w.r: block sum, partials pushed | cluster arrive
+//   q = Ahat w over this CTA's own columns | cluster wait | q += remote columns
+//   beta = gamma/gamma_old, alpha = gamma/(delta - beta gamma/alpha_old)
+//   z = q + beta z; s = w + beta s; p = r + beta p; y += alpha p;
+//   r -= alpha s; w -= alpha z
+// w and the partials are double-buffered by iteration parity, so that the one
+// barrier also orders each CTA's writes after every other CTA's reads of the
+// iteration before.  Same iterates as the textbook recurrence in exact
+// arithmetic; 11 FP64 FMAs a row against 9, and the recurrences drift sooner
+// near the FP64 floor (the host's true residual then decides on a restart).
+constexpr size_t kRowBytes2 = 3 * sizeof(double) + 3 * sizeof(int32_t) + 9 * sizeof(double);
+__host__ __device__ inline size_t cluster2_red_offset(int R) {
+    return ((size_t)R * kRowBytes2 + 15) / 16 * 16;
+}
+__host__ __device__ inline size_t cluster2_smem_bytes(int R) {
+    return cluster2_red_offset(R) + kRedBufBytes;
+}
+
+__device__ __forceinline__ void cluster_arrive_release() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait_acquire() {
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kClusterThreads, 1) k_cluster_cgp(ClusterArgs A) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int C = (int)cluster.num_blocks();
+    const int rank = (int)cluster.block_rank();
+    const int R = A.rows;
+    const int64_t n = A.n;
+    const int64_t r0 = (int64_t)rank * R;
+    const int nloc = (int)((r0 + R <= n) ? R : (n > r0 ? n - r0 : 0));
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    double* a_s = reinterpret_cast<double*>(smem);          // [3][R]
+    double* p_s = a_s + 3 * R;
+    double* r_s = p_s + R;
+    double* y_s = r_s + R;
+    double* sv_s = y_s + R;         // s = Ahat p
+    double* z_s = sv_s + R;         // z = Ahat s
+    double* q_s = z_s + R;          // q = Ahat w
+    double* w_s[2] = {q_s + R, q_s + 2 * R};
+    double* s_s = q_s + 3 * R;      // the scaling S
+    int32_t* c_s = reinterpret_cast<int32_t*>(s_s + R);      // [3][R] packed (rank << 16) | local
+    double* rbuf = reinterpret_cast<double*>(smem + cluster2_red_offset(R));
+    __shared__ double red[2][4][16];   // red[parity][k][c]: partial k of CTA c
+    __shared__ double tot[4];
+    __shared__ double sc[2];           // alpha, beta, derived once per CTA by thread 0
+    __shared__ int s_stop;
+
+    const int tid = threadIdx.x;
+    for (int i = tid; i < nloc; i += blockDim.x) {
+        const int64_t e = r0 + i;
+        for (int j = 0; j < 3; ++j) {
+            a_s[j * R + i] = A.a[j * n + e];
+            const int32_t c = A.col[j * n + e];
+            const int cr = c / R;
+            c_s[j * R + i] = (cr << 16) | (c - cr * R);
+        }
+        const double se = A.s[e];
+        s_s[i] = se;
+        y_s[i] = se * A.x[e];
+        p_s[i] = 0.0;
+        sv_s[i] = 0.0;
+        z_s[i] = 0.0;
+    }
+    cluster.sync();
+    auto gather = [&](double* base, int32_t packed) -> double {
+        const int cr = packed >> 16, li = packed & 0xFFFF;
+        if (cr == rank) return base[li];
+        return cluster.map_shared_rank(base, cr)[li];
+    };
+    auto push = [&](int par, int k, double v) {
+        if (tid < C) cluster.map_shared_rank(&red[par][k][0], tid)[rank] = v;
+    };
+    auto cluster_sum = [&](int par, int k) -> double {
+        double t = 0.0;
+        for (int c = 0; c < C; ++c) t += red[par][k][c];
+        return t;
+    };
+
+    // r = S^-1 b - Ahat y; ||b||^2
+    {
+        double v1[1] = {0.0};
+        for (int i = tid; i < nloc; i += blockDim.x) {
+            double ay = y_s[i];
+            for (int j = 0; j < 3; ++j) ay = fma(a_s[j * R + i], gather(y_s, c_s[j * R + i]), ay);
+            const double be = A.b[r0 + i];
+            r_s[i] = be / s_s[i] - ay;
+            v1[0] = fma(be, be, v1[0]);
+        }
+        block_sum_buf<1>(v1, rbuf, tot);
+        push(0, 3, v1[0]);
+    }
+    cluster.sync();         // r complete everywhere
+    // w = Ahat r; gamma = r.r, delta = w.r, ||S r||^2
+    {
+        double v3[3] = {0.0, 0.0, 0.0};
+        for (int i = tid; i < nloc; i += blockDim.x) {
+            const double re = r_s[i];
+            double v = re;
+            for (int j = 0; j < 3; ++j) v = fma(a_s[j * R + i], gather(r_s, c_s[j * R + i]), v);
+            w_s[0][i] = v;
+            v3[0] = fma(re, re, v3[0]);
+            v3[1] = fma(v, re, v3[1]);
+            const double t = s_s[i] * re;
+            v3[2] = fma(t, t, v3[2]);
+        }
+        block_sum_buf<3>(v3, rbuf, tot);
+        push(0, 0, v3[0]);
+        push(0, 1, v3[1]);
+        push(0, 2, v3[2]);
+    }
+    cluster.sync();         // w complete everywhere; the partials are in place
+    double gamma = 0.0, alpha = 0.0, bnorm2 = 0.0, rnorm2 = 0.0, thresh2 = 0.0;
+    int status = CPS_OK;
+    if (tid == 0) {
+        gamma = cluster_sum(0, 0);
+        const double delta = cluster_sum(0, 1);
+        rnorm2 = cluster_sum(0, 2);
+        bnorm2 = cluster_sum(0, 3);
+        thresh2 = A.rtol * A.rtol * bnorm2;
+        int stop = (bnorm2 == 0.0 || rnorm2 <= thresh2 || A.max_iter <= 0) ? 1 : 0;
+        if (!stop && (!(delta > 0.0) || !isfinite(delta))) stop = 2;
+        alpha = stop ? 0.0 : gamma / delta;
+        sc[0] = alpha;
+        sc[1] = 0.0;
+        s_stop = stop;
+    }
+    // q = Ahat w
+    for (int i = tid; i < nloc; i += blockDim.x) {
+        double v = w_s[0][i];
+        for (int j = 0; j < 3; ++j) v = fma(a_s[j * R + i], gather(w_s[0], c_s[j * R + i]), v);
+        q_s[i] = v;
+    }
+    __syncthreads();
+    long long it = 0;
+    int par = 0;            // w_s[par] holds the current w
+    int stop = s_stop;
+    if (stop == 2) status = CPS_ERR_NOT_SPD;
+    while (!stop) {
+        const double al = sc[0], be = sc[1];
+        {
+            const double* __restrict__ wc = w_s[par];
+            double* __restrict__ wn = w_s[par ^ 1];
+            for (int i = tid; i < nloc; i += blockDim.x) {
+                const double ze = fma(be, z_s[i], q_s[i]);
+                const double se = fma(be, sv_s[i], wc[i]);
+                const double pe = fma(be, p_s[i], r_s[i]);
+                z_s[i] = ze;
+                sv_s[i] = se;
+                p_s[i] = pe;
+                y_s[i] = fma(al, pe, y_s[i]);
+                r_s[i] = fma(-al, se, r_s[i]);
+                wn[i] = fma(-al, ze, wc[i]);
+            }
+        }
+        ++it;
+        par ^= 1;
+        const int rp = (int)(it & 1);
+        const bool check = (it % kCheck) == 0;
+        {
+            double v3[3] = {0.0, 0.0, 0.0};
+            const double* __restrict__ wc = w_s[par];
+            for (int i = tid; i < nloc; i += blockDim.x) {
+                const double re = r_s[i];
+                v3[0] = fma(re, re, v3[0]);
+                v3[1] = fma(wc[i], re, v3[1]);
+                if (check) {
+                    const double t = s_s[i] * re;
+                    v3[2] = fma(t, t, v3[2]);
+                }
+            }
+            block_sum_buf<3>(v3, rbuf, tot);   // also orders this CTA's w writes
+            push(rp, 0, v3[0]);
+            push(rp, 1, v3[1]);
+            push(rp, 2, v3[2]);
+        }
+        cluster_arrive_release();
+        // q = Ahat w: this CTA's own columns while the reduction completes
+        for (int i = tid; i < nloc; i += blockDim.x) {
+            double v = w_s[par][i];
+            for (int j = 0; j < 3; ++j) {
+                const int32_t pk = c_s[j * R + i];
+                if ((pk >> 16) == rank) v = fma(a_s[j * R + i], w_s[par][pk & 0xFFFF], v);
+            }
+            q_s[i] = v;
+        }
+        cluster_wait_acquire();
+        for (int i = tid; i < nloc; i += blockDim.x) {
+            double v = q_s[i];
+            bool any = false;
+            for (int j = 0; j < 3; ++j) {
+                const int32_t pk = c_s[j * R + i];
+                const int cr = pk >> 16;
+                if (cr != rank) {
+                    v = fma(a_s[j * R + i], cluster.map_shared_rank(w_s[par], cr)[pk & 0xFFFF], v);
+                    any = true;
+                }
+            }
+            if (any) q_s[i] = v;
+        }
+        if (tid == 0) {
+            const double g = cluster_sum(rp, 0);
+            const double delta = cluster_sum(rp, 1);
+            int halt = (!(g > 0.0) || it >= A.max_iter) ? 1 : 0;
+            if (check) {
+                rnorm2 = cluster_sum(rp, 2);
+                if (rnorm2 <= thresh2) halt = 1;
+            }
+            const double beta = g / gamma;
+            const double den = delta - beta * g / alpha;
+            // a difference that lost its digits at the FP64 floor: stop and
+            // let the true residual decide (restart or not converged)
+            if (!halt && (!(den > 0.0) || !isfinite(den))) halt = 1;
+            alpha = halt ? alpha : g / den;
+            gamma = g;
+            sc[0] = alpha;
+            sc[1] = beta;
+            s_stop = halt;
+        }
+        __syncthreads();
+        stop = s_stop;
+    }
+    for (int i = tid; i < nloc; i += blockDim.x) A.y_out[r0 + i] = y_s[i];
+    if (rank == 0 && tid == 0) {
+        CgState* st = A.st;
+        st->rho = gamma;
+        st->bnorm2 = bnorm2;
+        st->thresh2 = thresh2;
+        st->rnorm2 = rnorm2;
+        st->iter = it;
+        st->max_iter = A.max_iter;
+        st->status = status;
+        st->done = 2;
+        st->alpha = 0.0;
+        st->beta = 0.0;
+    }
+    cluster.sync();         // no CTA leaves while others may still read its memory
+}
+
 }  // namespace
+
+// The cluster kernel of a variant: 0 textbook, 1 single reduction, 2 pipelined.
+static void (*cluster_kernel(int variant))(ClusterArgs) {
+    return variant == 2 ? k_cluster_cgp : (variant == 1 ? k_cluster_cg1 : k_cluster_cg);
+}
+
+static size_t cluster_row_bytes(int variant) {
+    return variant == 2 ? kRowBytes2 : (variant == 1 ? kRowBytes1 : kRowBytes);
+}
+
+static size_t cluster_smem_for(int variant, int R) {
+    return variant == 2 ? cluster2_smem_bytes(R)
+                        : (variant == 1 ? cluster1_smem_bytes(R) : cluster_smem_bytes(R));
+}
 
 // Dynamic shared memory a CTA of the cluster kernel may use on this device:
 // the opt-in limit minus the kernel's static shared memory.
@@ -437,20 +697,20 @@ static size_t cluster_dyn_smem_limit(int dev, int variant) {
         return 0;
     }
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, variant ? k_cluster_cg1 : k_cluster_cg) != cudaSuccess) {
+    if (cudaFuncGetAttributes(&fa, cluster_kernel(variant)) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     return (size_t)smem_optin > fa.sharedSizeBytes ? (size_t)smem_optin - fa.sharedSizeBytes : 0;
 }
 
-// Largest system the cluster path (variant 0 textbook, 1 single reduction)
-// takes on this GPU (0: not available).
+// Largest system the cluster path (variant 0 textbook, 1 single reduction,
+// 2 pipelined) takes on this GPU (0: not available).
 int64_t cluster_max_rows(cps_ctx ctx, int variant) {
     const size_t lim = cluster_dyn_smem_limit(ctx->device, variant);
     const size_t fixed = kRedBufBytes + 16;
     if (lim <= fixed) return 0;
-    const int64_t R = (int64_t)((lim - fixed) / (variant ? kRowBytes1 : kRowBytes));
+    const int64_t R = (int64_t)((lim - fixed) / cluster_row_bytes(variant));
     return std::min<int64_t>(R, 0xFFFF) * 16;
 }
 
@@ -458,9 +718,9 @@ int64_t cluster_max_rows(cps_ctx ctx, int variant) {
 // scaled iterate in y and the final scalars in s->st (done = 2).
 int cluster_solve(cps_sys s, const double* b, const double* x, double* y, double rtol,
                   long long max_iter, cudaStream_t stream, int variant) {
-    static std::atomic<bool> configured[2][64];   // zero-initialised (static storage)
-    variant = variant ? 1 : 0;
-    void (*kern)(ClusterArgs) = variant ? k_cluster_cg1 : k_cluster_cg;
+    static std::atomic<bool> configured[3][64];   // zero-initialised (static storage)
+    variant = (variant == 1 || variant == 2) ? variant : 0;
+    void (*kern)(ClusterArgs) = cluster_kernel(variant);
     const int64_t n = s->nt;
     int csize = 16;
     cudaError_t e = cudaSuccess;
@@ -490,7 +750,7 @@ int cluster_solve(cps_sys s, const double* b, const double* x, double* y, double
     A.max_iter = max_iter;
     for (; csize >= 2; csize /= 2) {
         const int R = (int)((n + csize - 1) / csize);
-        const size_t smem = variant ? cluster1_smem_bytes(R) : cluster_smem_bytes(R);
+        const size_t smem = cluster_smem_for(variant, R);
         if (R > 0xFFFF || smem > lim) continue;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(csize, 1, 1);
