@@ -465,16 +465,20 @@ static int solve_batch_mixed(const cps_sys* systems, int nsys, const double* con
 
 // Static teams for one launch of G blocks.  System i's estimated work is
 // W_i = n_i^1.5 (the iteration count grows with the mesh's side) and a
-// block's fair share is T = sum W / G.  The systems above T / 2 share the
-// whole grid in proportion to their work: k_i = floor(G W_i / W_large)
-// blocks (at most kMaxTeam, and at least kMinTeamRows rows, 4 per thread, a
-// member), so that the teams end at about the same time; a system left with
-// fewer than two blocks joins the others in the work queue, largest first,
-// which the blocks no team holds take from the start and every team's
-// blocks take once their system is done.  (Measured on the 256-system
-// ensemble: teams above 2T of ceil(W_i / T) blocks beside blocks reserved
-// for the queue kept only 61% of the blocks busy over the launch, since the
-// queue's small systems ran out long before the teams' systems: 4.34 s.)
+// block's fair share is T = sum W / G.  A system above T / 2 gets a team of
+// ceil(2 W_i / T) blocks (at most kMaxTeam, and at least kMinTeamRows rows,
+// 4 per thread, a member); the others go to the work queue, largest first.
+// The queue keeps the blocks its own work needs (ceil(W_queue / T)), and the
+// teams are scaled down if they would take more than the rest.  The blocks no
+// team holds take from the queue from the start, and every team's blocks
+// once their system is done.  Measured on the 256-system ensemble (FP64):
+//   teams above 2T of ceil(W_i / T) blocks                      4.34 s
+//   this rule                                                   3.96-4.02 s
+//   this rule without the queue's reserve                       4.32 s
+//   teams sharing the whole grid, k_i = floor(G W_i / W_large)  4.25 s
+// In every plan the teams' systems end between about 2 and 3.9 s: W_i
+// predicts a team's time only roughly, and about 60% of the blocks are busy
+// over the launch on average.
 static void plan_teams(const std::vector<BatchDesc>& hd, int G, std::vector<TeamPlan>& teams,
                        std::vector<int>& order) {
     const int nsys = (int)hd.size();
@@ -490,51 +494,35 @@ static void plan_teams(const std::vector<BatchDesc>& hd, int G, std::vector<Team
     teams.clear();
     order.clear();
     const double T = total / std::max(G, 1);
-    constexpr int kPlan = 1;     // 0 proportional, 1 share with queue reserve, 2 share, no reserve
-    if (kPlan == 0) {
-        double wl = 0.0;
-        for (int i : idx)
-            if (T > 0.0 && w[i] > 0.5 * T) wl += w[i];
-        for (int i : idx) {
-            int k = 1;
-            if (T > 0.0 && w[i] > 0.5 * T && wl > 0.0) {
-                k = (int)std::min<double>(kMaxTeam, std::floor((double)G * w[i] / wl));
-                k = (int)std::min<int64_t>(k, std::max<int64_t>(1, hd[i].n / kMinTeamRows));
-            }
-            if (k >= 2) teams.push_back(TeamPlan{i, 0, k, 0});
-            else order.push_back(i);
+    double wq = 0.0;
+    long long sumk = 0;
+    for (int i : idx) {
+        int k = T > 0.0 && w[i] > 0.5 * T
+                    ? (int)std::min<double>(kMaxTeam, std::ceil(2.0 * w[i] / T))
+                    : 1;
+        k = (int)std::min<int64_t>(k, std::max<int64_t>(1, hd[i].n / kMinTeamRows));
+        if (k >= 2) {
+            teams.push_back(TeamPlan{i, 0, k, 0});
+            sumk += k;
+        } else {
+            order.push_back(i);
+            wq += w[i];
         }
-    } else {
-        double wq = 0.0;
-        long long sumk = 0;
-        for (int i : idx) {
-            int k = T > 0.0 && w[i] > 0.5 * T
-                        ? (int)std::min<double>(kMaxTeam, std::ceil(2.0 * w[i] / T))
-                        : 1;
-            k = (int)std::min<int64_t>(k, std::max<int64_t>(1, hd[i].n / kMinTeamRows));
-            if (k >= 2) {
-                teams.push_back(TeamPlan{i, 0, k, 0});
-                sumk += k;
-            } else {
-                order.push_back(i);
-                wq += w[i];
-            }
+    }
+    const int queue_blocks = T > 0.0 ? (int)std::ceil(wq / T) : G;
+    const int avail = std::max(0, G - std::min(G, queue_blocks));
+    if (sumk > avail) {
+        // scale the teams down; a team of one becomes a queue entry again
+        const double f = (double)avail / (double)sumk;
+        std::vector<TeamPlan> kept;
+        std::vector<int> back;
+        for (const TeamPlan& t : teams) {
+            const int k = (int)std::floor(t.k * f);
+            if (k >= 2) kept.push_back(TeamPlan{t.sys, 0, k, 0});
+            else back.push_back(t.sys);
         }
-        const int queue_blocks = kPlan == 2 ? 0 : (T > 0.0 ? (int)std::ceil(wq / T) : G);
-        const int avail = std::max(0, G - std::min(G, queue_blocks));
-        if (sumk > avail) {
-            // scale the teams down; a team of one becomes a queue entry again
-            const double f = (double)avail / (double)sumk;
-            std::vector<TeamPlan> kept;
-            std::vector<int> back;
-            for (const TeamPlan& t : teams) {
-                const int k = (int)std::floor(t.k * f);
-                if (k >= 2) kept.push_back(TeamPlan{t.sys, 0, k, 0});
-                else back.push_back(t.sys);
-            }
-            teams.swap(kept);
-            order.insert(order.begin(), back.begin(), back.end());
-        }
+        teams.swap(kept);
+        order.insert(order.begin(), back.begin(), back.end());
     }
     int first = 0;
     for (TeamPlan& t : teams) {
