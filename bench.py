@@ -119,7 +119,11 @@ def loop_name(tf: dict) -> str:
         kname = {"single_reduction": "k_cluster_cg1 (whole Jacobi-PCG solve in one thread-block "
                                      "cluster, Chronopoulos-Gear recurrences)",
                  "pipelined": "k_cluster_cgp (whole Jacobi-PCG solve in one thread-block "
-                              "cluster, pipelined Ghysels-Vanroose recurrences)"}.get(
+                              "cluster, pipelined Ghysels-Vanroose recurrences)",
+                 "s_step2": "k_cluster_cgs<2> (whole Jacobi-PCG solve in one thread-block "
+                            "cluster, s-step CG, s = 2)",
+                 "s_step3": "k_cluster_cgs<3> (whole Jacobi-PCG solve in one thread-block "
+                            "cluster, s-step CG, s = 3)"}.get(
             tf.get("cluster_recurrence"),
             "k_cluster_cg (whole Jacobi-PCG solve in one thread-block cluster)")
     elif tf["stream_single_reduction"]:
@@ -182,8 +186,6 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="default line only: skip the config 0 latency, config 3 ensemble and "
                          "config 4 chain summaries")
-    ap.add_argument("--cpu-seconds", type=float, default=10.0,
-                    help="seconds of multi-threaded oracle PCG in the CPU baseline sample")
     ap.add_argument("--batch", type=int, default=0,
                     help="ensemble mode: this many systems of log-uniform 2k-500k cells, "
                          "batched solve vs a loop of single solves (prints its own line)")
@@ -346,6 +348,41 @@ def cpu_baseline(problem, b, seconds: float = 10.0) -> dict:
                       f"loops on {threads} threads, same {nt}-cell system",
             "pcg_only_cell_iters_per_s": nt * st.iters / (t3 - t2),
             "single_thread_oracle_pcg_cell_iters_per_s": nt * st1.iters / (t4 - t3)}
+
+
+def cpu_solve_to_tolerance(problem, b, rtol: float, ref_rtol: float = 1e-13):
+    """The CPU baseline on the whole workload, timed to tolerance: the
+    oracle's assembly and its Jacobi-PCG with OpenMP parallel loops on all the
+    host's cores to rtol (value: cells x iterations / (assembly + solve)
+    time, the GPU line's metric), then, untimed, the same PCG continued from
+    that solution to ref_rtol: the reference solution against which the GPU
+    solutions' errors are reported.  Returns (baseline dict, reference x)."""
+    import oracle
+    t0 = time.perf_counter()
+    A = oracle.assemble_problem(problem)
+    t1 = time.perf_counter()
+    nt = problem.mesh.nt
+    x, st = oracle.pcg_jacobi_omp(A, b, rtol=rtol, maxit=200000)
+    t2 = time.perf_counter()
+    xr, st_ref = oracle.pcg_jacobi_omp(A, b, x0=x, rtol=ref_rtol, maxit=200000)
+    t3 = time.perf_counter()
+    threads = oracle.omp_threads()
+    one_iters = max(5, min(st.iters, 200) // threads)
+    _, st1 = oracle.pcg(A, b, rtol=0.0, maxit=one_iters, precond=oracle.PC_JACOBI,
+                        raise_on_error=False)
+    t4 = time.perf_counter()
+    out = {"value": nt * st.iters / (t2 - t0), "unit": UNIT, "cores": threads,
+           "host_cores": host_cores(), "kind": "oracle",
+           "sample": f"the whole workload to tolerance: oracle assembly ({t1 - t0:.2f} s, single "
+                     f"thread) + Jacobi-PCG to rtol {rtol:g} ({st.iters} iterations, "
+                     f"{t2 - t1:.2f} s) with OpenMP parallel loops on {threads} threads, "
+                     f"{nt}-cell system",
+           "time_to_rtol_s": t2 - t0, "iters": st.iters, "rel_res": st.rel_res,
+           "pcg_only_cell_iters_per_s": nt * st.iters / (t2 - t1),
+           "single_thread_oracle_pcg_cell_iters_per_s": nt * st1.iters / (t4 - t3),
+           "reference_solution": {"rtol": ref_rtol, "extra_iters": st_ref.iters,
+                                  "rel_res": st_ref.rel_res, "seconds": t3 - t2}}
+    return out, xr
 
 
 def run_reference(args):
@@ -634,6 +671,8 @@ def latency_summary(n: int, rtol: float, reps: int = 5) -> dict:
     out = {"workload": f"centred-block lattice n={n}", "cells": m.nt, "rtol": rtol}
     for name, path in (("tuned", cps.PATH_AUTO), ("cluster_1red", cps.PATH_CLUSTER_1RED),
                        ("cluster_pipelined", cps.PATH_CLUSTER_PIPE),
+                       ("cluster_s_step2", cps.PATH_CLUSTER_SSTEP2),
+                       ("cluster_s_step3", cps.PATH_CLUSTER_SSTEP3),
                        ("cluster", cps.PATH_CLUSTER), ("stream_1red", cps.PATH_STREAM_1RED),
                        ("stream", cps.PATH_STREAM), ("persistent_1red", cps.PATH_PERSISTENT_1RED)):
         try:
@@ -1119,7 +1158,7 @@ def main():
     s = ctx.assemble(d["xy"], d["tri"], d["dir"], d["eps"], d["kinv"], cps.PER_VERTEX,
                      cps.KIND_CP2, p.nu, p.dt)
     peak, peak_kind = measured_peaks()
-    variants = {}
+    variants, solutions = {}, {}
     for pc_name, pc in (("jacobi", cps.PC_JACOBI), ("ic0", cps.PC_IC0),
                         ("reduced", cps.PC_REDUCED)):
         try:
@@ -1145,6 +1184,7 @@ def main():
             variants[f"{pc_name}_{prec_name}"] = {
                 "time_to_rtol_s": t, "iters": st.iters, "refinements": st.refinements,
                 "rel_res": st.rel_res, "us_per_iter": 1e6 * t / max(st.iters, 1)}
+            solutions[f"{pc_name}_{prec_name}"] = x.cpu().numpy().copy()
     tuning = {"fp64": s.tuning(cps.FP64), "mixed": s.tuning(cps.MIXED)}
     # each way of running the loop, forced: streaming kernels, the one-launch
     # cluster solve (small systems), the persistent grid-synchronised launch
@@ -1224,7 +1264,14 @@ def main():
                 line[key] = {"error": repr(e)[:400]}
             line[key]["wall_s"] = time.perf_counter() - t0
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(p, b_np, seconds=args.cpu_seconds)
+        # the oracle's PCG on all host cores, timed to tolerance on the whole
+        # workload; its solution (continued to 1e-13) gives every solve
+        # variant's error against the oracle
+        cb, x_oracle = cpu_solve_to_tolerance(p, b_np, args.rtol)
+        line["cpu_baseline"] = cb
+        nref = float(np.linalg.norm(x_oracle))
+        for k, xs in solutions.items():
+            variants[k]["rel_err_vs_oracle"] = float(np.linalg.norm(xs - x_oracle)) / nref
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg is not None:

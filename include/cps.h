@@ -371,6 +371,15 @@ int cps_cp2_kernel_times(cps_sys sys, float* ms);
  *     more vectors in shared memory, a smaller size limit).  Pinned only:
  *     CPS_PATH_AUTO does not take it, since its recurrences lose accuracy
  *     sooner and need more iterations than the per-iteration gain repays;
+ *   CPS_PATH_CLUSTER_SSTEP2, CPS_PATH_CLUSTER_SSTEP3 (FP64 Jacobi only): the
+ *     one-cluster launch with s-step CG, s = 2 or 3 -- per outer step a
+ *     Chebyshev basis of s + 1 powers of the matrix applied to p and s
+ *     applied to r, their Gram matrix in one reduction, then s CG steps on
+ *     the basis coordinates: s + 1 cluster barriers per s iterations instead
+ *     of 2s, for more arithmetic per row (2s + 1 vectors in shared memory,
+ *     a smaller size limit); the stop test runs once per outer step, so the
+ *     count may exceed the single-reduction one by up to s - 1.  Pinned
+ *     only: CPS_PATH_AUTO does not take it;
  *   CPS_PATH_PERSISTENT_1RED, CPS_PATH_PERSISTENT_1RED_L2 (FP64 Jacobi,
  *     and FP64 IC(0) in a two-colour order): the persistent launch with the
  *     single-reduction recurrences -- per iteration one grid reduction and
@@ -396,6 +405,8 @@ int cps_cp2_kernel_times(cps_sys sys, float* ms);
 #define CPS_PATH_PERSISTENT_1RED 9
 #define CPS_PATH_PERSISTENT_1RED_L2 10
 #define CPS_PATH_CLUSTER_PIPE 11
+#define CPS_PATH_CLUSTER_SSTEP2 12
+#define CPS_PATH_CLUSTER_SSTEP3 13
 int cps_set_solver_path(cps_sys sys, int path);
 
 /* Pin the launch shapes of the iteration kernels of one precision instead of

@@ -31,6 +31,7 @@ PATH_AUTO, PATH_STREAM, PATH_CLUSTER, PATH_PERSISTENT, PATH_STREAM_L2, PATH_PERS
     0, 1, 2, 3, 4, 5)
 PATH_CLUSTER_1RED = 6
 PATH_CLUSTER_PIPE = 11
+PATH_CLUSTER_SSTEP2, PATH_CLUSTER_SSTEP3 = 12, 13
 PATH_STREAM_1RED, PATH_STREAM_1RED_L2 = 7, 8
 PATH_PERSISTENT_1RED, PATH_PERSISTENT_1RED_L2 = 9, 10
 BATCH_ONE_LAUNCH, BATCH_GRAPH = 0, 1

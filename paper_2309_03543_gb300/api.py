@@ -154,7 +154,8 @@ class System:
                        "cps_get_gear_shape")
         return {"unroll": list(u), "grid": list(g), "block": list(bl),
                 "cluster": bool(f[0]),
-                "cluster_recurrence": (None, "textbook", "single_reduction", "pipelined")[f[0]],
+                "cluster_recurrence": (None, "textbook", "single_reduction", "pipelined", "s_step2",
+                                       "s_step3")[f[0]],
                 "l2_window": ("none", "matrix", "vectors", "vectors5")[f[1]],
                 "persistent": bool(f[2]), "reduced_persistent": bool(f[3]),
                 "reduced_l2_window": ("none", "matrix", "vectors")[f[4]],
@@ -174,7 +175,7 @@ class System:
 
     def set_solver_path(self, path: int):
         """PATH_AUTO, PATH_STREAM, PATH_CLUSTER, PATH_CLUSTER_1RED, PATH_CLUSTER_PIPE,
-        PATH_PERSISTENT, PATH_STREAM_L2, PATH_PERSISTENT_L2, PATH_STREAM_1RED,
+        PATH_CLUSTER_SSTEP2, PATH_CLUSTER_SSTEP3, PATH_PERSISTENT, PATH_STREAM_L2, PATH_PERSISTENT_L2, PATH_STREAM_1RED,
         PATH_STREAM_1RED_L2, PATH_PERSISTENT_1RED or PATH_PERSISTENT_1RED_L2 for
         FP64 Jacobi (and reduced-system) solves."""
         self.ctx.check(self.ctx.lib.cps_set_solver_path(self.handle, path), "cps_set_solver_path")

@@ -304,8 +304,13 @@ int cps_set_solver_path(cps_sys sys, int path) {
         t.red_path = 0;
         t.red_win = 2;
     } else if (path == CPS_PATH_CLUSTER || path == CPS_PATH_CLUSTER_1RED ||
-               path == CPS_PATH_CLUSTER_PIPE) {
-        const int var = path == CPS_PATH_CLUSTER_PIPE ? 2 : (path == CPS_PATH_CLUSTER_1RED ? 1 : 0);
+               path == CPS_PATH_CLUSTER_PIPE || path == CPS_PATH_CLUSTER_SSTEP2 ||
+               path == CPS_PATH_CLUSTER_SSTEP3) {
+        const int var = path == CPS_PATH_CLUSTER_SSTEP3   ? 4
+                        : path == CPS_PATH_CLUSTER_SSTEP2 ? 3
+                        : path == CPS_PATH_CLUSTER_PIPE   ? 2
+                        : path == CPS_PATH_CLUSTER_1RED   ? 1
+                                                          : 0;
         if (sys->nt > cps::cluster_max_rows(sys->ctx, var)) {
             cps::set_error(sys->ctx, "set_solver_path: system too large for one cluster");
             return CPS_ERR_ARG;

@@ -26,6 +26,7 @@
 // Same iterates as the textbook recurrence in exact arithmetic; one barrier
 // fewer per iteration for the latency-bound small systems this path serves.
 #include "cps_internal.cuh"
+#include "exact_sum.cuh"
 
 #include <cooperative_groups.h>
 
@@ -671,20 +672,355 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_cluster_cgp(ClusterArgs 
     cluster.sync();         // no CTA leaves while others may still read its memory
 }
 
+
+// s-step variant (s inner iterations per outer step; the s-step CG of
+// Chronopoulos and Gear, in the communication-avoiding form that carries the
+// coefficients of the iterates in a Krylov basis).  Per outer step:
+//   basis  V = [P_0 .. P_s, R_0 .. R_{s-1}], P_k = T_k(N) p, R_k = T_k(N) r,
+//          with N = Ahat - I (the scaled off-diagonals) and T_k the Chebyshev
+//          polynomials (T_0 = 1, T_1 = z, T_{k+1} = 2 z T_k - T_{k-1}): the
+//          spectrum of N lies in [-1, 1] (Ahat is SPD with unit diagonal and
+//          2I - Ahat is diagonally dominant), so every basis vector stays of
+//          the size of p and r; s sweeps, one cluster barrier before each;
+//   Gram   G = V^T V (and ||S r||^2 for the stop test) from the last sweep,
+//          one exact block sum and one cluster barrier;
+//   inner  s CG steps on the coefficient vectors (length m = 2s + 1) with
+//          Ahat V = V B on the columns that have an image in the basis:
+//          B e_{P_0} = e_{P_0} + e_{P_1}, B e_{P_k} = (e_{P_{k-1}} + e_{P_{k+1}})/2
+//          + e_{P_k}, and the same in the R block; warp 0 of every CTA, one
+//          lane per coefficient, identical in every CTA;
+//   update p = V p', r = V r', y += V y' (row-local).
+// s + 1 cluster barriers per s iterations (the single-reduction solve: 2s).
+// The iterates are those of CG in exact arithmetic; the stop test runs once
+// per outer step, on ||S r|| of the residual at its start.
+constexpr int kSStepThreads = 512;   // <= 128 registers a thread for the Gram sums
+
+template <int SS>
+struct SStep {
+    static constexpr int M = 2 * SS + 1;        // basis vectors
+    static constexpr int NG = M * (M + 1) / 2;  // Gram entries, upper triangle
+    static constexpr int QSR = NG;              // ||S R_0||^2
+    static constexpr int QB = NG + 1;           // ||b||^2 (set-up)
+    static constexpr int NQ = NG + 2;
+    static_assert(NQ <= 32, "one lane per reduced quantity in the scalar stage");
+};
+
+// Index of Gram entry (i, j), i <= j, in the upper triangle stored row by row.
+__host__ __device__ constexpr int gram_index(int i, int j, int M) {
+    return i * M - i * (i - 1) / 2 + (j - i);
+}
+
+template <int M>
+__host__ __device__ constexpr size_t sstep_row_bytes() {
+    return (size_t)(3 + 2 + M) * sizeof(double) + 3 * sizeof(int32_t);
+}
+
+// Exact, order-independent sum over the CTA's warps of v[0..NV) (integer
+// sums of the values aligned to each quantity's largest exponent in the CTA,
+// exact_sum.cuh); totals into tot[0..NV) in shared memory.  FP64 adds would
+// cost 16 SM clocks a warp instruction on GB300's FP64 pipe.
+template <int NV>
+__device__ __forceinline__ void cta_sum_exact(const double (&v)[NV], double* tot) {
+    __shared__ int s_e[NV][32];
+    __shared__ long long s_w[NV][32];
+    __shared__ int s_eb[NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const int em = __reduce_max_sync(0xffffffffu, align_exp(v[k]));
+        if (lane == 0) s_e[k][warp] = em;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const int E = __reduce_max_sync(0xffffffffu, lane < W ? s_e[k][lane] : 1);
+        const long long w = warp_sum_fixed<52>(align_fixed(v[k], E, 1));
+        if (lane == 0) {
+            s_w[k][warp] = w;
+            if (warp == 0) s_eb[k] = E;
+        }
+    }
+    __syncthreads();
+    for (int k = warp; k < NV; k += W) {
+        const long long T = warp_sum_fixed<57>(lane < W ? s_w[k][lane] : 0LL);
+        if (lane == 0) tot[k] = fixed_to_double(T, s_eb[k], 1);
+    }
+    __syncthreads();
+}
+
+// Sum of v over lanes 0..7, returned to every lane of the warp.
+__device__ __forceinline__ double sum8(double v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    return __shfl_sync(0xffffffffu, v, 0);
+}
+
+template <int SS>
+__global__ void __launch_bounds__(kSStepThreads, 1) k_cluster_cgs(ClusterArgs A) {
+    using Q = SStep<SS>;
+    constexpr int M = Q::M;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int C = (int)cluster.num_blocks();
+    const int rank = (int)cluster.block_rank();
+    const int R = A.rows;
+    const int64_t n = A.n;
+    const int64_t r0 = (int64_t)rank * R;
+    const int nloc = (int)((r0 + R <= n) ? R : (n > r0 ? n - r0 : 0));
+
+    // a [3][R], S, y, then the basis V [M][R] (P_0..P_s, R_0..R_{s-1}),
+    // then col [3][R] int32 packed (rank << 16) | local
+    extern __shared__ __align__(16) unsigned char smem[];
+    double* a_s = reinterpret_cast<double*>(smem);
+    double* s_s = a_s + 3 * R;
+    double* y_s = s_s + R;
+    double* V = y_s + R;
+    int32_t* c_s = reinterpret_cast<int32_t*>(V + M * R);
+    double* P0 = V;
+    double* R0 = V + (SS + 1) * R;
+    __shared__ double red[Q::NQ][16];   // red[k][c]: quantity k of CTA c
+    __shared__ double tot[Q::NQ];
+    __shared__ double coef[3][M];       // new p, new r, y increment (basis coordinates)
+    __shared__ int s_stop, s_nin;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < nloc; i += blockDim.x) {
+        const int64_t e = r0 + i;
+        for (int j = 0; j < 3; ++j) {
+            a_s[j * R + i] = A.a[j * n + e];
+            const int32_t c = A.col[j * n + e];
+            const int cr = c / R;
+            c_s[j * R + i] = (cr << 16) | (c - cr * R);
+        }
+        const double se = A.s[e];
+        s_s[i] = se;
+        y_s[i] = se * A.x[e];
+    }
+    cluster.sync();
+    auto gather = [&](const double* base, int32_t packed) -> double {
+        const int cr = packed >> 16, li = packed & 0xFFFF;
+        if (cr == rank) return base[li];
+        return cluster.map_shared_rank(const_cast<double*>(base), cr)[li];
+    };
+    // this CTA's totals tot[0..nq) go to slots [q0 + k][rank] of every CTA
+    auto push = [&](int q0, int nq) {
+        for (int t = tid; t < nq * C; t += blockDim.x) {
+            const int k = t / C, c = t - k * C;
+            cluster.map_shared_rank(&red[q0 + k][0], c)[rank] = tot[k];
+        }
+    };
+
+    // r = S^-1 b - Ahat y, p = r; ||b||^2
+    {
+        double v1[1] = {0.0};
+        for (int i = tid; i < nloc; i += blockDim.x) {
+            double ay = y_s[i];
+            for (int j = 0; j < 3; ++j) ay = fma(a_s[j * R + i], gather(y_s, c_s[j * R + i]), ay);
+            const double be = A.b[r0 + i];
+            const double re = be / s_s[i] - ay;
+            P0[i] = re;
+            R0[i] = re;
+            v1[0] = fma(be, be, v1[0]);
+        }
+        cta_sum_exact<1>(v1, tot);
+        push(Q::QB, 1);
+    }
+
+    // B of the coefficient space, row of this lane: (B x)_i = bcm x_{i-1} +
+    // bc0 x_i + bcp x_{i+1}, within the lane's block (P or R); column k of a
+    // block has an image in the basis for k <= K (P: s - 1, R: s - 2)
+    double bcm = 0.0, bc0 = 0.0, bcp = 0.0;
+    if (lane < M) {
+        const bool inP = lane <= SS;
+        const int k = inP ? lane : lane - (SS + 1);
+        const int K = inP ? SS - 1 : SS - 2;
+        if (k >= 1 && k - 1 <= K) bcm = (k == 1) ? 1.0 : 0.5;
+        if (k <= K) bc0 = 1.0;
+        if (k + 1 <= K) bcp = 0.5;
+    }
+    // run scalars, held by warp 0 of every CTA (identical everywhere)
+    double gam = 0.0, bnorm2 = 0.0, rnorm2 = 0.0, thresh2 = 0.0;
+    long long it = 0;
+    int status = CPS_OK;
+    bool first = true;
+    for (;;) {
+        cluster.sync();     // P_0, R_0 complete everywhere; the last step's slots read
+#pragma unroll
+        for (int k = 1; k <= SS; ++k) {
+            if (k > 1) cluster.sync();      // P_{k-1}, R_{k-1} complete everywhere
+            const double* Pp = V + (k - 1) * R;
+            const double* Rp = R0 + (k - 1) * R;
+            double* Pk = V + k * R;
+            double* Rk = R0 + k * R;
+            double g[Q::NG + 1];
+            if (k == SS) {
+#pragma unroll
+                for (int q = 0; q <= Q::NG; ++q) g[q] = 0.0;
+            }
+            for (int i = tid; i < nloc; i += blockDim.x) {
+                double np = 0.0, nr = 0.0;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const double aj = a_s[j * R + i];
+                    const int32_t pk = c_s[j * R + i];
+                    np = fma(aj, gather(Pp, pk), np);
+                    if (k <= SS - 1) nr = fma(aj, gather(Rp, pk), nr);
+                }
+                const double pv = (k == 1) ? np : fma(2.0, np, -V[(k - 2) * R + i]);
+                Pk[i] = pv;
+                if (k <= SS - 1) Rk[i] = (k == 1) ? nr : fma(2.0, nr, -R0[(k - 2) * R + i]);
+                if (k == SS) {
+                    double vv[M];
+#pragma unroll
+                    for (int c = 0; c < M; ++c) vv[c] = (c == SS) ? pv : V[c * R + i];
+#pragma unroll
+                    for (int a = 0; a < M; ++a)
+#pragma unroll
+                        for (int b2 = a; b2 < M; ++b2)
+                            g[gram_index(a, b2, M)] = fma(vv[a], vv[b2], g[gram_index(a, b2, M)]);
+                    const double t = s_s[i] * vv[SS + 1];
+                    g[Q::NG] = fma(t, t, g[Q::NG]);
+                }
+            }
+            if (k == SS) {
+                cta_sum_exact<Q::NG + 1>(g, tot);
+                push(0, Q::NG + 1);
+            }
+        }
+        cluster.sync();     // every CTA's Gram partials in place
+        if (warp == 0) {
+            double tq = 0.0;
+            if (lane < Q::NQ)
+                for (int c = 0; c < C; ++c) tq += red[lane][c];   // rank order everywhere
+            if (lane < Q::NQ) tot[lane] = tq;
+            __syncwarp();
+            if (first) {
+                bnorm2 = tot[Q::QB];
+                thresh2 = A.rtol * A.rtol * bnorm2;
+            }
+            rnorm2 = tot[Q::QSR];
+            int halt = (bnorm2 == 0.0 || rnorm2 <= thresh2 || it >= A.max_iter) ? 1 : 0;
+            double gr[M];
+#pragma unroll
+            for (int j = 0; j < M; ++j)
+                gr[j] = lane < M ? tot[gram_index(min(lane, j), max(lane, j), M)] : 0.0;
+            double pc = lane == 0 ? 1.0 : 0.0;          // p' = e_{P_0}
+            double rc = lane == SS + 1 ? 1.0 : 0.0;     // r' = e_{R_0}
+            double yc = 0.0;
+            double grc = lane < M ? gr[SS + 1] : 0.0;   // G r'
+            gam = tot[gram_index(SS + 1, SS + 1, M)];   // r.r
+            if (!halt && !(gam > 0.0 && isfinite(gam))) halt = 1;
+            int nin = 0;
+            const long long room = A.max_iter - it;
+            for (int j = 0; j < SS && !halt && j < room; ++j) {
+                const double pm = __shfl_up_sync(0xffffffffu, pc, 1);
+                const double pp = __shfl_down_sync(0xffffffffu, pc, 1);
+                const double qc = fma(bcp, pp, fma(bcm, pm, bc0 * pc));   // B p'
+                double u = 0.0;                                             // G B p'
+#pragma unroll
+                for (int c = 0; c < M; ++c) u = fma(gr[c], __shfl_sync(0xffffffffu, qc, c), u);
+                const double d = sum8(pc * u);                              // p.Ahat p
+                if (!(d > 0.0) || !isfinite(d)) {
+                    // on the first step of the run the matrix is not SPD;
+                    // later, a difference that lost its digits at the FP64
+                    // floor: stop and let the true residual decide
+                    halt = (it == 0 && j == 0) ? 2 : 1;
+                    break;
+                }
+                const double al = gam / d;
+                yc = fma(al, pc, yc);
+                rc = fma(-al, qc, rc);
+                grc = fma(-al, u, grc);
+                ++nin;
+                const double gn = sum8(rc * grc);                           // r.r
+                if (!(gn > 0.0) || !isfinite(gn)) {
+                    halt = 1;
+                    break;
+                }
+                const double be = gn / gam;
+                gam = gn;
+                pc = fma(be, pc, rc);
+            }
+            it += nin;
+            if (!halt && it >= A.max_iter) halt = 1;
+            if (lane < M) {
+                coef[0][lane] = pc;
+                coef[1][lane] = rc;
+                coef[2][lane] = yc;
+            }
+            if (lane == 0) {
+                s_stop = halt;
+                s_nin = nin;
+            }
+        }
+        __syncthreads();
+        first = false;
+        if (s_stop == 2) status = CPS_ERR_NOT_SPD;
+        if (s_nin > 0)
+            for (int i = tid; i < nloc; i += blockDim.x) {
+                double pn = 0.0, rn = 0.0, dy = 0.0;
+#pragma unroll
+                for (int c = 0; c < M; ++c) {
+                    const double vc = V[c * R + i];
+                    pn = fma(coef[0][c], vc, pn);
+                    rn = fma(coef[1][c], vc, rn);
+                    dy = fma(coef[2][c], vc, dy);
+                }
+                P0[i] = pn;
+                R0[i] = rn;
+                y_s[i] += dy;
+            }
+        if (s_stop) break;
+    }
+    for (int i = tid; i < nloc; i += blockDim.x) A.y_out[r0 + i] = y_s[i];
+    if (rank == 0 && tid == 0) {
+        CgState* st = A.st;
+        st->rho = gam;
+        st->bnorm2 = bnorm2;
+        st->thresh2 = thresh2;
+        st->rnorm2 = rnorm2;
+        st->iter = it;
+        st->max_iter = A.max_iter;
+        st->status = status;
+        st->done = 2;
+        st->alpha = 0.0;
+        st->beta = 0.0;
+    }
+    cluster.sync();         // no CTA leaves while others may still read its memory
+}
+
 }  // namespace
 
-// The cluster kernel of a variant: 0 textbook, 1 single reduction, 2 pipelined.
+// The cluster kernel of a variant: 0 textbook, 1 single reduction, 2 pipelined,
+// 3 s-step with s = 2, 4 s-step with s = 3.
 static void (*cluster_kernel(int variant))(ClusterArgs) {
-    return variant == 2 ? k_cluster_cgp : (variant == 1 ? k_cluster_cg1 : k_cluster_cg);
+    switch (variant) {
+        case 1: return k_cluster_cg1;
+        case 2: return k_cluster_cgp;
+        case 3: return k_cluster_cgs<2>;
+        case 4: return k_cluster_cgs<3>;
+        default: return k_cluster_cg;
+    }
 }
 
 static size_t cluster_row_bytes(int variant) {
-    return variant == 2 ? kRowBytes2 : (variant == 1 ? kRowBytes1 : kRowBytes);
+    switch (variant) {
+        case 1: return kRowBytes1;
+        case 2: return kRowBytes2;
+        case 3: return sstep_row_bytes<SStep<2>::M>();
+        case 4: return sstep_row_bytes<SStep<3>::M>();
+        default: return kRowBytes;
+    }
 }
 
 static size_t cluster_smem_for(int variant, int R) {
-    return variant == 2 ? cluster2_smem_bytes(R)
-                        : (variant == 1 ? cluster1_smem_bytes(R) : cluster_smem_bytes(R));
+    switch (variant) {
+        case 1: return cluster1_smem_bytes(R);
+        case 2: return cluster2_smem_bytes(R);
+        case 3:
+        case 4: return ((size_t)R * cluster_row_bytes(variant) + 15) / 16 * 16;
+        default: return cluster_smem_bytes(R);
+    }
 }
 
 // Dynamic shared memory a CTA of the cluster kernel may use on this device:
@@ -705,7 +1041,8 @@ static size_t cluster_dyn_smem_limit(int dev, int variant) {
 }
 
 // Largest system the cluster path (variant 0 textbook, 1 single reduction,
-// 2 pipelined) takes on this GPU (0: not available).
+// 2 pipelined, 3 and 4 s-step with s = 2 and 3) takes on this GPU (0: not
+// available).
 int64_t cluster_max_rows(cps_ctx ctx, int variant) {
     const size_t lim = cluster_dyn_smem_limit(ctx->device, variant);
     const size_t fixed = kRedBufBytes + 16;
@@ -718,8 +1055,8 @@ int64_t cluster_max_rows(cps_ctx ctx, int variant) {
 // scaled iterate in y and the final scalars in s->st (done = 2).
 int cluster_solve(cps_sys s, const double* b, const double* x, double* y, double rtol,
                   long long max_iter, cudaStream_t stream, int variant) {
-    static std::atomic<bool> configured[3][64];   // zero-initialised (static storage)
-    variant = (variant == 1 || variant == 2) ? variant : 0;
+    static std::atomic<bool> configured[5][64];   // zero-initialised (static storage)
+    variant = (variant >= 1 && variant <= 4) ? variant : 0;
     void (*kern)(ClusterArgs) = cluster_kernel(variant);
     const int64_t n = s->nt;
     int csize = 16;
@@ -756,8 +1093,8 @@ int cluster_solve(cps_sys s, const double* b, const double* x, double* y, double
         cfg.gridDim = dim3(csize, 1, 1);
         // one row per thread where the rows allow (fewer threads: cheaper
         // block reductions); at least 4 warps for the 3-quantity sums
-        const int threads =
-            R >= kClusterThreads ? kClusterThreads : (R < 128 ? 128 : (R + 31) / 32 * 32);
+        const int tmax = variant >= 3 ? kSStepThreads : kClusterThreads;
+        const int threads = R >= tmax ? tmax : (R < 128 ? 128 : (R + 31) / 32 * 32);
         cfg.blockDim = dim3(threads, 1, 1);
         cfg.dynamicSmemBytes = smem;
         cfg.stream = stream;

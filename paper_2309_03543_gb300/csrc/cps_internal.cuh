@@ -77,7 +77,8 @@ struct Tuning {
     int red_win = 0;         // reduced system: persisting L2 window (0 none, 2 r, p, q)
     int pgrid = 0;           // blocks of the persistent launch (0: all that stay resident)
     int red_pgrid = 0;       // the same for the reduced system
-    int cluster_variant = 0; // one-cluster launch: 0 textbook CG, 1 single reduction
+    int cluster_variant = 0; // one-cluster launch: 0 textbook CG, 1 single reduction,
+                             // 2 pipelined, 3 / 4 s-step (s = 2 / 3)
     KCfg kg;                 // single-reduction update kernel (if kg_set; else k[1])
     bool kg_set = false;
     // FP64 IC(0) in a two-colour order: 0 graph-replayed streaming kernels,

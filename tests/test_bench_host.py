@@ -7,6 +7,7 @@ import os
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 
 import oracle
@@ -86,3 +87,18 @@ def test_reference_arm_prints_its_json_line():
     assert line["config"]["workload"] == bench.workload_label(24, 1e-10)
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"],
                            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_cpu_baseline_to_tolerance_reaches_rtol_and_gives_a_reference_solution():
+    """The GPU line's CPU baseline: the oracle's OpenMP PCG timed to rtol on
+    the whole workload, then continued to 1e-13; the reference solution it
+    returns is the oracle's (checked against the single-threaded oracle)."""
+    p = synth.channel_block_problem(24, seed=0)
+    b = synth.rhs(p.mesh, seed=1)
+    out, xr = bench.cpu_solve_to_tolerance(p, b, 1e-10)
+    assert out["kind"] == "oracle" and out["cores"] == oracle.omp_threads()
+    assert out["rel_res"] <= 1e-10 and out["iters"] > 0
+    assert abs(out["value"] - p.mesh.nt * out["iters"] / out["time_to_rtol_s"]) < 1e-6 * out["value"]
+    assert out["reference_solution"]["rel_res"] <= 1e-12
+    xo, _, _ = oracle.solve_problem(p, b, rtol=1e-13)
+    assert np.linalg.norm(xr - xo) / np.linalg.norm(xo) < 1e-9

@@ -60,8 +60,8 @@ def test_tiny_systems_every_path(ctx, name):
     s = _assemble(ctx, p)
     bt = torch.as_tensor(b, device="cuda")
     paths = [cps.PATH_AUTO, cps.PATH_STREAM, cps.PATH_STREAM_1RED, cps.PATH_CLUSTER,
-             cps.PATH_CLUSTER_1RED, cps.PATH_CLUSTER_PIPE, cps.PATH_PERSISTENT,
-             cps.PATH_PERSISTENT_1RED]
+             cps.PATH_CLUSTER_1RED, cps.PATH_CLUSTER_PIPE, cps.PATH_CLUSTER_SSTEP2,
+             cps.PATH_CLUSTER_SSTEP3, cps.PATH_PERSISTENT, cps.PATH_PERSISTENT_1RED]
     for path in paths:
         s.set_solver_path(path)
         x, st = s.solve(bt, rtol=1e-12)
