@@ -9,9 +9,10 @@ set-up) and one FP64 Jacobi-PCG solve to relative residual 1e-10.
 value = PCG cell-iterations per second of the whole step (cells x iterations
 / step time), summed over ranks.  Extra keys report the mixed-precision and
 IC(0) time-to-1e-10, the iteration roofline (the method's 108 B/cell/iter), the
-CPU baseline (the oracle's PCG on all host cores), and compact summaries of the
-other workloads: the 7,938-cell latency case, the 256-system ensemble and the
-50-step differentiable chain.
+CPU baseline (the oracle's PCG on all host cores, timed to tolerance), each
+solve variant's error against the oracle, and compact summaries of the other
+workloads: the 7,938-cell latency case, the 256-system ensemble, the 50-step
+differentiable chain, the CP1 step and the 33.5M-cell sequence.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--n 1024]
     python bench.py --impl reference   # the CPU oracle on the host cores
@@ -184,8 +185,8 @@ def parse():
     ap.add_argument("--impl", default="cps", choices=["cps", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="default line only: skip the config 0 latency, config 3 ensemble and "
-                         "config 4 chain summaries")
+                    help="default line only: skip the config 0 latency, config 3 ensemble, "
+                         "config 4 chain, CP1 step and config 2 sequence summaries")
     ap.add_argument("--batch", type=int, default=0,
                     help="ensemble mode: this many systems of log-uniform 2k-500k cells, "
                          "batched solve vs a loop of single solves (prints its own line)")
@@ -691,6 +692,65 @@ def latency_summary(n: int, rtol: float, reps: int = 5) -> dict:
         if path == cps.PATH_AUTO:
             tf = s.tuning(cps.FP64)
             out["tuned_path"] = loop_name(tf)
+    s.free()
+    ctx.close()
+    return out
+
+
+def sequence_summary(n: int, rtol: float, iters: int = 200) -> dict:
+    """Config 2, compactly: the n x n channel-block lattice (33.5M cells at
+    n = 4096), matrix assembled once.  FP64 Jacobi, mixed Jacobi and FP64
+    IC(0) are timed per iteration over a fixed `iters`-iteration solve (each
+    after one untimed solve that also tunes); the reduced system, the fastest
+    FP64 solver here, is timed to rtol on a second right-hand side,
+    warm-started from the first one's solution.  GB/s are the method's
+    algorithmic bytes (108 B/cell/iter Jacobi, 60.5 mixed inner, 148 IC(0),
+    80 reduced) over the measured copy bandwidth.  `bench.py --sequence`
+    runs the longer sequence of solves to rtol."""
+    import torch
+    import paper_2309_03543_gb300 as cps
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    t0 = time.perf_counter()
+    p = synth.channel_block_problem(n, seed=0)
+    m = p.mesh
+    nt = m.nt
+    rhs = [torch.as_tensor(synth.rhs(m, seed=t), device=dev) for t in range(2)]
+    ctx = cps.Context(0)
+    s = ctx.assemble(m.xy, m.tri, m.dirichlet, p.eps, p.kinv, p.field_loc, cps.KIND_CP2,
+                     p.nu, p.dt)
+    setup = time.perf_counter() - t0
+    peak, peak_kind = measured_peaks()
+    x = torch.zeros(nt, dtype=torch.float64, device=dev)
+    out = {"workload": f"channel-block-aniso lattice n={n}", "cells": nt, "rtol": rtol,
+           "host_setup_s": setup, "peak": peak, "peak_kind": peak_kind,
+           "per_iteration_over": iters}
+    for name, pc, prec, bpc in (("jacobi_fp64", cps.PC_JACOBI, cps.FP64,
+                                 BYTES_PER_CELL_ITER_METHOD),
+                                ("jacobi_mixed", cps.PC_JACOBI, cps.MIXED,
+                                 BYTES_PER_CELL_ITER_MIXED),
+                                ("ic0_fp64", cps.PC_IC0, cps.FP64, BYTES_PER_CELL_ITER_METHOD + 40)):
+        s.set_precond(pc)
+        x.zero_()
+        s.solve(rhs[0], x=x, rtol=rtol, max_iter=iters, precision=prec, check=False)
+        x.zero_()
+        t, st = timed(lambda: s.solve(rhs[0], x=x, rtol=rtol, max_iter=iters, precision=prec,
+                                      check=False)[1], stream)
+        gbs = bpc * nt * st.iters / t / 1e9
+        out[name] = {"iters": st.iters, "us_per_iter": 1e6 * t / max(st.iters, 1),
+                     "bytes_per_cell_iter": bpc, "algorithmic_gbs": gbs, "frac": gbs / peak}
+        if name == "jacobi_fp64":
+            out[name]["path"] = loop_name(s.tuning(cps.FP64))
+    s.set_precond(cps.PC_REDUCED)
+    x.zero_()
+    s.solve(rhs[0], x=x, rtol=rtol, max_iter=iters, check=False)      # tunes its path
+    t, st = timed(lambda: s.solve(rhs[1], x=x, rtol=rtol, check=False)[1], stream)
+    gbs = 80 * nt * st.iters / t / 1e9
+    out["reduced_fp64_to_rtol"] = {
+        "time_to_rtol_s": t, "iters": st.iters, "rel_res": st.rel_res, "status": st.status,
+        "warm_start": "from the solution of a capped solve of the first right-hand side",
+        "us_per_iter": 1e6 * t / max(st.iters, 1), "bytes_per_cell_iter": 80,
+        "algorithmic_gbs": gbs, "frac": gbs / peak}
     s.free()
     ctx.close()
     return out
@@ -1249,13 +1309,15 @@ def main():
     # the other workloads, compactly (each in its own context, after the
     # headline measurement): config 0 latency, config 3 ensemble (batched
     # FP64 and mixed against a loop of FP64 single solves), config 4 chain,
-    # and the CP1 step on the headline lattice (one launch and host sweeps)
+    # the CP1 step on the headline lattice (one launch and host sweeps), and
+    # config 2 (33.5M cells: per-iteration rates, a reduced solve to rtol)
     if rank == 0 and world == 1 and not args.no_extras:
         extras = (("n64_latency", lambda: latency_summary(64, args.rtol)),
                   ("batch", lambda: batch_summary(256, args.rtol, 1, loops=True,
                                                   mixed_loop=False)),
                   ("chain", lambda: chain_summary(512, 50, 1e-8)),
-                  ("cp1_step", lambda: cp1_summary(args.n, 3, 2, 1e-4, args.rtol)))
+                  ("cp1_step", lambda: cp1_summary(args.n, 3, 2, 1e-4, args.rtol)),
+                  ("n4096_sequence", lambda: sequence_summary(4096, args.rtol)))
         for key, fn in extras:
             t0 = time.perf_counter()
             try:

@@ -25,6 +25,10 @@
 //   beta = gamma/gamma_old, alpha = gamma/(delta - beta gamma/alpha_old).
 // Same iterates as the textbook recurrence in exact arithmetic; one barrier
 // fewer per iteration for the latency-bound small systems this path serves.
+//
+// Two more variants, pinned only (described at their kernels): the pipelined
+// (Ghysels-Vanroose) recurrences with one split cluster barrier per
+// iteration, and s-step CG (s = 2, 3) with s + 1 barriers per s iterations.
 #include "cps_internal.cuh"
 #include "exact_sum.cuh"
 
