@@ -225,6 +225,12 @@ def parse():
                     help="graded-mesh mode: FP64 Jacobi and IC(0) solves on the unstructured "
                          "graded Delaunay mesh of this lattice size (900: ~2.0M cells), Morton "
                          "and triangulation numbering (own line)")
+    ap.add_argument("--latency", default="",
+                    help="latency mode: FP64 Jacobi solves of the centred-block lattice of "
+                         "--n vertices a side on the listed ways of running the loop (comma "
+                         "separated: tuned, cluster_1red, cluster_pipelined, cluster_s_step2, "
+                         "cluster_s_step3, cluster, stream_1red, stream, persistent_1red; "
+                         "'all' for every one), own line")
     ap.add_argument("--pin", default="",
                     help="profiling run only: pin the FP64 Jacobi configuration instead of "
                          "tuning it (a profiler's replay skews the tuner), as "
@@ -651,13 +657,14 @@ def run_chain(args):
     print(json.dumps(line), flush=True)
 
 
-def latency_summary(n: int, rtol: float, reps: int = 5) -> dict:
+def latency_summary(n: int, rtol: float, reps: int = 5, names=None) -> dict:
     """Config 0: the centred-block lattice of n x n vertices (7,938 cells at
     n = 64, isotropic Kozeny-Carman, Dirichlet on the right edge), FP64
     Jacobi-PCG to rtol from x = 0, on the tuned path and on each forced path;
     median of `reps` solve times.  At this size the system is cache-resident
     and the loop is latency-bound: the figures are microseconds per
-    iteration, not bandwidth."""
+    iteration, not bandwidth.  names: the subset of paths to run (all if
+    None)."""
     import torch
     import paper_2309_03543_gb300 as cps
     dev = torch.device("cuda", 0)
@@ -676,6 +683,8 @@ def latency_summary(n: int, rtol: float, reps: int = 5) -> dict:
                        ("cluster_s_step3", cps.PATH_CLUSTER_SSTEP3),
                        ("cluster", cps.PATH_CLUSTER), ("stream_1red", cps.PATH_STREAM_1RED),
                        ("stream", cps.PATH_STREAM), ("persistent_1red", cps.PATH_PERSISTENT_1RED)):
+        if names is not None and name not in names:
+            continue
         try:
             s.set_solver_path(path)
         except cps.CpsError:
@@ -1054,6 +1063,11 @@ def main():
         return
     if args.graded:
         run_graded(args)
+        return
+    if args.latency:
+        names = None if args.latency == "all" else args.latency.split(",")
+        print(json.dumps({"latency": latency_summary(args.n, args.rtol, names=names)}),
+              flush=True)
         return
     import torch
     import paper_2309_03543_gb300 as cps
