@@ -1275,9 +1275,7 @@ def main():
                                 ("persistent_1red", cps.PATH_PERSISTENT_1RED),
                                 ("persistent_1red_l2", cps.PATH_PERSISTENT_1RED_L2)):
             if pc == cps.PC_REDUCED and path in (cps.PATH_CLUSTER, cps.PATH_STREAM_1RED,
-                                                 cps.PATH_STREAM_1RED_L2,
-                                                 cps.PATH_PERSISTENT_1RED,
-                                                 cps.PATH_PERSISTENT_1RED_L2):
+                                                 cps.PATH_STREAM_1RED_L2):
                 continue
             if pc == cps.PC_IC0 and path not in (cps.PATH_STREAM, cps.PATH_PERSISTENT_1RED,
                                                  cps.PATH_PERSISTENT_1RED_L2):

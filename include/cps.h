@@ -381,14 +381,16 @@ int cps_cp2_kernel_times(cps_sys sys, float* ms);
  *     count may exceed the single-reduction one by up to s - 1.  Pinned
  *     only: CPS_PATH_AUTO does not take it;
  *   CPS_PATH_PERSISTENT_1RED, CPS_PATH_PERSISTENT_1RED_L2 (FP64 Jacobi,
- *     and FP64 IC(0) in a two-colour order): the persistent launch with the
- *     single-reduction recurrences -- per iteration one grid reduction and
- *     waits on the neighbouring blocks only (Jacobi: one; IC(0): two, in
- *     Eisenstat's form of the preconditioned iteration, which applies the
- *     two-colour IC(0) factor and the matrix in one pass over the matrix,
- *     with the same iterates) -- without / with its vectors in persisting L2
- *     (Jacobi: five, CPS_ERR_ARG when the set-aside cannot hold them; IC(0):
- *     six where they fit, else five, else none).
+ *     FP64 IC(0) in a two-colour order, and the reduced system): the
+ *     persistent launch with the single-reduction recurrences -- per
+ *     iteration one grid reduction and waits on the neighbouring blocks only
+ *     (Jacobi: one; IC(0): two, in Eisenstat's form of the preconditioned
+ *     iteration, which applies the two-colour IC(0) factor and the matrix in
+ *     one pass over the matrix, with the same iterates; reduced system: two,
+ *     around the two halves of the Schur product) -- without / with its
+ *     vectors in persisting L2 (Jacobi and the reduced system: five,
+ *     CPS_ERR_ARG when the set-aside cannot hold them; IC(0): six where they
+ *     fit, else five, else none).
  * FP64 IC(0) in a two-colour order runs on the streaming kernels for every
  * other pin, and CPS_PATH_AUTO times both ways on the first such solve; with
  * more colours it always streams.
@@ -446,18 +448,21 @@ int cps_test_inject(cps_sys sys, int fault);
  * single-reduction recurrences, 3 the pipelined ones), persisting-L2 window (0 none, 1 the
  * matrix, 2 the vectors r, p, q, 3 the five vectors of the single-reduction
  * loop), persistent launch chosen (either recurrence), reduced system:
- * persistent launch chosen, reduced system: window (0 or 2), single-reduction
+ * persistent launch chosen (0 no, 1 textbook recurrences, 2 single-reduction
+ * recurrences), reduced system: window (0, 2, or 3 the five vectors of its
+ * single-reduction loop), single-reduction
  * streaming chosen, single-reduction persistent launch chosen, IC(0):
  * persistent single-reduction launch chosen (0 no, 1 without a window, 2
  * with its first five vectors, 3 with all six in persisting L2)}, flags
  * then taking 8 entries; probe_us (may be
- * NULL, 16 entries) the microseconds per iteration measured for {streaming,
+ * NULL, 18 entries) the microseconds per iteration measured for {streaming,
  * one cluster (the best of its three recurrences), streaming + matrix in L2, persistent, streaming + vectors in
  * L2, persistent + vectors in L2, reduced system: streaming, persistent,
  * streaming + vectors in L2, persistent + vectors in L2, single-reduction
  * streaming, single-reduction streaming + vectors in L2, single-reduction
  * persistent, single-reduction persistent + vectors in L2, IC(0): streaming,
- * persistent single-reduction (the better window)} (0 where not tried; the
+ * persistent single-reduction (the better window), reduced system:
+ * persistent single-reduction, the same + its vectors in L2} (0 where not tried; the
  * persistent figures are the best over the grid sizes tried, the one-cluster
  * figure the better of its two recurrences).
  * The context remembers what the tuner chose per mesh size (cells,

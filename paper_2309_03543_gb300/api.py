@@ -145,7 +145,7 @@ class System:
         g = (ctypes.c_int32 * 3)()
         bl = (ctypes.c_int32 * 3)()
         f = (ctypes.c_int32 * 8)()
-        pr = (ctypes.c_double * 16)()
+        pr = (ctypes.c_double * 18)()
         self.ctx.check(self.ctx.lib.cps_get_tuning(self.handle, precision, u, g, bl, f, pr),
                        "cps_get_tuning")
         gu, gg, gb = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
@@ -158,7 +158,8 @@ class System:
                                        "s_step3")[f[0]],
                 "l2_window": ("none", "matrix", "vectors", "vectors5")[f[1]],
                 "persistent": bool(f[2]), "reduced_persistent": bool(f[3]),
-                "reduced_l2_window": ("none", "matrix", "vectors")[f[4]],
+                "reduced_single_reduction": f[3] == 2,
+                "reduced_l2_window": ("none", "matrix", "vectors", "vectors5")[f[4]],
                 "stream_single_reduction": bool(f[5]),
                 "persistent_single_reduction": bool(f[6]),
                 "ic0_persistent": bool(f[7]),
@@ -171,7 +172,9 @@ class System:
                     "reduced_stream_l2_vectors": pr[8], "reduced_persistent_l2_vectors": pr[9],
                     "stream_1red": pr[10], "stream_1red_l2_vectors": pr[11],
                     "persistent_1red": pr[12], "persistent_1red_l2_vectors": pr[13],
-                    "ic0_stream": pr[14], "ic0_persistent": pr[15]}}
+                    "ic0_stream": pr[14], "ic0_persistent": pr[15],
+                    "reduced_persistent_1red": pr[16],
+                    "reduced_persistent_1red_l2_vectors": pr[17]}}
 
     def set_solver_path(self, path: int):
         """PATH_AUTO, PATH_STREAM, PATH_CLUSTER, PATH_CLUSTER_1RED, PATH_CLUSTER_PIPE,

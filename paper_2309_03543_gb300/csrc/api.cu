@@ -270,6 +270,10 @@ int cps_set_solver_path(cps_sys sys, int path) {
         t.path = 4;
         t.l2win = path == CPS_PATH_PERSISTENT_1RED_L2 ? 3 : 0;
         t.pgrid = 0;
+        t.red_done = true;
+        t.red_path = 2;
+        t.red_win = path == CPS_PATH_PERSISTENT_1RED_L2 ? 3 : 0;
+        t.red_pgrid = 0;
     } else if (path == CPS_PATH_PERSISTENT) {
         t.path_done = true;
         t.path = 2;
@@ -373,7 +377,7 @@ int cps_get_tuning(cps_sys sys, int precision, int32_t* unroll, int32_t* grid, i
         flags[0] = (t.path_done && t.path == 1) ? 1 + t.cluster_variant : 0;
         flags[1] = t.path_done ? t.l2win : 0;
         flags[2] = t.path_done && (t.path == 2 || t.path == 4);
-        flags[3] = t.red_done && t.red_path == 1;
+        flags[3] = t.red_done ? t.red_path : 0;
         flags[4] = t.red_done ? t.red_win : 0;
         flags[5] = t.path_done && t.path == 3;
         flags[6] = t.path_done && t.path == 4;
@@ -384,6 +388,8 @@ int cps_get_tuning(cps_sys sys, int precision, int32_t* unroll, int32_t* grid, i
     if (probe_us) {
         for (int k = 0; k < 6; ++k) probe_us[k] = t.probe_us[k];
         for (int k = 0; k < 4; ++k) probe_us[6 + k] = t.red_probe_us[k];
+        probe_us[16] = t.red_probe_us[4];
+        probe_us[17] = t.red_probe_us[5];
         probe_us[10] = t.probe_us[6];
         probe_us[11] = t.probe_us[7];
         probe_us[12] = t.probe_us[8];

@@ -61,7 +61,8 @@ struct Tuning {
                              // 2 one persistent grid-synchronised launch, 3 graph-replayed
                              // single-reduction kernels, 4 one persistent launch of the
                              // single-reduction recurrences
-    int red_path = 0;        // reduced system: 0 graph-replayed kernels, 1 persistent launch
+    int red_path = 0;        // reduced system: 0 graph-replayed kernels, 1 persistent launch,
+                             // 2 persistent launch of the single-reduction recurrences
     bool red_done = false;
     bool path_done = false;
     int l2win = 0;           // FP64 Jacobi stream path, persisting L2 window: 0 none,
@@ -72,9 +73,12 @@ struct Tuning {
                                                // in L2, single-reduction stream (+ vectors in
                                                // L2), single-reduction persistent (+ vectors
                                                // in L2)
-    double red_probe_us[4] = {0, 0, 0, 0};   // reduced system: stream, persistent, and the
-                                             // same with r, p, q in persisting L2
-    int red_win = 0;         // reduced system: persisting L2 window (0 none, 2 r, p, q)
+    double red_probe_us[6] = {0, 0, 0, 0, 0, 0};   // reduced system: stream, persistent,
+                                             // the same with r, p, q in persisting L2, then
+                                             // persistent single-reduction without and with
+                                             // its five vectors in persisting L2
+    int red_win = 0;         // reduced system: persisting L2 window (0 none, 2 r, p, q,
+                             // 3 r, p, q, y, p1)
     int pgrid = 0;           // blocks of the persistent launch (0: all that stay resident)
     int red_pgrid = 0;       // the same for the reduced system
     int cluster_variant = 0; // one-cluster launch: 0 textbook CG, 1 single reduction,

@@ -1147,13 +1147,16 @@ static int solve_reduced(cps_sys s, const double* b, double* x, double rtol, int
         return CPS_OK;
     };
     // Runs CG from the state k_black_init left, on the graph-replayed kernels
-    // or (pers) in one persistent grid-synchronised launch of pgrid blocks,
-    // with window win (the caller holds its set-aside); state into *hh.
-    auto run_cg = [&](bool pers, int win, int pgrid, CgState* hh) -> int {
-        if (pers) {
-            int rc = persistent_solve(s, 1, A, col, S, y, r, p, q, t, n, nR,
+    // (kind 0) or in one persistent grid-synchronised launch of pgrid blocks
+    // (kind 1 the textbook recurrences, 2 the single-reduction ones, with
+    // s = S p in q and w = S r in p1), with window win (the caller holds its
+    // set-aside); state into *hh.
+    auto run_cg = [&](int kind, int win, int pgrid, CgState* hh) -> int {
+        if (kind) {
+            int rc = persistent_solve(s, kind == 2 ? 4 : 1, A, col, S, y, r, p, q, t, n, nR,
                                       win ? l2_window_base(s, win) : nullptr,
-                                      win ? l2_window_bytes(s, win) : 0, pgrid, stream);
+                                      win ? l2_window_bytes(s, win) : 0, pgrid, stream,
+                                      kind == 2 ? s->wp1 : nullptr);
             if (rc) return rc;
             ++launches;
             return read_state(s, stream, hh);
@@ -1179,19 +1182,21 @@ static int solve_reduced(cps_sys s, const double* b, double* x, double rtol, int
     Tuning& tu = s->tune[CPS_FP64];
     if (!tu.red_done) {
         // time a short run of each way from x = 0 and keep the fastest:
-        // slot 0 graph, 1 persistent, 2 graph + window, 3 persistent + window
-        // (persistent at a few grid sizes)
+        // slot 0 graph, 1 persistent, 2 graph + window, 3 persistent + window,
+        // 4 persistent single-reduction, 5 the same + its five vectors in
+        // persisting L2 (persistent at a few grid sizes)
         const long long probe = nB >= kTuneMinRows ? 256 : 64;
         const bool try_win = nB >= kTuneMinRows && l2_window_fits(s, 2);
+        const bool try_win5 = nB >= kTuneMinRows && l2_window_fits(s, 3);
         struct Cand {
             int slot, win, grid;
         };
-        Cand cands[10];
+        Cand cands[16];
         int nc = 0;
         cands[nc++] = {0, 0, 0};
         if (try_win) cands[nc++] = {2, 2, 0};
-        {
-            const int gmax = persistent_max_grid(s, 1);
+        for (int kind = 1; kind <= 2; ++kind) {
+            const int gmax = persistent_max_grid(s, kind == 2 ? 4 : 1);
             int grids[3] = {gmax, (int)((nB + 8191) / 8192), (int)((nB + 2047) / 2048)};
             for (int i = 0; i < 3; ++i) {
                 const int gi = grids[i] < 1 ? 1 : (grids[i] > gmax ? gmax : grids[i]);
@@ -1199,20 +1204,27 @@ static int solve_reduced(cps_sys s, const double* b, double* x, double rtol, int
                 for (int j = 0; j < i; ++j) dup = dup || grids[j] == gi;
                 grids[i] = gi;
                 if (dup) continue;
-                cands[nc++] = {1, 0, gi};
-                if (try_win) cands[nc++] = {3, 2, gi};
+                if (kind == 1) {
+                    cands[nc++] = {1, 0, gi};
+                    if (try_win) cands[nc++] = {3, 2, gi};
+                } else {
+                    cands[nc++] = {4, 0, gi};
+                    if (try_win5) cands[nc++] = {5, 3, gi};
+                }
             }
         }
         cudaEvent_t e0, e1;
         CPS_CUDA_TRY(s->ctx, cudaEventCreate(&e0));
         CPS_CUDA_TRY(s->ctx, cudaEventCreate(&e1));
-        double per_iter[4] = {0.0, 0.0, 0.0, 0.0};
+        double per_iter[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         double best_t = 0.0;
         Cand best{0, 0, 0};
         int rc = CPS_OK;
+        auto kind_of = [](int slot) { return slot >= 4 ? 2 : (slot & 1); };
         for (int ci = 0; ci < nc && rc == CPS_OK; ++ci) {
             const Cand c = cands[ci];
-            const bool pers = (c.slot & 1) != 0;
+            const int kind = kind_of(c.slot);
+            const bool pers = kind != 0;
             rc = l2_set_aside(s, c.win, stream);
             double us = 0.0;
             for (int rep = 0; rep < 2 && rc == CPS_OK; ++rep) {
@@ -1224,7 +1236,7 @@ static int solve_reduced(cps_sys s, const double* b, double* x, double rtol, int
                 k_black_init<<<g, kBlock, 0, stream>>>(bb, xx, S, A, col, n, nR, y, r, p, 0.0,
                                                        probe, s->partials, s->st);
                 CgState hp{};
-                rc = run_cg(pers, c.win, c.grid, &hp);
+                rc = run_cg(kind, c.win, c.grid, &hp);
                 if (rc == CPS_OK && hp.status != CPS_OK) rc = CPS_ERR_ARG;
                 CPS_CUDA_TRY(s->ctx, cudaEventRecord(e1, stream));
                 CPS_CUDA_TRY(s->ctx, cudaEventSynchronize(e1));
@@ -1252,19 +1264,19 @@ static int solve_reduced(cps_sys s, const double* b, double* x, double rtol, int
         }
         if (rc != CPS_OK) return rc;
         tu.red_done = true;
-        tu.red_path = best.slot & 1;
+        tu.red_path = kind_of(best.slot);
         tu.red_win = best.win;
         tu.red_pgrid = best.grid;
-        for (int c = 0; c < 4; ++c) tu.red_probe_us[c] = per_iter[c];
+        for (int c = 0; c < 6; ++c) tu.red_probe_us[c] = per_iter[c];
         update_cached_tuning(s, CPS_FP64, [&](Tuning& c) {
             c.red_done = true;
             c.red_path = tu.red_path;
             c.red_win = tu.red_win;
             c.red_pgrid = tu.red_pgrid;
-            for (int k = 0; k < 4; ++k) c.red_probe_us[k] = tu.red_probe_us[k];
+            for (int k = 0; k < 6; ++k) c.red_probe_us[k] = tu.red_probe_us[k];
         });
     }
-    const bool pers = tu.red_path == 1;
+    const int kind = tu.red_path;
     const int win = tu.red_win;
     if (win) {
         int rc = l2_set_aside(s, win, stream);
@@ -1279,7 +1291,7 @@ static int solve_reduced(cps_sys s, const double* b, double* x, double rtol, int
                                                s->partials, s->st);
         launches += 2;
         CPS_CUDA_TRY(s->ctx, cudaGetLastError());
-        int rc = run_cg(pers, win, tu.red_pgrid, &h);
+        int rc = run_cg(kind, win, tu.red_pgrid, &h);
         if (rc) return rc;
         total += h.iter;
         status = h.status;

@@ -1161,16 +1161,219 @@ __global__ void __launch_bounds__(kPBlock, 1) k_persistent_reduced(PersistArgs P
     }
 }
 
+// The reduced (black-cell Schur complement) CG with the single-reduction
+// (Chronopoulos-Gear) recurrences, from the state k_black_init left (y_B,
+// r_B, ||b||^2, ||S r||^2): s_B = Schur p_B and w_B = Schur r_B are carried,
+// so that both inner products of an iteration come from one Schur product:
+//   [wait for the halo] t_R = E r_B | post, [wait] w_B = r_B - E^T t_R,
+//   gamma = r.r, delta = w.r (every 8th: ||S r||^2) | one grid reduction:
+//   stop test; first pass alpha = gamma/delta, beta = 0; later beta =
+//   gamma/gamma_old, alpha = gamma/(delta - beta gamma/alpha_old) |
+//   p = r + beta p; s = w + beta s; y += alpha p; r -= alpha s | post
+// Two neighbour waits and one grid reduction per iteration (the textbook
+// reduced loop, k_persistent_reduced, has two reductions), at 9 FP64 FMAs a
+// black row plus 3 a red row.  s lives in q, w in z; p and s start at zero.
+__global__ void __launch_bounds__(kPBlock, 1) k_persistent_reduced1(PersistArgs P) {
+    __shared__ double rbuf[3][kPBlock];
+    // gamma, alpha, beta, ||S r||^2, 1/gamma, 1/(gamma alpha), stop threshold
+    __shared__ double sc[7];
+    __shared__ long long s_max_iter;
+    __shared__ int s_stop;
+    CgState* st = P.st;
+    if (st->done) return;                      // uniform: set before the launch
+    const int64_t n = P.n, nR = P.nR, nB = n - nR;
+    const double* __restrict__ A = P.a;
+    const int32_t* __restrict__ C = P.col;
+    double* __restrict__ p = P.p;
+    double* __restrict__ sv = P.q;
+    double* __restrict__ w = P.z;
+    double* __restrict__ r = P.r;
+    double* __restrict__ y = P.y;
+    double* __restrict__ t = P.t;
+    GridSync* gs = P.gs;
+    const int Rr = (int)rows_per_block(nR), Rb = (int)rows_per_block(nB);
+    const int rlo = (int)blockIdx.x * Rr < nR ? (int)blockIdx.x * Rr : (int)nR;
+    const int rhi = rlo + Rr < nR ? rlo + Rr : (int)nR;
+    const int blo = (int)nR + ((int)blockIdx.x * Rb < nB ? (int)blockIdx.x * Rb : (int)nB);
+    const int bhi = blo + Rb < n ? blo + Rb : (int)n;
+    if (threadIdx.x == 0) {
+        sc[0] = st->rho;
+        sc[1] = 0.0;
+        sc[2] = 0.0;
+        sc[3] = st->rnorm2;
+        sc[4] = 0.0;
+        sc[5] = 0.0;
+        sc[6] = st->thresh2;
+        s_max_iter = st->max_iter;
+        s_stop = 0;
+    }
+    bool ok = true;
+    Epoch ep;
+    ep.target = P.stall ? 1ull : 0ull;
+    // the red phase reads r at black rows, the black phase t at red rows
+    // (slot 0: r updated, slot 1: t computed), as in k_persistent_reduced
+    int dplo, dphi, dtlo, dthi;
+    column_blocks(C, n, rlo, rhi, nR, Rb, &dplo, &dphi);
+    column_blocks(C, n, blo, bhi, 0, Rr, &dtlo, &dthi);
+    bool halo;
+    {
+        const bool wide = dphi - dplo + 1 > kMaxDeps || dthi - dtlo + 1 > kMaxDeps;
+        double wv[1] = {wide ? 1.0 : 0.0};
+        double none[1];
+        int any = 0;
+        ok = grid_allreduce<1, 1>(rbuf, wv, none, any, P.partials, gs, ep,
+                                  [](const double (&tt)[1], double* o, int& f) {
+                                      o[0] = 0.0;
+                                      f = tt[0] > 0.0 ? 1 : 0;
+                                  });
+        halo = any == 0;
+    }
+    // the recurrences start from p = s = 0 (own rows only)
+    for (int64_t e = blo + threadIdx.x; e < bhi; e += kPBlock) {
+        p[e] = 0.0;
+        sv[e] = 0.0;
+    }
+    long long it = 0;
+    while (ok) {
+        if (halo && it > 0) {
+            ok = halo_wait(gs, dplo, dphi, (unsigned long long)it, 0);
+            if (!ok) break;
+        }
+        {
+            double a0[kU], a1[kU], a2[kU];
+            int32_t c0[kU], c1[kU], c2[kU];
+            CPS_B_LOOP(rlo, rhi, kU,
+                (a0[u] = A[e], a1[u] = A[n + e], a2[u] = A[2 * n + e], c0[u] = C[e],
+                 c1[u] = C[n + e], c2[u] = C[2 * n + e]),
+                {
+                    double acc = 0.0;
+                    if (c0[u] != (int32_t)e) acc = fma(a0[u], r[c0[u]], acc);
+                    if (c1[u] != (int32_t)e) acc = fma(a1[u], r[c1[u]], acc);
+                    if (c2[u] != (int32_t)e) acc = fma(a2[u], r[c2[u]], acc);
+                    t[e] = acc;
+                })
+        }
+        if (halo) {
+            halo_post(gs, (unsigned long long)(it + 1), 1);
+            ok = halo_wait(gs, dtlo, dthi, (unsigned long long)(it + 1), 1);
+        } else {
+            ok = grid_barrier(gs, ep);
+        }
+        if (!ok) break;
+        const bool check = ((it + 1) % 8) == 0;
+        double sums[3] = {0.0, 0.0, 0.0};
+        {
+            double re[kUGS], a0[kUGS], a1[kUGS], a2[kUGS];
+            int32_t c0[kUGS], c1[kUGS], c2[kUGS];
+            CPS_B_LOOP(blo, bhi, kUGS,
+                (re[u] = r[e], a0[u] = A[e], a1[u] = A[n + e], a2[u] = A[2 * n + e],
+                 c0[u] = C[e], c1[u] = C[n + e], c2[u] = C[2 * n + e]),
+                {
+                    double v = re[u];
+                    if (c0[u] != (int32_t)e) v = fma(-a0[u], t[c0[u]], v);
+                    if (c1[u] != (int32_t)e) v = fma(-a1[u], t[c1[u]], v);
+                    if (c2[u] != (int32_t)e) v = fma(-a2[u], t[c2[u]], v);
+                    w[e] = v;
+                    sums[0] = fma(re[u], re[u], sums[0]);
+                    sums[1] = fma(v, re[u], sums[1]);
+                    if (check) {
+                        const double tt = P.s[e] * re[u];
+                        sums[2] = fma(tt, tt, sums[2]);
+                    }
+                })
+        }
+        // thread 0, from the totals: the stop test and the step scalars (1/gamma
+        // and 1/(gamma alpha) carried, one divide on the critical path)
+        const long long it0 = it;
+        auto post = [&](const double* tt, bool chk, int& f) {
+            const double g = tt[0], d = tt[1];
+            bool halt = !(g > 0.0) || it0 >= s_max_iter;       // exact solution, budget
+            if (chk) {
+                sc[3] = tt[2];
+                if (tt[2] <= sc[6]) halt = true;
+            }
+            f = halt ? 1 : 0;
+            if (!halt) {
+                const double den = it0 == 0 ? d : fma(-(g * g), sc[5], d);
+                if (!(den > 0.0) || !isfinite(den)) {
+                    // on the run's first pass p.Sp <= 0: not SPD; later, the
+                    // recurrence's difference lost its digits at the FP64
+                    // floor: stop, and let the true residual decide
+                    f = it0 > 0 ? 1 : 2;
+                } else {
+                    const double ig = 1.0 / g;
+                    sc[1] = g / den;
+                    sc[2] = it0 == 0 ? 0.0 : g * sc[4];
+                    sc[4] = ig;
+                    sc[5] = den * ig * ig;
+                }
+            }
+            sc[0] = g;
+        };
+        double none[1];
+        int flag = 0;
+        if (check) {
+            double v3[3] = {sums[0], sums[1], sums[2]};
+            ok = grid_allreduce<3, 1>(rbuf, v3, none, flag, P.partials, gs, ep,
+                                      [&](const double (&tt)[3], double* o, int& f) {
+                                          o[0] = 0.0;
+                                          post(tt, true, f);
+                                      });
+        } else {
+            double v2[2] = {sums[0], sums[1]};
+            ok = grid_allreduce<2, 1>(rbuf, v2, none, flag, P.partials, gs, ep,
+                                      [&](const double (&tt)[2], double* o, int& f) {
+                                          o[0] = 0.0;
+                                          post(tt, false, f);
+                                      });
+        }
+        if (!ok) break;
+        if (flag) {
+            if (threadIdx.x == 0) s_stop = flag;
+            break;
+        }
+        {
+            const double alpha = sc[1], beta = sc[2];
+            double pe[kUG], se[kUG], we[kUG], re[kUG], ye[kUG];
+            CPS_B_LOOP(blo, bhi, kUG,
+                (pe[u] = p[e], se[u] = sv[e], we[u] = w[e], re[u] = r[e], ye[u] = y[e]),
+                {
+                    const double pn = fma(beta, pe[u], re[u]);
+                    const double sn = fma(beta, se[u], we[u]);
+                    p[e] = pn;
+                    sv[e] = sn;
+                    y[e] = fma(alpha, pn, ye[u]);
+                    r[e] = fma(-alpha, sn, re[u]);
+                })
+        }
+        ++it;
+        if (halo) {
+            halo_post(gs, (unsigned long long)it, 0);
+        } else {
+            ok = grid_barrier(gs, ep);
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->iter = it;
+        st->rho = sc[0];
+        st->rnorm2 = sc[3];
+        st->status = ok ? (s_stop == 2 ? CPS_ERR_NOT_SPD : CPS_OK) : CPS_ERR_TIMEOUT;
+        st->done = 2;
+    }
+}
+
 }  // namespace
 
 // The persistent kernel of a solve kind: 0 textbook Jacobi, 1 the reduced
 // system, 2 single-reduction Jacobi, 3 single-reduction IC(0) in a
-// two-colour order.
+// two-colour order, 4 the reduced system with the single-reduction
+// recurrences.
 static void (*persistent_kernel(int kind))(PersistArgs) {
     switch (kind) {
         case 1: return k_persistent_reduced;
         case 2: return k_persistent_gear;
         case 3: return k_persistent_ic0;
+        case 4: return k_persistent_reduced1;
         default: return k_persistent_cg;
     }
 }
@@ -1192,7 +1395,9 @@ int persistent_max_grid(cps_sys s, int reduced) {
 // reduced system; 2: single-reduction Jacobi on all rows, after k_init64 and
 // k_gear_start, with s = A p in q and w = A r in t; 3: single-reduction IC(0)
 // in the two-colour order after k_init64, s in q, w in t, z and the inverse
-// pivots in z, dinv) after the caller's init kernel; state in s->st.  With
+// pivots in z, dinv; 4: the reduced system with the single-reduction
+// recurrences after k_black_init, s in q, w in z, the red scratch in t)
+// after the caller's init kernel; state in s->st.  With
 // win_bytes > 0 the launch carries a persisting L2 access-policy window over
 // [win_base, win_base + win_bytes) (the caller holds the set-aside).  grid:
 // blocks of the launch, at most what stays resident (0: that maximum).

@@ -74,7 +74,7 @@ def test_tiny_systems_every_path(ctx, name):
     assert _err(x, xo) < 1e-9
     if p.mesh.nt > 1:                         # these lattices are two-coloured
         s.set_precond(cps.PC_REDUCED)
-        for path in (cps.PATH_STREAM, cps.PATH_PERSISTENT):
+        for path in (cps.PATH_STREAM, cps.PATH_PERSISTENT, cps.PATH_PERSISTENT_1RED):
             s.set_solver_path(path)
             x, st = s.solve(bt, rtol=1e-12)
             assert _err(x, xo) < 1e-9, ("reduced", path)

@@ -28,13 +28,13 @@ def ctx(cuda_device):
 
 
 @pytest.mark.parametrize("precond", ["jacobi", "jacobi_single_reduction", "ic0_single_reduction",
-                                     "reduced"])
+                                     "reduced", "reduced_single_reduction"])
 def test_stalled_grid_barrier_times_out_and_recovers(ctx, precond):
     p = synth.channel_block_problem(64, seed=5)
     m = p.mesh
     s = ctx.assemble(m.xy, m.tri, m.dirichlet, p.eps, p.kinv, p.field_loc, cps.KIND_CP2,
                      p.nu, p.dt)
-    if precond == "reduced":
+    if precond.startswith("reduced"):
         s.set_precond(cps.PC_REDUCED)
     if precond == "ic0_single_reduction":
         s.set_precond(cps.PC_IC0)

@@ -451,24 +451,43 @@ def test_persistent_path_matches_oracle(ctx, name):
     s.free()
 
 
+@pytest.mark.parametrize("path", ["textbook", "single_reduction", "single_reduction_l2"])
 @pytest.mark.parametrize("name", ["block37", "channel64", "channel300"])
-def test_persistent_reduced_system_matches_oracle(ctx, name):
-    """The reduced (black-cell Schur complement) CG in one persistent launch."""
+def test_persistent_reduced_system_matches_oracle(ctx, name, path):
+    """The reduced (black-cell Schur complement) CG in one persistent launch,
+    with the textbook and with the single-reduction (Chronopoulos-Gear)
+    recurrences (the latter also with its five vectors in persisting L2):
+    against the oracle, and the iteration count against the streaming loop
+    (the same iterates in exact arithmetic)."""
     p = PROBLEMS[name] if name in PROBLEMS else synth.channel_block_problem(300, seed=8)
     s = assemble(ctx, p)
     s.set_precond(cps.PC_REDUCED)
-    s.set_solver_path(cps.PATH_PERSISTENT)
+    pin = {"textbook": cps.PATH_PERSISTENT, "single_reduction": cps.PATH_PERSISTENT_1RED,
+           "single_reduction_l2": cps.PATH_PERSISTENT_1RED_L2}[path]
+    try:
+        s.set_solver_path(pin)
+    except cps.CpsError:
+        assert path == "single_reduction_l2"      # the set-aside cannot hold five vectors
+        pytest.skip("persisting L2 set-aside too small for five vectors")
     b = synth.rhs(p.mesh, 37)
     bt = torch.as_tensor(b, device="cuda")
     x, st = s.solve(bt, rtol=1e-12, check=False)
     assert st.status in (0, cps._cps.ERR_NOT_CONVERGED) and st.rel_res < 1e-10
-    assert s.tuning()["reduced_persistent"]
+    tu = s.tuning()
+    assert tu["reduced_persistent"]
+    assert tu["reduced_single_reduction"] == (path != "textbook")
+    assert tu["reduced_l2_window"] == ("vectors5" if path == "single_reduction_l2" else "none")
     xo, _, A = oracle.solve_problem(p, b, rtol=1e-13)
     err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
     assert err < 1e-9, err
     s.set_solver_path(cps.PATH_STREAM)
     x2, st2 = s.solve(bt, rtol=1e-12, check=False)
-    assert abs(st2.iters - st.iters) <= max(8, 0.02 * st.iters)
+    if path == "textbook":
+        assert abs(st2.iters - st.iters) <= max(8, 0.02 * st.iters)
+    else:
+        # the single-reduction recurrences drift sooner near the FP64 floor
+        # and may restart from the true residual once more
+        assert abs(st2.iters - st.iters) <= 8 + 0.08 * st2.iters
     assert torch.allclose(x, x2, rtol=1e-9, atol=1e-12 * float(x.abs().max()))
     s.free()
 
@@ -506,11 +525,16 @@ def test_path_autotuner_reports_every_candidate(ctx):
     tu = s.tuning()
     pr = tu["probe_us_per_iter"]
     assert pr["reduced_stream"] > 0 and pr["reduced_persistent"] > 0
+    assert pr["reduced_persistent_1red"] > 0
     red = [k for k in ("reduced_stream", "reduced_persistent", "reduced_stream_l2_vectors",
-                       "reduced_persistent_l2_vectors") if pr[k] > 0]
+                       "reduced_persistent_l2_vectors", "reduced_persistent_1red",
+                       "reduced_persistent_1red_l2_vectors") if pr[k] > 0]
     best = min(red, key=lambda k: pr[k])
     assert tu["reduced_persistent"] == best.startswith("reduced_persistent")
-    assert tu["reduced_l2_window"] == ("vectors" if best.endswith("l2_vectors") else "none")
+    assert tu["reduced_single_reduction"] == best.startswith("reduced_persistent_1red")
+    want = {"reduced_stream_l2_vectors": "vectors", "reduced_persistent_l2_vectors": "vectors",
+            "reduced_persistent_1red_l2_vectors": "vectors5"}.get(best, "none")
+    assert tu["reduced_l2_window"] == want
     s.free()
 
 
