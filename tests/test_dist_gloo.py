@@ -47,7 +47,9 @@ def _worker(rank, world, port, out):
 def test_two_gloo_ranks_combine_time_and_work():
     world = 2
     port = _free_port()
-    with mp.Manager() as mgr:
+    # the manager's server process is spawned too: forking a process that
+    # already runs OpenMP or torch threads can deadlock the child
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
