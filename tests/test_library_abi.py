@@ -105,3 +105,20 @@ def test_c_program_links_and_runs_without_a_gpu(tmp_path, lib):
     run = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
     assert run.returncode == 0 and run.stdout.strip() == "ok", (run.returncode, run.stdout,
                                                                  run.stderr)
+
+
+def test_header_constants_match_the_python_binding():
+    """Every value #define of include/cps.h (status codes, kinds, field
+    locations, preconditioners, precisions, batch / CP1 / solver paths)
+    has the same value under the same name, CPS_ prefix dropped, in the
+    ctypes binding."""
+    from paper_2309_03543_gb300 import _cps
+    text = open(os.path.join(ROOT, "include", "cps.h")).read()
+    defs = re.findall(r"^#define CPS_([A-Z0-9_]+)\s+\(?(-?\d+)\)?\s*(?:/\*.*)?$", text, flags=re.M)
+    assert len(defs) > 30
+    skip = {"TEST_STALL_BARRIER"}          # test hook, passed as a plain int
+    for name, value in defs:
+        if name in skip:
+            continue
+        assert hasattr(_cps, name), name
+        assert getattr(_cps, name) == int(value), (name, getattr(_cps, name), value)
